@@ -1,0 +1,377 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these checks re-derives a value by calling the oracle's own formula a
+second time: each compares against a hand-worked fixture (tests/golden/), a
+closed form of a *different* equation, an invariant, a textbook special case,
+or brute force over tiny inputs.
+"""
+import itertools
+import math
+import struct
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from paper_1805_07384_gb300 import synth
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+# --------------------------------------------------------------------------
+# Eq. 6-8 closed forms
+# --------------------------------------------------------------------------
+
+def test_eb_worked_values(oracle):
+    """Eq. 8 against hand-evaluated decimal values (closed_forms.txt)."""
+    for key, t in read_golden("closed_forms.txt"):
+        assert key == "psnr"
+        psnr, vr, eb = float(t[0]), float(t[2]), float(t[4])
+        got = oracle.eb_rel_from_psnr(psnr) * vr
+        assert got == pytest.approx(eb, rel=4e-16, abs=0)
+
+
+@pytest.mark.parametrize("psnr", [0.5, 20.0, 37.3, 40.0, 80.0, 100.0, 120.0, 179.0])
+def test_eq8_inverts_eq7_and_eq6(oracle, psnr):
+    """Eq. 8 is Eq. 7 solved for eb_rel; Eq. 7 is Eq. 6 with bin width 2 eb."""
+    for vr in (1e-3, 1.0, 2.0, 12345.0):
+        eb = oracle.eb_rel_from_psnr(psnr) * vr
+        eq7 = oracle.psnr_model(vr, eb)
+        eq6 = 20.0 * math.log10(vr / (2.0 * eb)) + 10.0 * math.log10(12.0)
+        assert abs(eq7 - psnr) < 1e-12
+        assert abs(eq6 - psnr) < 1e-12
+
+
+def test_plan_scalars_threshold(oracle):
+    """thr is the largest float whose upper half-ulp neighbourhood stays below eb."""
+    for eb_rel, lo, hi in [(0.25, 0.0, 1.0), (1e-4, -3.0, 7.5), (3e-7, 1e5, 1e5 + 1.0),
+                           (0.0625, 0.0, 8.0)]:
+        s = oracle.plan_scalars(eb_rel, lo, hi, 10)
+        eb = s.eb_abs
+        thr = np.float32(s.thr)
+        up = np.nextafter(thr, np.float32(np.inf))
+        assert float(thr) + (float(up) - float(thr)) / 2 < eb
+        assert float(np.nextafter(up, np.float32(np.inf))) >= eb or float(up) >= eb * (1 - 1e-6)
+        assert s.s == np.float32(2 * eb)
+        assert s.inv == np.float32(1.0 / (2 * eb))
+
+
+def test_plan_scalars_degenerate(oracle):
+    s = oracle.plan_scalars(0.1, 3.0, 3.0, 5)
+    assert s.flags == oracle.FLAG_CONSTANT and s.eb_abs == 0.0
+    s = oracle.plan_scalars(0.1, 0.0, 0.0, 0)
+    assert s.flags == oracle.FLAG_CONSTANT
+    # range too small for a float32 bin reciprocal -> lattice off
+    s = oracle.plan_scalars(1e-9, 0.0, 1e-44, 5)
+    assert s.flags == oracle.FLAG_LATTICE_OFF and s.s == 0.0 and s.inv == 0.0
+    # range beyond float32 -> lattice off
+    s = oracle.plan_scalars(0.1, -3e38, 3e38, 5)
+    assert s.flags == oracle.FLAG_LATTICE_OFF
+
+
+# --------------------------------------------------------------------------
+# lattice: hand-worked tiny fields
+# --------------------------------------------------------------------------
+
+def _lattice_cases():
+    cases, cur = [], None
+    for key, t in read_golden("lattice_tiny.txt"):
+        if key == "case":
+            cur = {"name": t[0]}
+            cases.append(cur)
+        elif key == "shape":
+            cur["shape"] = tuple(int(v) for v in t)
+        elif key in ("x",):
+            cur[key] = np.array([float(v) for v in t], np.float32)
+        elif key in ("q", "delta", "verbatim"):
+            cur[key] = np.array([int(v) for v in t], np.int64)
+        else:
+            cur[key] = float(t[0])
+    return cases
+
+
+@pytest.mark.parametrize("case", _lattice_cases(), ids=lambda c: c["name"])
+@pytest.mark.parametrize("radius", [32768, 4, 2])
+def test_lattice_tiny(oracle, case, radius):
+    x = case["x"].reshape(case["shape"])
+    s = oracle.plan_scalars(case["eb_rel"], float(x.min()), float(x.max()), x.size)
+    r = oracle.lattice(x, s, radius)
+    delta = case["delta"]
+    want_codes = np.where(np.abs(delta) < radius, delta + radius, 0)
+    assert np.array_equal(r["codes"].ravel().astype(np.int64), want_codes)
+    out = np.nonzero(np.abs(delta) >= radius)[0]
+    assert np.array_equal(r["out_idx"], out)
+    assert np.array_equal(r["out_delta"], delta[out])
+    assert np.array_equal(r["vb_idx"], case["verbatim"])
+    assert np.array_equal(r["vb_bits"], x.ravel()[case["verbatim"]].view(np.uint32))
+    assert r["sse"] == case["sse"]
+
+
+@pytest.mark.parametrize("case", _lattice_cases(), ids=lambda c: c["name"])
+def test_inverse_lorenzo_tiny(oracle, case):
+    """Prefix sums of the hand-worked residuals give back the lattice q."""
+    ld = len(case["shape"])
+    q = oracle.inverse_lorenzo(case["delta"].reshape(case["shape"]), ld)
+    assert np.array_equal(q.ravel(), case["q"])
+
+
+def _naive_lorenzo(q, ld):
+    """Residual by explicit neighbour sums with zero padding (brute force)."""
+    qp = np.pad(q.astype(np.int64), [(1, 0)] * q.ndim)
+    if ld == 1:
+        f = np.concatenate([[0], q.ravel().astype(np.int64)])
+        return (f[1:] - f[:-1]).reshape(q.shape)
+    d = np.zeros(q.shape, np.int64)
+    for offs in itertools.product((0, 1), repeat=q.ndim):
+        sign = (-1) ** sum(offs)
+        sl = tuple(slice(1 - o, 1 - o + n) for o, n in zip(offs, q.shape))
+        d += sign * qp[sl]
+    return d
+
+
+@pytest.mark.parametrize("shape,ld", [((37,), 1), ((9, 13), 2), ((5, 6, 7), 3), ((4, 11), 1),
+                                      ((3, 4, 9), 2)])
+def test_lattice_random_bruteforce(oracle, shape, ld):
+    """Random fields: codes equal the brute-force inclusion-exclusion residual
+    of the rounded lattice, and prefix sums invert it (any rounding or sign
+    slip in the oracle's Lorenzo makes one of these fail)."""
+    rng = np.random.default_rng(7)
+    x = rng.uniform(-2.0, 3.0, size=shape).astype(np.float32)
+    s = oracle.plan_scalars(0.01, float(x.min()), float(x.max()), x.size)
+    q = np.rint((x - np.float32(s.xmin)) * np.float32(s.inv)).astype(np.int64)
+    view = q.reshape(-1, shape[-1]) if ld == 2 and len(shape) == 3 else q
+    d = _naive_lorenzo(view if ld != 1 else q.ravel(), ld).ravel()
+    for radius in (32768, 8):
+        r = oracle.lattice(x, s, radius, lorenzo_dims=ld)
+        want = np.where(np.abs(d) < radius, d + radius, 0)
+        assert np.array_equal(r["codes"].ravel().astype(np.int64), want)
+        assert np.array_equal(r["out_delta"], d[np.abs(d) >= radius])
+    inv_shape = view.shape if ld != 1 else (q.size,)
+    back = oracle.inverse_lorenzo(d.reshape(inv_shape), ld)
+    assert np.array_equal(back.ravel(), q.ravel())
+
+
+# --------------------------------------------------------------------------
+# Huffman: textbook example, tie rule, length limit, brute-force optimality
+# --------------------------------------------------------------------------
+
+def _huffman_cases():
+    cases = {}
+    for key, t in read_golden("huffman_tiny.txt"):
+        name, vals = t[0], [int(v) for v in t[1:]]
+        cases.setdefault(name, {})[key] = vals
+    return cases
+
+
+@pytest.mark.parametrize("name", list(_huffman_cases()))
+def test_huffman_golden(oracle, name):
+    c = _huffman_cases()[name]
+    lens = oracle.huffman_lengths(np.array(c["counts"]), c["lmax"][0])
+    assert lens.tolist() == c["lengths"]
+    if "codes" in c:
+        codes, _ = oracle.canonical_codes(lens)
+        assert codes.tolist() == c["codes"]
+
+
+def _bruteforce_min_cost(counts):
+    used = [c for c in counts if c > 0]
+    n = len(used)
+    if n <= 1:
+        return sum(used)
+    best = None
+    for ls in itertools.product(range(1, n), repeat=n):
+        if sum(2.0 ** -l for l in ls) <= 1.0:
+            cost = sum(c * l for c, l in zip(used, ls))
+            best = cost if best is None else min(best, cost)
+    return best
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_huffman_optimal_bruteforce(oracle, seed):
+    """Total coded bits equal the minimum over every prefix-code length vector
+    (exhaustive on alphabets of up to 6 used symbols); Kraft sum is exactly 1."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 7))
+    counts = rng.integers(1, 40, size=n)
+    if seed % 3 == 0:
+        counts[rng.integers(0, n)] = 0
+    lens = oracle.huffman_lengths(counts, 27)
+    used = counts > 0
+    assert np.all((lens > 0) == used)
+    assert int((counts * lens).sum()) == _bruteforce_min_cost(counts.tolist())
+    if used.sum() >= 2:
+        assert sum(2.0 ** -int(l) for l in lens[used]) == 1.0
+
+
+@pytest.mark.parametrize("lmax", [9, 10, 12])
+def test_huffman_length_limit_large(oracle, lmax):
+    """Geometric counts force deep trees; limited lengths stay within lmax,
+    keep Kraft <= 1 and remain a complete code."""
+    counts = np.array([2 ** min(i, 30) for i in range(40)] + [0, 3, 0], dtype=np.uint64)
+    counts = np.minimum(counts, 2**32 - 1).astype(np.uint32)
+    lens = oracle.huffman_lengths(counts, lmax)
+    used = counts > 0
+    assert lens[used].max() <= lmax
+    assert sum(2.0 ** -int(l) for l in lens[used]) == 1.0
+
+
+def test_canonical_prefix_free(oracle):
+    rng = np.random.default_rng(3)
+    counts = rng.integers(0, 1000, size=300)
+    lens = oracle.huffman_lengths(counts, 27)
+    codes, order = oracle.canonical_codes(lens)
+    words = [format(int(codes[s]), "b").zfill(int(lens[s])) for s in order]
+    for a, b in zip(words, words[1:]):
+        assert not b.startswith(a)
+    ws = sorted(words)
+    for a, b in zip(ws, ws[1:]):
+        assert not b.startswith(a)
+
+
+# --------------------------------------------------------------------------
+# whole pipeline
+# --------------------------------------------------------------------------
+
+def test_stream_tiny_golden(oracle):
+    """Bytes of the hand-worked 4-point example (stream_tiny.txt)."""
+    g = dict(read_golden("stream_tiny.txt"))
+    x = np.array([0.0, 0.5, 1.0, 0.25], np.float32)
+    psnr = 20.0 * math.log10(math.sqrt(3.0) / 0.25)
+    blob, st = oracle.compress(x, psnr, radius=int(g["radius"][0]), chunk=int(g["chunk"][0]))
+    h = oracle.parse_blob(blob)
+    assert h["magic"] == struct.unpack("<I", b"FPS1")[0]
+    assert h["dims"] == [4, 1, 1] and h["ndim"] == 1
+    assert [hex(v) for v in h["codebook"]] == [hex(int(v, 16)) for v in g["codebook"]]
+    assert h["chunk_table"].tolist() == [int(v) for v in g["chunk_table"]]
+    assert h["stream"].tolist() == [int(v, 16) for v in g["stream"]]
+    assert h["vb_idx"].tolist() == [int(g["verbatim"][0])]
+    assert h["vb_bits"].tolist() == [int(g["verbatim"][1], 16)]
+    assert h["n_outlier"] == 0
+    assert h["total"] == len(blob)
+    xr = oracle.decompress(blob, x.shape)
+    assert xr.tolist() == [0.0, 0.5, 1.0, 0.25]
+
+
+@pytest.mark.parametrize("shape,ld,psnr", [((257,), 1, 60.0), ((33, 47), 2, 80.0),
+                                           ((9, 10, 11), 3, 100.0), ((7, 40), 1, 40.0),
+                                           ((6, 5, 8), 2, 120.0), ((5, 300), 2, 20.0)])
+@pytest.mark.parametrize("chunk", [1, 7, 256])
+def test_roundtrip_invariants(oracle, shape, ld, psnr, chunk):
+    """Decompression reproduces the lattice reconstruction exactly (Eq. 1: the
+    integer stages are lossless, so X - X~ is the prequantization error),
+    every point is within eb (the SZ bound, Sec. IV), the SSE reported at
+    compression time equals the SSE of the decompressed field."""
+    x = synth.smooth_3d(shape, 5) if len(shape) == 3 else (
+        synth.rescale(synth.grf(shape, 3.0, 11), -1, 1).astype(np.float32))
+    blob, st = oracle.compress(x, psnr, chunk=chunk, lorenzo_dims=ld)
+    xr = oracle.decompress(blob, x.shape)
+    err = np.abs(x.astype(np.float64) - xr.astype(np.float64))
+    assert err.max() <= st["eb_abs"]
+    # Eq. 1: reconstruction = midpoint of the prequantization bin, or exact
+    s = oracle.plan_scalars(st["eb_rel"], st["xmin"], st["xmax"], x.size)
+    q = np.rint((x - np.float32(s.xmin)) * np.float32(s.inv)).astype(np.float32)
+    lat = (q.astype(np.float64) * float(np.float32(s.s)) + float(s.xmin)).astype(np.float32)
+    vb = oracle.parse_blob(blob)["vb_idx"]
+    mask = np.ones(x.size, bool)
+    mask[vb] = False
+    # fmaf vs separate mul/add may differ by one rounding: compare within 1 ulp
+    assert np.all(np.abs(lat.ravel()[mask] - xr.ravel()[mask]) <=
+                  np.spacing(np.abs(xr.ravel()[mask])))
+    assert np.array_equal(xr.ravel()[~mask], x.ravel()[~mask])
+    assert oracle.sse(x, xr) == pytest.approx(st["sse"], rel=1e-12, abs=0)
+
+
+def test_config0_psnr_within_model(oracle):
+    """512x512 GRF at 80 dB: the lattice error is ~uniform on [-eb, eb], so the
+    actual PSNR lands on the Eq. 7-8 model within +-0.05 dB (the relative
+    std of an MSE estimate over 262144 points is sqrt(0.8/N) -> 0.0076 dB)."""
+    x = synth.single_2d()
+    blob, st = oracle.compress(x, 80.0)
+    xr = oracle.decompress(blob, x.shape)
+    p, mse, vr = oracle.psnr(x, xr)
+    assert abs(p - 80.0) < 0.05
+    assert mse == pytest.approx(st["eb_abs"] ** 2 / 3.0, rel=0.012)
+    assert abs(p - st["psnr_actual"]) < 1e-9
+    assert vr == pytest.approx(2.0, rel=1e-6)
+
+
+@pytest.mark.parametrize("psnr", [40.0, 60.0, 100.0, 120.0])
+def test_psnr_model_tracks_target(oracle, psnr):
+    """Sec. V trend: deviation from the target shrinks as the target rises;
+    at >= 60 dB a smooth field lands within 0.1 dB."""
+    x = synth.single_2d(256, seed=4)
+    blob, st = oracle.compress(x, psnr)
+    xr = oracle.decompress(blob, x.shape)
+    p, _, _ = oracle.psnr(x, xr)
+    if psnr >= 60:
+        assert abs(p - psnr) < 0.1
+    else:
+        assert p > psnr - 1.0
+
+
+def test_constant_and_empty_fields(oracle):
+    x = np.full((17, 9), 3.25, np.float32)
+    blob, st = oracle.compress(x, 80.0)
+    h = oracle.parse_blob(blob)
+    assert h["flags"] == oracle.FLAG_CONSTANT and len(blob) == 128
+    assert np.array_equal(oracle.decompress(blob, x.shape), x)
+    assert st["psnr_actual"] == math.inf
+    e = np.zeros((0, 5), np.float32)
+    blob, st = oracle.compress(e, 80.0)
+    assert len(blob) == 128 and oracle.decompress(blob, e.shape).size == 0
+
+
+def test_nonfinite_and_bad_args(oracle):
+    x = np.ones((4, 4), np.float32)
+    x[2, 1] = np.nan
+    assert oracle.compress_status(x, 80.0) == oracle.ENONFINITE
+    x[2, 1] = np.inf
+    assert oracle.compress_status(x, 80.0) == oracle.ENONFINITE
+    y = np.ones(8, np.float32)
+    assert oracle.compress_status(y, -5.0) == oracle.EINVAL
+    assert oracle.compress_status(y, 200.0) == oracle.EINVAL
+    assert oracle.compress_status(y, 80.0, radius=32768, lmax=15) == oracle.EINVAL
+
+
+def test_outliers_forced_small_radius(oracle):
+    """White noise with a tiny radius: most residuals leave (-R, R) and travel in
+    the outlier list; decompression is unchanged."""
+    x = synth.uniform_noise((40, 50), 9)
+    blob, st = oracle.compress(x, 60.0, radius=4, lmax=10)
+    h = oracle.parse_blob(blob)
+    assert h["n_outlier"] > 100
+    assert np.all(np.diff(h["out_idx"].astype(np.int64)) > 0)
+    xr = oracle.decompress(blob, x.shape)
+    blob2, _ = oracle.compress(x, 60.0)
+    assert np.array_equal(xr, oracle.decompress(blob2, x.shape))
+
+
+def test_corrupt_blob_detected(oracle):
+    x = synth.single_2d(64, seed=1)
+    blob, _ = oracle.compress(x, 60.0)
+    assert oracle.decompress_status(blob[:100], x.size) == oracle.ECORRUPT
+    assert oracle.decompress_status(blob[:-16], x.size) == oracle.ECORRUPT
+    bad = bytearray(blob)
+    bad[0] ^= 1
+    assert oracle.decompress_status(bytes(bad), x.size) == oracle.ECORRUPT
+    assert oracle.decompress_status(blob, x.size + 1) == oracle.ECORRUPT
+
+
+def test_lattice_off_all_verbatim(oracle):
+    """Denormal-range field: the bin reciprocal overflows float32, every q is 0
+    and every point that is not the minimum travels verbatim (lossless)."""
+    x = (np.arange(12, dtype=np.float32) * np.float32(1e-45)).reshape(3, 4)
+    blob, st = oracle.compress(x, 150.0)
+    assert st["flags"] == oracle.FLAG_LATTICE_OFF
+    assert np.array_equal(oracle.decompress(blob, x.shape), x)
+
+
+def test_classic_sz_comparison(oracle):
+    """Comparison path (parity unpinned against SZ 1.4 bytes): same bound and
+    same PSNR model as the lattice form."""
+    x = synth.single_2d(128, seed=2)
+    for psnr in (60.0, 80.0):
+        xr, nu, p = oracle.classic_sz(x, psnr)
+        eb = oracle.eb_rel_from_psnr(psnr) * 2.0
+        assert np.abs(x.astype(np.float64) - xr).max() <= eb
+        assert abs(p - psnr) < 0.2
