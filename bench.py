@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Throughput of fixed-PSNR compression + decompression on GB300.
+
+Workload (one step): the climate-like batch of 24 float32 fields of
+1800 x 3600 points (622 MB, larger than the 129 MB L2), each compressed at a
+target PSNR from the sweep {40, 60, 80, 100, 120} dB (field i gets
+sweep[i mod 5]) with the 2D Lorenzo predictor and R = 32768, then
+decompressed.  metric = original bytes / (compress + decompress time).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on the
+host cores instead (the reference arm of this method: the paper ships no GPU
+code).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compress+decompress GB/s at target PSNR"
+STAGE_BYTES_NOTE = "algorithmic bytes per launch, N = points of one field"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--streams", type=int, default=4)
+    ap.add_argument("--fields", type=int, default=24)
+    ap.add_argument("--ny", type=int, default=1800)
+    ap.add_argument("--nx", type=int, default=3600)
+    ap.add_argument("--chunk", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-roofline", action="store_true")
+    ap.add_argument("--cpu-workers", type=int, default=0, help="0 = all host cores")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 4 + k and r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def oracle_field(args):
+    """One oracle compress + decompress (worker process)."""
+    x, psnr, chunk = args
+    import oracle
+    t0 = time.perf_counter()
+    blob, st = oracle.compress(x, psnr, chunk=chunk)
+    oracle.decompress(blob, x.shape)
+    return time.perf_counter() - t0, len(blob), st["psnr_actual"]
+
+
+def cpu_pool(workers: int):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    return ctx.Pool(workers)
+
+
+def run_oracle_sample(pool, fields_np, psnrs, chunk):
+    t0 = time.perf_counter()
+    res = pool.map(oracle_field, [(f, p, chunk) for f, p in zip(fields_np, psnrs)])
+    wall = time.perf_counter() - t0
+    return wall, res
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1805_07384_gb300 import synth
+    import oracle
+    oracle.build()
+    fields, meta = synth.climate_batch(a.fields, a.ny, a.nx)
+    psnrs = [synth.mixed_psnr(i) for i in range(a.fields)]
+    workers = a.cpu_workers or os.cpu_count() or 1
+    workers = max(1, min(workers, a.fields))
+    nbytes = sum(4 * f.size for f in fields)
+    with cpu_pool(workers) as pool:
+        for _ in range(a.warmup):
+            run_oracle_sample(pool, fields[:workers], psnrs[:workers], a.chunk)
+        times = []
+        for _ in range(a.steps):
+            wall, _ = run_oracle_sample(pool, fields, psnrs, a.chunk)
+            times.append(wall)
+    ms = 1e3 * sum(times) / len(times)
+    value = nbytes / (ms / 1e3) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(a, streams=None),
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": workers, "kind": "oracle",
+                         "sample": f"all {a.fields} fields per step, one field per worker process"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(a, streams):
+    c = {"workload": f"{a.fields} climate-like 2D float32 GRF fields {a.ny}x{a.nx} "
+                     f"(alpha~U[2,4], affine offsets 1e-3..1e5, 1 field with a constant "
+                     f"rectangle), target PSNR field i -> {{40,60,80,100,120}}[i mod 5] dB, "
+                     f"2D Lorenzo, R=32768, chunk {a.chunk}",
+         "fields": a.fields, "shape": [a.ny, a.nx], "radius": 32768, "chunk": a.chunk,
+         "lorenzo_dims": 2,
+         "l2": f"inputs {a.fields * a.ny * a.nx * 4 / 1e6:.0f} MB > 129 MB L2, no flush"}
+    if streams is not None:
+        c["streams"] = streams
+    return c
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+# algorithmic bytes per launch of each stage (N points, B compressed bytes of one field)
+def stage_bytes(stage, N, B):
+    return {"range_plan": 4 * N, "predict_quantize": 6 * N, "chunk_bits": 2 * N,
+            "pack": 2 * N + B, "decode": B + 4 * N, "scan_x": 8 * N,
+            "scan_final_dequant": 8 * N, "scan_y": 8 * N}.get(stage)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    # CPU baseline pool first (spawn), rank 0 only
+    pool = None
+    if rank == 0 and not a.no_cpu_baseline:
+        workers = a.cpu_workers or os.cpu_count() or 1
+        workers = max(1, min(workers, a.fields))
+        import oracle
+        oracle.build()
+        pool = cpu_pool(workers)
+        pool_workers = workers
+
+    from paper_1805_07384_gb300 import build as fbuild
+    fbuild.build()
+    from paper_1805_07384_gb300 import fpsnr, synth
+
+    F, S = a.fields, max(1, a.streams)
+    fields, meta = synth.climate_batch(F, a.ny, a.nx, seed=1 + 1000 * rank, device=dev)
+    psnrs = [synth.mixed_psnr(i) for i in range(F)]
+    N = a.ny * a.nx
+    plans = [fpsnr.Plan((a.ny, a.nx), psnrs[i], chunk=a.chunk) for i in range(F)]
+    outs = [p.alloc_out() for p in plans]
+    nbs = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(F)]
+    sts = [torch.zeros(fpsnr.STATS_BYTES, dtype=torch.uint8, device=dev) for _ in range(F)]
+    recs = [torch.empty((a.ny, a.nx), dtype=torch.float32, device=dev) for _ in range(F)]
+    dsts = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in range(F)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(S)]
+    main_s = torch.cuda.current_stream(dev)
+
+    def step(nstreams, h2d=None, d2h=None):
+        ev = torch.cuda.Event()
+        ev.record(main_s)
+        for s in streams[:nstreams]:
+            s.wait_event(ev)
+        for i in range(F):
+            s = streams[i % nstreams]
+            if h2d is not None:
+                with torch.cuda.stream(s):
+                    fields[i].copy_(h2d[i], non_blocking=True)
+            plans[i].compress(fields[i], out=outs[i], nbytes=nbs[i], stats=sts[i], stream=s)
+            plans[i].decompress(outs[i], outs[i].numel(), out=recs[i], status=dsts[i], stream=s)
+            if d2h is not None:
+                with torch.cuda.stream(s):
+                    d2h[0][i].copy_(recs[i], non_blocking=True)
+                    d2h[1][i].copy_(sts[i], non_blocking=True)
+        for s in streams[:nstreams]:
+            e = torch.cuda.Event()
+            e.record(s)
+            main_s.wait_event(e)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(k, nstreams, **kw):
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        wall0 = time.perf_counter()
+        t0.record(main_s)
+        for _ in range(k):
+            step(nstreams, **kw)
+        t1.record(main_s)
+        barrier()
+        ms = t0.elapsed_time(t1) / k
+        if world > 1:
+            tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms, (time.perf_counter() - wall0)
+
+    for _ in range(max(3, a.warmup)):
+        step(S)
+    barrier()
+    for p in plans:
+        fpsnr.fpsnr_plan_profile_read(p.handle)  # reset launch counters
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, wall = timed(a.steps, S)
+    clk = clocks.stop()
+    launches = 0
+    for p in plans:
+        launches += sum(v[1] for v in fpsnr.fpsnr_plan_profile_read(p.handle).values())
+
+    total_bytes = 4 * N * F
+    value = world * total_bytes / (ms / 1e3) / 1e9
+
+    # per-field results (outside the timed region)
+    per_field = []
+    dev_abs, meets, crs = [], [], []
+    for i in range(F):
+        st = fpsnr.parse_stats(sts[i])
+        assert st["status"] == 0 and int(dsts[i].item()) == 0, (i, st["status"], int(dsts[i].item()))
+        p_meas, _, _ = fpsnr.psnr(fields[i], recs[i])
+        assert p_meas == st["psnr_actual"] or abs(p_meas - st["psnr_actual"]) < 1e-9
+        cr = 4 * N / st["bytes"]
+        per_field.append({"target": psnrs[i], "actual": round(st["psnr_actual"], 6),
+                          "model": round(st["psnr_model"], 6), "cr": round(cr, 3),
+                          "outliers": st["n_outlier"], "verbatims": st["n_verbatim"],
+                          "symbols": st["n_sym"]})
+        if math.isfinite(st["psnr_actual"]):
+            dev_abs.append(abs(st["psnr_actual"] - psnrs[i]))
+            meets.append(st["psnr_actual"] >= psnrs[i])
+        crs.append(cr)
+
+    # roofline pass: same K steps, one stream, per-launch events
+    roof = None
+    stage_table = None
+    if not a.no_roofline:
+        for p in plans:
+            fpsnr.fpsnr_plan_profile(p.handle, True)
+            fpsnr.fpsnr_plan_profile_read(p.handle)
+        ms1, _ = timed(a.steps, 1)
+        agg = {}
+        for i, p in enumerate(plans):
+            B = fpsnr.parse_stats(sts[i])["bytes"]
+            for name, (t, n) in fpsnr.fpsnr_plan_profile_read(p.handle).items():
+                e = agg.setdefault(name, [0.0, 0, 0])
+                e[0] += t
+                e[1] += n
+                sb = stage_bytes(name, N, B)
+                e[2] += (sb or 0) * n
+            fpsnr.fpsnr_plan_profile(p.handle, False)
+        step_ms = ms1
+        stage_table = {k: {"ms_per_step": round(v[0] / a.steps, 4), "launches_per_step": v[1] // a.steps,
+                           "share": round(v[0] / a.steps / step_ms, 4),
+                           "gbs": round(v[2] / (v[0] / 1e3) / 1e9, 1) if v[0] > 0 and v[2] else None}
+                       for k, v in agg.items() if v[1]}
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+        peak = peaks["hbm_gbs"] if peaks else 6800.0
+        bw_stages = {k: v for k, v in agg.items() if stage_bytes(k, N, 1) is not None and v[0] > 0}
+        dom = max(bw_stages.items(), key=lambda kv: kv[1][0]) if bw_stages else None
+        if dom:
+            name, (t, n, byts) = dom
+            achieved = byts / (t / 1e3) / 1e9
+            traffic = None
+            tf = os.path.join(ROOT, "profiles", "traffic.json")
+            if os.path.exists(tf):
+                traffic = json.load(open(tf)).get(name)
+            roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1),
+                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                    "traffic": traffic, "peak_source": "measured" if peaks else "fallback",
+                    "bytes_per_launch": byts // n, "launch_ms": round(t / n, 5),
+                    "timing": f"CUDA events around each launch over a second timed pass of "
+                              f"{a.steps} steps on one stream",
+                    "step_ms_one_stream": round(ms1, 4)}
+
+    # end to end through host buffers
+    e2e = None
+    if not a.no_e2e:
+        h2d = [f.cpu().pin_memory() for f in fields]
+        d2h = ([torch.empty((a.ny, a.nx), dtype=torch.float32).pin_memory() for _ in range(F)],
+               [torch.empty(fpsnr.STATS_BYTES, dtype=torch.uint8).pin_memory() for _ in range(F)])
+        step(S, h2d=h2d, d2h=d2h)
+        ms_e, _ = timed(a.steps, S, h2d=h2d, d2h=d2h)
+        e2e = {"value": round(world * total_bytes / (ms_e / 1e3) / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": total_bytes,
+               "d2h_bytes_per_step": total_bytes + F * fpsnr.STATS_BYTES,
+               "ms_per_step": round(ms_e, 4)}
+
+    cpu = None
+    if pool is not None:
+        fields_np = [f.cpu().numpy() for f in fields]
+        wall, res = run_oracle_sample(pool, fields_np, psnrs, a.chunk)
+        pool.close()
+        cpu = {"value": round(total_bytes / wall / 1e9, 4), "unit": "GB/s",
+               "cores": pool_workers, "kind": "oracle",
+               "sample": f"all {F} fields of one step (compress + decompress), one field per "
+                         f"worker process, {wall:.1f} s wall"}
+        for (t, nbyt, p_or), pf in zip(res, per_field):
+            pf["oracle_psnr"] = round(p_or, 6)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": a.steps, "warmup": max(3, a.warmup), "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(a, S),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+            "hbm_frac_of_step": round(value / (6775.6 if roof is None else roof["peak"]), 4),
+            "psnr": {"mean_abs_dev_db": round(sum(dev_abs) / len(dev_abs), 4) if dev_abs else None,
+                     "meet_rate": round(sum(meets) / len(meets), 4) if meets else None},
+            "cr_mean": round(sum(crs) / len(crs), 3),
+            "stages": stage_table, "per_field": per_field,
+        }
+        print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * fpsnr.h -- C ABI of the GB300 fixed-PSNR lossy compressor.
+ *
+ * Method: Tao, Di, Liang, Chen, Cappello, "Fixed-PSNR Lossy Compression for
+ * Scientific Data".  The caller states a target PSNR; the library derives the
+ * value-range-relative error bound from it (Eq. 8, Sec. IV), multiplies it by
+ * the field's value range (eb_abs = eb_rel * vr, Sec. IV after Eq. 7), runs a
+ * prediction-based compressor at that bound (Sec. II-A steps 1-2, Sec. III),
+ * and reports the PSNR the reconstruction actually reaches (Eq. 4-5).
+ *
+ * Every step runs on the GPU in this library's own sm_103a kernels.  All
+ * pointers named d_* are device pointers on the plan's device; h_* are host
+ * pointers.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  No function throws; every function returns 0 (FPSNR_OK) or a
+ * negative FPSNR_E* code for errors known when the work is enqueued.  Errors
+ * that depend on the data (non-finite input, output too small, corrupt blob)
+ * are written to a device status word and are visible after the stream is
+ * synchronized.
+ *
+ * Data layout: a field is a dense float32 array of 1 to 3 dimensions, C order
+ * with x the fastest axis; dims[0] = nx, dims[1] = ny, dims[2] = nz.
+ * At most 2^32 - 1 points per field.
+ *
+ * Compressed byte format (little-endian; every section padded to 16 bytes):
+ *   header, 128 bytes:
+ *     0 u32 magic "FPS1"  4 u32 version (1)  8 u32 ndim  12 u32 lorenzo dims
+ *    16 u64 dims[3] (x fastest, unused = 1)
+ *    40 f64 target PSNR  48 f64 eb_rel  56 f64 eb_abs  64 f64 vr
+ *    72 f32 xmin  76 f32 xmax  80 f32 s = (float)(2 eb_abs)
+ *    84 f32 inv = (float)(1 / (2 eb_abs))  88 f32 thr (verbatim threshold)
+ *    92 u32 flags (1 = constant field, 2 = lattice off)
+ *    96 u32 radius R  100 u32 chunk C  104 u32 lmax  108 u32 n_sym
+ *   112 u32 n_chunks  116 u32 stream_words  120 u32 n_outlier  124 u32 n_verbatim
+ *   codebook:   n_sym u32 entries (len << 16 | symbol), ascending (len, symbol)
+ *   chunk table: n_chunks u32 word offsets into the stream
+ *   stream:     stream_words u32 words, canonical Huffman codes MSB-first;
+ *               each chunk of C symbols starts on a fresh word
+ *   outliers:   n_outlier (u32 index, i32 residual), ascending index
+ *   verbatims:  n_verbatim (u32 index, u32 float bits), ascending index
+ * Symbols: residual delta of the integer lattice q = round((x - xmin) * inv)
+ * under the zero-padded Lorenzo predictor; symbol = delta + R when
+ * |delta| < R, else 0 and the residual travels in the outlier list.  A point
+ * whose reconstruction fmaf((float)q, s, xmin) misses the bound travels
+ * verbatim.
+ */
+#ifndef FPSNR_H
+#define FPSNR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FPSNR_OK 0
+#define FPSNR_EINVAL (-1)     /* bad argument (ndim, dims, PSNR, options, alignment) */
+#define FPSNR_ENOMEM (-2)     /* device allocation failed while planning */
+#define FPSNR_ECUDA (-3)      /* a CUDA call or kernel launch failed */
+#define FPSNR_ENONFINITE (-4) /* (device status) input holds NaN or Inf */
+#define FPSNR_ECAPACITY (-5)  /* (device status) compressed size exceeds out_cap */
+#define FPSNR_ECORRUPT (-6)   /* (device status) blob malformed or mismatched */
+#define FPSNR_ETIMEOUT (-7)   /* (device status) an inter-block wait gave up */
+
+/* Limits on the target PSNR: 0 < target <= FPSNR_MAX_PSNR dB.  Above 180 dB
+ * the integer lattice of a 3D residual could overflow int32. */
+#define FPSNR_MAX_PSNR 180.0
+
+typedef struct fpsnr_plan_s* fpsnr_plan_t;
+
+/* Options; fpsnr_default_opts fills the defaults shown. */
+typedef struct {
+    int radius;       /* R, 1..32768: residuals in (-R, R) are Huffman symbols (32768) */
+    int chunk;        /* C, symbols per independently decodable chunk, 32..65536 (256) */
+    int lmax;         /* longest Huffman code in bits, 1..27, 2^lmax >= 2R (27) */
+    int lorenzo_dims; /* predictor dimension d, 0 = ndim; d < ndim merges the
+                         slowest axes into the slowest predictor axis */
+} fpsnr_opts;
+
+/* Per-call statistics, written by fpsnr_compress to device memory. */
+typedef struct {
+    double target_psnr; /* dB, as planned */
+    double eb_rel;      /* Eq. 8 */
+    double eb_abs;      /* eb_rel * vr */
+    double vr;          /* max - min of the input, FP64 */
+    double psnr_model;  /* Eq. 7 at eb_abs (equals the target up to rounding) */
+    double sse;         /* sum of squared reconstruction errors, FP64 */
+    double mse;         /* sse / n */
+    double psnr_actual; /* 20 log10 vr - 10 log10 mse; +inf when mse == 0 */
+    uint64_t bytes;     /* compressed size, 0 on error */
+    uint64_t n_outlier; /* residuals outside (-R, R) */
+    uint64_t n_verbatim;/* points stored as raw floats */
+    uint64_t n_sym;     /* Huffman symbols in use */
+    float xmin, xmax;
+    uint32_t flags;     /* 1 constant field, 2 lattice off */
+    int32_t status;     /* FPSNR_OK or a device-side error code */
+} fpsnr_stats;
+
+/* Fill *opts with the defaults.  Returns FPSNR_OK, or FPSNR_EINVAL if NULL. */
+int fpsnr_default_opts(fpsnr_opts* opts);
+
+/* Create a plan for fields of one shape on the current CUDA device.
+ *   ndim 1..3; dims[ndim], x fastest, each >= 0 (a zero extent gives an empty
+ *   field); target_psnr_db in (0, FPSNR_MAX_PSNR]; opts NULL = defaults.
+ * The plan owns all device scratch (about 20 bytes per point) and is not
+ * thread-safe: one call at a time per plan (calls on one stream serialize).
+ * Returns FPSNR_OK, FPSNR_EINVAL, FPSNR_ENOMEM or FPSNR_ECUDA. */
+int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_psnr_db,
+               const fpsnr_opts* opts);
+
+/* Change the plan's target PSNR (Eq. 8 is re-evaluated on the host; no
+ * allocation).  Returns FPSNR_OK or FPSNR_EINVAL. */
+int fpsnr_plan_set_psnr(fpsnr_plan_t plan, double target_psnr_db);
+
+/* eb_rel of the plan's current target (Eq. 8), computed on the host in FP64. */
+double fpsnr_plan_eb_rel(fpsnr_plan_t plan);
+
+/* Number of points of the plan's shape. */
+uint64_t fpsnr_plan_points(fpsnr_plan_t plan);
+
+/* Upper bound on the compressed size of any field of the plan's shape. */
+uint64_t fpsnr_max_compressed_bytes(fpsnr_plan_t plan);
+
+/* Compress d_in (n float32 points of the plan's shape) into d_out.
+ *   d_in: 4-byte aligned; d_out: 16-byte aligned, out_cap bytes.
+ *   d_out_bytes (device, may be NULL): receives the blob size, 0 on error.
+ *   d_stats (device, may be NULL): receives fpsnr_stats.
+ * Asynchronous on `stream`; no host synchronization, no allocation.
+ * Enqueue errors: FPSNR_EINVAL, FPSNR_ECUDA.  Device status: FPSNR_ENONFINITE,
+ * FPSNR_ECAPACITY (nothing beyond out_cap is written). */
+int fpsnr_compress(fpsnr_plan_t plan, const float* d_in, void* d_out, uint64_t out_cap,
+                   uint64_t* d_out_bytes, fpsnr_stats* d_stats, void* stream);
+
+/* Decompress a blob produced for a field of the plan's shape.
+ *   d_blob: 16-byte aligned, blob_bytes long; d_out: n_out floats, 16-byte
+ *   aligned, n_out == fpsnr_plan_points(plan).  d_out is also used as int32
+ *   scratch while decoding.  d_status (device, may be NULL) receives
+ *   FPSNR_OK or FPSNR_ECORRUPT (bad header, shape mismatch, malformed stream).
+ * Asynchronous on `stream`; no allocation. */
+int fpsnr_decompress(fpsnr_plan_t plan, const void* d_blob, uint64_t blob_bytes, float* d_out,
+                     uint64_t n_out, int* d_status, void* stream);
+
+/* Distortion of a reconstruction (Eq. 4-5): vr = max - min of d_x (FP64),
+ * MSE = sum((x - xr)^2) / n with exact squares accumulated to FP64,
+ * PSNR = 20 log10 vr - 10 log10 MSE (+inf when MSE == 0), log10 on the host.
+ *   d_x, d_xr: n float32 points each, 4-byte aligned.
+ * Synchronous: returns after the result is on the host.  Allocates a small
+ * scratch (under 64 KB) with cudaMallocAsync on `stream` and frees it.
+ * Returns FPSNR_OK, FPSNR_EINVAL, FPSNR_ENONFINITE (NaN/Inf in d_x) or
+ * FPSNR_ECUDA. */
+int fpsnr_psnr(const float* d_x, const float* d_xr, uint64_t n, double* h_psnr_db,
+               double* h_mse, double* h_vr, void* stream);
+
+/* Device pointer to the uint16 symbol array (n entries) the last
+ * fpsnr_compress on this plan produced; valid until the next call on the plan.
+ * For inspection and tests. */
+const uint16_t* fpsnr_plan_codes(fpsnr_plan_t plan);
+
+/* Stage profiler.  The library's kernels are grouped into FPSNR_NSTAGES
+ * stages (fpsnr_stage_name gives each name).  Launches per stage are always
+ * counted on the host.  With fpsnr_plan_profile(plan, 1) every launch is also
+ * bracketed by CUDA events on its stream; fpsnr_plan_profile_read
+ * synchronizes those events, adds each stage's total milliseconds and launch
+ * count since the last read into ms[i] and launches[i] (arrays of nstages
+ * entries, either may be NULL), and resets the counters.  Recording adds one
+ * event pair per launch; it does not change what the kernels compute.
+ * Returns FPSNR_OK, FPSNR_EINVAL or FPSNR_ECUDA. */
+#define FPSNR_NSTAGES 16
+int fpsnr_plan_profile(fpsnr_plan_t plan, int enable);
+int fpsnr_plan_profile_read(fpsnr_plan_t plan, double* ms, uint64_t* launches, int nstages);
+const char* fpsnr_stage_name(int stage);
+
+/* Release the plan and its device scratch (synchronizes the device first). */
+void fpsnr_plan_destroy(fpsnr_plan_t plan);
+
+/* Static string for an FPSNR_* code. */
+const char* fpsnr_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPSNR_H */

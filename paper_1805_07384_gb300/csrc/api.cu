@@ -1,0 +1,394 @@
+// api.cu -- C ABI entry points: plan creation (validation, launch geometry,
+// device scratch), compress / decompress dispatch, error strings.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "common.cuh"
+
+namespace {
+
+using fp::PQGeom;
+using fp::ScanPass;
+
+bool psnr_ok(double t) { return t > 0.0 && t <= FPSNR_MAX_PSNR; }
+
+double eb_rel_of(double psnr) { return sqrt(3.0) * pow(10.0, -psnr / 20.0); }  // Eq. 8
+
+uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+// Carves a slab into 256-byte aligned arrays; first pass only measures.
+struct Carver {
+    uint8_t* base;
+    size_t off = 0;
+    template <class T>
+    T* take(uint64_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += (size_t)count * sizeof(T);
+        return p;
+    }
+};
+
+void carve(fpsnr_plan_s* p, uint8_t* base, size_t* total) {
+    Carver c{base};
+    fp::Workspace& w = p->w;
+    const uint64_t n = std::max<uint64_t>(p->n, 1);
+    uint64_t pow2 = 2;
+    while (pow2 < p->nsym) pow2 <<= 1;
+    w.par = c.take<fp::DevParams>(1);
+    w.hist = c.take<uint32_t>(p->nsym);
+    w.enc = c.take<uint32_t>(p->nsym);
+    w.len_sym = c.take<uint8_t>(p->nsym);
+    w.codes = c.take<uint16_t>(n + 8);
+    w.chunk_off = c.take<uint32_t>(std::max<uint64_t>(p->nchunks, 1));
+    w.stage_out = c.take<uint2>(n);
+    w.stage_vb = c.take<uint2>(n);
+    w.bm = c.take<uint32_t>(2 * std::max<uint64_t>(p->nwords, 1));
+    w.wpre = c.take<uint32_t>(2 * std::max<uint64_t>(p->nwords, 1));
+    w.bpre = c.take<uint32_t>(2 * std::max<uint64_t>(p->nbmblk, 1));
+    w.sse_part = c.take<double>(std::max<uint32_t>(p->pq.nblocks, 1));
+    w.range_part = c.take<float>(3 * (uint64_t)p->n_range_blocks);
+    w.hkeys = c.take<unsigned long long>(pow2);
+    w.hseqA = c.take<unsigned long long>(p->nsym);
+    w.hseqB = c.take<unsigned long long>(p->nsym);
+    w.hnew = c.take<unsigned long long>(p->nsym);
+    w.hnode = c.take<unsigned long long>(2ull * p->nsym);
+    w.hpar = c.take<uint32_t>(2ull * p->nsym);
+    w.hlw = c.take<uint32_t>(p->nsym);
+    w.hlsym = c.take<uint16_t>(p->nsym);
+    w.dlut = c.take<uint32_t>(1u << fp::kLutBits);
+    w.dsyms = c.take<uint16_t>(fp::kMaxSym);
+    w.lb_flags = c.take<uint32_t>(std::max<uint64_t>(p->lb_tiles_total, 1));
+    w.lb_vals = c.take<uint32_t>(2 * std::max<uint64_t>(p->lb_tiles_total, 1) * p->lb_width);
+    w.lb_ctr = c.take<uint32_t>(8);
+    *total = (c.off + 255) & ~(size_t)255;
+}
+
+ScanPass contig_pass(uint64_t rows, uint64_t W, bool final_pass) {
+    ScanPass s{};
+    s.kind = 0;
+    s.A = (uint32_t)rows;
+    s.L = (uint32_t)W;
+    s.B = 1;
+    s.ipt = W <= 1024 ? 4 : (W <= 2048 ? 8 : 16);
+    s.tiles = (uint32_t)(rows * cdiv(W, 256ull * s.ipt));
+    s.tb = 1;
+    s.vec = (W % 4) == 0;
+    s.final_pass = final_pass;
+    return s;
+}
+
+ScanPass strided_pass(uint64_t A, uint64_t L, uint64_t B, bool final_pass) {
+    ScanPass s{};
+    s.kind = 1;
+    s.A = (uint32_t)A;
+    s.L = (uint32_t)L;
+    s.B = (uint32_t)B;
+    s.vec = (B % 4) == 0;
+    s.tb = s.vec ? 1024 : 256;
+    s.ipt = 16;
+    s.tiles = (uint32_t)(cdiv(L, 16) * A * cdiv(B, (uint64_t)s.tb));
+    s.final_pass = final_pass;
+    return s;
+}
+
+}  // namespace
+
+namespace fp {
+
+cudaEvent_t Profiler::take() {
+    if (used == npool) {
+        size_t nn = npool ? 2 * npool : 256;
+        cudaEvent_t* np_ = static_cast<cudaEvent_t*>(realloc(pool, nn * sizeof(cudaEvent_t)));
+        if (!np_) return nullptr;
+        pool = np_;
+        for (size_t i = npool; i < nn; i++)
+            if (cudaEventCreate(&pool[i]) != cudaSuccess) { nn = i; break; }
+        npool = nn;
+        if (used == npool) return nullptr;
+    }
+    return pool[used++];
+}
+
+void Profiler::begin(int stage, cudaStream_t st, cudaEvent_t* a) {
+    launches[stage]++;
+    *a = nullptr;
+    if (!on) return;
+    *a = take();
+    if (*a) cudaEventRecord(*a, st);
+}
+
+void Profiler::end(int stage, cudaStream_t st, cudaEvent_t a) {
+    if (!on || !a) return;
+    cudaEvent_t b = take();
+    if (!b) return;
+    cudaEventRecord(b, st);
+    if (nrec == cap) {
+        size_t nc = cap ? 2 * cap : 256;
+        Rec* nr = static_cast<Rec*>(realloc(recs, nc * sizeof(Rec)));
+        if (!nr) return;
+        recs = nr;
+        cap = nc;
+    }
+    recs[nrec++] = Rec{stage, a, b};
+}
+
+void Profiler::release() {
+    for (size_t i = 0; i < npool; i++) cudaEventDestroy(pool[i]);
+    free(pool);
+    free(recs);
+    pool = nullptr;
+    recs = nullptr;
+    npool = used = nrec = cap = 0;
+}
+
+}  // namespace fp
+
+extern "C" {
+
+static const char* kStageNames[FPSNR_NSTAGES] = {
+    "range_plan", "predict_quantize", "rank_popc", "codebook", "chunk_bits", "scan_chunks",
+    "pack", "emit", "finalize", "decode_setup", "decode", "scatter", "scan_x", "scan_y",
+    "scan_final_dequant", "patch"};
+
+const char* fpsnr_stage_name(int stage) {
+    return (stage >= 0 && stage < FPSNR_NSTAGES) ? kStageNames[stage] : "unknown";
+}
+
+int fpsnr_plan_profile(fpsnr_plan_t p, int enable) {
+    if (!p) return FPSNR_EINVAL;
+    p->prof.on = enable != 0;
+    return FPSNR_OK;
+}
+
+int fpsnr_plan_profile_read(fpsnr_plan_t p, double* ms, uint64_t* launches, int nstages) {
+    if (!p || nstages < 0) return FPSNR_EINVAL;
+    fp::Profiler& pr = p->prof;
+    int rc = FPSNR_OK;
+    for (int i = 0; i < nstages && i < FPSNR_NSTAGES; i++) {
+        if (ms) ms[i] = 0.0;
+        if (launches) launches[i] = pr.launches[i];
+    }
+    for (size_t r = 0; r < pr.nrec; r++) {
+        float t = 0.0f;
+        if (cudaEventSynchronize(pr.recs[r].b) != cudaSuccess ||
+            cudaEventElapsedTime(&t, pr.recs[r].a, pr.recs[r].b) != cudaSuccess) {
+            rc = FPSNR_ECUDA;
+            continue;
+        }
+        if (ms && pr.recs[r].stage < nstages) ms[pr.recs[r].stage] += t;
+    }
+    pr.nrec = 0;
+    pr.used = 0;
+    for (int i = 0; i < FPSNR_NSTAGES; i++) pr.launches[i] = 0;
+    return rc;
+}
+
+int fpsnr_default_opts(fpsnr_opts* o) {
+    if (!o) return FPSNR_EINVAL;
+    o->radius = 32768;
+    o->chunk = 256;
+    o->lmax = 27;
+    o->lorenzo_dims = 0;
+    return FPSNR_OK;
+}
+
+const char* fpsnr_strerror(int code) {
+    switch (code) {
+        case FPSNR_OK: return "ok";
+        case FPSNR_EINVAL: return "invalid argument";
+        case FPSNR_ENOMEM: return "device memory allocation failed";
+        case FPSNR_ECUDA: return "CUDA error";
+        case FPSNR_ENONFINITE: return "input contains NaN or Inf";
+        case FPSNR_ECAPACITY: return "output buffer too small";
+        case FPSNR_ECORRUPT: return "compressed stream is corrupt or does not match the plan";
+        case FPSNR_ETIMEOUT: return "inter-block wait timed out";
+        default: return "unknown error";
+    }
+}
+
+int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_psnr_db,
+               const fpsnr_opts* opts) {
+    if (!out) return FPSNR_EINVAL;
+    *out = nullptr;
+    if (ndim < 1 || ndim > 3 || !dims || !psnr_ok(target_psnr_db)) return FPSNR_EINVAL;
+    fpsnr_opts o;
+    fpsnr_default_opts(&o);
+    if (opts) o = *opts;
+    const int ld = o.lorenzo_dims ? o.lorenzo_dims : ndim;
+    if (ld < 1 || ld > ndim) return FPSNR_EINVAL;
+    if (o.radius < 1 || o.radius > fp::kMaxRadius) return FPSNR_EINVAL;
+    if (o.chunk < 32 || o.chunk > 65536 || (o.chunk % 32) != 0) return FPSNR_EINVAL;
+    if (o.lmax < 1 || o.lmax > fp::kMaxLmax || (1ull << o.lmax) < 2ull * o.radius) return FPSNR_EINVAL;
+    uint64_t d[3] = {1, 1, 1};
+    uint64_t n = 1;
+    for (int i = 0; i < ndim; i++) {
+        d[i] = dims[i];
+        if (d[i] > 0xFFFFFFFFull) return FPSNR_EINVAL;
+        n *= d[i];
+        if (n > 0xFFFFFFFFull) return FPSNR_EINVAL;
+    }
+    fpsnr_plan_s* p = new (std::nothrow) fpsnr_plan_s();
+    if (!p) return FPSNR_ENOMEM;
+    p->ndim = ndim;
+    p->ld = ld;
+    memcpy(p->dims, d, sizeof(d));
+    p->n = n;
+    p->target_psnr = target_psnr_db;
+    p->eb_rel = eb_rel_of(target_psnr_db);
+    p->radius = o.radius;
+    p->chunk = o.chunk;
+    p->lmax = o.lmax;
+    p->nsym = 2u * (uint32_t)o.radius;
+    p->nchunks = cdiv(n, (uint64_t)o.chunk);
+    p->nwords = cdiv(n, 32);
+    p->nbmblk = cdiv(p->nwords, 1024);
+    p->epoch = 0;
+    if (cudaGetDevice(&p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+        delete p;
+        return FPSNR_ECUDA;
+    }
+
+    // predictor geometry
+    PQGeom& g = p->pq;
+    if (ld == 1) {
+        g.mode = 1; g.tx = 512; g.ty = 1; g.zs = 32;
+        g.vx = 512; g.vy = 1; g.vz = (uint32_t)std::max<uint64_t>(cdiv(n, 512), 1);
+    } else if (ld == 2) {
+        const uint64_t nx = d[0], rows = nx ? n / nx : 0;
+        g.mode = 2; g.ty = 1;
+        g.tx = nx <= 128 ? 128 : (nx <= 256 ? 256 : 512);
+        g.zs = std::max(1, 16384 / g.tx);
+        g.vx = (uint32_t)nx; g.vy = 1; g.vz = (uint32_t)rows;
+    } else {
+        g.mode = 3; g.tx = 128; g.ty = 8; g.zs = 16;
+        g.vx = (uint32_t)d[0]; g.vy = (uint32_t)d[1]; g.vz = (uint32_t)d[2];
+    }
+    g.vec = (g.vx % 4) == 0;
+    if (n > 0) {
+        g.nbx = (uint32_t)cdiv(g.vx, g.tx);
+        g.nby = (uint32_t)cdiv(g.vy, g.ty);
+        g.nbz = (uint32_t)cdiv(g.vz, g.zs);
+        const uint64_t nb = (uint64_t)g.nbx * g.nby * g.nbz;
+        if (nb > 0x7FFFFFFFull) { delete p; return FPSNR_EINVAL; }
+        g.nblocks = (uint32_t)nb;
+    }
+    p->n_range_blocks = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(cdiv(n, 512ull * 16),
+                                                                            2ull * p->sm_count));
+
+    // inverse-Lorenzo passes
+    p->n_passes = 0;
+    if (n > 0) {
+        if (ld == 1) {
+            p->pass[p->n_passes++] = contig_pass(1, n, true);
+        } else if (ld == 2) {
+            const uint64_t nx = d[0], rows = n / nx;
+            p->pass[p->n_passes++] = contig_pass(rows, nx, false);
+            p->pass[p->n_passes++] = strided_pass(1, rows, nx, true);
+        } else {
+            p->pass[p->n_passes++] = contig_pass(d[2] * d[1], d[0], false);
+            p->pass[p->n_passes++] = strided_pass(d[2], d[1], d[0], false);
+            p->pass[p->n_passes++] = strided_pass(1, d[2], d[1] * d[0], true);
+        }
+    }
+    p->lb_tiles_total = 0;
+    p->lb_width = 1;
+    for (int i = 0; i < p->n_passes; i++) {
+        p->pass[i].val_off = p->lb_tiles_total;
+        p->pass[i].ctr_slot = i;
+        p->lb_tiles_total += p->pass[i].tiles;
+        p->lb_width = std::max<uint64_t>(p->lb_width, (uint64_t)p->pass[i].tb);
+    }
+
+    size_t bytes = 0;
+    carve(p, nullptr, &bytes);
+    void* slab = nullptr;
+    if (cudaMalloc(&slab, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return FPSNR_ENOMEM;
+    }
+    p->slab = slab;
+    p->slab_bytes = bytes;
+    carve(p, reinterpret_cast<uint8_t*>(slab), &bytes);
+    const fp::Workspace& w = p->w;
+    bool ok = cudaMemset(w.par, 0, sizeof(fp::DevParams)) == cudaSuccess &&
+              cudaMemset(w.bm, 0, 2 * std::max<uint64_t>(p->nwords, 1) * 4) == cudaSuccess &&
+              cudaMemset(w.lb_flags, 0, std::max<uint64_t>(p->lb_tiles_total, 1) * 4) == cudaSuccess &&
+              cudaMemset(w.lb_ctr, 0, 8 * 4) == cudaSuccess &&
+              fp::codebook_prepare() == FPSNR_OK && cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) {
+        cudaFree(slab);
+        delete p;
+        return FPSNR_ECUDA;
+    }
+    p->cb_smem = fp::codebook_smem_bytes();
+    *out = p;
+    return FPSNR_OK;
+}
+
+int fpsnr_plan_set_psnr(fpsnr_plan_t p, double target_psnr_db) {
+    if (!p || !psnr_ok(target_psnr_db)) return FPSNR_EINVAL;
+    p->target_psnr = target_psnr_db;
+    p->eb_rel = eb_rel_of(target_psnr_db);
+    return FPSNR_OK;
+}
+
+double fpsnr_plan_eb_rel(fpsnr_plan_t p) { return p ? p->eb_rel : NAN; }
+
+uint64_t fpsnr_plan_points(fpsnr_plan_t p) { return p ? p->n : 0; }
+
+uint64_t fpsnr_max_compressed_bytes(fpsnr_plan_t p) {
+    if (!p) return 0;
+    auto pad = [](uint64_t b) { return (b + 15u) & ~(uint64_t)15u; };
+    const uint64_t words = cdiv(p->n * (uint64_t)p->lmax, 32) + p->nchunks;
+    return fp::kHeaderBytes + pad(4ull * p->nsym) + pad(4ull * p->nchunks) + pad(4ull * words) +
+           pad(8ull * p->n) + pad(8ull * p->n);
+}
+
+int fpsnr_compress(fpsnr_plan_t p, const float* d_in, void* d_out, uint64_t out_cap,
+                   uint64_t* d_out_bytes, fpsnr_stats* d_stats, void* stream) {
+    if (!p || !d_out || (p->n > 0 && !d_in)) return FPSNR_EINVAL;
+    if (((uintptr_t)d_in & 3u) || ((uintptr_t)d_out & 15u)) return FPSNR_EINVAL;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return FPSNR_ECUDA;
+    if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return FPSNR_ECUDA;
+    int rc = fp::launch_compress(p, d_in, d_out, out_cap, d_out_bytes, d_stats,
+                                 reinterpret_cast<cudaStream_t>(stream));
+    if (cur != p->device) cudaSetDevice(cur);
+    return rc;
+}
+
+int fpsnr_decompress(fpsnr_plan_t p, const void* d_blob, uint64_t blob_bytes, float* d_out,
+                     uint64_t n_out, int* d_status, void* stream) {
+    if (!p || !d_blob || n_out != p->n || (p->n > 0 && !d_out)) return FPSNR_EINVAL;
+    if (((uintptr_t)d_blob & 15u) || ((uintptr_t)d_out & 15u)) return FPSNR_EINVAL;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return FPSNR_ECUDA;
+    if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return FPSNR_ECUDA;
+    int rc = fp::launch_decompress(p, d_blob, blob_bytes, d_out, d_status,
+                                   reinterpret_cast<cudaStream_t>(stream));
+    if (cur != p->device) cudaSetDevice(cur);
+    return rc;
+}
+
+const uint16_t* fpsnr_plan_codes(fpsnr_plan_t p) { return p ? p->w.codes : nullptr; }
+
+void fpsnr_plan_destroy(fpsnr_plan_t p) {
+    if (!p) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    p->prof.release();
+    cudaFree(p->slab);
+    if (cur != p->device && cur >= 0) cudaSetDevice(cur);
+    delete p;
+}
+
+}  // extern "C"

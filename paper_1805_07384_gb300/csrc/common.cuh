@@ -1,0 +1,278 @@
+// common.cuh -- internal declarations shared by the fpsnr CUDA translation units.
+//
+// The plan owns one device slab carved into the arrays of `Workspace`.  The
+// per-call scalars (value range, error bound, counters, section offsets,
+// status) live in one `DevParams` record on the device, so that a whole
+// compress or decompress call is a chain of kernels on one stream with no
+// host round trip.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fpsnr.h"
+
+namespace fp {
+
+constexpr uint32_t kMagic = 0x31535046u;  // bytes "FPS1"
+constexpr uint32_t kVersion = 1u;
+constexpr uint32_t kHeaderBytes = 128u;
+constexpr uint32_t kFlagConstant = 1u;     // vr == 0 (or empty): header only
+constexpr uint32_t kFlagLatticeOff = 2u;   // bin width not representable: q = 0
+constexpr uint32_t kFlagError = 1u << 31;  // internal: a device-side error occurred
+constexpr int kMaxRadius = 32768;
+constexpr int kMaxSym = 2 * kMaxRadius;
+constexpr int kMaxLmax = 27;
+constexpr int kLutBits = 11;  // decode look-up table width
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// Per-call device record.  Written by kernels, read by later kernels.
+struct DevParams {
+    double vr, eb_abs, eb_rel, target_psnr;
+    double sse;
+    float xmin, xmax, s, inv, thr;
+    uint32_t flags;
+    int32_t status;
+    uint32_t n_out, n_vb;     // staged outlier / verbatim counts
+    uint32_t n_sym;           // Huffman symbols in use
+    uint32_t stream_words;
+    uint32_t done_range;      // self-resetting last-block counter
+    uint64_t cap;             // output capacity of this call
+    uint64_t off_cb, off_ct, off_st, off_ou, off_vb, total;
+    // decompression: header fields of the blob being decoded
+    uint32_t d_radius, d_chunk, d_lmax, d_nsym, d_nchunks, d_words, d_nout, d_nvb;
+    uint32_t d_count[32], d_first_code[32], d_first_index[32];
+};
+
+// Device arrays carved from the plan's slab.
+struct Workspace {
+    DevParams* par;
+    uint32_t* hist;         // [nsym] symbol counts
+    uint32_t* enc;          // [nsym] (code << 5) | len, 0 = unused
+    uint8_t* len_sym;       // [nsym] code length per symbol
+    uint16_t* codes;        // [n] symbols
+    uint32_t* chunk_off;    // [nchunks] words per chunk, then exclusive word offsets
+    uint2* stage_out;       // [n] (idx, delta) in discovery order
+    uint2* stage_vb;        // [n] (idx, float bits) in discovery order
+    uint32_t* bm;           // [2][nwords] membership bitmaps (kept all-zero between calls)
+    uint32_t* wpre;         // [2][nwords] in-block exclusive popcount prefix
+    uint32_t* bpre;         // [2][nbmblk] block totals, then exclusive prefix
+    double* sse_part;       // [n_pq_blocks]
+    float* range_part;      // [3][n_range_blocks]
+    // Huffman construction scratch (used when the alphabet is too large for shared memory)
+    unsigned long long* hkeys;  // [nsym]
+    unsigned long long* hseqA;  // [nsym]
+    unsigned long long* hseqB;  // [nsym]
+    unsigned long long* hnew;   // [nsym]
+    unsigned long long* hnode;  // [2*nsym]
+    uint32_t* hpar;             // [2*nsym]
+    uint32_t* hlw;              // [nsym] leaf weights
+    uint16_t* hlsym;            // [nsym] leaf symbols
+    // decoding tables
+    uint32_t* dlut;  // [1 << kLutBits]
+    uint16_t* dsyms; // [kMaxSym]
+    // inverse-Lorenzo look-back state
+    uint32_t* lb_flags;  // [n_lb_tiles]
+    uint32_t* lb_vals;   // [2][n_lb_tiles * lb_width] aggregate, inclusive
+    uint32_t* lb_ctr;    // [8] dynamic tile counters (pairs: counter, done)
+};
+
+// Launch geometry of the predict-quantize kernel.
+struct PQGeom {
+    int mode;          // 1: flat 1D, 2: rows x nx, 3: nz x ny x nx
+    int tx, ty, zs;    // tile width (x), tile height (y), planes per block
+    uint32_t vx, vy, vz;  // predictor view (x fastest)
+    uint32_t nbx, nby, nbz;
+    uint32_t nblocks;
+    bool vec;          // rows start on 16-byte boundaries
+};
+
+// Geometry of one inverse-Lorenzo scan pass.
+struct ScanPass {
+    int kind;          // 0: contiguous rows, 1: strided (middle axis)
+    uint32_t A, L, B;  // outer count, scan length, inner count (B = 1 for contiguous)
+    uint32_t tiles;
+    int ipt;           // contiguous: items per thread; strided: rows per tile
+    int tb;            // strided: columns per tile
+    bool vec;
+    bool final_pass;
+    int ctr_slot;      // which lb_ctr pair
+    uint64_t val_off;  // offset (in tiles) into the look-back arrays
+};
+
+}  // namespace fp
+
+namespace fp {
+enum Stage {
+    kStRange = 0, kStPq, kStRank, kStCodebook, kStChunkBits, kStScanChunks, kStPack, kStEmit,
+    kStFinalize, kStDsetup, kStDecode, kStScatter, kStScanX, kStScanY, kStScanFinal, kStPatch
+};
+
+// Host-side launch counters and optional per-launch CUDA events.
+struct Profiler {
+    bool on = false;
+    uint64_t launches[FPSNR_NSTAGES] = {};
+    struct Rec { int stage; cudaEvent_t a, b; };
+    Rec* recs = nullptr;
+    size_t nrec = 0, cap = 0;
+    cudaEvent_t* pool = nullptr;
+    size_t npool = 0, used = 0;
+    cudaEvent_t take();
+    void begin(int stage, cudaStream_t st, cudaEvent_t* a);
+    void end(int stage, cudaStream_t st, cudaEvent_t a);
+    void release();
+};
+}  // namespace fp
+
+struct fpsnr_plan_s {
+    int device;
+    int ndim, ld;
+    uint64_t dims[3];
+    uint64_t n;
+    double target_psnr, eb_rel;
+    int radius, chunk, lmax;
+    uint32_t nsym;
+    uint64_t nchunks, nwords, nbmblk;
+    fp::PQGeom pq;
+    uint32_t n_range_blocks;
+    int n_passes;
+    fp::ScanPass pass[3];
+    uint64_t lb_tiles_total, lb_width;
+    uint32_t epoch;
+    void* slab;
+    size_t slab_bytes;
+    fp::Workspace w;
+    int sm_count;
+    int cb_smem;  // dynamic shared memory of the codebook kernel
+    fp::Profiler prof;
+};
+
+// Brackets one kernel launch with the plan's profiler.
+struct StageScope {
+    fp::Profiler& pr;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    StageScope(fp::Profiler& p, int s, cudaStream_t stream) : pr(p), stage(s), st(stream) {
+        pr.begin(stage, st, &a);
+    }
+    ~StageScope() { pr.end(stage, st, a); }
+};
+
+namespace fp {
+
+// ---- host-side launchers (one per translation unit) ----
+int launch_compress(fpsnr_plan_s* p, const float* d_in, void* d_out, uint64_t cap,
+                    uint64_t* d_out_bytes, fpsnr_stats* d_stats, cudaStream_t st);
+int launch_codebook(fpsnr_plan_s* p, void* d_out, cudaStream_t st);
+int launch_decompress(fpsnr_plan_s* p, const void* d_blob, uint64_t bytes, float* d_out,
+                      int* d_status, cudaStream_t st);
+int codebook_smem_bytes();
+int codebook_prepare();
+
+// ---- device helpers ----
+#ifdef __CUDACC__
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Sets the device status once (first error wins) and raises the error flag.
+__device__ __forceinline__ void set_error(DevParams* par, int code) {
+    atomicCAS(reinterpret_cast<int*>(&par->status), 0, code);
+    atomicOr(&par->flags, kFlagError);
+}
+
+// Block-wide exclusive scan of one uint32 per thread (blockDim.x multiple of 32,
+// at most 1024).  `sh` needs 33 words.  Returns the exclusive prefix; *total
+// receives the block sum.  Contains __syncthreads.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* sh, uint32_t* total) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? sh[lane] : 0u;
+        uint32_t s = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= (uint32_t)o) s += y;
+        }
+        if (lane < nw) sh[lane] = s - w;
+        if (lane == nw - 1) sh[32] = s;
+    }
+    __syncthreads();
+    uint32_t r = sh[warp] + x - v;
+    *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// Error-free transformations on float32 (Knuth TwoSum, FMA-based TwoProd).
+// Every operation is an explicit round-to-nearest intrinsic so that the
+// compiler neither contracts nor reassociates them.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void ff_add_sq_diff(FF& acc, float a, float b) {
+    // exact d = a - b as dh + dl
+    float nb = -b;
+    float dh = __fadd_rn(a, nb);
+    float bb = __fsub_rn(dh, a);
+    float dl = __fadd_rn(__fsub_rn(a, __fsub_rn(dh, bb)), __fsub_rn(nb, bb));
+    // d^2 = p + e (+ 2 dh dl + dl^2, both far below the float-float precision needed)
+    float p = __fmul_rn(dh, dh);
+    float e = __fmaf_rn(dh, dh, -p);
+    e = __fadd_rn(e, __fmul_rn(__fmul_rn(2.0f, dh), dl));
+    // acc += p + e
+    float t = __fadd_rn(acc.hi, p);
+    float tb = __fsub_rn(t, acc.hi);
+    float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(t, tb)), __fsub_rn(p, tb));
+    acc.hi = t;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ double ff_to_double(const FF& a) { return (double)a.hi + (double)a.lo; }
+
+// Deterministic block reduction of one double per thread (fixed tree order).
+// `sh` needs blockDim.x/32 doubles.  Result valid in thread 0.
+__device__ __forceinline__ double block_sum_double(double v, double* sh) {
+    const uint32_t tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    const uint32_t lane = tid & 31u, warp = tid >> 5;
+    const uint32_t nw = (blockDim.x * blockDim.y * blockDim.z) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (tid == 0)
+        for (uint32_t i = 0; i < nw; i++) r += sh[i];
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+#endif  // __CUDACC__
+
+}  // namespace fp

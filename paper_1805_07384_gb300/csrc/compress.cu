@@ -1,0 +1,800 @@
+// compress.cu -- the compression chain of the fixed-PSNR method on sm_103a.
+//
+//   k_range_plan   value range vr = max - min (Sec. IV, under Eq. 5) and the
+//                  error bound eb_abs = eb_rel * vr (Sec. IV, after Eq. 7),
+//                  bin width 2 eb (Sec. IV, before Eq. 7)
+//   k_pq           prequantization onto the integer lattice + Lorenzo residual
+//                  (Sec. II-A step 1, Sec. III) + uniform quantization into
+//                  symbols (Sec. IV) + verbatim test + histogram + outlier
+//                  staging + exact squared-error partials (Eq. 4)
+//   k_rank_popc    order-preserving compaction ranks for outliers/verbatims
+//   (k_codebook    Huffman code, huffman.cu)
+//   k_chunk_bits   coded bits per chunk
+//   k_scan_chunks  chunk word offsets and section layout
+//   k_pack         warp-cooperative MSB-first bit packing (SZ step 2, Sec. II-A)
+//   k_emit         outliers and verbatims written in index order
+//   k_finalize     header, size, statistics
+#include <float.h>
+
+#include "common.cuh"
+
+namespace fp {
+
+// ---------------------------------------------------------------------------
+// value range and plan scalars
+// ---------------------------------------------------------------------------
+
+template <bool VEC>
+__global__ void __launch_bounds__(512) k_range_plan(const float* __restrict__ x, uint64_t n,
+                                                    DevParams* par, float* part,
+                                                    uint32_t* hist, uint32_t nsym,
+                                                    double eb_rel, double target, uint64_t cap) {
+    const uint32_t tid = threadIdx.x;
+    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + tid;
+    const uint64_t gsz = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = gtid; i < nsym; i += gsz) hist[i] = 0u;
+
+    float lo = FLT_MAX, hi = -FLT_MAX;
+    int nf = 0;
+    if (VEC) {
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        const uint64_t n4 = n >> 2;
+        for (uint64_t i = gtid; i < n4; i += gsz) {
+            float4 v = __ldcs(x4 + i);
+            nf |= !isfinite(v.x) | !isfinite(v.y) | !isfinite(v.z) | !isfinite(v.w);
+            lo = fminf(lo, fminf(fminf(v.x, v.y), fminf(v.z, v.w)));
+            hi = fmaxf(hi, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+        }
+        for (uint64_t i = (n4 << 2) + gtid; i < n; i += gsz) {
+            float v = x[i];
+            nf |= !isfinite(v);
+            lo = fminf(lo, v);
+            hi = fmaxf(hi, v);
+        }
+    } else {
+        for (uint64_t i = gtid; i < n; i += gsz) {
+            float v = x[i];
+            nf |= !isfinite(v);
+            lo = fminf(lo, v);
+            hi = fmaxf(hi, v);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        nf |= __shfl_xor_sync(0xffffffffu, nf, o);
+    }
+    __shared__ float slo[16], shi[16];
+    __shared__ int snf[16];
+    __shared__ bool last;
+    if ((tid & 31) == 0) { slo[tid >> 5] = lo; shi[tid >> 5] = hi; snf[tid >> 5] = nf; }
+    __syncthreads();
+    if (tid == 0) {
+        for (uint32_t w = 1; w < (blockDim.x >> 5); w++) {
+            lo = fminf(lo, slo[w]); hi = fmaxf(hi, shi[w]); nf |= snf[w];
+        }
+        part[3 * blockIdx.x] = lo;
+        part[3 * blockIdx.x + 1] = hi;
+        part[3 * blockIdx.x + 2] = nf ? 1.0f : 0.0f;
+        __threadfence();
+        last = (atomicAdd(&par->done_range, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    lo = FLT_MAX; hi = -FLT_MAX; nf = 0;
+    for (uint32_t b = tid; b < gridDim.x; b += blockDim.x) {
+        lo = fminf(lo, __ldcg(part + 3 * b));
+        hi = fmaxf(hi, __ldcg(part + 3 * b + 1));
+        nf |= __ldcg(part + 3 * b + 2) != 0.0f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        nf |= __shfl_xor_sync(0xffffffffu, nf, o);
+    }
+    __syncthreads();
+    if ((tid & 31) == 0) { slo[tid >> 5] = lo; shi[tid >> 5] = hi; snf[tid >> 5] = nf; }
+    __syncthreads();
+    if (tid != 0) return;
+    for (uint32_t w = 1; w < (blockDim.x >> 5); w++) {
+        lo = fminf(lo, slo[w]); hi = fmaxf(hi, shi[w]); nf |= snf[w];
+    }
+    if (n == 0) { lo = 0.0f; hi = 0.0f; }
+    double vr = (double)hi - (double)lo;
+    uint32_t flags = 0;
+    int status = 0;
+    double eb = 0.0;
+    float s = 0.0f, inv = 0.0f, thr = 0.0f;
+    if (nf) {
+        status = FPSNR_ENONFINITE;
+        flags = kFlagError;
+    } else if (n == 0 || vr == 0.0) {
+        flags = kFlagConstant;
+    } else {
+        eb = eb_rel * vr;
+        double two_eb = 2.0 * eb;
+        s = __double2float_rn(two_eb);
+        inv = __double2float_rn(1.0 / two_eb);
+        if (!(s > 0.0f) || isinf(inv) || !(vr <= (double)FLT_MAX)) {
+            flags = kFlagLatticeOff;
+            s = 0.0f;
+            inv = 0.0f;
+        }
+        float f = __double2float_rd(eb);
+        float t = f > 0.0f ? __int_as_float(__float_as_int(f) - 1) : 0.0f;
+        thr = t > 0.0f ? t : 0.0f;
+    }
+    par->vr = vr;
+    par->eb_abs = eb;
+    par->eb_rel = eb_rel;
+    par->target_psnr = target;
+    par->sse = 0.0;
+    par->xmin = lo;
+    par->xmax = hi;
+    par->s = s;
+    par->inv = inv;
+    par->thr = thr;
+    par->flags = flags;
+    par->status = status;
+    par->n_out = 0;
+    par->n_vb = 0;
+    par->n_sym = 0;
+    par->stream_words = 0;
+    par->cap = cap;
+    par->off_cb = kHeaderBytes;
+    par->off_ct = par->off_st = par->off_ou = par->off_vb = par->total = kHeaderBytes;
+    par->done_range = 0;
+}
+
+// ---------------------------------------------------------------------------
+// fused prequantize + Lorenzo + quantize + verbatim test + histogram
+// ---------------------------------------------------------------------------
+
+struct PQArgs {
+    DevParams* par;
+    uint16_t* codes;
+    uint32_t* hist;
+    uint2* stage_out;
+    uint2* stage_vb;
+    uint32_t* bm_out;
+    uint32_t* bm_vb;
+    double* sse_part;
+    uint64_t n;
+    uint32_t vx, vy, vz, zs;
+    uint32_t nbx, nby;
+    int radius;
+};
+
+constexpr int kHistWin = 4096;
+
+__device__ __forceinline__ int32_t prequant(float x, float xmin, float inv, bool off) {
+    return off ? 0 : __float2int_rn(__fmul_rn(__fsub_rn(x, xmin), inv));
+}
+
+// MODE 1: flat 1D predictor over a (rows x vx) traversal, left neighbour of a
+//         row start is the previous row's last point, no upper-row term.
+// MODE 2: 2D predictor on (vz rows) x vx, TY must be 1 (vy == 1).
+// MODE 3: 3D predictor on vz x vy x vx with TY rows per tile.
+template <int MODE, int TX, int TY, bool VEC>
+__global__ void __launch_bounds__(TX / 4 * TY) k_pq(const float* __restrict__ x, PQArgs a) {
+    constexpr int NT = TX / 4 * TY;
+    DevParams* par = a.par;
+    const uint32_t flags = par->flags;
+    if (flags & (kFlagConstant | kFlagError)) return;
+    const float xmin = par->xmin, inv = par->inv, s = par->s, thr = par->thr;
+    const bool off = (flags & kFlagLatticeOff) != 0;
+    const int R = a.radius;
+
+    __shared__ uint32_t shist[kHistWin];
+    __shared__ int32_t sL1[(MODE == 3) ? 2 : 1][(MODE == 3) ? TY + 1 : 1][(MODE == 3) ? TX : 1];
+    __shared__ double ssum[NT / 32];
+
+    const uint32_t tid = threadIdx.y * (TX / 4) + threadIdx.x;
+    for (uint32_t i = tid; i < kHistWin; i += NT) shist[i] = 0u;
+    __syncthreads();
+
+    const uint32_t b = blockIdx.x;
+    const uint32_t bx = b % a.nbx;
+    const uint32_t by = (b / a.nbx) % a.nby;
+    const uint32_t bz = b / (a.nbx * a.nby);
+    const uint32_t x0 = bx * TX, y0 = by * TY, z0 = bz * a.zs;
+    const uint32_t z1 = min(z0 + a.zs, a.vz);
+    const uint32_t xb = x0 + 4u * threadIdx.x;
+    const uint32_t y = y0 + threadIdx.y;
+    const uint32_t lane = tid & 31u;
+    const int wlo = R - kHistWin / 2;
+
+    int32_t L2prev[4] = {0, 0, 0, 0};
+    FF acc = {0.0f, 0.0f};
+    int buf = 0;
+    const uint32_t zstart = (MODE != 1 && z0 > 0) ? z0 - 1 : z0;
+
+    for (uint32_t z = zstart; z < z1; z++) {
+        // ---- own row: x values, lattice q, row difference L1 ----
+        float xv[4];
+        int32_t q[4];
+        bool in[4];
+        const uint64_t rowbase = ((uint64_t)z * a.vy + y) * a.vx;
+        const bool rowin = (MODE == 3) ? (y < a.vy) : true;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            uint64_t gi = rowbase + xb + k;
+            in[k] = rowin && (xb + k < a.vx) && (MODE != 1 || gi < a.n);
+        }
+        if (VEC && in[3]) {
+            float4 v = __ldcs(reinterpret_cast<const float4*>(x + rowbase + xb));
+            xv[0] = v.x; xv[1] = v.y; xv[2] = v.z; xv[3] = v.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) xv[k] = in[k] ? x[rowbase + xb + k] : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) q[k] = in[k] ? prequant(xv[k], xmin, inv, off) : 0;
+        // left neighbour of q[0]
+        int32_t qleft = __shfl_up_sync(0xffffffffu, q[3], 1);
+        if (lane == 0) {
+            // lane 0 of a warp that starts past the row end needs nothing: all its
+            // points and the next lane's are out of the field
+            qleft = 0;
+            if (rowin) {
+                if (xb > 0) {
+                    if (xb <= a.vx && (MODE != 1 || rowbase + xb - 1 < a.n))
+                        qleft = prequant(x[rowbase + xb - 1], xmin, inv, off);
+                } else if (MODE == 1 && rowbase > 0 && rowbase - 1 < a.n) {
+                    qleft = prequant(x[rowbase - 1], xmin, inv, off);
+                }
+            }
+        }
+        int32_t L1[4];
+        L1[0] = q[0] - qleft;
+#pragma unroll
+        for (int k = 1; k < 4; k++) L1[k] = q[k] - q[k - 1];
+
+        int32_t L2[4];
+        if (MODE == 3) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) sL1[buf][threadIdx.y + 1][4 * threadIdx.x + k] = L1[k];
+            if (threadIdx.y == 0) {
+                // halo row y0 - 1 of this plane
+                int32_t h[4] = {0, 0, 0, 0};
+                int32_t hl = 0;
+                if (y0 > 0) {
+                    const uint64_t hb = ((uint64_t)z * a.vy + (y0 - 1)) * a.vx;
+                    float hv[4];
+                    if (VEC && xb + 3 < a.vx) {
+                        float4 v = *reinterpret_cast<const float4*>(x + hb + xb);
+                        hv[0] = v.x; hv[1] = v.y; hv[2] = v.z; hv[3] = v.w;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; k++) hv[k] = (xb + k < a.vx) ? x[hb + xb + k] : 0.0f;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; k++) h[k] = (xb + k < a.vx) ? prequant(hv[k], xmin, inv, off) : 0;
+                    if (lane == 0 && xb > 0 && xb <= a.vx) hl = prequant(x[hb + xb - 1], xmin, inv, off);
+                }
+                int32_t hs = __shfl_up_sync(0xffffffffu, h[3], 1);
+                if (lane != 0) hl = hs;
+                sL1[buf][0][4 * threadIdx.x] = h[0] - hl;
+#pragma unroll
+                for (int k = 1; k < 4; k++) sL1[buf][0][4 * threadIdx.x + k] = h[k] - h[k - 1];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < 4; k++) L2[k] = L1[k] - sL1[buf][threadIdx.y][4 * threadIdx.x + k];
+            buf ^= 1;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) L2[k] = L1[k];
+        }
+
+        if (z >= z0) {
+            int32_t d[4];
+            uint32_t code[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                d[k] = (MODE == 1) ? L2[k] : L2[k] - L2prev[k];
+                code[k] = (d[k] > -R && d[k] < R) ? (uint32_t)(d[k] + R) : 0u;
+            }
+            // symbols
+            if (VEC && in[3]) {
+                uint2 pk;
+                pk.x = code[0] | (code[1] << 16);
+                pk.y = code[2] | (code[3] << 16);
+                *reinterpret_cast<uint2*>(a.codes + rowbase + xb) = pk;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (in[k]) a.codes[rowbase + xb + k] = (uint16_t)code[k];
+            }
+            // histogram: warp-uniform fast path, else per point
+            const bool all4 = in[0] && in[1] && in[2] && in[3] && code[0] == code[1] &&
+                              code[1] == code[2] && code[2] == code[3];
+            const uint32_t c0 = __shfl_sync(0xffffffffu, code[0], 0);
+            if (__all_sync(0xffffffffu, all4 && code[0] == c0)) {
+                if (lane == 0) {
+                    int bin = (int)c0 - wlo;
+                    if (bin >= 0 && bin < kHistWin) atomicAdd(&shist[bin], 128u);
+                    else atomicAdd(&a.hist[c0], 128u);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    if (!in[k]) continue;
+                    int bin = (int)code[k] - wlo;
+                    if (bin >= 0 && bin < kHistWin) atomicAdd(&shist[bin], 1u);
+                    else atomicAdd(&a.hist[code[k]], 1u);
+                }
+            }
+            // reconstruction, verbatim test, exact squared error, staging
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t gi = (uint32_t)(rowbase + xb + k);
+                float xr = __fmaf_rn(__int2float_rn(q[k]), s, xmin);
+                float df = __fsub_rn(xv[k], xr);
+                bool vb = in[k] && !(fabsf(df) <= thr);
+                if (in[k] && !vb) ff_add_sq_diff(acc, xv[k], xr);
+                bool ol = in[k] && code[k] == 0u;
+                uint32_t mo = __ballot_sync(0xffffffffu, ol);
+                if (mo) {
+                    uint32_t leader = __ffs(mo) - 1, base = 0;
+                    if (lane == leader) base = atomicAdd(&par->n_out, __popc(mo));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (ol) {
+                        uint32_t slot = base + __popc(mo & lanemask_lt());
+                        a.stage_out[slot] = make_uint2(gi, (uint32_t)d[k]);
+                        atomicOr(&a.bm_out[gi >> 5], 1u << (gi & 31u));
+                    }
+                }
+                uint32_t mv = __ballot_sync(0xffffffffu, vb);
+                if (mv) {
+                    uint32_t leader = __ffs(mv) - 1, base = 0;
+                    if (lane == leader) base = atomicAdd(&par->n_vb, __popc(mv));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (vb) {
+                        uint32_t slot = base + __popc(mv & lanemask_lt());
+                        a.stage_vb[slot] = make_uint2(gi, __float_as_uint(xv[k]));
+                        atomicOr(&a.bm_vb[gi >> 5], 1u << (gi & 31u));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) L2prev[k] = L2[k];
+    }
+
+    // flush histogram window and squared-error partial
+    __syncthreads();
+    for (uint32_t i = tid; i < kHistWin; i += NT) {
+        uint32_t c = shist[i];
+        if (c) atomicAdd(&a.hist[wlo + (int)i], c);
+    }
+    double tot = block_sum_double(ff_to_double(acc), ssum);
+    if (tid == 0) a.sse_part[blockIdx.x] = tot;
+}
+
+// ---------------------------------------------------------------------------
+// order-preserving ranks: popcount prefix of the membership bitmaps
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(1024) k_rank_popc(const DevParams* __restrict__ par,
+                                                    const uint32_t* __restrict__ bm,
+                                                    uint32_t* wpre, uint32_t* bpre,
+                                                    uint64_t nwords, uint32_t nbmblk) {
+    const uint32_t list = blockIdx.y;
+    const uint32_t cnt = list == 0 ? par->n_out : par->n_vb;
+    if (cnt == 0 || (par->flags & (kFlagConstant | kFlagError))) return;
+    __shared__ uint32_t sh[33];
+    const uint64_t w = (uint64_t)blockIdx.x * 1024u + threadIdx.x;
+    uint32_t c = w < nwords ? __popc(bm[list * nwords + w]) : 0u;
+    uint32_t total;
+    uint32_t ex = block_excl_scan(c, sh, &total);
+    if (w < nwords) wpre[list * nwords + w] = ex;
+    if (threadIdx.x == 0) bpre[list * nbmblk + blockIdx.x] = total;
+}
+
+// ---------------------------------------------------------------------------
+// encoder: bits per chunk, offsets, packing
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_chunk_bits(const DevParams* __restrict__ par,
+                                                    const uint16_t* __restrict__ codes,
+                                                    const uint32_t* __restrict__ enc,
+                                                    uint32_t* chunk_words, uint64_t n,
+                                                    uint32_t chunk, uint64_t nchunks) {
+    if (par->flags & (kFlagConstant | kFlagError)) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t c = warp; c < nchunks; c += nwarps) {
+        const uint64_t beg = c * chunk;
+        const uint64_t end = min(beg + chunk, n);
+        uint32_t bits = 0;
+        // 8 symbols per lane per step (16-byte loads); chunk is a multiple of 32
+        for (uint64_t i = beg + 8u * lane; i < end; i += 256u) {
+            if (i + 8 <= end) {
+                uint4 v = *reinterpret_cast<const uint4*>(codes + i);
+                uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    bits += __ldg(enc + (wv[k] & 0xffffu)) & 31u;
+                    bits += __ldg(enc + (wv[k] >> 16)) & 31u;
+                }
+            } else {
+                for (uint64_t j = i; j < end; j++) bits += __ldg(enc + codes[j]) & 31u;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
+        if (lane == 0) chunk_words[c] = (bits + 31u) >> 5;
+    }
+}
+
+static __device__ __forceinline__ uint64_t pad16(uint64_t b) { return (b + 15u) & ~(uint64_t)15u; }
+
+// Single-block exclusive scan of the chunk word counts -> word offsets; lays
+// out the sections and checks the capacity.
+__global__ void __launch_bounds__(1024) k_scan_chunks(DevParams* par, uint32_t* chunk_off,
+                                                      uint8_t* out, uint64_t nchunks) {
+    if (par->flags & (kFlagConstant | kFlagError)) {
+        if (threadIdx.x == 0 && (par->flags & kFlagConstant)) {
+            par->total = kHeaderBytes;
+            if (par->cap < kHeaderBytes) set_error(par, FPSNR_ECAPACITY);
+        }
+        return;
+    }
+    __shared__ uint32_t sh[33];
+    constexpr int IPT = 8;
+    const uint64_t off_ct = par->off_ct;
+    const bool write_tab = off_ct + 4 * nchunks <= par->cap;
+    uint32_t* tab = reinterpret_cast<uint32_t*>(out + off_ct);
+    uint32_t carry = 0;
+    for (uint64_t base = 0; base < nchunks; base += 1024u * IPT) {
+        uint32_t v[IPT];
+        uint32_t sum = 0;
+        const uint64_t i0 = base + (uint64_t)threadIdx.x * IPT;
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            v[k] = (i0 + k < nchunks) ? chunk_off[i0 + k] : 0u;
+            sum += v[k];
+        }
+        uint32_t total;
+        uint32_t ex = block_excl_scan(sum, sh, &total) + carry;
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            if (i0 + k < nchunks) {
+                chunk_off[i0 + k] = ex;
+                if (write_tab) tab[i0 + k] = ex;
+            }
+            ex += v[k];
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        par->stream_words = carry;
+        uint64_t off_st = off_ct + pad16(4ull * nchunks);
+        uint64_t off_ou = off_st + pad16(4ull * carry);
+        uint64_t off_vb = off_ou + pad16(8ull * par->n_out);
+        uint64_t total = off_vb + pad16(8ull * par->n_vb);
+        par->off_st = off_st;
+        par->off_ou = off_ou;
+        par->off_vb = off_vb;
+        par->total = total;
+        if (total > par->cap) set_error(par, FPSNR_ECAPACITY);
+    }
+}
+
+// One warp per chunk.  Pieces of 256 symbols (8 per lane) are packed into a
+// per-warp shared-memory word buffer with atomicOr; full words go to global
+// memory coalesced and the trailing partial word is carried to the next piece.
+constexpr int kPackWarps = 8;
+constexpr int kPieceWords = (256 * kMaxLmax + 31) / 32 + 2;
+
+__global__ void __launch_bounds__(kPackWarps * 32) k_pack(const DevParams* __restrict__ par,
+                                                          const uint16_t* __restrict__ codes,
+                                                          const uint32_t* __restrict__ enc,
+                                                          const uint32_t* __restrict__ chunk_off,
+                                                          uint8_t* out, uint64_t n,
+                                                          uint32_t chunk, uint64_t nchunks) {
+    if (par->flags & (kFlagConstant | kFlagError)) return;
+    __shared__ uint32_t sbuf[kPackWarps][kPieceWords];
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    uint32_t* buf = sbuf[wib];
+    uint32_t* stream = reinterpret_cast<uint32_t*>(out + par->off_st);
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t c = warp; c < nchunks; c += nwarps) {
+        const uint64_t beg = c * chunk;
+        const uint64_t end = min(beg + chunk, n);
+        uint32_t wpos = chunk_off[c];  // next word to write
+        uint32_t carry = 0;            // partial word (bits from previous pieces)
+        uint32_t cbits = 0;            // valid bits in carry (< 32)
+        for (uint64_t pb = beg; pb < end; pb += 256u) {
+            // codes of this lane's 8 symbols
+            uint32_t cw[8], cl[8];
+            uint32_t mybits = 0;
+            const uint64_t i = pb + 8u * lane;
+            if (i + 8 <= end) {
+                uint4 v = *reinterpret_cast<const uint4*>(codes + i);
+                uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    uint32_t e0 = __ldg(enc + (wv[k] & 0xffffu));
+                    uint32_t e1 = __ldg(enc + (wv[k] >> 16));
+                    cw[2 * k] = e0 >> 5; cl[2 * k] = e0 & 31u;
+                    cw[2 * k + 1] = e1 >> 5; cl[2 * k + 1] = e1 & 31u;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    uint32_t e = (i + k < end) ? __ldg(enc + codes[i + k]) : 0u;
+                    cw[k] = e >> 5; cl[k] = e & 31u;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) mybits += cl[k];
+            // exclusive prefix of bits across the warp
+            uint32_t incl = mybits;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (uint32_t)o) incl += y;
+            }
+            const uint32_t piece_bits = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t nwords_piece = (cbits + piece_bits + 31u) >> 5;
+            for (uint32_t k = lane; k < nwords_piece; k += 32) buf[k] = 0u;
+            __syncwarp();
+            if (lane == 0) buf[0] = carry;
+            __syncwarp();
+            uint32_t bp = cbits + incl - mybits;  // bit position in buf
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const uint32_t l = cl[k];
+                if (l) {
+                    const uint32_t w = bp >> 5, o = bp & 31u;
+                    if (o + l <= 32u) {
+                        atomicOr(&buf[w], cw[k] << (32u - o - l));
+                    } else {
+                        atomicOr(&buf[w], cw[k] >> (o + l - 32u));
+                        atomicOr(&buf[w + 1], cw[k] << (64u - o - l));
+                    }
+                    bp += l;
+                }
+            }
+            __syncwarp();
+            const uint32_t tot = cbits + piece_bits;
+            const uint32_t full = tot >> 5;
+            for (uint32_t k = lane; k < full; k += 32) stream[wpos + k] = buf[k];
+            carry = (tot & 31u) ? buf[full] : 0u;
+            cbits = tot & 31u;
+            wpos += full;
+            __syncwarp();
+        }
+        if (cbits && lane == 0) stream[wpos] = carry;
+        __syncwarp();
+    }
+}
+
+// Outliers and verbatims in ascending index: rank = number of set bitmap bits
+// before the index.
+__global__ void __launch_bounds__(256) k_emit(const DevParams* __restrict__ par,
+                                              const uint2* __restrict__ stage_out,
+                                              const uint2* __restrict__ stage_vb,
+                                              const uint32_t* __restrict__ bm,
+                                              const uint32_t* __restrict__ wpre,
+                                              const uint32_t* __restrict__ bpre, uint8_t* out,
+                                              uint64_t nwords, uint32_t nbmblk) {
+    if (par->flags & (kFlagConstant | kFlagError)) return;
+    const uint32_t list = blockIdx.y;
+    const uint32_t cnt = list == 0 ? par->n_out : par->n_vb;
+    const uint2* stage = list == 0 ? stage_out : stage_vb;
+    uint2* dst = reinterpret_cast<uint2*>(out + (list == 0 ? par->off_ou : par->off_vb));
+    const uint32_t* b = bm + list * nwords;
+    const uint32_t* wp = wpre + list * nwords;
+    const uint32_t* bp = bpre + list * nbmblk;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        uint2 e = stage[i];
+        const uint32_t idx = e.x, w = idx >> 5;
+        const uint32_t r = bp[w >> 10] + wp[w] + __popc(b[w] & ((1u << (idx & 31u)) - 1u));
+        dst[r] = e;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_finalize(DevParams* par, uint32_t* bm,
+                                                  const uint2* __restrict__ stage_out,
+                                                  const uint2* __restrict__ stage_vb,
+                                                  uint8_t* out, uint64_t* out_bytes,
+                                                  fpsnr_stats* stats, int ndim, int ld,
+                                                  uint64_t d0, uint64_t d1, uint64_t d2,
+                                                  uint64_t n, int radius, int chunk, int lmax,
+                                                  uint64_t nchunks, uint64_t nwords) {
+    // clear the membership bitmaps (only the words that were set)
+    const uint32_t no = par->n_out, nv = par->n_vb;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < no; i += gridDim.x * blockDim.x)
+        bm[stage_out[i].x >> 5] = 0u;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x)
+        bm[nwords + (stage_vb[i].x >> 5)] = 0u;
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+
+    const uint32_t flags = par->flags;
+    const bool err = (flags & kFlagError) != 0;
+    const bool cst = (flags & kFlagConstant) != 0;
+    const uint64_t total = err ? 0 : par->total;
+    if (!err) {
+        uint8_t* h = out;
+        auto put32 = [&](int o, uint32_t v) { *reinterpret_cast<uint32_t*>(h + o) = v; };
+        auto put64 = [&](int o, uint64_t v) { *reinterpret_cast<uint64_t*>(h + o) = v; };
+        auto putd = [&](int o, double v) { *reinterpret_cast<double*>(h + o) = v; };
+        auto putf = [&](int o, float v) { *reinterpret_cast<float*>(h + o) = v; };
+        put32(0, kMagic);
+        put32(4, kVersion);
+        put32(8, (uint32_t)ndim);
+        put32(12, (uint32_t)ld);
+        put64(16, d0);
+        put64(24, d1);
+        put64(32, d2);
+        putd(40, par->target_psnr);
+        putd(48, par->eb_rel);
+        putd(56, par->eb_abs);
+        putd(64, par->vr);
+        putf(72, par->xmin);
+        putf(76, par->xmax);
+        putf(80, par->s);
+        putf(84, par->inv);
+        putf(88, par->thr);
+        put32(92, flags & ~kFlagError);
+        put32(96, (uint32_t)radius);
+        put32(100, (uint32_t)chunk);
+        put32(104, (uint32_t)lmax);
+        put32(108, cst ? 0u : par->n_sym);
+        put32(112, cst ? 0u : (uint32_t)nchunks);
+        put32(116, cst ? 0u : par->stream_words);
+        put32(120, cst ? 0u : par->n_out);
+        put32(124, cst ? 0u : par->n_vb);
+    }
+    if (out_bytes) *out_bytes = total;
+    if (stats) {
+        fpsnr_stats s;
+        s.target_psnr = par->target_psnr;
+        s.eb_rel = par->eb_rel;
+        s.eb_abs = par->eb_abs;
+        s.vr = par->vr;
+        s.psnr_model = cst ? __longlong_as_double(0x7ff0000000000000ll)
+                           : 20.0 * log10(par->vr / par->eb_abs) + 10.0 * log10(3.0);
+        s.sse = par->sse;
+        s.mse = n ? par->sse / (double)n : 0.0;
+        s.psnr_actual = (s.mse == 0.0) ? __longlong_as_double(0x7ff0000000000000ll)
+                                       : 20.0 * log10(par->vr) - 10.0 * log10(s.mse);
+        s.bytes = total;
+        s.n_outlier = cst ? 0 : par->n_out;
+        s.n_verbatim = cst ? 0 : par->n_vb;
+        s.n_sym = cst ? 0 : par->n_sym;
+        s.xmin = par->xmin;
+        s.xmax = par->xmax;
+        s.flags = flags & ~kFlagError;
+        s.status = par->status;
+        *stats = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launcher
+// ---------------------------------------------------------------------------
+
+#define FP_LAUNCH_CHECK()                                \
+    do {                                                 \
+        if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA; \
+    } while (0)
+
+template <int MODE, int TX, int TY>
+static void launch_pq_t(const fpsnr_plan_s* p, const float* d_in, const PQArgs& a, cudaStream_t st) {
+    dim3 blk(TX / 4, TY);
+    if (p->pq.vec)
+        k_pq<MODE, TX, TY, true><<<p->pq.nblocks, blk, 0, st>>>(d_in, a);
+    else
+        k_pq<MODE, TX, TY, false><<<p->pq.nblocks, blk, 0, st>>>(d_in, a);
+}
+
+static void launch_pq(const fpsnr_plan_s* p, const float* d_in, const PQArgs& a, cudaStream_t st) {
+    const PQGeom& g = p->pq;
+    if (g.mode == 1) {
+        launch_pq_t<1, 512, 1>(p, d_in, a, st);
+    } else if (g.mode == 2) {
+        if (g.tx == 128) launch_pq_t<2, 128, 1>(p, d_in, a, st);
+        else if (g.tx == 256) launch_pq_t<2, 256, 1>(p, d_in, a, st);
+        else launch_pq_t<2, 512, 1>(p, d_in, a, st);
+    } else {
+        launch_pq_t<3, 128, 8>(p, d_in, a, st);
+    }
+}
+
+int launch_compress(fpsnr_plan_s* p, const float* d_in, void* d_out, uint64_t cap,
+                    uint64_t* d_out_bytes, fpsnr_stats* d_stats, cudaStream_t st) {
+    const Workspace& w = p->w;
+    const bool vec_in = ((uintptr_t)d_in & 15u) == 0;
+    {
+    StageScope sc(p->prof, kStRange, st);
+    if (vec_in)
+        k_range_plan<true><<<p->n_range_blocks, 512, 0, st>>>(d_in, p->n, w.par, w.range_part,
+                                                              w.hist, p->nsym, p->eb_rel,
+                                                              p->target_psnr, cap);
+    else
+        k_range_plan<false><<<p->n_range_blocks, 512, 0, st>>>(d_in, p->n, w.par, w.range_part,
+                                                               w.hist, p->nsym, p->eb_rel,
+                                                               p->target_psnr, cap);
+    }
+    FP_LAUNCH_CHECK();
+    if (p->n > 0) {
+        PQArgs a;
+        a.par = w.par;
+        a.codes = w.codes;
+        a.hist = w.hist;
+        a.stage_out = w.stage_out;
+        a.stage_vb = w.stage_vb;
+        a.bm_out = w.bm;
+        a.bm_vb = w.bm + p->nwords;
+        a.sse_part = w.sse_part;
+        a.n = p->n;
+        a.vx = p->pq.vx;
+        a.vy = p->pq.vy;
+        a.vz = p->pq.vz;
+        a.zs = (uint32_t)p->pq.zs;
+        a.nbx = p->pq.nbx;
+        a.nby = p->pq.nby;
+        a.radius = p->radius;
+        PQGeom g = p->pq;
+        fpsnr_plan_s tmp = *p;
+        tmp.pq.vec = g.vec && vec_in;
+        {
+            StageScope sc(p->prof, kStPq, st);
+            launch_pq(&tmp, d_in, a, st);
+        }
+        FP_LAUNCH_CHECK();
+        StageScope sc(p->prof, kStRank, st);
+        k_rank_popc<<<dim3((unsigned)p->nbmblk, 2), 1024, 0, st>>>(w.par, w.bm, w.wpre, w.bpre,
+                                                                 p->nwords, (uint32_t)p->nbmblk);
+        FP_LAUNCH_CHECK();
+    }
+    int rc = launch_codebook(p, d_out, st);
+    if (rc) return rc;
+    uint8_t* out = reinterpret_cast<uint8_t*>(d_out);
+    if (p->n > 0) {
+        const unsigned gchunk = (unsigned)std::min<uint64_t>((p->nchunks + kPackWarps - 1) / kPackWarps,
+                                                             (uint64_t)p->sm_count * 16);
+        StageScope sc(p->prof, kStChunkBits, st);
+        k_chunk_bits<<<gchunk, 256, 0, st>>>(w.par, w.codes, w.enc, w.chunk_off, p->n,
+                                             (uint32_t)p->chunk, p->nchunks);
+        FP_LAUNCH_CHECK();
+    }
+    {
+        StageScope sc(p->prof, kStScanChunks, st);
+        k_scan_chunks<<<1, 1024, 0, st>>>(w.par, w.chunk_off, out, p->nchunks);
+    }
+    FP_LAUNCH_CHECK();
+    if (p->n > 0) {
+        const unsigned gchunk = (unsigned)std::min<uint64_t>((p->nchunks + kPackWarps - 1) / kPackWarps,
+                                                             (uint64_t)p->sm_count * 16);
+        {
+            StageScope sc(p->prof, kStPack, st);
+            k_pack<<<gchunk, kPackWarps * 32, 0, st>>>(w.par, w.codes, w.enc, w.chunk_off, out, p->n,
+                                                   (uint32_t)p->chunk, p->nchunks);
+        }
+        FP_LAUNCH_CHECK();
+        StageScope sc(p->prof, kStEmit, st);
+        k_emit<<<dim3((unsigned)p->sm_count, 2), 256, 0, st>>>(w.par, w.stage_out, w.stage_vb, w.bm,
+                                                             w.wpre, w.bpre, out, p->nwords,
+                                                             (uint32_t)p->nbmblk);
+        FP_LAUNCH_CHECK();
+    }
+    StageScope sc(p->prof, kStFinalize, st);
+    k_finalize<<<(unsigned)p->sm_count, 256, 0, st>>>(
+        w.par, w.bm, w.stage_out, w.stage_vb, out, d_out_bytes, d_stats, p->ndim, p->ld,
+        p->dims[0], p->dims[1], p->dims[2], p->n, p->radius, p->chunk, p->lmax, p->nchunks,
+        p->nwords);
+    FP_LAUNCH_CHECK();
+    return FPSNR_OK;
+}
+
+}  // namespace fp

@@ -1,0 +1,297 @@
+"""Thin ctypes binding of the fpsnr C ABI (include/fpsnr.h).
+
+The functions below carry the C names and only marshal arguments: device
+buffers are passed as integer device pointers (e.g. ``tensor.data_ptr()``),
+streams as integer handles (``torch.cuda.Stream.cuda_stream``).  Every step of
+the method runs in the CUDA library; there is no CPU fallback: ``load()``
+raises if libfpsnr.so has not been built.
+
+``Plan`` is a convenience wrapper over torch tensors (torch supplies device
+memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfpsnr.so")
+
+FPSNR_OK = 0
+FPSNR_EINVAL = -1
+FPSNR_ENOMEM = -2
+FPSNR_ECUDA = -3
+FPSNR_ENONFINITE = -4
+FPSNR_ECAPACITY = -5
+FPSNR_ECORRUPT = -6
+FPSNR_ETIMEOUT = -7
+FPSNR_MAX_PSNR = 180.0
+
+# every function include/fpsnr.h declares
+EXPORTS = ("fpsnr_default_opts", "fpsnr_plan", "fpsnr_plan_set_psnr", "fpsnr_plan_eb_rel",
+           "fpsnr_plan_points", "fpsnr_max_compressed_bytes", "fpsnr_compress",
+           "fpsnr_decompress", "fpsnr_psnr", "fpsnr_plan_codes", "fpsnr_plan_destroy",
+           "fpsnr_strerror", "fpsnr_plan_profile", "fpsnr_plan_profile_read",
+           "fpsnr_stage_name")
+FPSNR_NSTAGES = 16
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FpsnrError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {fpsnr_strerror(code)} ({code})" if what else
+                         f"{fpsnr_strerror(code)} ({code})")
+
+
+class fpsnr_opts(C.Structure):
+    _fields_ = [("radius", C.c_int), ("chunk", C.c_int), ("lmax", C.c_int),
+                ("lorenzo_dims", C.c_int)]
+
+
+class fpsnr_stats(C.Structure):
+    _fields_ = [("target_psnr", C.c_double), ("eb_rel", C.c_double), ("eb_abs", C.c_double),
+                ("vr", C.c_double), ("psnr_model", C.c_double), ("sse", C.c_double),
+                ("mse", C.c_double), ("psnr_actual", C.c_double), ("bytes", C.c_uint64),
+                ("n_outlier", C.c_uint64), ("n_verbatim", C.c_uint64), ("n_sym", C.c_uint64),
+                ("xmin", C.c_float), ("xmax", C.c_float), ("flags", C.c_uint32),
+                ("status", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+STATS_BYTES = C.sizeof(fpsnr_stats)
+
+
+def load(path: str = LIB_PATH):
+    """Load libfpsnr.so (raises if it is missing: build it first)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} not found: run paper_1805_07384_gb300/build.py "
+                               "(or __graft_entry__.build()) first")
+        L = C.CDLL(path)
+        P, U64, D = C.c_void_p, C.c_uint64, C.c_double
+        L.fpsnr_default_opts.argtypes = [C.POINTER(fpsnr_opts)]
+        L.fpsnr_plan.argtypes = [C.POINTER(P), C.c_int, C.POINTER(U64), D, C.POINTER(fpsnr_opts)]
+        L.fpsnr_plan_set_psnr.argtypes = [P, D]
+        L.fpsnr_plan_eb_rel.argtypes = [P]
+        L.fpsnr_plan_eb_rel.restype = D
+        L.fpsnr_plan_points.argtypes = [P]
+        L.fpsnr_plan_points.restype = U64
+        L.fpsnr_max_compressed_bytes.argtypes = [P]
+        L.fpsnr_max_compressed_bytes.restype = U64
+        L.fpsnr_compress.argtypes = [P, P, P, U64, P, P, P]
+        L.fpsnr_decompress.argtypes = [P, P, U64, P, U64, P, P]
+        L.fpsnr_psnr.argtypes = [P, P, U64, C.POINTER(D), C.POINTER(D), C.POINTER(D), P]
+        L.fpsnr_plan_codes.argtypes = [P]
+        L.fpsnr_plan_codes.restype = P
+        L.fpsnr_plan_destroy.argtypes = [P]
+        L.fpsnr_plan_destroy.restype = None
+        L.fpsnr_strerror.argtypes = [C.c_int]
+        L.fpsnr_strerror.restype = C.c_char_p
+        L.fpsnr_plan_profile.argtypes = [P, C.c_int]
+        L.fpsnr_plan_profile_read.argtypes = [P, C.POINTER(D), C.POINTER(U64), C.c_int]
+        L.fpsnr_stage_name.argtypes = [C.c_int]
+        L.fpsnr_stage_name.restype = C.c_char_p
+        _lib = L
+        return L
+
+
+# ---------------------------------------------------------------------------
+# the C functions, same names
+# ---------------------------------------------------------------------------
+
+def fpsnr_default_opts() -> fpsnr_opts:
+    o = fpsnr_opts()
+    load().fpsnr_default_opts(C.byref(o))
+    return o
+
+
+def fpsnr_plan(ndim: int, dims, target_psnr_db: float, opts: fpsnr_opts | None = None):
+    """dims x-fastest; returns the plan handle (int) or raises FpsnrError."""
+    vals = [int(d) for d in dims]
+    vals += [1] * max(0, 3 - len(vals))
+    arr = (C.c_uint64 * len(vals))(*vals)
+    h = C.c_void_p()
+    rc = load().fpsnr_plan(C.byref(h), int(ndim), arr, float(target_psnr_db),
+                           C.byref(opts) if opts is not None else None)
+    if rc:
+        raise FpsnrError(rc, "fpsnr_plan")
+    return h.value
+
+
+def fpsnr_plan_set_psnr(plan, target_psnr_db: float) -> int:
+    return load().fpsnr_plan_set_psnr(plan, float(target_psnr_db))
+
+
+def fpsnr_plan_eb_rel(plan) -> float:
+    return load().fpsnr_plan_eb_rel(plan)
+
+
+def fpsnr_plan_points(plan) -> int:
+    return load().fpsnr_plan_points(plan)
+
+
+def fpsnr_max_compressed_bytes(plan) -> int:
+    return load().fpsnr_max_compressed_bytes(plan)
+
+
+def fpsnr_compress(plan, d_in: int, d_out: int, out_cap: int, d_out_bytes: int = 0,
+                   d_stats: int = 0, stream: int = 0) -> int:
+    return load().fpsnr_compress(plan, d_in, d_out, int(out_cap), d_out_bytes or None,
+                                 d_stats or None, stream or None)
+
+
+def fpsnr_decompress(plan, d_blob: int, blob_bytes: int, d_out: int, n_out: int,
+                     d_status: int = 0, stream: int = 0) -> int:
+    return load().fpsnr_decompress(plan, d_blob, int(blob_bytes), d_out, int(n_out),
+                                   d_status or None, stream or None)
+
+
+def fpsnr_psnr(d_x: int, d_xr: int, n: int, stream: int = 0):
+    """Returns (psnr_db, mse, vr); raises FpsnrError on failure."""
+    p, m, v = C.c_double(), C.c_double(), C.c_double()
+    rc = load().fpsnr_psnr(d_x, d_xr, int(n), C.byref(p), C.byref(m), C.byref(v), stream or None)
+    if rc:
+        raise FpsnrError(rc, "fpsnr_psnr")
+    return p.value, m.value, v.value
+
+
+def fpsnr_plan_codes(plan) -> int:
+    return load().fpsnr_plan_codes(plan)
+
+
+def fpsnr_plan_destroy(plan) -> None:
+    load().fpsnr_plan_destroy(plan)
+
+
+def fpsnr_strerror(code: int) -> str:
+    return load().fpsnr_strerror(int(code)).decode()
+
+
+def fpsnr_plan_profile(plan, enable: bool) -> int:
+    return load().fpsnr_plan_profile(plan, 1 if enable else 0)
+
+
+def fpsnr_plan_profile_read(plan):
+    """{stage name: (milliseconds, launches)} since the last read."""
+    ms = (C.c_double * FPSNR_NSTAGES)()
+    ln = (C.c_uint64 * FPSNR_NSTAGES)()
+    rc = load().fpsnr_plan_profile_read(plan, ms, ln, FPSNR_NSTAGES)
+    if rc:
+        raise FpsnrError(rc, "fpsnr_plan_profile_read")
+    return {fpsnr_stage_name(i): (ms[i], int(ln[i])) for i in range(FPSNR_NSTAGES)}
+
+
+def fpsnr_stage_name(stage: int) -> str:
+    return load().fpsnr_stage_name(int(stage)).decode()
+
+
+# ---------------------------------------------------------------------------
+# torch convenience wrapper
+# ---------------------------------------------------------------------------
+
+def _stream_handle(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def parse_stats(raw) -> dict:
+    """fpsnr_stats from a uint8 tensor/bytes of STATS_BYTES bytes."""
+    b = bytes(raw.cpu().numpy().tobytes()) if hasattr(raw, "cpu") else bytes(raw)
+    return fpsnr_stats.from_buffer_copy(b[:STATS_BYTES]).as_dict()
+
+
+class Plan:
+    """Owns one C plan for fields of one shape (numpy/torch C-order shape)."""
+
+    def __init__(self, shape, target_psnr_db: float, radius: int = 32768, chunk: int = 256,
+                 lmax: int = 27, lorenzo_dims: int = 0):
+        import torch
+        self.shape = tuple(int(s) for s in shape)
+        self.n = int(math.prod(self.shape))
+        o = fpsnr_default_opts()
+        o.radius, o.chunk, o.lmax, o.lorenzo_dims = radius, chunk, lmax, lorenzo_dims
+        self.opts = o
+        self.handle = fpsnr_plan(len(self.shape), list(reversed(self.shape)), target_psnr_db, o)
+        self.target = float(target_psnr_db)
+        self.max_bytes = fpsnr_max_compressed_bytes(self.handle)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def set_psnr(self, target_psnr_db: float) -> None:
+        rc = fpsnr_plan_set_psnr(self.handle, target_psnr_db)
+        if rc:
+            raise FpsnrError(rc, "fpsnr_plan_set_psnr")
+        self.target = float(target_psnr_db)
+
+    def alloc_out(self):
+        import torch
+        return torch.empty(self.max_bytes, dtype=torch.uint8, device=self.device)
+
+    def compress(self, x, out=None, nbytes=None, stats=None, stream=None):
+        """Enqueue compression of x (float32 CUDA tensor of the plan's shape).
+        Returns (out, nbytes, stats) device tensors: nbytes is int64[1] holding
+        the blob size, stats is uint8[STATS_BYTES] (see parse_stats)."""
+        import torch
+        assert x.dtype == torch.float32 and x.is_cuda and x.is_contiguous()
+        assert x.numel() == self.n
+        out = self.alloc_out() if out is None else out
+        nbytes = torch.zeros(1, dtype=torch.int64, device=x.device) if nbytes is None else nbytes
+        stats = torch.zeros(STATS_BYTES, dtype=torch.uint8, device=x.device) if stats is None else stats
+        rc = fpsnr_compress(self.handle, x.data_ptr(), out.data_ptr(), out.numel(),
+                            nbytes.data_ptr(), stats.data_ptr(), _stream_handle(stream))
+        if rc:
+            raise FpsnrError(rc, "fpsnr_compress")
+        return out, nbytes, stats
+
+    def decompress(self, blob, blob_bytes: int, out=None, status=None, stream=None):
+        """Enqueue decompression; returns (float32 tensor of the plan's shape,
+        int32[1] device status)."""
+        import torch
+        out = torch.empty(self.shape, dtype=torch.float32, device=blob.device) if out is None else out
+        status = torch.zeros(1, dtype=torch.int32, device=blob.device) if status is None else status
+        rc = fpsnr_decompress(self.handle, blob.data_ptr(), int(blob_bytes), out.data_ptr(), self.n,
+                              status.data_ptr(), _stream_handle(stream))
+        if rc:
+            raise FpsnrError(rc, "fpsnr_decompress")
+        return out, status
+
+    def codes(self):
+        """Copy of the uint16 symbols of the last compression (int16 tensor)."""
+        import torch
+        ptr = fpsnr_plan_codes(self.handle)
+
+        class _View:
+            pass
+
+        v = _View()
+        v.__cuda_array_interface__ = {"shape": (self.n,), "typestr": "<i2",
+                                      "data": (int(ptr), False), "version": 3}
+        torch.cuda.synchronize()
+        return torch.as_tensor(v, device=self.device).clone()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fpsnr_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def psnr(x, xr, stream=None):
+    """(PSNR dB, MSE, vr) of reconstruction xr against x (CUDA float32 tensors)."""
+    assert x.numel() == xr.numel()
+    return fpsnr_psnr(x.data_ptr(), xr.data_ptr(), x.numel(), _stream_handle(stream))

@@ -98,11 +98,15 @@ def single_2d(n: int = 512, seed: int = 0) -> np.ndarray:
     return rescale(grf((n, n), 3.0, seed), -1.0, 1.0).astype(np.float32)
 
 
-def climate_batch(count: int = 24, ny: int = 1800, nx: int = 3600, seed: int = 1):
+def climate_batch(count: int = 24, ny: int = 1800, nx: int = 3600, seed: int = 1, device=None):
     """ATM-like batch: per field alpha ~ U[2,4], value = offset + scale * g with
     g the GRF rescaled to [-1, 1], scale = 10^U(-3,5), offset = +-10^U(-3,5);
     round(5% of count) fields get a seeded rectangle held at the field minimum.
-    Returns (list of float32 arrays, list of per-field metadata dicts)."""
+    Returns (list of float32 arrays, list of per-field metadata dicts); with
+    `device` the GRFs are drawn with torch there and the fields are float32
+    torch tensors on that device (same recipe, different random stream)."""
+    if device is not None:
+        return _climate_batch_torch(count, ny, nx, seed, device)
     rng = np.random.default_rng(seed)
     n_const = int(round(0.05 * count))
     const_ids = set(rng.choice(count, size=n_const, replace=False).tolist()) if n_const else set()
@@ -124,6 +128,35 @@ def climate_batch(count: int = 24, ny: int = 1800, nx: int = 3600, seed: int = 1
             rect = (y0, x0, h, w)
         fields.append(f.astype(np.float32))
         meta.append(dict(alpha=alpha, scale=scale, offset=offset, seed=fseed, const_rect=rect))
+    return fields, meta
+
+
+def _climate_batch_torch(count, ny, nx, seed, device):
+    import torch
+    rng = np.random.default_rng(seed)
+    n_const = int(round(0.05 * count))
+    const_ids = set(rng.choice(count, size=n_const, replace=False).tolist()) if n_const else set()
+    fields, meta = [], []
+    for i in range(count):
+        alpha = float(rng.uniform(2.0, 4.0))
+        scale = 10.0 ** float(rng.uniform(-3.0, 5.0))
+        offset = (1.0 if rng.uniform() < 0.5 else -1.0) * 10.0 ** float(rng.uniform(-3.0, 5.0))
+        fseed = int(rng.integers(0, 2**31 - 1))
+        g = grf_torch((ny, nx), alpha, fseed, device)
+        gmin, gmax = g.min(), g.max()
+        g = (g - gmin) / (gmax - gmin) * 2.0 - 1.0
+        f = offset + scale * g
+        rect = None
+        if i in const_ids:
+            h = int(rng.integers(ny // 10, ny // 3))
+            w = int(rng.integers(nx // 10, nx // 3))
+            y0 = int(rng.integers(0, ny - h))
+            x0 = int(rng.integers(0, nx - w))
+            f[y0:y0 + h, x0:x0 + w] = f.min()
+            rect = (y0, x0, h, w)
+        fields.append(f.to(torch.float32).contiguous())
+        meta.append(dict(alpha=alpha, scale=scale, offset=offset, seed=fseed, const_rect=rect))
+        del g, f
     return fields, meta
 
 
