@@ -653,6 +653,17 @@ __global__ void __launch_bounds__(256) k_finalize(DevParams* par, uint32_t* bm,
         put32(116, cst ? 0u : par->stream_words);
         put32(120, cst ? 0u : par->n_out);
         put32(124, cst ? 0u : par->n_vb);
+        if (!cst) {
+            // zero the padding that rounds every section up to 16 bytes
+            auto zero = [&](uint64_t from, uint64_t to) {
+                for (uint64_t o = from; o < to; o += 4) *reinterpret_cast<uint32_t*>(h + o) = 0u;
+            };
+            zero(kHeaderBytes + 4ull * par->n_sym, par->off_ct);
+            zero(par->off_ct + 4ull * nchunks, par->off_st);
+            zero(par->off_st + 4ull * par->stream_words, par->off_ou);
+            zero(par->off_ou + 8ull * par->n_out, par->off_vb);
+            zero(par->off_vb + 8ull * par->n_vb, par->total);
+        }
     }
     if (out_bytes) *out_bytes = total;
     if (stats) {

@@ -42,7 +42,7 @@ def grf(shape, alpha: float, seed: int, stretch=None, rng=None) -> np.ndarray:
     k = _kgrid(shape, stretch)
     with np.errstate(divide="ignore"):
         amp = np.where(k > 0, k ** (-alpha / 2.0), 0.0)
-    f = np.fft.irfftn(spec * amp, s=shape)
+    f = np.fft.irfftn(spec * amp, s=shape, axes=list(range(len(shape))))
     f -= f.mean()
     sd = f.std()
     return f / sd if sd > 0 else f
