@@ -150,6 +150,31 @@ int fpsnr_decompress(fpsnr_plan_t plan, const void* d_blob, uint64_t blob_bytes,
 int fpsnr_psnr(const float* d_x, const float* d_xr, uint64_t n, double* h_psnr_db,
                double* h_mse, double* h_vr, void* stream);
 
+/* PSNR of a reconstruction without allocating device memory.  There is no
+ * counterpart in the paper: this entry point exists for callers that cannot
+ * allocate device memory while they run, such as code inside a device memory
+ * allocator's or memory pool's own callback (allocating there would re-enter
+ * the allocator), processes held to a fixed memory budget reserved up front,
+ * and latency-critical service loops that must stay out of the CUDA allocator
+ * (cudaMalloc and cudaFree can synchronize the whole device).
+ * It computes the same quantities as fpsnr_psnr with the same kernel; its
+ * scratch is one fixed 64 KiB device array inside this library, which every
+ * GPU that loads the library holds until the process exits.
+ *   n <= FPSNR_PSNR_STATIC_MAX_POINTS (2^28 points, 1 GiB of float32); a
+ *   larger n returns FPSNR_EINVAL without touching the device.
+ *   Results agree with fpsnr_psnr to rounding of the final FP64 sum (the
+ *   partial sums are combined over a different number of blocks).
+ * The first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array, which keeps the last call's contents; each call clears
+ * the part that must start at zero.  Calls that overlap on the GPU (from two
+ * host threads, or on two streams of one device) race on the array: the
+ * caller must serialize them.  Synchronous, like fpsnr_psnr.
+ * Returns FPSNR_OK, FPSNR_EINVAL, FPSNR_ENONFINITE or FPSNR_ECUDA. */
+#define FPSNR_PSNR_STATIC_MAX_POINTS (1ull << 28)
+int fpsnr_psnr_static(const float* d_x, const float* d_xr, uint64_t n, double* h_psnr_db,
+                      double* h_mse, double* h_vr, void* stream);
+
 /* Device pointer to the uint16 symbol array (n entries) the last
  * fpsnr_compress on this plan produced; valid until the next call on the plan.
  * For inspection and tests. */

@@ -168,6 +168,14 @@ int launch_codebook(fpsnr_plan_s* p, void* d_out, cudaStream_t st);
 int launch_decompress(fpsnr_plan_s* p, const void* d_blob, uint64_t bytes, float* d_out,
                       int* d_status, cudaStream_t st);
 int codebook_smem_bytes();
+// PSNR reduction (psnr.cu): scratch = 16-byte zeroed counter, 32-byte result,
+// then one partial per block.
+int psnr_enqueue(const float* d_x, const float* d_xr, uint64_t n, void* scratch, unsigned blocks,
+                 cudaStream_t st);
+int psnr_finish(const void* h_result, double* psnr_db, double* mse, double* vr, uint64_t n);
+size_t psnr_scratch_bytes_for(unsigned blocks);
+constexpr size_t kPsnrResultOffset = 16;
+constexpr size_t kPsnrResultBytes = 24;
 int codebook_prepare();
 
 // ---- device helpers ----

@@ -105,6 +105,11 @@ __global__ void __launch_bounds__(512) k_psnr(const float* __restrict__ x,
 // Scratch layout: [0] done counter (u32, padded to 16 B), [1] result, then partials.
 static size_t psnr_scratch_bytes(unsigned blocks) { return 16 + 32 + (size_t)blocks * sizeof(PsnrPart); }
 
+size_t psnr_scratch_bytes_for(unsigned blocks) {
+    static_assert(sizeof(PsnrPart) == kPsnrResultBytes, "result layout");
+    return psnr_scratch_bytes(blocks);
+}
+
 int psnr_blocks(uint64_t n, int sm_count) {
     uint64_t want = (n + 512ull * 16 - 1) / (512ull * 16);
     want = std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sm_count * 4));

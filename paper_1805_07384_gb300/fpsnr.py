@@ -34,7 +34,8 @@ EXPORTS = ("fpsnr_default_opts", "fpsnr_plan", "fpsnr_plan_set_psnr", "fpsnr_pla
            "fpsnr_plan_points", "fpsnr_max_compressed_bytes", "fpsnr_compress",
            "fpsnr_decompress", "fpsnr_psnr", "fpsnr_plan_codes", "fpsnr_plan_destroy",
            "fpsnr_strerror", "fpsnr_plan_profile", "fpsnr_plan_profile_read",
-           "fpsnr_stage_name")
+           "fpsnr_stage_name", "fpsnr_psnr_static")
+FPSNR_PSNR_STATIC_MAX_POINTS = 1 << 28
 FPSNR_NSTAGES = 16
 
 _lock = threading.Lock()
@@ -91,6 +92,7 @@ def load(path: str = LIB_PATH):
         L.fpsnr_compress.argtypes = [P, P, P, U64, P, P, P]
         L.fpsnr_decompress.argtypes = [P, P, U64, P, U64, P, P]
         L.fpsnr_psnr.argtypes = [P, P, U64, C.POINTER(D), C.POINTER(D), C.POINTER(D), P]
+        L.fpsnr_psnr_static.argtypes = [P, P, U64, C.POINTER(D), C.POINTER(D), C.POINTER(D), P]
         L.fpsnr_plan_codes.argtypes = [P]
         L.fpsnr_plan_codes.restype = P
         L.fpsnr_plan_destroy.argtypes = [P]
@@ -162,6 +164,16 @@ def fpsnr_psnr(d_x: int, d_xr: int, n: int, stream: int = 0):
     rc = load().fpsnr_psnr(d_x, d_xr, int(n), C.byref(p), C.byref(m), C.byref(v), stream or None)
     if rc:
         raise FpsnrError(rc, "fpsnr_psnr")
+    return p.value, m.value, v.value
+
+
+def fpsnr_psnr_static(d_x: int, d_xr: int, n: int, stream: int = 0):
+    """Allocation-free fpsnr_psnr: returns (psnr_db, mse, vr); raises FpsnrError."""
+    p, m, v = C.c_double(), C.c_double(), C.c_double()
+    rc = load().fpsnr_psnr_static(d_x, d_xr, int(n), C.byref(p), C.byref(m), C.byref(v),
+                                  stream or None)
+    if rc:
+        raise FpsnrError(rc, "fpsnr_psnr_static")
     return p.value, m.value, v.value
 
 
