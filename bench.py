@@ -36,7 +36,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--streams", type=int, default=4)
+    ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--fields", type=int, default=24)
     ap.add_argument("--ny", type=int, default=1800)
     ap.add_argument("--nx", type=int, default=3600)
@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true")
     ap.add_argument("--cpu-workers", type=int, default=0, help="0 = all host cores")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch every call eagerly instead of replaying one CUDA graph per step")
     return ap.parse_args()
 
 
@@ -172,6 +174,7 @@ def workload_config(a, streams):
          "l2": f"inputs {a.fields * a.ny * a.nx * 4 / 1e6:.0f} MB > 129 MB L2, no flush"}
     if streams is not None:
         c["streams"] = streams
+        c["launch"] = "eager" if getattr(a, "no_graph", False) else "one CUDA graph per step"
     return c
 
 
@@ -181,8 +184,8 @@ def workload_config(a, streams):
 
 # algorithmic bytes per launch of each stage (N points, B compressed bytes of one field)
 def stage_bytes(stage, N, B):
-    return {"range_plan": 4 * N, "predict_quantize": 6 * N, "chunk_bits": 2 * N,
-            "pack": 2 * N + B, "decode": B + 4 * N, "scan_x": 8 * N,
+    return {"range_plan": 4 * N, "predict_quantize": 6 * N, "encode": 2 * N + B,
+            "decode": B + 4 * N, "scan_x": 8 * N,
             "scan_final_dequant": 8 * N, "scan_y": 8 * N}.get(stage)
 
 
@@ -231,8 +234,9 @@ def main():
     main_s = torch.cuda.current_stream(dev)
 
     def step(nstreams, h2d=None, d2h=None):
+        cur = torch.cuda.current_stream(dev)
         ev = torch.cuda.Event()
-        ev.record(main_s)
+        ev.record(cur)
         for s in streams[:nstreams]:
             s.wait_event(ev)
         for i in range(F):
@@ -249,21 +253,38 @@ def main():
         for s in streams[:nstreams]:
             e = torch.cuda.Event()
             e.record(s)
-            main_s.wait_event(e)
+            cur.wait_event(e)
+
+    graphs = {}
+
+    def run_step(nstreams, graph, **kw):
+        """One step: a replay of the captured graph, or eager launches."""
+        if not graph:
+            step(nstreams, **kw)
+            return
+        key = (nstreams, "h2d" in kw and kw["h2d"] is not None)
+        if key not in graphs:
+            torch.cuda.synchronize(dev)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                step(nstreams, **kw)
+            torch.cuda.synchronize(dev)
+            graphs[key] = g
+        graphs[key].replay()
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def timed(k, nstreams, **kw):
+    def timed(k, nstreams, graph=False, **kw):
         barrier()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         wall0 = time.perf_counter()
         t0.record(main_s)
         for _ in range(k):
-            step(nstreams, **kw)
+            run_step(nstreams, graph, **kw)
         t1.record(main_s)
         barrier()
         ms = t0.elapsed_time(t1) / k
@@ -273,19 +294,31 @@ def main():
             ms = float(tt.item())
         return ms, (time.perf_counter() - wall0)
 
+    use_graph = not a.no_graph
     for _ in range(max(3, a.warmup)):
         step(S)
+    # kernels one step launches (the same kernels run eagerly or inside the graph)
+    barrier()
+    for p in plans:
+        fpsnr.fpsnr_plan_profile_read(p.handle)
+    step(S)
+    barrier()
+    launches_per_step = 0
+    for p in plans:
+        launches_per_step += sum(v[1] for v in fpsnr.fpsnr_plan_profile_read(p.handle).values())
+    if use_graph:
+        run_step(S, True)  # capture
+        for _ in range(2):
+            run_step(S, True)
     barrier()
     for p in plans:
         fpsnr.fpsnr_plan_profile_read(p.handle)  # reset launch counters
 
     clocks = ClockSampler(local)
     clocks.start()
-    ms, wall = timed(a.steps, S)
+    ms, wall = timed(a.steps, S, graph=use_graph)
     clk = clocks.stop()
-    launches = 0
-    for p in plans:
-        launches += sum(v[1] for v in fpsnr.fpsnr_plan_profile_read(p.handle).values())
+    launches = launches_per_step * a.steps
 
     total_bytes = 4 * N * F
     value = world * total_bytes / (ms / 1e3) / 1e9
@@ -358,7 +391,9 @@ def main():
         d2h = ([torch.empty((a.ny, a.nx), dtype=torch.float32).pin_memory() for _ in range(F)],
                [torch.empty(fpsnr.STATS_BYTES, dtype=torch.uint8).pin_memory() for _ in range(F)])
         step(S, h2d=h2d, d2h=d2h)
-        ms_e, _ = timed(a.steps, S, h2d=h2d, d2h=d2h)
+        if use_graph:
+            run_step(S, True, h2d=h2d, d2h=d2h)
+        ms_e, _ = timed(a.steps, S, graph=use_graph, h2d=h2d, d2h=d2h)
         e2e = {"value": round(world * total_bytes / (ms_e / 1e3) / 1e9, 3), "unit": "GB/s",
                "h2d_bytes_per_step": total_bytes,
                "d2h_bytes_per_step": total_bytes + F * fpsnr.STATS_BYTES,

@@ -37,8 +37,6 @@ void carve(fpsnr_plan_s* p, uint8_t* base, size_t* total) {
     Carver c{base};
     fp::Workspace& w = p->w;
     const uint64_t n = std::max<uint64_t>(p->n, 1);
-    uint64_t pow2 = 2;
-    while (pow2 < p->nsym) pow2 <<= 1;
     w.par = c.take<fp::DevParams>(1);
     w.hist = c.take<uint32_t>(p->nsym);
     w.enc = c.take<uint32_t>(p->nsym);
@@ -52,19 +50,17 @@ void carve(fpsnr_plan_s* p, uint8_t* base, size_t* total) {
     w.bpre = c.take<uint32_t>(2 * std::max<uint64_t>(p->nbmblk, 1));
     w.sse_part = c.take<double>(std::max<uint32_t>(p->pq.nblocks, 1));
     w.range_part = c.take<float>(3 * (uint64_t)p->n_range_blocks);
-    w.hkeys = c.take<unsigned long long>(pow2);
-    w.hseqA = c.take<unsigned long long>(p->nsym);
-    w.hseqB = c.take<unsigned long long>(p->nsym);
-    w.hnew = c.take<unsigned long long>(p->nsym);
-    w.hnode = c.take<unsigned long long>(2ull * p->nsym);
+    w.hlist = c.take<unsigned long long>(p->nsym);
+    w.hbuf1 = c.take<unsigned long long>(p->nsym);
+    w.hbuf2 = c.take<unsigned long long>(p->nsym);
     w.hpar = c.take<uint32_t>(2ull * p->nsym);
-    w.hlw = c.take<uint32_t>(p->nsym);
-    w.hlsym = c.take<uint16_t>(p->nsym);
     w.dlut = c.take<uint32_t>(1u << fp::kLutBits);
     w.dsyms = c.take<uint16_t>(fp::kMaxSym);
     w.lb_flags = c.take<uint32_t>(std::max<uint64_t>(p->lb_tiles_total, 1));
     w.lb_vals = c.take<uint32_t>(2 * std::max<uint64_t>(p->lb_tiles_total, 1) * p->lb_width);
     w.lb_ctr = c.take<uint32_t>(8);
+    w.enc_flags = c.take<uint32_t>(3 * std::max<uint64_t>(p->enc_tiles, 1));
+    w.enc_ctr = c.take<uint32_t>(2);
     *total = (c.off + 255) & ~(size_t)255;
 }
 
@@ -151,8 +147,8 @@ void Profiler::release() {
 extern "C" {
 
 static const char* kStageNames[FPSNR_NSTAGES] = {
-    "range_plan", "predict_quantize", "rank_popc", "codebook", "chunk_bits", "scan_chunks",
-    "pack", "emit", "finalize", "decode_setup", "decode", "scatter", "scan_x", "scan_y",
+    "range_plan", "predict_quantize", "rank_popc", "codebook", "unused4", "unused5",
+    "encode", "emit", "finalize", "decode_setup", "decode", "scatter", "scan_x", "scan_y",
     "scan_final_dequant", "patch"};
 
 const char* fpsnr_stage_name(int stage) {
@@ -247,7 +243,7 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
     p->nchunks = cdiv(n, (uint64_t)o.chunk);
     p->nwords = cdiv(n, 32);
     p->nbmblk = cdiv(p->nwords, 1024);
-    p->epoch = 0;
+    p->enc_tiles = cdiv(p->nchunks, 8);
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
         delete p;
@@ -257,13 +253,13 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
     // predictor geometry
     PQGeom& g = p->pq;
     if (ld == 1) {
-        g.mode = 1; g.tx = 512; g.ty = 1; g.zs = 32;
+        g.mode = 1; g.tx = 512; g.ty = 1; g.zs = 16;
         g.vx = 512; g.vy = 1; g.vz = (uint32_t)std::max<uint64_t>(cdiv(n, 512), 1);
     } else if (ld == 2) {
         const uint64_t nx = d[0], rows = nx ? n / nx : 0;
         g.mode = 2; g.ty = 1;
         g.tx = nx <= 128 ? 128 : (nx <= 256 ? 256 : 512);
-        g.zs = std::max(1, 16384 / g.tx);
+        g.zs = std::max(4, 8192 / g.tx);
         g.vx = (uint32_t)nx; g.vy = 1; g.vz = (uint32_t)rows;
     } else {
         g.mode = 3; g.tx = 128; g.ty = 8; g.zs = 16;
@@ -321,7 +317,10 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
               cudaMemset(w.bm, 0, 2 * std::max<uint64_t>(p->nwords, 1) * 4) == cudaSuccess &&
               cudaMemset(w.lb_flags, 0, std::max<uint64_t>(p->lb_tiles_total, 1) * 4) == cudaSuccess &&
               cudaMemset(w.lb_ctr, 0, 8 * 4) == cudaSuccess &&
-              fp::codebook_prepare() == FPSNR_OK && cudaDeviceSynchronize() == cudaSuccess;
+              cudaMemset(w.enc_flags, 0, 3 * std::max<uint64_t>(p->enc_tiles, 1) * 4) == cudaSuccess &&
+              cudaMemset(w.enc_ctr, 0, 2 * 4) == cudaSuccess &&
+              fp::codebook_prepare() == FPSNR_OK && fp::decode_prepare(p) == FPSNR_OK &&
+              cudaDeviceSynchronize() == cudaSuccess;
     if (!ok) {
         cudaFree(slab);
         delete p;

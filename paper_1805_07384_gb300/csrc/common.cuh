@@ -23,7 +23,7 @@ constexpr uint32_t kFlagError = 1u << 31;  // internal: a device-side error occu
 constexpr int kMaxRadius = 32768;
 constexpr int kMaxSym = 2 * kMaxRadius;
 constexpr int kMaxLmax = 27;
-constexpr int kLutBits = 11;  // decode look-up table width
+constexpr int kLutBits = 12;  // decode look-up table width
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 // Per-call device record.  Written by kernels, read by later kernels.
@@ -37,6 +37,10 @@ struct DevParams {
     uint32_t n_sym;           // Huffman symbols in use
     uint32_t stream_words;
     uint32_t done_range;      // self-resetting last-block counter
+    uint32_t sym_lo, sym_hi;  // smallest / largest nonzero symbol seen by the predictor
+    // look-back epochs, advanced on the device by the first kernel of every
+    // compress / decompress call (so a captured CUDA graph replays correctly)
+    uint32_t enc_epoch, dec_epoch;
     uint64_t cap;             // output capacity of this call
     uint64_t off_cb, off_ct, off_st, off_ou, off_vb, total;
     // decompression: header fields of the blob being decoded
@@ -59,15 +63,11 @@ struct Workspace {
     uint32_t* bpre;         // [2][nbmblk] block totals, then exclusive prefix
     double* sse_part;       // [n_pq_blocks]
     float* range_part;      // [3][n_range_blocks]
-    // Huffman construction scratch (used when the alphabet is too large for shared memory)
-    unsigned long long* hkeys;  // [nsym]
-    unsigned long long* hseqA;  // [nsym]
-    unsigned long long* hseqB;  // [nsym]
-    unsigned long long* hnew;   // [nsym]
-    unsigned long long* hnode;  // [2*nsym]
-    uint32_t* hpar;             // [2*nsym]
-    uint32_t* hlw;              // [nsym] leaf weights
-    uint16_t* hlsym;            // [nsym] leaf symbols
+    // Huffman construction scratch
+    unsigned long long* hlist;  // [nsym] used symbols (count << 16 | symbol), ascending symbol
+    unsigned long long* hbuf1;  // [nsym] sort ping-pong
+    unsigned long long* hbuf2;  // [nsym] sort ping-pong
+    uint32_t* hpar;             // [2*nsym] parent of every node
     // decoding tables
     uint32_t* dlut;  // [1 << kLutBits]
     uint16_t* dsyms; // [kMaxSym]
@@ -75,6 +75,9 @@ struct Workspace {
     uint32_t* lb_flags;  // [n_lb_tiles]
     uint32_t* lb_vals;   // [2][n_lb_tiles * lb_width] aggregate, inclusive
     uint32_t* lb_ctr;    // [8] dynamic tile counters (pairs: counter, done)
+    // encoder look-back state
+    uint32_t* enc_flags; // [3][enc_tiles] flags, tile words, inclusive words
+    uint32_t* enc_ctr;   // [2] tile counter, done counter
 };
 
 // Launch geometry of the predict-quantize kernel.
@@ -104,7 +107,7 @@ struct ScanPass {
 
 namespace fp {
 enum Stage {
-    kStRange = 0, kStPq, kStRank, kStCodebook, kStChunkBits, kStScanChunks, kStPack, kStEmit,
+    kStRange = 0, kStPq, kStRank, kStCodebook, kStUnused4, kStUnused5, kStEncode, kStEmit,
     kStFinalize, kStDsetup, kStDecode, kStScatter, kStScanX, kStScanY, kStScanFinal, kStPatch
 };
 
@@ -138,7 +141,7 @@ struct fpsnr_plan_s {
     int n_passes;
     fp::ScanPass pass[3];
     uint64_t lb_tiles_total, lb_width;
-    uint32_t epoch;
+    uint64_t enc_tiles;
     void* slab;
     size_t slab_bytes;
     fp::Workspace w;
@@ -177,6 +180,8 @@ size_t psnr_scratch_bytes_for(unsigned blocks);
 constexpr size_t kPsnrResultOffset = 16;
 constexpr size_t kPsnrResultBytes = 24;
 int codebook_prepare();
+int decode_prepare(const fpsnr_plan_s* p);
+int decode_smem_bytes(const fpsnr_plan_s* p);
 
 // ---- device helpers ----
 #ifdef __CUDACC__
@@ -271,6 +276,48 @@ __device__ __forceinline__ double block_sum_double(double v, double* sh) {
     return r;
 }
 
+// ---- TMA bulk copies (cp.async.bulk) completing on an mbarrier ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arrive once and announce `bytes` of asynchronous transactions.
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy; dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         unsigned long long* mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* mbar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_u32(mbar)), "r"(phase) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `phase` of an mbarrier; false after the limit.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* mbar, uint32_t phase) {
+    for (uint32_t it = 0; it < kSpinLimit; it++)
+        if (mbar_try_wait(mbar, phase)) return true;
+    return false;
+}
+
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
     uint32_t v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -279,6 +326,48 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
 
 __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Decoupled look-back over tiles [first, t): one warp inspects 32 predecessors
+// per round trip.  Each tile publishes flags[tile] = epoch << 2 | state with
+// state 1 (its own aggregate in agg[tile]) or 2 (inclusive prefix in inc[tile]).
+// Waits (bounded) until every inspected predecessor has published, adds the
+// aggregates of those nearer than the nearest inclusive prefix plus that
+// prefix, and stops there.  Returns the exclusive prefix of tile t in every
+// lane; on a timeout sets FPSNR_ETIMEOUT and returns what it has.
+__device__ __forceinline__ uint32_t warp_lookback(const uint32_t* flags, const uint32_t* agg,
+                                                  const uint32_t* inc, uint32_t t, uint32_t first,
+                                                  uint32_t epoch, DevParams* par) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t carry = 0;
+    int64_t hi = (int64_t)t - 1;
+    while (hi >= (int64_t)first) {
+        const int64_t p = hi - lane;
+        const bool valid = p >= (int64_t)first;
+        uint32_t st = 0;
+        for (uint32_t it = 0;; it++) {
+            if (valid && st == 0) {
+                const uint32_t f = ld_acquire(flags + p);
+                if ((f >> 2) == epoch && (f & 3u)) st = f & 3u;
+            }
+            if (__all_sync(0xffffffffu, !valid || st != 0)) break;
+            if (it >= kSpinLimit) {
+                if (lane == 0) set_error(par, FPSNR_ETIMEOUT);
+                return __shfl_sync(0xffffffffu, carry, 0);
+            }
+            __nanosleep(32);
+        }
+        const uint32_t pmask = __ballot_sync(0xffffffffu, valid && st == 2u);
+        const uint32_t stop = pmask ? (uint32_t)(__ffs(pmask) - 1) : 32u;
+        uint32_t v = 0;
+        if (valid && lane <= stop) v = (st == 2u) ? __ldcg(inc + p) : __ldcg(agg + p);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        carry += v;
+        if (pmask) break;
+        hi -= 32;
+    }
+    return carry;
 }
 
 #endif  // __CUDACC__

@@ -28,7 +28,8 @@ template <bool VEC>
 __global__ void __launch_bounds__(512) k_range_plan(const float* __restrict__ x, uint64_t n,
                                                     DevParams* par, float* part,
                                                     uint32_t* hist, uint32_t nsym,
-                                                    double eb_rel, double target, uint64_t cap) {
+                                                    double eb_rel, double target, uint64_t cap,
+                                                    uint32_t* enc_ctr) {
     const uint32_t tid = threadIdx.x;
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + tid;
     const uint64_t gsz = (uint64_t)gridDim.x * blockDim.x;
@@ -147,6 +148,14 @@ __global__ void __launch_bounds__(512) k_range_plan(const float* __restrict__ x,
     par->off_cb = kHeaderBytes;
     par->off_ct = par->off_st = par->off_ou = par->off_vb = par->total = kHeaderBytes;
     par->done_range = 0;
+    par->sym_lo = 0xffffffffu;
+    par->sym_hi = 0u;
+    // the encoder's tile counters start every call at zero, even after an
+    // earlier call ended in an error that stopped some of its blocks early
+    enc_ctr[0] = 0;
+    enc_ctr[1] = 0;
+    const uint32_t e = (par->enc_epoch + 1) & 0x3fffffffu;
+    par->enc_epoch = e ? e : 1u;
 }
 
 // ---------------------------------------------------------------------------
@@ -209,45 +218,69 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const float* __restrict__ x,
 
     int32_t L2prev[4] = {0, 0, 0, 0};
     FF acc = {0.0f, 0.0f};
+    uint32_t sym_lo = 0xffffffffu, sym_hi = 0u;
     int buf = 0;
     const uint32_t zstart = (MODE != 1 && z0 > 0) ? z0 - 1 : z0;
 
-    for (uint32_t z = zstart; z < z1; z++) {
-        // ---- own row: x values, lattice q, row difference L1 ----
-        float xv[4];
-        int32_t q[4];
-        bool in[4];
-        const uint64_t rowbase = ((uint64_t)z * a.vy + y) * a.vx;
-        const bool rowin = (MODE == 3) ? (y < a.vy) : true;
+    // rows are loaded G at a time ahead of their processing so that several
+    // 16-byte loads per thread are in flight (the walk is otherwise latency bound)
+    constexpr int G = (MODE == 3) ? 1 : 4;
+    for (uint32_t zg = zstart; zg < z1; zg += G) {
+        float xg[G][4];
+        float xlg[G];
+        bool hlg[G];
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            uint64_t gi = rowbase + xb + k;
-            in[k] = rowin && (xb + k < a.vx) && (MODE != 1 || gi < a.n);
-        }
-        if (VEC && in[3]) {
-            float4 v = __ldcs(reinterpret_cast<const float4*>(x + rowbase + xb));
-            xv[0] = v.x; xv[1] = v.y; xv[2] = v.z; xv[3] = v.w;
-        } else {
+        for (int g = 0; g < G; g++) {
+            const uint32_t z = zg + g;
+            const uint64_t rowbase = ((uint64_t)z * a.vy + y) * a.vx;
+            const float* xrow = x + rowbase;
+            const bool rowin = (z < z1) && ((MODE == 3) ? (y < a.vy) : true);
+            const uint64_t rowend = (MODE == 1) ? a.n - min(a.n, rowbase) : 0xffffffffull;
+            bool inb[4];
 #pragma unroll
-            for (int k = 0; k < 4; k++) xv[k] = in[k] ? x[rowbase + xb + k] : 0.0f;
-        }
+            for (int k = 0; k < 4; k++) inb[k] = rowin && (xb + k < a.vx) && (xb + k < rowend);
+            if (VEC && inb[3]) {
+                const float4 v = __ldcs(reinterpret_cast<const float4*>(xrow + xb));
+                xg[g][0] = v.x; xg[g][1] = v.y; xg[g][2] = v.z; xg[g][3] = v.w;
+            } else {
 #pragma unroll
-        for (int k = 0; k < 4; k++) q[k] = in[k] ? prequant(xv[k], xmin, inv, off) : 0;
-        // left neighbour of q[0]
-        int32_t qleft = __shfl_up_sync(0xffffffffu, q[3], 1);
-        if (lane == 0) {
-            // lane 0 of a warp that starts past the row end needs nothing: all its
-            // points and the next lane's are out of the field
-            qleft = 0;
-            if (rowin) {
+                for (int k = 0; k < 4; k++) xg[g][k] = inb[k] ? xrow[xb + k] : 0.0f;
+            }
+            // left neighbour of the lane's first point (lane 0 only; a warp that
+            // starts past the row end needs nothing: its points are out of the field)
+            hlg[g] = false;
+            xlg[g] = 0.0f;
+            if (lane == 0 && rowin) {
                 if (xb > 0) {
-                    if (xb <= a.vx && (MODE != 1 || rowbase + xb - 1 < a.n))
-                        qleft = prequant(x[rowbase + xb - 1], xmin, inv, off);
+                    if (xb <= a.vx && xb - 1 < rowend) {
+                        xlg[g] = xrow[xb - 1];
+                        hlg[g] = true;
+                    }
                 } else if (MODE == 1 && rowbase > 0 && rowbase - 1 < a.n) {
-                    qleft = prequant(x[rowbase - 1], xmin, inv, off);
+                    xlg[g] = x[rowbase - 1];
+                    hlg[g] = true;
                 }
             }
         }
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        const uint32_t z = zg + g;
+        if (z >= z1) break;  // uniform across the block
+        // ---- own row: lattice q, row difference L1 ----
+        const uint64_t rowbase = ((uint64_t)z * a.vy + y) * a.vx;
+        const bool rowin = (MODE == 3) ? (y < a.vy) : true;
+        const uint64_t rowend = (MODE == 1) ? a.n - min(a.n, rowbase) : 0xffffffffull;
+        float xv[4];
+        int32_t q[4];
+        bool in[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            in[k] = rowin && (xb + k < a.vx) && (xb + k < rowend);
+            xv[k] = xg[g][k];
+            q[k] = in[k] ? prequant(xv[k], xmin, inv, off) : 0;
+        }
+        int32_t qleft = __shfl_up_sync(0xffffffffu, q[3], 1);
+        if (lane == 0) qleft = hlg[g] ? prequant(xlg[g], xmin, inv, off) : 0;
         int32_t L1[4];
         L1[0] = q[0] - qleft;
 #pragma unroll
@@ -262,18 +295,18 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const float* __restrict__ x,
                 int32_t h[4] = {0, 0, 0, 0};
                 int32_t hl = 0;
                 if (y0 > 0) {
-                    const uint64_t hb = ((uint64_t)z * a.vy + (y0 - 1)) * a.vx;
+                    const float* hrow = x + ((uint64_t)z * a.vy + (y0 - 1)) * a.vx;
                     float hv[4];
                     if (VEC && xb + 3 < a.vx) {
-                        float4 v = *reinterpret_cast<const float4*>(x + hb + xb);
+                        float4 v = *reinterpret_cast<const float4*>(hrow + xb);
                         hv[0] = v.x; hv[1] = v.y; hv[2] = v.z; hv[3] = v.w;
                     } else {
 #pragma unroll
-                        for (int k = 0; k < 4; k++) hv[k] = (xb + k < a.vx) ? x[hb + xb + k] : 0.0f;
+                        for (int k = 0; k < 4; k++) hv[k] = (xb + k < a.vx) ? hrow[xb + k] : 0.0f;
                     }
 #pragma unroll
                     for (int k = 0; k < 4; k++) h[k] = (xb + k < a.vx) ? prequant(hv[k], xmin, inv, off) : 0;
-                    if (lane == 0 && xb > 0 && xb <= a.vx) hl = prequant(x[hb + xb - 1], xmin, inv, off);
+                    if (lane == 0 && xb > 0 && xb <= a.vx) hl = prequant(hrow[xb - 1], xmin, inv, off);
                 }
                 int32_t hs = __shfl_up_sync(0xffffffffu, h[3], 1);
                 if (lane != 0) hl = hs;
@@ -299,16 +332,20 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const float* __restrict__ x,
                 code[k] = (d[k] > -R && d[k] < R) ? (uint32_t)(d[k] + R) : 0u;
             }
             // symbols
+            uint16_t* crow = a.codes + rowbase;
             if (VEC && in[3]) {
                 uint2 pk;
                 pk.x = code[0] | (code[1] << 16);
                 pk.y = code[2] | (code[3] << 16);
-                *reinterpret_cast<uint2*>(a.codes + rowbase + xb) = pk;
+                *reinterpret_cast<uint2*>(crow + xb) = pk;
             } else {
 #pragma unroll
                 for (int k = 0; k < 4; k++)
-                    if (in[k]) a.codes[rowbase + xb + k] = (uint16_t)code[k];
+                    if (in[k]) crow[xb + k] = (uint16_t)code[k];
             }
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (in[k] && code[k]) { sym_lo = min(sym_lo, code[k]); sym_hi = max(sym_hi, code[k]); }
             // histogram: warp-uniform fast path, else per point
             const bool all4 = in[0] && in[1] && in[2] && in[3] && code[0] == code[1] &&
                               code[1] == code[2] && code[2] == code[3];
@@ -328,41 +365,52 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const float* __restrict__ x,
                     else atomicAdd(&a.hist[code[k]], 1u);
                 }
             }
-            // reconstruction, verbatim test, exact squared error, staging
+            // reconstruction, verbatim test, exact squared error
+            bool vb[4], ol[4];
+            bool rare = false;
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                const uint32_t gi = (uint32_t)(rowbase + xb + k);
-                float xr = __fmaf_rn(__int2float_rn(q[k]), s, xmin);
-                float df = __fsub_rn(xv[k], xr);
-                bool vb = in[k] && !(fabsf(df) <= thr);
-                if (in[k] && !vb) ff_add_sq_diff(acc, xv[k], xr);
-                bool ol = in[k] && code[k] == 0u;
-                uint32_t mo = __ballot_sync(0xffffffffu, ol);
-                if (mo) {
-                    uint32_t leader = __ffs(mo) - 1, base = 0;
-                    if (lane == leader) base = atomicAdd(&par->n_out, __popc(mo));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    if (ol) {
-                        uint32_t slot = base + __popc(mo & lanemask_lt());
-                        a.stage_out[slot] = make_uint2(gi, (uint32_t)d[k]);
-                        atomicOr(&a.bm_out[gi >> 5], 1u << (gi & 31u));
+                const float xr = __fmaf_rn(__int2float_rn(q[k]), s, xmin);
+                const float df = __fsub_rn(xv[k], xr);
+                vb[k] = in[k] && !(fabsf(df) <= thr);
+                ol[k] = in[k] && code[k] == 0u;
+                if (in[k] && !vb[k]) ff_add_sq_diff(acc, xv[k], xr);
+                rare |= vb[k] | ol[k];
+            }
+            // outliers and verbatims are rare: one vote per row decides whether any
+            // lane of the warp needs the order-preserving staging below
+            if (__any_sync(0xffffffffu, rare)) {
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t gi = (uint32_t)rowbase + xb + k;
+                    const uint32_t mo = __ballot_sync(0xffffffffu, ol[k]);
+                    if (mo) {
+                        uint32_t leader = __ffs(mo) - 1, base = 0;
+                        if (lane == leader) base = atomicAdd(&par->n_out, __popc(mo));
+                        base = __shfl_sync(0xffffffffu, base, leader);
+                        if (ol[k]) {
+                            const uint32_t slot = base + __popc(mo & lanemask_lt());
+                            a.stage_out[slot] = make_uint2(gi, (uint32_t)d[k]);
+                            atomicOr(&a.bm_out[gi >> 5], 1u << (gi & 31u));
+                        }
                     }
-                }
-                uint32_t mv = __ballot_sync(0xffffffffu, vb);
-                if (mv) {
-                    uint32_t leader = __ffs(mv) - 1, base = 0;
-                    if (lane == leader) base = atomicAdd(&par->n_vb, __popc(mv));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    if (vb) {
-                        uint32_t slot = base + __popc(mv & lanemask_lt());
-                        a.stage_vb[slot] = make_uint2(gi, __float_as_uint(xv[k]));
-                        atomicOr(&a.bm_vb[gi >> 5], 1u << (gi & 31u));
+                    const uint32_t mv = __ballot_sync(0xffffffffu, vb[k]);
+                    if (mv) {
+                        uint32_t leader = __ffs(mv) - 1, base = 0;
+                        if (lane == leader) base = atomicAdd(&par->n_vb, __popc(mv));
+                        base = __shfl_sync(0xffffffffu, base, leader);
+                        if (vb[k]) {
+                            const uint32_t slot = base + __popc(mv & lanemask_lt());
+                            a.stage_vb[slot] = make_uint2(gi, __float_as_uint(xv[k]));
+                            atomicOr(&a.bm_vb[gi >> 5], 1u << (gi & 31u));
+                        }
                     }
                 }
             }
         }
 #pragma unroll
         for (int k = 0; k < 4; k++) L2prev[k] = L2[k];
+    }
     }
 
     // flush histogram window and squared-error partial
@@ -373,6 +421,15 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const float* __restrict__ x,
     }
     double tot = block_sum_double(ff_to_double(acc), ssum);
     if (tid == 0) a.sse_part[blockIdx.x] = tot;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sym_lo = min(sym_lo, __shfl_xor_sync(0xffffffffu, sym_lo, o));
+        sym_hi = max(sym_hi, __shfl_xor_sync(0xffffffffu, sym_hi, o));
+    }
+    if (lane == 0 && sym_lo <= sym_hi) {
+        atomicMin(&par->sym_lo, sym_lo);
+        atomicMax(&par->sym_hi, sym_hi);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -396,184 +453,195 @@ __global__ void __launch_bounds__(1024) k_rank_popc(const DevParams* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// encoder: bits per chunk, offsets, packing
+// encoder: bits per chunk, offsets, packing -- one fused pass
 // ---------------------------------------------------------------------------
-
-__global__ void __launch_bounds__(256) k_chunk_bits(const DevParams* __restrict__ par,
-                                                    const uint16_t* __restrict__ codes,
-                                                    const uint32_t* __restrict__ enc,
-                                                    uint32_t* chunk_words, uint64_t n,
-                                                    uint32_t chunk, uint64_t nchunks) {
-    if (par->flags & (kFlagConstant | kFlagError)) return;
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t c = warp; c < nchunks; c += nwarps) {
-        const uint64_t beg = c * chunk;
-        const uint64_t end = min(beg + chunk, n);
-        uint32_t bits = 0;
-        // 8 symbols per lane per step (16-byte loads); chunk is a multiple of 32
-        for (uint64_t i = beg + 8u * lane; i < end; i += 256u) {
-            if (i + 8 <= end) {
-                uint4 v = *reinterpret_cast<const uint4*>(codes + i);
-                uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    bits += __ldg(enc + (wv[k] & 0xffffu)) & 31u;
-                    bits += __ldg(enc + (wv[k] >> 16)) & 31u;
-                }
-            } else {
-                for (uint64_t j = i; j < end; j++) bits += __ldg(enc + codes[j]) & 31u;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
-        if (lane == 0) chunk_words[c] = (bits + 31u) >> 5;
-    }
-}
 
 static __device__ __forceinline__ uint64_t pad16(uint64_t b) { return (b + 15u) & ~(uint64_t)15u; }
 
-// Single-block exclusive scan of the chunk word counts -> word offsets; lays
-// out the sections and checks the capacity.
-__global__ void __launch_bounds__(1024) k_scan_chunks(DevParams* par, uint32_t* chunk_off,
-                                                      uint8_t* out, uint64_t nchunks) {
-    if (par->flags & (kFlagConstant | kFlagError)) {
-        if (threadIdx.x == 0 && (par->flags & kFlagConstant)) {
-            par->total = kHeaderBytes;
-            if (par->cap < kHeaderBytes) set_error(par, FPSNR_ECAPACITY);
-        }
-        return;
-    }
-    __shared__ uint32_t sh[33];
-    constexpr int IPT = 8;
-    const uint64_t off_ct = par->off_ct;
-    const bool write_tab = off_ct + 4 * nchunks <= par->cap;
-    uint32_t* tab = reinterpret_cast<uint32_t*>(out + off_ct);
-    uint32_t carry = 0;
-    for (uint64_t base = 0; base < nchunks; base += 1024u * IPT) {
-        uint32_t v[IPT];
-        uint32_t sum = 0;
-        const uint64_t i0 = base + (uint64_t)threadIdx.x * IPT;
+constexpr int kEncWarps = 8;  // chunks per tile, one warp each
+constexpr int kPieceWords = (256 * kMaxLmax + 31) / 32 + 2;
+constexpr uint32_t kEncA = 1u, kEncP = 2u;
+
+struct EncArgs {
+    DevParams* par;
+    const uint16_t* codes;
+    const uint32_t* enc;
+    uint8_t* out;
+    uint64_t n;
+    uint32_t chunk;
+    uint64_t nchunks;
+    uint32_t ntiles;
+    uint32_t* flags;  // [ntiles] look-back flags (epoch << 2 | state)
+    uint32_t* agg;    // [ntiles] words of the tile
+    uint32_t* inc;    // [ntiles] words up to and including the tile
+    uint32_t* ctr;    // [2] tile counter, done counter
+};
+
+// Coded bits of symbols [beg, end) summed over the warp (8 per lane per step).
+__device__ __forceinline__ uint32_t warp_chunk_bits(const uint16_t* __restrict__ codes,
+                                                    const uint32_t* __restrict__ enc, uint64_t beg,
+                                                    uint64_t end, uint32_t lane) {
+    uint32_t bits = 0;
+    for (uint64_t i = beg + 8u * lane; i < end; i += 256u) {
+        if (i + 8 <= end) {
+            const uint4 v = *reinterpret_cast<const uint4*>(codes + i);
+            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int k = 0; k < IPT; k++) {
-            v[k] = (i0 + k < nchunks) ? chunk_off[i0 + k] : 0u;
-            sum += v[k];
-        }
-        uint32_t total;
-        uint32_t ex = block_excl_scan(sum, sh, &total) + carry;
-#pragma unroll
-        for (int k = 0; k < IPT; k++) {
-            if (i0 + k < nchunks) {
-                chunk_off[i0 + k] = ex;
-                if (write_tab) tab[i0 + k] = ex;
+            for (int k = 0; k < 4; k++) {
+                bits += __ldg(enc + (wv[k] & 0xffffu)) & 31u;
+                bits += __ldg(enc + (wv[k] >> 16)) & 31u;
             }
-            ex += v[k];
+        } else {
+            for (uint64_t j = i; j < end; j++) bits += __ldg(enc + codes[j]) & 31u;
         }
-        carry += total;
     }
-    if (threadIdx.x == 0) {
-        par->stream_words = carry;
-        uint64_t off_st = off_ct + pad16(4ull * nchunks);
-        uint64_t off_ou = off_st + pad16(4ull * carry);
-        uint64_t off_vb = off_ou + pad16(8ull * par->n_out);
-        uint64_t total = off_vb + pad16(8ull * par->n_vb);
-        par->off_st = off_st;
-        par->off_ou = off_ou;
-        par->off_vb = off_vb;
-        par->total = total;
-        if (total > par->cap) set_error(par, FPSNR_ECAPACITY);
-    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
+    return bits;
 }
 
-// One warp per chunk.  Pieces of 256 symbols (8 per lane) are packed into a
-// per-warp shared-memory word buffer with atomicOr; full words go to global
-// memory coalesced and the trailing partial word is carried to the next piece.
-constexpr int kPackWarps = 8;
-constexpr int kPieceWords = (256 * kMaxLmax + 31) / 32 + 2;
-
-__global__ void __launch_bounds__(kPackWarps * 32) k_pack(const DevParams* __restrict__ par,
-                                                          const uint16_t* __restrict__ codes,
-                                                          const uint32_t* __restrict__ enc,
-                                                          const uint32_t* __restrict__ chunk_off,
-                                                          uint8_t* out, uint64_t n,
-                                                          uint32_t chunk, uint64_t nchunks) {
-    if (par->flags & (kFlagConstant | kFlagError)) return;
-    __shared__ uint32_t sbuf[kPackWarps][kPieceWords];
-    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-    uint32_t* buf = sbuf[wib];
-    uint32_t* stream = reinterpret_cast<uint32_t*>(out + par->off_st);
-    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t c = warp; c < nchunks; c += nwarps) {
-        const uint64_t beg = c * chunk;
-        const uint64_t end = min(beg + chunk, n);
-        uint32_t wpos = chunk_off[c];  // next word to write
-        uint32_t carry = 0;            // partial word (bits from previous pieces)
-        uint32_t cbits = 0;            // valid bits in carry (< 32)
-        for (uint64_t pb = beg; pb < end; pb += 256u) {
-            // codes of this lane's 8 symbols
-            uint32_t cw[8], cl[8];
-            uint32_t mybits = 0;
-            const uint64_t i = pb + 8u * lane;
-            if (i + 8 <= end) {
-                uint4 v = *reinterpret_cast<const uint4*>(codes + i);
-                uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    uint32_t e0 = __ldg(enc + (wv[k] & 0xffffu));
-                    uint32_t e1 = __ldg(enc + (wv[k] >> 16));
-                    cw[2 * k] = e0 >> 5; cl[2 * k] = e0 & 31u;
-                    cw[2 * k + 1] = e1 >> 5; cl[2 * k + 1] = e1 & 31u;
-                }
+// Each warp sizes its chunk; the tile's chunks get consecutive word offsets
+// from a decoupled look-back over earlier tiles; the warp then packs its chunk
+// MSB-first: pieces of 256 symbols (8 per lane) are OR-ed into a per-warp
+// shared-memory word buffer, full words go out coalesced and the partial last
+// word carries into the next piece.  The last tile lays out the sections and
+// checks the output capacity; every write is also checked against it.
+__global__ void __launch_bounds__(kEncWarps * 32) k_encode(EncArgs a) {
+    DevParams* par = a.par;
+    if (par->flags & (kFlagConstant | kFlagError)) return;  // the whole grid leaves
+    __shared__ uint32_t s_tile, s_carry, s_words[kEncWarps], s_excl[kEncWarps];
+    __shared__ uint32_t sbuf[kEncWarps][kPieceWords];
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, wib = tid >> 5;
+    const uint32_t epoch = par->enc_epoch;
+    if (tid == 0) s_tile = atomicAdd(a.ctr, 1u);
+    __syncthreads();
+    const uint32_t t = s_tile;
+    const uint64_t c = (uint64_t)t * kEncWarps + wib;
+    const uint64_t beg = c * a.chunk;
+    const uint64_t end = min(beg + a.chunk, a.n);
+    const uint32_t bits = (c < a.nchunks) ? warp_chunk_bits(a.codes, a.enc, beg, end, lane) : 0u;
+    if (lane == 0) s_words[wib] = (bits + 31u) >> 5;
+    __syncthreads();
+    const uint64_t cap = par->cap;
+    const uint64_t off_ct = par->off_ct;
+    const uint64_t off_st = off_ct + pad16(4ull * a.nchunks);
+    if (tid < 32) {
+        uint32_t agg = 0;
+        for (int w = 0; w < kEncWarps; w++) agg += s_words[w];
+        if (tid == 0) {
+            uint32_t e = 0;
+            for (int w = 0; w < kEncWarps; w++) {
+                s_excl[w] = e;
+                e += s_words[w];
+            }
+            if (t == 0) {
+                a.inc[0] = agg;
+                __threadfence();
+                st_release(a.flags, (epoch << 2) | kEncP);
             } else {
+                a.agg[t] = agg;
+                __threadfence();
+                st_release(a.flags + t, (epoch << 2) | kEncA);
+            }
+        }
+        const uint32_t carry = (t == 0) ? 0u : warp_lookback(a.flags, a.agg, a.inc, t, 0, epoch, par);
+        if (tid == 0) {
+            if (t > 0) {
+                a.inc[t] = carry + agg;
+                __threadfence();
+                st_release(a.flags + t, (epoch << 2) | kEncP);
+            }
+            s_carry = carry;
+            if (t == a.ntiles - 1) {
+                const uint32_t words = carry + agg;
+                const uint64_t off_ou = off_st + pad16(4ull * words);
+                const uint64_t off_vb = off_ou + pad16(8ull * par->n_out);
+                const uint64_t total = off_vb + pad16(8ull * par->n_vb);
+                par->stream_words = words;
+                par->off_st = off_st;
+                par->off_ou = off_ou;
+                par->off_vb = off_vb;
+                par->total = total;
+                if (total > cap) set_error(par, FPSNR_ECAPACITY);
+            }
+        }
+    }
+    __syncthreads();
+    if (c < a.nchunks) {
+        uint32_t wpos = s_carry + s_excl[wib];  // first word of the chunk
+        const uint32_t nwc = s_words[wib];
+        if (lane == 0 && off_ct + 4ull * (c + 1) <= cap)
+            reinterpret_cast<uint32_t*>(a.out + off_ct)[c] = wpos;
+        if (off_st + 4ull * ((uint64_t)wpos + nwc) <= cap) {
+            uint32_t* stream = reinterpret_cast<uint32_t*>(a.out + off_st);
+            uint32_t* buf = sbuf[wib];
+            uint32_t carry = 0;  // partial word (bits from previous pieces)
+            uint32_t cbits = 0;  // valid bits in carry (< 32)
+            for (uint64_t pb = beg; pb < end; pb += 256u) {
+                uint32_t cw[8], cl[8];
+                uint32_t mybits = 0;
+                const uint64_t i = pb + 8u * lane;
+                if (i + 8 <= end) {
+                    const uint4 v = *reinterpret_cast<const uint4*>(a.codes + i);
+                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const uint32_t e0 = __ldg(a.enc + (wv[k] & 0xffffu));
+                        const uint32_t e1 = __ldg(a.enc + (wv[k] >> 16));
+                        cw[2 * k] = e0 >> 5; cl[2 * k] = e0 & 31u;
+                        cw[2 * k + 1] = e1 >> 5; cl[2 * k + 1] = e1 & 31u;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        const uint32_t e = (i + k < end) ? __ldg(a.enc + a.codes[i + k]) : 0u;
+                        cw[k] = e >> 5; cl[k] = e & 31u;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 8; k++) mybits += cl[k];
+                uint32_t incl = mybits;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= (uint32_t)o) incl += y;
+                }
+                const uint32_t piece_bits = __shfl_sync(0xffffffffu, incl, 31);
+                const uint32_t nw = (cbits + piece_bits + 31u) >> 5;
+                for (uint32_t k = lane; k < nw; k += 32) buf[k] = 0u;
+                __syncwarp();
+                if (lane == 0) buf[0] = carry;
+                __syncwarp();
+                uint32_t bp = cbits + incl - mybits;  // bit position in buf
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
-                    uint32_t e = (i + k < end) ? __ldg(enc + codes[i + k]) : 0u;
-                    cw[k] = e >> 5; cl[k] = e & 31u;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 8; k++) mybits += cl[k];
-            // exclusive prefix of bits across the warp
-            uint32_t incl = mybits;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= (uint32_t)o) incl += y;
-            }
-            const uint32_t piece_bits = __shfl_sync(0xffffffffu, incl, 31);
-            const uint32_t nwords_piece = (cbits + piece_bits + 31u) >> 5;
-            for (uint32_t k = lane; k < nwords_piece; k += 32) buf[k] = 0u;
-            __syncwarp();
-            if (lane == 0) buf[0] = carry;
-            __syncwarp();
-            uint32_t bp = cbits + incl - mybits;  // bit position in buf
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const uint32_t l = cl[k];
-                if (l) {
-                    const uint32_t w = bp >> 5, o = bp & 31u;
-                    if (o + l <= 32u) {
-                        atomicOr(&buf[w], cw[k] << (32u - o - l));
-                    } else {
-                        atomicOr(&buf[w], cw[k] >> (o + l - 32u));
-                        atomicOr(&buf[w + 1], cw[k] << (64u - o - l));
+                    const uint32_t l = cl[k];
+                    if (l) {
+                        const uint32_t w = bp >> 5, o = bp & 31u;
+                        if (o + l <= 32u) {
+                            atomicOr(&buf[w], cw[k] << (32u - o - l));
+                        } else {
+                            atomicOr(&buf[w], cw[k] >> (o + l - 32u));
+                            atomicOr(&buf[w + 1], cw[k] << (64u - o - l));
+                        }
+                        bp += l;
                     }
-                    bp += l;
                 }
+                __syncwarp();
+                const uint32_t tot = cbits + piece_bits;
+                const uint32_t full = tot >> 5;
+                for (uint32_t k = lane; k < full; k += 32) stream[wpos + k] = buf[k];
+                carry = (tot & 31u) ? buf[full] : 0u;
+                cbits = tot & 31u;
+                wpos += full;
+                __syncwarp();
             }
-            __syncwarp();
-            const uint32_t tot = cbits + piece_bits;
-            const uint32_t full = tot >> 5;
-            for (uint32_t k = lane; k < full; k += 32) stream[wpos + k] = buf[k];
-            carry = (tot & 31u) ? buf[full] : 0u;
-            cbits = tot & 31u;
-            wpos += full;
-            __syncwarp();
+            if (cbits && lane == 0) stream[wpos] = carry;
         }
-        if (cbits && lane == 0) stream[wpos] = carry;
-        __syncwarp();
+    }
+    if (tid == 0 && atomicAdd(a.ctr + 1, 1u) == a.ntiles - 1) {
+        a.ctr[0] = 0;
+        a.ctr[1] = 0;
     }
 }
 
@@ -618,7 +686,12 @@ __global__ void __launch_bounds__(256) k_finalize(DevParams* par, uint32_t* bm,
         bm[nwords + (stage_vb[i].x >> 5)] = 0u;
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
 
-    const uint32_t flags = par->flags;
+    uint32_t flags = par->flags;
+    if ((flags & kFlagConstant) && !(flags & kFlagError) && par->cap < kHeaderBytes) {
+        par->status = FPSNR_ECAPACITY;  // even the header does not fit
+        flags |= kFlagError;
+        par->flags = flags;
+    }
     const bool err = (flags & kFlagError) != 0;
     const bool cst = (flags & kFlagConstant) != 0;
     const uint64_t total = err ? 0 : par->total;
@@ -730,11 +803,11 @@ int launch_compress(fpsnr_plan_s* p, const float* d_in, void* d_out, uint64_t ca
     if (vec_in)
         k_range_plan<true><<<p->n_range_blocks, 512, 0, st>>>(d_in, p->n, w.par, w.range_part,
                                                               w.hist, p->nsym, p->eb_rel,
-                                                              p->target_psnr, cap);
+                                                              p->target_psnr, cap, w.enc_ctr);
     else
         k_range_plan<false><<<p->n_range_blocks, 512, 0, st>>>(d_in, p->n, w.par, w.range_part,
                                                                w.hist, p->nsym, p->eb_rel,
-                                                               p->target_psnr, cap);
+                                                               p->target_psnr, cap, w.enc_ctr);
     }
     FP_LAUNCH_CHECK();
     if (p->n > 0) {
@@ -772,25 +845,22 @@ int launch_compress(fpsnr_plan_s* p, const float* d_in, void* d_out, uint64_t ca
     if (rc) return rc;
     uint8_t* out = reinterpret_cast<uint8_t*>(d_out);
     if (p->n > 0) {
-        const unsigned gchunk = (unsigned)std::min<uint64_t>((p->nchunks + kPackWarps - 1) / kPackWarps,
-                                                             (uint64_t)p->sm_count * 16);
-        StageScope sc(p->prof, kStChunkBits, st);
-        k_chunk_bits<<<gchunk, 256, 0, st>>>(w.par, w.codes, w.enc, w.chunk_off, p->n,
-                                             (uint32_t)p->chunk, p->nchunks);
-        FP_LAUNCH_CHECK();
-    }
-    {
-        StageScope sc(p->prof, kStScanChunks, st);
-        k_scan_chunks<<<1, 1024, 0, st>>>(w.par, w.chunk_off, out, p->nchunks);
-    }
-    FP_LAUNCH_CHECK();
-    if (p->n > 0) {
-        const unsigned gchunk = (unsigned)std::min<uint64_t>((p->nchunks + kPackWarps - 1) / kPackWarps,
-                                                             (uint64_t)p->sm_count * 16);
+        EncArgs e;
+        e.par = w.par;
+        e.codes = w.codes;
+        e.enc = w.enc;
+        e.out = out;
+        e.n = p->n;
+        e.chunk = (uint32_t)p->chunk;
+        e.nchunks = p->nchunks;
+        e.ntiles = (uint32_t)((p->nchunks + kEncWarps - 1) / kEncWarps);
+        e.flags = w.enc_flags;
+        e.agg = w.enc_flags + e.ntiles;
+        e.inc = w.enc_flags + 2 * (uint64_t)e.ntiles;
+        e.ctr = w.enc_ctr;
         {
-            StageScope sc(p->prof, kStPack, st);
-            k_pack<<<gchunk, kPackWarps * 32, 0, st>>>(w.par, w.codes, w.enc, w.chunk_off, out, p->n,
-                                                   (uint32_t)p->chunk, p->nchunks);
+            StageScope sc(p->prof, kStEncode, st);
+            k_encode<<<e.ntiles, kEncWarps * 32, 0, st>>>(e);
         }
         FP_LAUNCH_CHECK();
         StageScope sc(p->prof, kStEmit, st);

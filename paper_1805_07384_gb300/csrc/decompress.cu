@@ -34,12 +34,16 @@ __global__ void __launch_bounds__(1024) k_dsetup(DevParams* par, const uint8_t* 
                                                  uint64_t bytes, int ndim, int ld, uint64_t d0,
                                                  uint64_t d1, uint64_t d2, uint64_t n,
                                                  uint32_t chunk, uint64_t nchunks, uint32_t* lut,
-                                                 uint16_t* syms) {
+                                                 uint16_t* syms, uint32_t* lb_ctr) {
     __shared__ int s_ok;
     __shared__ uint32_t s_cnt[32];
     __shared__ unsigned long long s_kraft;
     const uint32_t tid = threadIdx.x;
+    // the scans' tile counters start every call at zero (see k_scan_contig)
+    if (tid < 8) lb_ctr[tid] = 0;
     if (tid == 0) {
+        const uint32_t e = (par->dec_epoch + 1) & 0x3fffffffu;
+        par->dec_epoch = e ? e : 1u;
         int ok = bytes >= kHeaderBytes;
         uint32_t flags = 0, radius = 0, ch = 0, lmax = 0, nsym = 0, nck = 0, words = 0, no = 0, nv = 0;
         if (ok) {
@@ -130,77 +134,161 @@ __global__ void __launch_bounds__(1024) k_dsetup(DevParams* par, const uint8_t* 
         par->d_first_code[0] = 0;
         par->d_first_index[0] = 0;
     }
-    for (uint32_t i = tid; i < (1u << kLutBits); i += blockDim.x) lut[i] = 0u;
     __syncthreads();
     if (par->flags & kFlagError) return;
-    for (uint32_t i = tid; i < nsym; i += blockDim.x) {
-        const uint32_t e = cb[i];
-        const uint32_t l = e >> 16, s = e & 0xffffu;
-        if (l <= (uint32_t)kLutBits) {
-            const uint32_t code = par->d_first_code[l] + (i - par->d_first_index[l]);
-            const uint32_t b0 = code << (kLutBits - l), cnt = 1u << (kLutBits - l);
-            if (code < (1u << l))
-                for (uint32_t j = 0; j < cnt; j++) lut[b0 + j] = (s << 8) | l;
+    // every table entry v (the next kLutBits bits) finds its code length as the
+    // first length whose canonical range ends above v (ranges are contiguous and
+    // ascending); prefixes of longer codes get 0
+    const uint32_t lm = min(lmax, (uint32_t)kLutBits);
+    for (uint32_t v = tid; v < (1u << kLutBits); v += blockDim.x) {
+        const unsigned long long w = (unsigned long long)v << (32 - kLutBits);
+        uint32_t e = 0;
+        for (uint32_t l = 1; l <= lm; l++) {
+            const unsigned long long lje =
+                (unsigned long long)(par->d_first_code[l] + par->d_count[l]) << (32 - l);
+            if (w < lje) {
+                const uint32_t code = v >> (kLutBits - l);
+                const uint32_t k = code - par->d_first_code[l];
+                if (k < par->d_count[l]) e = ((uint32_t)syms[par->d_first_index[l] + k] << 8) | l;
+                break;
+            }
         }
+        lut[v] = e;
     }
 }
 
-// One thread decodes one chunk of `chunk` symbols into int32 residuals.
-__global__ void __launch_bounds__(256) k_decode(DevParams* par, const uint8_t* __restrict__ blob,
-                                                const uint32_t* __restrict__ lut_g,
-                                                const uint16_t* __restrict__ syms,
-                                                int32_t* __restrict__ out, uint64_t n,
-                                                uint32_t chunk, uint64_t nchunks) {
-    __shared__ uint32_t slut[1u << kLutBits];
-    __shared__ uint32_t s_cnt[32], s_fc[32], s_fi[32];
+// One thread decodes one chunk of `chunk` symbols into int32 residuals.  The
+// block's chunks are consecutive, so their words form one contiguous range of
+// the stream: the block copies it into shared memory with coalesced loads and
+// every thread then reads its bits from there.  The serial chain per symbol is
+// one look-up-table read plus a few shifts: the next stream word is fetched
+// into a register ahead of the refill, 8 residuals are decoded into registers
+// and written as two 16-byte stores into the thread's own chunk.  Codes longer
+// than the table are located by comparing the left-justified window with the
+// end of each length's canonical range.
+constexpr int kDecThreads = 64;
+constexpr int kMaxDynSmem = 227 * 1024;
+
+// STAGED = false (chunks too large for the window to fit shared memory): the
+// words are read from global memory directly.
+template <bool STAGED>
+__global__ void __launch_bounds__(kDecThreads) k_decode(DevParams* par, const uint8_t* __restrict__ blob,
+                                                        const uint32_t* __restrict__ lut_g,
+                                                        const uint16_t* __restrict__ syms,
+                                                        int32_t* __restrict__ out, uint64_t n,
+                                                        uint32_t chunk, uint64_t nchunks,
+                                                        uint32_t win_cap) {
+    extern __shared__ __align__(16) uint32_t dsw[];
+    uint32_t* slut = dsw;                   // 1 << kLutBits entries
+    uint32_t* sw = dsw + (1u << kLutBits);  // the block's stream words (from a 16-byte boundary)
+    __shared__ uint32_t s_fc[32], s_fi[32];
+    __shared__ unsigned long long s_lje[33];
+    __shared__ uint32_t s_ws, s_we, s_bad;
+    __shared__ __align__(8) unsigned long long s_mbar;
     const uint32_t flags = par->flags;
     if (flags & kFlagError) return;
     const bool cst = (flags & kFlagConstant) != 0;
-    if (!cst) {
-        for (uint32_t i = threadIdx.x; i < (1u << kLutBits); i += blockDim.x) slut[i] = lut_g[i];
-        if (threadIdx.x < 32) {
-            s_cnt[threadIdx.x] = par->d_count[threadIdx.x];
-            s_fc[threadIdx.x] = par->d_first_code[threadIdx.x];
-            s_fi[threadIdx.x] = par->d_first_index[threadIdx.x];
-        }
-    }
-    __syncthreads();
-    const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nchunks) return;
-    const uint64_t beg = c * chunk;
-    const uint64_t end = min(beg + chunk, n);
+    const uint64_t cb0 = (uint64_t)blockIdx.x * kDecThreads;
+    const uint64_t c = cb0 + threadIdx.x;
+    const uint64_t cb1 = min(cb0 + kDecThreads, nchunks);
     if (cst) {
-        for (uint64_t i = beg; i < end; i++) out[i] = 0;
+        if (c < nchunks) {
+            const uint64_t beg = c * chunk, end = min(beg + chunk, n);
+            for (uint64_t i = beg; i < end; i++) out[i] = 0;
+        }
         return;
     }
-    const uint32_t R = par->d_radius, lmax = par->d_lmax, words = par->d_words;
+    const uint32_t words = par->d_words;
     const uint32_t* tab = reinterpret_cast<const uint32_t*>(blob + par->off_ct);
     const uint32_t* stream = reinterpret_cast<const uint32_t*>(blob + par->off_st);
+    if (threadIdx.x < 32) {
+        const uint32_t l = threadIdx.x;
+        s_fc[l] = par->d_first_code[l];
+        s_fi[l] = par->d_first_index[l];
+        // end of length l's codes, left-justified in 32 bits (2^32 once the code is complete)
+        s_lje[l] = l ? (unsigned long long)(par->d_first_code[l] + par->d_count[l]) << (32 - l) : 0ull;
+    }
+    if (threadIdx.x == 0) {
+        s_lje[32] = ~0ull;
+        const uint32_t ws = tab[cb0];
+        const uint32_t we = (cb1 < nchunks) ? tab[cb1] : words;
+        // a non-monotone table or an oversized chunk cannot come from the encoder
+        const bool bad = ws > we || we > words || (STAGED && we - ws > win_cap);
+        if (bad) set_error(par, FPSNR_ECORRUPT);
+        s_bad = bad;
+        s_ws = bad ? 0 : ws;
+        s_we = bad ? 0 : we;
+        mbar_init(&s_mbar, 1);
+    }
+    __syncthreads();
+    if (s_bad) return;
+    const uint32_t ws = s_ws, we = s_we;
+    // the look-up table and the 16-byte aligned cover of the window arrive by two
+    // bulk copies (the stream section is padded to 16 bytes, so the cover stays in it)
+    const uint32_t ws_al = ws & ~3u;
+    const uint32_t win_bytes = STAGED ? (((we + 3u) & ~3u) - ws_al) * 4u : 0u;
+    if (threadIdx.x == 0) {
+        const uint32_t lut_bytes = (1u << kLutBits) * 4u;
+        mbar_arrive_expect_tx(&s_mbar, lut_bytes + win_bytes);
+        bulk_g2s(slut, lut_g, lut_bytes, &s_mbar);
+        if (win_bytes) bulk_g2s(sw, stream + ws_al, win_bytes, &s_mbar);
+    }
+    if (!mbar_wait_bounded(&s_mbar, 0)) {
+        // never expected; record it, let the copies land, then leave
+        set_error(par, FPSNR_ETIMEOUT);
+        mbar_wait_bounded(&s_mbar, 0);
+        return;
+    }
+    if (c >= nchunks) return;
+    const uint64_t beg = c * chunk;
+    const uint32_t cnt = (uint32_t)(min(beg + chunk, n) - beg);
+    const int32_t R = (int32_t)par->d_radius;
+    const uint32_t lmax = par->d_lmax;
     const uint32_t w0 = tab[c];
     const uint32_t w1 = (c + 1 < nchunks) ? tab[c + 1] : words;
-    if (w0 > w1 || w1 > words) { set_error(par, FPSNR_ECORRUPT); return; }
+    if (w0 > w1 || w0 < ws || w1 > we) { set_error(par, FPSNR_ECORRUPT); return; }
+    auto word = [&](uint32_t k) -> uint32_t { return STAGED ? sw[k - ws_al] : __ldg(stream + k); };
     uint64_t buf = 0;
     uint32_t nb = 0, wi = w0;
-    for (uint64_t i = beg; i < end; i++) {
-        while (nb <= 32 && wi < w1) {
-            buf |= (uint64_t)__ldg(stream + wi) << (32 - nb);
-            wi++;
+    uint32_t nxt = wi < w1 ? word(wi) : 0u;
+    bool bad = false;
+    // decodes one residual; sets `bad` on a malformed stream
+    auto one = [&]() -> int32_t {
+        if (nb <= 32 && wi < w1) {
+            buf |= (uint64_t)nxt << (32 - nb);
             nb += 32;
+            wi++;
+            nxt = wi < w1 ? word(wi) : 0u;
         }
         const uint32_t e = slut[(uint32_t)(buf >> (64 - kLutBits))];
         uint32_t l = e & 0xffu, sym = e >> 8;
         if (l == 0) {
-            for (l = kLutBits + 1; l <= lmax; l++) {
-                const uint32_t code = (uint32_t)(buf >> (64 - l));
-                const uint32_t k = code - s_fc[l];
-                if (k < s_cnt[l]) { sym = syms[s_fi[l] + k]; break; }
-            }
-            if (l > lmax) { set_error(par, FPSNR_ECORRUPT); return; }
+            const uint32_t w32 = (uint32_t)(buf >> 32);
+            l = kLutBits + 1;
+            while (l <= lmax && (unsigned long long)w32 >= s_lje[l]) l++;
+            if (l > lmax) { bad = true; l = 0; sym = 0; }
+            else sym = syms[s_fi[l] + ((w32 >> (32 - l)) - s_fc[l])];
         }
-        if (l > nb) { set_error(par, FPSNR_ECORRUPT); return; }
+        if (l > nb) { bad = true; l = 0; }
         buf <<= l;
         nb -= l;
-        out[i] = sym ? (int32_t)sym - (int32_t)R : 0;
+        return sym ? (int32_t)sym - R : 0;
+    };
+    int32_t* dst = out + beg;
+    const uint32_t cnt8 = cnt & ~7u;
+    for (uint32_t i = 0; i < cnt8; i += 8) {
+        int32_t o[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) o[k] = one();
+        if (bad) { set_error(par, FPSNR_ECORRUPT); return; }
+        int4* d4 = reinterpret_cast<int4*>(dst + i);
+        d4[0] = make_int4(o[0], o[1], o[2], o[3]);
+        d4[1] = make_int4(o[4], o[5], o[6], o[7]);
+    }
+    for (uint32_t i = cnt8; i < cnt; i++) {
+        const int32_t v = one();
+        if (bad) { set_error(par, FPSNR_ECORRUPT); return; }
+        dst[i] = v;
     }
 }
 
@@ -236,19 +324,6 @@ __global__ void k_status(const DevParams* par, int* status) { *status = par->sta
 
 constexpr uint32_t kStA = 1u, kStP = 2u;
 
-// Waits (bounded) for tile `p` of this epoch to publish; returns its state
-// (kStA or kStP), or 0 after a timeout (the tile then counts as zero).
-__device__ __forceinline__ uint32_t wait_flag(const uint32_t* flags, uint64_t p, uint32_t epoch,
-                                              DevParams* par) {
-    for (uint32_t it = 0; it < kSpinLimit; it++) {
-        const uint32_t f = ld_acquire(flags + p);
-        if ((f >> 2) == epoch && (f & 3u)) return f & 3u;
-        __nanosleep(64);
-    }
-    set_error(par, FPSNR_ETIMEOUT);
-    return 0;
-}
-
 struct ScanArgs {
     DevParams* par;
     uint32_t* data;
@@ -260,7 +335,6 @@ struct ScanArgs {
     uint32_t* agg;          // [tiles * width]
     uint32_t* inc;          // [tiles * width]
     uint32_t* ctr;          // [2]: tile counter, done counter
-    uint32_t epoch;
 };
 
 __device__ __forceinline__ void tile_done(uint32_t* ctr, uint32_t tiles) {
@@ -276,6 +350,7 @@ __global__ void __launch_bounds__(256) k_scan_contig(ScanArgs a) {
     __shared__ uint32_t sh[33];
     __shared__ uint32_t s_id, s_carry;
     const uint32_t tid = threadIdx.x;
+    const uint32_t epoch = a.par->dec_epoch;
     if (tid == 0) s_id = atomicAdd(a.ctr, 1u);
     __syncthreads();
     const uint32_t id = s_id;
@@ -300,28 +375,22 @@ __global__ void __launch_bounds__(256) k_scan_contig(ScanArgs a) {
     const uint32_t ex = block_excl_scan(v[IPT - 1], sh, &agg);
     uint32_t carry = 0;
     if (a.tpr > 1) {
-        if (tid == 0) {
-            if (t == 0) {
-                a.inc[id] = agg;
+        if (tid < 32) {
+            if (tid == 0) {
+                if (t == 0) a.inc[id] = agg;
+                else a.agg[id] = agg;
                 __threadfence();
-                st_release(a.flags + id, (a.epoch << 2) | kStP);
-            } else {
-                a.agg[id] = agg;
-                __threadfence();
-                st_release(a.flags + id, (a.epoch << 2) | kStA);
-                uint64_t p = id - 1;
-                for (;;) {
-                    const uint32_t st = wait_flag(a.flags, p, a.epoch, a.par);
-                    if (st == kStP) { carry += __ldcg(a.inc + p); break; }
-                    if (st == 0) break;
-                    carry += __ldcg(a.agg + p);
-                    p--;
-                }
-                a.inc[id] = carry + agg;
-                __threadfence();
-                st_release(a.flags + id, (a.epoch << 2) | kStP);
+                st_release(a.flags + id, (epoch << 2) | (t == 0 ? kStP : kStA));
             }
-            s_carry = carry;
+            if (t > 0) {
+                carry = warp_lookback(a.flags, a.agg, a.inc, id, id - t, epoch, a.par);
+                if (tid == 0) {
+                    a.inc[id] = carry + agg;
+                    __threadfence();
+                    st_release(a.flags + id, (epoch << 2) | kStP);
+                }
+            }
+            if (tid == 0) s_carry = carry;
         }
         __syncthreads();
         carry = s_carry;
@@ -365,6 +434,7 @@ __global__ void __launch_bounds__(256) k_scan_strided(ScanArgs a) {
     constexpr uint32_t TB = 256u * CPT;
     __shared__ uint32_t s_id, s_st;
     const uint32_t tid = threadIdx.x;
+    const uint32_t epoch = a.par->dec_epoch;
     if (tid == 0) s_id = atomicAdd(a.ctr, 1u);
     __syncthreads();
     const uint32_t id = s_id;
@@ -405,33 +475,62 @@ __global__ void __launch_bounds__(256) k_scan_strided(ScanArgs a) {
         for (int k = 0; k < CPT; k++) a.inc[vb + k] = v[SEG - 1][k];
         __threadfence();
         __syncthreads();
-        if (tid == 0) st_release(a.flags + id, (a.epoch << 2) | kStP);
+        if (tid == 0) st_release(a.flags + id, (epoch << 2) | kStP);
     } else {
 #pragma unroll
         for (int k = 0; k < CPT; k++) a.agg[vb + k] = v[SEG - 1][k];
         __threadfence();
         __syncthreads();
-        if (tid == 0) st_release(a.flags + id, (a.epoch << 2) | kStA);
+        if (tid == 0) st_release(a.flags + id, (epoch << 2) | kStA);
+        // warp 0 inspects up to 32 earlier segments of this column strip per round
+        // trip; every thread then adds their vectors up to the nearest inclusive one
         const uint32_t step = a.nbt * a.A;
-        uint64_t p = id;
+        int64_t shi = (int64_t)seg - 1;
         for (;;) {
-            p -= step;
-            if (tid == 0) s_st = wait_flag(a.flags, p, a.epoch, a.par);
+            if (tid < 32) {
+                const int64_t sp = shi - tid;
+                const bool valid = sp >= 0;
+                const uint64_t pt = valid ? (uint64_t)id - (uint64_t)(seg - sp) * step : 0;
+                uint32_t st = 0;
+                bool timeout = false;
+                for (uint32_t it = 0;; it++) {
+                    if (valid && st == 0) {
+                        const uint32_t f = ld_acquire(a.flags + pt);
+                        if ((f >> 2) == epoch && (f & 3u)) st = f & 3u;
+                    }
+                    if (__all_sync(0xffffffffu, !valid || st != 0)) break;
+                    if (it >= kSpinLimit) { timeout = true; break; }
+                    __nanosleep(32);
+                }
+                const uint32_t pmask = __ballot_sync(0xffffffffu, valid && st == kStP);
+                const uint32_t nvalid = __popc(__ballot_sync(0xffffffffu, valid));
+                if (tid == 0) {
+                    if (timeout) set_error(a.par, FPSNR_ETIMEOUT);
+                    // number of segments to add, and whether the last one is inclusive
+                    s_st = timeout ? 0u : (pmask ? ((uint32_t)__ffs(pmask) | 0x80000000u) : nvalid);
+                }
+            }
             __syncthreads();
-            const uint32_t st = s_st;
+            const uint32_t code = s_st;
             __syncthreads();
-            if (st == 0) break;
-            const uint32_t* src = (st == kStP) ? a.inc : a.agg;
-            const uint64_t pb = p * TB + tid * CPT;
+            const uint32_t cnt = code & 0x7fffffffu;
+            for (uint32_t j = 0; j < cnt; j++) {
+                const uint64_t pt = (uint64_t)id - (uint64_t)(seg - (shi - (int64_t)j)) * step;
+                const bool last_inc = (code & 0x80000000u) && j + 1 == cnt;
+                const uint32_t* src = last_inc ? a.inc : a.agg;
+                const uint64_t pb = pt * TB + tid * CPT;
 #pragma unroll
-            for (int k = 0; k < CPT; k++) carry[k] += __ldcg(src + pb + k);
-            if (st == kStP) break;
+                for (int k = 0; k < CPT; k++) carry[k] += __ldcg(src + pb + k);
+            }
+            if (code == 0u || (code & 0x80000000u)) break;
+            shi -= 32;
+            if (shi < 0) break;
         }
 #pragma unroll
         for (int k = 0; k < CPT; k++) a.inc[vb + k] = carry[k] + v[SEG - 1][k];
         __threadfence();
         __syncthreads();
-        if (tid == 0) st_release(a.flags + id, (a.epoch << 2) | kStP);
+        if (tid == 0) st_release(a.flags + id, (epoch << 2) | kStP);
     }
     const DevParams* par = a.par;
     const float s = par->s, xmin = par->xmin;
@@ -483,6 +582,24 @@ static void launch_contig(const ScanArgs& a, int ipt, bool vec, cudaStream_t st)
     else launch_contig_t<16, FINAL>(a, vec, st);
 }
 
+// Words of the largest stream window one decode block can need: every chunk
+// holds at most ceil(chunk * lmax / 32) words.
+uint32_t decode_window_words(const fpsnr_plan_s* p) {
+    return (uint32_t)(kDecThreads * (((uint64_t)p->chunk * p->lmax + 31) / 32));
+}
+
+// LUT + window + 3 words for rounding the window's start down to 16 bytes and
+// 3 for rounding its end up
+int decode_smem_bytes(const fpsnr_plan_s* p) {
+    return (int)(((1u << kLutBits) + decode_window_words(p) + 8) * 4);
+}
+
+int decode_prepare(const fpsnr_plan_s* p) {
+    if (decode_smem_bytes(p) > kMaxDynSmem) return FPSNR_OK;  // the unstaged kernel needs 8 KB
+    return cudaFuncSetAttribute(k_decode<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                decode_smem_bytes(p)) == cudaSuccess ? FPSNR_OK : FPSNR_ECUDA;
+}
+
 int launch_decompress(fpsnr_plan_s* p, const void* d_blob, uint64_t bytes, float* d_out,
                       int* d_status, cudaStream_t st) {
     const Workspace& w = p->w;
@@ -490,24 +607,28 @@ int launch_decompress(fpsnr_plan_s* p, const void* d_blob, uint64_t bytes, float
     {
     StageScope sc(p->prof, kStDsetup, st);
     k_dsetup<<<1, 1024, 0, st>>>(w.par, blob, bytes, p->ndim, p->ld, p->dims[0], p->dims[1],
-                                 p->dims[2], p->n, (uint32_t)p->chunk, p->nchunks, w.dlut, w.dsyms);
+                                 p->dims[2], p->n, (uint32_t)p->chunk, p->nchunks, w.dlut, w.dsyms,
+                                 w.lb_ctr);
     }
     if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
     if (p->n > 0) {
         int32_t* out = reinterpret_cast<int32_t*>(d_out);
-        const unsigned gdec = (unsigned)((p->nchunks + 255) / 256);
+        const unsigned gdec = (unsigned)((p->nchunks + kDecThreads - 1) / kDecThreads);
         {
         StageScope sc(p->prof, kStDecode, st);
-        k_decode<<<gdec, 256, 0, st>>>(w.par, blob, w.dlut, w.dsyms, out, p->n, (uint32_t)p->chunk,
-                                       p->nchunks);
+        if (decode_smem_bytes(p) <= kMaxDynSmem)
+            k_decode<true><<<gdec, kDecThreads, decode_smem_bytes(p), st>>>(
+                w.par, blob, w.dlut, w.dsyms, out, p->n, (uint32_t)p->chunk, p->nchunks,
+                decode_window_words(p));
+        else
+            k_decode<false><<<gdec, kDecThreads, (1u << kLutBits) * 4, st>>>(
+                w.par, blob, w.dlut, w.dsyms, out, p->n, (uint32_t)p->chunk, p->nchunks, 0u);
         }
         {
         StageScope sc(p->prof, kStScatter, st);
         k_scatter<<<(unsigned)p->sm_count, 256, 0, st>>>(w.par, blob, out, p->n);
         }
         if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
-        p->epoch = (p->epoch + 1) & 0x3fffffffu;
-        if (p->epoch == 0) p->epoch = 1;
         for (int i = 0; i < p->n_passes; i++) {
             const ScanPass& sp = p->pass[i];
             ScanArgs a;
@@ -521,7 +642,6 @@ int launch_decompress(fpsnr_plan_s* p, const void* d_blob, uint64_t bytes, float
             a.agg = w.lb_vals + sp.val_off * p->lb_width;
             a.inc = w.lb_vals + (p->lb_tiles_total + sp.val_off) * p->lb_width;
             a.ctr = w.lb_ctr + 2 * sp.ctr_slot;
-            a.epoch = p->epoch;
             StageScope sc(p->prof, sp.final_pass ? kStScanFinal : (i == 0 ? kStScanX : kStScanY), st);
             if (sp.kind == 0) {
                 a.tpr = (sp.L + 256u * sp.ipt - 1) / (256u * sp.ipt);

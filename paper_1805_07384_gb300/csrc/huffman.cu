@@ -9,20 +9,28 @@
 // assigned in ascending (length, symbol) order.  The paper leaves these
 // choices open; the library fixes them so the bytes are deterministic.
 //
-// Parallel construction ("bulk merge"): with the available nodes kept in one
-// sequence ordered as the two-queue algorithm would take them, the sequential
-// algorithm pairs (a0,a1), (a2,a3), ... for as long as the next pair's second
-// node does not weigh more than a0 + a1 (every new node weighs at least that
-// and is queued behind every older node of equal weight).  All those pairs are
-// merged at once, and the new nodes are merged back into the sequence with a
-// merge path (old node first on equal weight).  The smallest pair sum grows by
-// at least 1.5x per round, so there are O(log n) rounds.  Depths come from
-// pointer jumping on the parent links.
+// Parallel construction ("bulk rounds" over the two queues): the sequence in
+// which the sequential algorithm takes nodes is the merge of the sorted leaf
+// queue and the internal-node queue (leaf first on equal weight).  It pairs
+// the 1st and 2nd node, the 3rd and 4th, ... for as long as the next node
+// does not weigh more than w1 = (1st + 2nd): every new node weighs at least w1
+// and queues behind every older node of equal weight.  One round pairs all of
+// those at once; w1 grows by at least 1.5x per round, so there are O(log n)
+// rounds.  Internal nodes are identified by creation order, so the internal
+// queue only stores weights.  Depths follow from one pass over the rounds in
+// reverse (a parent is always created in a later round than its children).
+//
+// Sorting: used symbols are collected in ascending symbol order; a stable sort
+// by count then gives the (count, symbol) leaf order, and a stable sort by
+// code length gives the canonical order.  Small alphabets use a rank sort,
+// larger ones a stable LSD radix sort with one warp per contiguous segment.
 #include "common.cuh"
 
 namespace fp {
 
-constexpr int kSmemLeaves = 4096;  // alphabets up to this many used symbols stay in shared memory
+constexpr uint32_t kRankMax = 1024;     // rank sort up to this many items
+constexpr uint32_t kSmemQueue = 32768;  // internal-node queue in shared memory up to n leaves
+constexpr int kMaxRounds = 128;         // w1 grows 1.5x per round: <= 55 rounds for 2^32 points
 
 struct CBArgs {
     DevParams* par;
@@ -35,51 +43,114 @@ struct CBArgs {
     uint32_t n_sse;
     uint32_t* bpre;
     uint32_t nbmblk;
-    unsigned long long* gkeys;
-    unsigned long long* gA;
-    unsigned long long* gB;
-    unsigned long long* gN;
-    unsigned long long* gnode;
-    uint32_t* gpar;
-    uint32_t* glw;
-    uint16_t* glsym;
+    unsigned long long* list;
+    unsigned long long* buf1;
+    unsigned long long* buf2;
+    uint32_t* parent;
     uint8_t* out;
 };
 
-int codebook_smem_bytes() {
-    // keys | A (node aliases keys+A) | B | N | par | lw | lsym
-    return kSmemLeaves * 8 * 2 + kSmemLeaves * 8 + kSmemLeaves * 4 + kSmemLeaves * 2 * 4 +
-           kSmemLeaves * 4 + kSmemLeaves * 2;
+// dynamic shared memory: internal queue (u32 weights) | internal-node depths (u8)
+int codebook_smem_bytes() { return (int)(kSmemQueue * 4 + kMaxSym); }
+
+__device__ __forceinline__ uint32_t key_w(unsigned long long k) { return (uint32_t)(k >> 16); }
+
+// Rank sort of n <= kRankMax distinct keys: out[rank] = key.  kbuf: n u64 of smem.
+__device__ void rank_sort(const unsigned long long* in, unsigned long long* out, uint32_t n,
+                          unsigned long long* kbuf) {
+    const uint32_t tid = threadIdx.x;
+    if (tid < n) kbuf[tid] = in[tid];
+    __syncthreads();
+    if (tid < n) {
+        const unsigned long long k = kbuf[tid];
+        uint32_t r = 0;
+        for (uint32_t j = 0; j < n; j++) r += kbuf[j] < k;
+        out[r] = k;
+    }
+    __syncthreads();
 }
 
-__device__ __forceinline__ uint32_t wgt(unsigned long long v) { return (uint32_t)(v >> 32); }
-
-__device__ void bitonic_sort(unsigned long long* K, uint32_t P) {
-    for (uint32_t k = 2; k <= P; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-                uint32_t ixj = i ^ j;
-                if (ixj > i) {
-                    unsigned long long x = K[i], y = K[ixj];
-                    bool up = (i & k) == 0;
-                    if ((x > y) == up) { K[i] = y; K[ixj] = x; }
-                }
-            }
-            __syncthreads();
-        }
+// One stable LSD radix pass on digit (key >> shift) & mask (mask < 256): each
+// warp owns a contiguous segment; per-warp digit counts are scanned in
+// (digit, warp) order; within a group of 32 keys, equal digits are ranked by
+// lane.  whist: 32 x 256 u32 of smem.  Block of 1024 threads.
+__device__ void radix_pass(const unsigned long long* in, unsigned long long* out, uint32_t n,
+                           int shift, uint32_t mask, uint32_t* whist, uint32_t* sh) {
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const uint32_t S = (n + 31) / 32;
+    const uint32_t b0 = min(n, w * S), b1 = min(n, b0 + S);
+    for (uint32_t d = lane; d < 256; d += 32) whist[w * 256 + d] = 0;
+    __syncwarp();
+    for (uint32_t i = b0 + lane; i < b1; i += 32)
+        atomicAdd(&whist[w * 256 + (uint32_t)((in[i] >> shift) & mask)], 1u);
+    __syncthreads();
+    uint32_t v[8], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const uint32_t e = 8 * threadIdx.x + k;  // e = digit * 32 + warp
+        v[k] = whist[(e & 31u) * 256 + (e >> 5)];
+        sum += v[k];
     }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan(sum, sh, &tot);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const uint32_t e = 8 * threadIdx.x + k;
+        whist[(e & 31u) * 256 + (e >> 5)] = ex;
+        ex += v[k];
+    }
+    __syncthreads();
+    for (uint32_t base = b0; base < b1; base += 32) {
+        const uint32_t i = base + lane;
+        const bool valid = i < b1;
+        const unsigned long long key = valid ? in[i] : 0ull;
+        const uint32_t d = valid ? (uint32_t)((key >> shift) & mask) : 0xffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & lanemask_lt());
+        uint32_t pos = 0;
+        if (valid) pos = whist[w * 256 + d] + rank;
+        __syncwarp();
+        if (valid) {
+            out[pos] = key;
+            if ((uint32_t)(__ffs(peers) - 1) == lane) whist[w * 256 + d] += __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+// Warp-cooperative search: first index in [lo, hi) where pred(index) is false,
+// pred monotone (true ... true false ... false).  The whole warp calls it.
+template <class P>
+__device__ __forceinline__ uint32_t warp_first_false(uint32_t lo, uint32_t hi, P pred) {
+    const uint32_t lane = threadIdx.x & 31u;
+    while (hi - lo > 32) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t probe = lo + (lane + 1) * step - 1;
+        const bool t = probe < hi && pred(probe);
+        const uint32_t k = __popc(__ballot_sync(0xffffffffu, t));
+        const uint32_t nlo = lo + k * step;
+        hi = min(hi, nlo + step);
+        lo = nlo;
+    }
+    const uint32_t idx = lo + lane;
+    const bool t = idx < hi && pred(idx);
+    return lo + __popc(__ballot_sync(0xffffffffu, t));
 }
 
 __global__ void __launch_bounds__(1024, 1) k_codebook(CBArgs a) {
-    extern __shared__ unsigned long long dsm[];
+    extern __shared__ uint32_t dsm[];
+    uint32_t* sq = dsm;                                              // internal queue (n <= 32768)
+    uint8_t* depth8 = reinterpret_cast<uint8_t*>(dsm + kSmemQueue);  // internal-node depths
+    uint32_t* whist = dsm;                                           // radix histograms (alias)
+    unsigned long long* kbuf = reinterpret_cast<unsigned long long*>(dsm + 8192);  // rank sort (alias)
     __shared__ uint32_t sh[33];
     __shared__ double sdbl[32];
-    __shared__ uint32_t s_val, s_any;
-    __shared__ uint32_t s_cnt[32], s_fc[32], s_fi[32], s_carry[32];
-    __shared__ uint32_t s_wcnt[32][28];
+    __shared__ uint32_t s_m, s_a, s_err, s_max;
+    __shared__ uint32_t s_cnt[32], s_fc[32], s_fi[32];
+    __shared__ uint32_t s_round[kMaxRounds + 2];
     DevParams* par = a.par;
     const uint32_t tid = threadIdx.x;
-    const uint32_t lane = tid & 31u, warp = tid >> 5;
     const uint32_t flags = par->flags;
 
     // ---- squared-error total, fixed order ----
@@ -109,160 +180,191 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(CBArgs a) {
         }
     }
 
-    // ---- used symbols, ascending symbol order ----
-    for (uint32_t s = tid; s < a.nsym; s += blockDim.x) a.len_sym[s] = 0;
-    uint32_t n = 0;
-    for (uint32_t base = 0; base < a.nsym; base += blockDim.x) {
-        const uint32_t s = base + tid;
-        const uint32_t c = s < a.nsym ? a.hist[s] : 0u;
-        uint32_t tot;
-        uint32_t ex = block_excl_scan(c > 0 ? 1u : 0u, sh, &tot);
-        if (c > 0) a.gkeys[n + ex] = ((unsigned long long)c << 16) | s;
-        n += tot;
+    // ---- used symbols in ascending order (only the range the predictor saw) ----
+    const uint32_t c0 = a.hist[0];
+    uint32_t n = c0 > 0 ? 1u : 0u;
+    uint32_t maxc = c0;
+    if (tid == 0 && c0 > 0) a.list[0] = (unsigned long long)c0 << 16;
+    const uint32_t lo = par->sym_lo, hi = min(par->sym_hi, a.nsym - 1);
+    if (lo <= hi) {
+        for (uint32_t base = lo; base <= hi; base += 4 * blockDim.x) {
+            const uint32_t s0 = base + 4 * tid;
+            uint32_t c[4], cnt = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                c[k] = (s0 + k <= hi) ? a.hist[s0 + k] : 0u;
+                cnt += c[k] > 0;
+                maxc = max(maxc, c[k]);
+            }
+            uint32_t tot;
+            uint32_t pos = n + block_excl_scan(cnt, sh, &tot);
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (c[k]) a.list[pos++] = ((unsigned long long)c[k] << 16) | (s0 + k);
+            n += tot;
+        }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, o));
+    if (tid == 0) { s_max = 0; s_err = 0; }
     __syncthreads();
+    if ((tid & 31) == 0) atomicMax(&s_max, maxc);
+    __syncthreads();
+    maxc = s_max;
 
     if (n == 1) {
-        if (tid == 0) a.len_sym[(uint32_t)(a.gkeys[0] & 0xffffu)] = 1;
+        if (tid == 0) a.len_sym[(uint32_t)(a.list[0] & 0xffffu)] = 1;
     } else if (n > 1) {
-        const bool small = n <= (uint32_t)kSmemLeaves;
-        unsigned long long* keys = small ? dsm : a.gkeys;
-        unsigned long long* A = small ? dsm + kSmemLeaves : a.gA;
-        unsigned long long* B = small ? dsm + 2 * kSmemLeaves : a.gB;
-        unsigned long long* Nn = small ? dsm + 3 * kSmemLeaves : a.gN;
-        unsigned long long* node = small ? dsm : a.gnode;  // aliases keys + A when small
-        uint32_t* par_ = small ? reinterpret_cast<uint32_t*>(dsm + 3 * kSmemLeaves + kSmemLeaves / 2)
-                               : a.gpar;
-        uint32_t* lw = small ? par_ + 2 * kSmemLeaves : a.glw;
-        uint16_t* lsym = small ? reinterpret_cast<uint16_t*>(lw + kSmemLeaves) : a.glsym;
-        if (small)
-            for (uint32_t i = tid; i < n; i += blockDim.x) keys[i] = a.gkeys[i];
-        uint32_t P = 2;
-        while (P < n) P <<= 1;
-        __syncthreads();
-        // each rebuild halves every count > 1, so 33 rebuilds leave all counts at 1,
-        // whose code fits 2^lmax >= 2R symbols; the cap only guards against a fault
+        const bool smallq = n <= kSmemQueue;
         for (int rebuild = 0;; rebuild++) {
-            if (rebuild > 40) {
+            if (rebuild > 40) {  // 33 halvings leave every count at 1, which always fits
                 if (tid == 0) set_error(par, FPSNR_ETIMEOUT);
                 return;
             }
-            for (uint32_t i = n + tid; i < P; i += blockDim.x) keys[i] = ~0ull;
-            __syncthreads();
-            bitonic_sort(keys, P);
-            for (uint32_t i = tid; i < n; i += blockDim.x) {
-                const unsigned long long k = keys[i];
-                lsym[i] = (uint16_t)(k & 0xffffu);
-                lw[i] = (uint32_t)(k >> 16);
-                A[i] = ((k >> 16) << 32) | i;
+            // ---- leaves sorted by (count, symbol) ----
+            const unsigned long long* leaves;
+            unsigned long long* spare;
+            if (n <= kRankMax) {
+                rank_sort(a.list, a.buf1, n, kbuf);
+                leaves = a.buf1;
+                spare = a.buf2;
+            } else {
+                const int bits = 32 - __clz(maxc);
+                const int passes = (bits + 7) / 8;
+                const unsigned long long* src = a.list;
+                unsigned long long* dst = a.buf1;
+                for (int pss = 0; pss < passes; pss++) {
+                    radix_pass(src, dst, n, 16 + 8 * pss, 255u, whist, sh);
+                    src = dst;
+                    dst = (dst == a.buf1) ? a.buf2 : a.buf1;
+                }
+                leaves = src;
+                spare = dst;
             }
-            __syncthreads();
-            // bulk merge rounds
-            uint32_t L = n, next = n;
-            unsigned long long* cur = A;
-            unsigned long long* oth = B;
+            // internal queue, indexed by creation order (capacity >= n - 1)
+            uint32_t* iq = smallq ? sq : reinterpret_cast<uint32_t*>(spare);
+            // ---- bulk rounds over the two queues ----
+            uint32_t lh = 0, ih = 0, it = 0, next = n, L = n;
+            int rounds = 0;
             while (L > 1) {
-                if (tid == 0) {
-                    const uint32_t w1 = wgt(cur[0]) + wgt(cur[1]);
-                    uint32_t lo = 2, hi = L;  // first index with weight > w1
-                    while (lo < hi) {
-                        uint32_t mid = (lo + hi) >> 1;
-                        if (wgt(cur[mid]) <= w1) lo = mid + 1;
-                        else hi = mid;
-                    }
-                    s_val = lo >> 1;
+                if (rounds >= kMaxRounds) {
+                    if (tid == 0) s_err = 1;
+                    break;
                 }
-                __syncthreads();
-                const uint32_t m = s_val;
-                for (uint32_t i = tid; i < m; i += blockDim.x) {
-                    const unsigned long long x0 = cur[2 * i], x1 = cur[2 * i + 1];
-                    const uint32_t id = next + i;
-                    par_[(uint32_t)x0] = id;
-                    par_[(uint32_t)x1] = id;
-                    Nn[i] = ((unsigned long long)(wgt(x0) + wgt(x1)) << 32) | id;
-                }
-                __syncthreads();
-                const unsigned long long* O = cur + 2 * m;
-                const uint32_t no = L - 2 * m, tot = L - m;
-                const uint32_t E = (tot + blockDim.x - 1) / blockDim.x;
-                const uint32_t t0 = tid * E;
-                if (t0 < tot) {
-                    uint32_t lo = t0 > m ? t0 - m : 0, hi = min(t0, no);
-                    while (lo < hi) {
-                        uint32_t mid = (lo + hi) >> 1;
-                        if (wgt(O[mid]) <= wgt(Nn[t0 - mid - 1])) lo = mid + 1;
-                        else hi = mid;
+                if (tid < 32) {
+                    const uint32_t nl = n - lh, ni = it - ih;
+                    uint32_t w[2];
+                    {
+                        uint32_t i = lh, j = ih;
+                        for (int t = 0; t < 2; t++) {
+                            const bool tl = i < n && (j >= it || key_w(leaves[i]) <= iq[j]);
+                            w[t] = tl ? key_w(leaves[i++]) : iq[j++];
+                        }
                     }
-                    uint32_t i = lo, j = t0 - lo;
-                    const uint32_t t1 = min(t0 + E, tot);
-                    for (uint32_t t = t0; t < t1; t++) {
-                        if (j >= m || (i < no && wgt(O[i]) <= wgt(Nn[j]))) oth[t] = O[i++];
-                        else oth[t] = Nn[j++];
+                    const uint32_t w1 = w[0] + w[1];
+                    const uint32_t kl =
+                        warp_first_false(lh, n, [&](uint32_t x) { return key_w(leaves[x]) <= w1; }) - lh;
+                    const uint32_t ki =
+                        warp_first_false(ih, it, [&](uint32_t x) { return iq[x] <= w1; }) - ih;
+                    const uint32_t m = (kl + ki) >> 1;
+                    // leaves among the first 2m nodes (merge path, leaf first on ties)
+                    const uint32_t d = 2 * m;
+                    const uint32_t plo = d > ni ? d - ni : 0, phi = min(d, nl);
+                    const uint32_t na = warp_first_false(plo, phi, [&](uint32_t x) {
+                        return key_w(leaves[lh + x]) <= iq[ih + d - x - 1];
+                    });
+                    if (tid == 0) {
+                        s_m = m;
+                        s_a = na;
+                        s_round[rounds] = next;
                     }
                 }
                 __syncthreads();
-                unsigned long long* tmp = cur;
-                cur = oth;
-                oth = tmp;
-                L = tot;
+                const uint32_t m = s_m, na = s_a, nb = 2 * m - na;
+                const uint32_t E = (m + blockDim.x - 1) / blockDim.x;
+                const uint32_t p0 = tid * E, p1 = min(p0 + E, m);
+                if (p0 < p1) {
+                    // position of node 2*p0 within the merged prefix (na leaves, nb internal)
+                    const uint32_t d = 2 * p0;
+                    uint32_t lo2 = d > nb ? d - nb : 0, hi2 = min(d, na);
+                    while (lo2 < hi2) {
+                        const uint32_t mid = (lo2 + hi2) >> 1;
+                        if (key_w(leaves[lh + mid]) <= iq[ih + d - mid - 1]) lo2 = mid + 1;
+                        else hi2 = mid;
+                    }
+                    uint32_t i = lo2, j = d - lo2;
+                    for (uint32_t p = p0; p < p1; p++) {
+                        uint32_t id[2], w[2];
+                        for (int t = 0; t < 2; t++) {
+                            const bool tl = i < na && (j >= nb || key_w(leaves[lh + i]) <= iq[ih + j]);
+                            if (tl) { id[t] = lh + i; w[t] = key_w(leaves[lh + i]); i++; }
+                            else { id[t] = n + ih + j; w[t] = iq[ih + j]; j++; }
+                        }
+                        a.parent[id[0]] = next + p;
+                        a.parent[id[1]] = next + p;
+                        // new nodes go behind every live one: [it, it + m) is never read this round
+                        iq[it + p] = w[0] + w[1];
+                    }
+                }
+                __syncthreads();
+                lh += na;
+                ih += nb;
+                it += m;
                 next += m;
+                L -= m;
+                rounds++;
             }
-            // depths by pointer jumping: node[v] = (distance << 32) | ancestor
-            const uint32_t total = 2 * n - 1, root = total - 1;
-            for (uint32_t v = tid; v < total; v += blockDim.x)
-                node[v] = (v == root) ? (unsigned long long)root
-                                      : ((1ull << 32) | par_[v]);
+            if (s_err) {
+                if (tid == 0) set_error(par, FPSNR_ETIMEOUT);
+                return;
+            }
+            if (tid == 0) s_round[rounds] = next;
             __syncthreads();
-            // pointer jumping halves every remaining distance: 18 rounds reach the root
-            // of a 2^17-node tree; 64 rounds can only be exceeded by a broken tree
-            for (int round = 0;; round++) {
-                if (round > 64) {
-                    if (tid == 0) set_error(par, FPSNR_ETIMEOUT);
-                    return;
-                }
-                uint32_t changed = 0;
-                for (uint32_t v = tid; v < total; v += blockDim.x) {
-                    const unsigned long long e = node[v];
-                    const uint32_t anc = (uint32_t)e;
-                    if (anc != root) {
-                        const unsigned long long f = node[anc];
-                        node[v] = (((e >> 32) + (f >> 32)) << 32) | (uint32_t)f;
-                        changed = 1;
-                    }
-                }
-                if (!__syncthreads_or(changed)) break;
+            // ---- depths: internal nodes round by round from the root down ----
+            const uint32_t root = 2 * n - 2;
+            for (int r = rounds - 1; r >= 0; r--) {
+                const uint32_t r0 = s_round[r], r1 = s_round[r + 1];
+                for (uint32_t id = r0 + tid; id < r1; id += blockDim.x)
+                    depth8[id - n] = (id == root) ? 0 : (uint8_t)(depth8[a.parent[id] - n] + 1);
+                __syncthreads();
             }
             uint32_t mx = 0;
-            for (uint32_t i = tid; i < n; i += blockDim.x) mx = max(mx, (uint32_t)(node[i] >> 32));
+            for (uint32_t i = tid; i < n; i += blockDim.x)
+                mx = max(mx, (uint32_t)depth8[a.parent[i] - n] + 1);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if (tid == 0) s_any = 0;
+            if (tid == 0) s_max = 0;
             __syncthreads();
-            if (lane == 0) atomicMax(&s_any, mx);
+            if ((tid & 31) == 0) atomicMax(&s_max, mx);
             __syncthreads();
-            if (s_any <= (uint32_t)a.lmax) {
+            if (s_max <= (uint32_t)a.lmax) {
                 for (uint32_t i = tid; i < n; i += blockDim.x)
-                    a.len_sym[lsym[i]] = (uint8_t)(node[i] >> 32);
+                    a.len_sym[(uint32_t)(leaves[i] & 0xffffu)] = (uint8_t)(depth8[a.parent[i] - n] + 1);
                 break;
             }
-            // too long: halve the counts and rebuild (keys alias node when small)
-            __syncthreads();
+            // too long: halve every count (in the symbol-ordered list) and rebuild
             for (uint32_t i = tid; i < n; i += blockDim.x) {
-                uint32_t h = lw[i] >> 1;
-                keys[i] = ((unsigned long long)(h ? h : 1u) << 16) | lsym[i];
+                const unsigned long long k = a.list[i];
+                const uint32_t h = key_w(k) >> 1;
+                a.list[i] = ((unsigned long long)(h ? h : 1u) << 16) | (k & 0xffffu);
             }
+            maxc = (maxc >> 1) ? (maxc >> 1) : 1u;
             __syncthreads();
         }
     }
     __syncthreads();
 
-    // ---- canonical codes ----
-    if (tid < 32) { s_cnt[tid] = 0; s_carry[tid] = 0; }
-    __syncthreads();
-    for (uint32_t s = tid; s < a.nsym; s += blockDim.x) {
-        uint32_t l = a.len_sym[s];
-        if (l) atomicAdd(&s_cnt[l], 1u);
+    // ---- canonical order: stable sort of the symbol-ordered list by length ----
+    for (uint32_t i = tid; i < n; i += blockDim.x) {
+        const uint32_t s = (uint32_t)(a.list[i] & 0xffffu);
+        a.buf2[i] = ((unsigned long long)a.len_sym[s] << 16) | s;
     }
+    if (tid < 32) s_cnt[tid] = 0;
+    __syncthreads();
+    if (n <= kRankMax) rank_sort(a.buf2, a.buf1, n, kbuf);
+    else radix_pass(a.buf2, a.buf1, n, 16, 31u, whist, sh);
+    const unsigned long long* canon = a.buf1;
+    for (uint32_t i = tid; i < n; i += blockDim.x) atomicAdd(&s_cnt[(uint32_t)(canon[i] >> 16)], 1u);
     __syncthreads();
     if (tid == 0) {
         uint32_t code = 0, idx = 0;
@@ -278,36 +380,11 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(CBArgs a) {
     __syncthreads();
     const bool write_cb = kHeaderBytes + 4ull * n <= par->cap;
     uint32_t* cb = reinterpret_cast<uint32_t*>(a.out + kHeaderBytes);
-    for (uint32_t base = 0; base < a.nsym; base += blockDim.x) {
-        const uint32_t s = base + tid;
-        const uint32_t l = s < a.nsym ? a.len_sym[s] : 0u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, l);
-        const uint32_t rank = __popc(peers & lanemask_lt());
-        if (lane < 28) s_wcnt[warp][lane] = 0;
-        __syncwarp();
-        if ((uint32_t)(__ffs(peers) - 1) == lane) s_wcnt[warp][l] = __popc(peers);
-        __syncthreads();
-        if (tid < 28) {
-            uint32_t run = s_carry[tid];
-            for (uint32_t wv = 0; wv < 32; wv++) {
-                uint32_t c = s_wcnt[wv][tid];
-                s_wcnt[wv][tid] = run;
-                run += c;
-            }
-            s_carry[tid] = run;
-        }
-        __syncthreads();
-        if (s < a.nsym) {
-            if (l) {
-                const uint32_t pos = s_wcnt[warp][l] + rank;  // rank among length-l symbols
-                const uint32_t code = s_fc[l] + pos;
-                a.enc[s] = (code << 5) | l;
-                if (write_cb) cb[s_fi[l] + pos] = (l << 16) | s;
-            } else {
-                a.enc[s] = 0u;
-            }
-        }
-        __syncthreads();
+    for (uint32_t i = tid; i < n; i += blockDim.x) {
+        const uint32_t e = (uint32_t)canon[i];
+        const uint32_t l = e >> 16, s = e & 0xffffu;
+        a.enc[s] = ((s_fc[l] + (i - s_fi[l])) << 5) | l;
+        if (write_cb) cb[i] = e;
     }
 }
 
@@ -324,14 +401,10 @@ int launch_codebook(fpsnr_plan_s* p, void* d_out, cudaStream_t st) {
     a.n_sse = p->n ? p->pq.nblocks : 0;
     a.bpre = w.bpre;
     a.nbmblk = (uint32_t)p->nbmblk;
-    a.gkeys = w.hkeys;
-    a.gA = w.hseqA;
-    a.gB = w.hseqB;
-    a.gN = w.hnew;
-    a.gnode = w.hnode;
-    a.gpar = w.hpar;
-    a.glw = w.hlw;
-    a.glsym = w.hlsym;
+    a.list = w.hlist;
+    a.buf1 = w.hbuf1;
+    a.buf2 = w.hbuf2;
+    a.parent = w.hpar;
     a.out = reinterpret_cast<uint8_t*>(d_out);
     StageScope sc(p->prof, kStCodebook, st);
     k_codebook<<<1, 1024, p->cb_smem, st>>>(a);
