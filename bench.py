@@ -179,6 +179,30 @@ def workload_config(a, streams):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank helpers (one process per GPU; fields shard with no data-path collective)
+# ---------------------------------------------------------------------------
+
+def max_over_ranks(ms: float, world: int, dist=None, device=None) -> float:
+    """Step time of the slowest rank (the only collective: one float)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gbs(bytes_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: every rank processes its own batch (weak scaling)."""
+    return world * bytes_per_rank / (ms / 1e3) / 1e9
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank compresses its own seeded batch."""
+    return 1 + 1000 * rank
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -221,7 +245,7 @@ def main():
     from paper_1805_07384_gb300 import fpsnr, synth
 
     F, S = a.fields, max(1, a.streams)
-    fields, meta = synth.climate_batch(F, a.ny, a.nx, seed=1 + 1000 * rank, device=dev)
+    fields, meta = synth.climate_batch(F, a.ny, a.nx, seed=rank_seed(rank), device=dev)
     psnrs = [synth.mixed_psnr(i) for i in range(F)]
     N = a.ny * a.nx
     plans = [fpsnr.Plan((a.ny, a.nx), psnrs[i], chunk=a.chunk) for i in range(F)]
@@ -287,11 +311,7 @@ def main():
             run_step(nstreams, graph, **kw)
         t1.record(main_s)
         barrier()
-        ms = t0.elapsed_time(t1) / k
-        if world > 1:
-            tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(t0.elapsed_time(t1) / k, world, dist, dev)
         return ms, (time.perf_counter() - wall0)
 
     use_graph = not a.no_graph
@@ -321,7 +341,7 @@ def main():
     launches = launches_per_step * a.steps
 
     total_bytes = 4 * N * F
-    value = world * total_bytes / (ms / 1e3) / 1e9
+    value = aggregate_gbs(total_bytes, world, ms)
 
     # per-field results (outside the timed region)
     per_field = []
@@ -394,7 +414,7 @@ def main():
         if use_graph:
             run_step(S, True, h2d=h2d, d2h=d2h)
         ms_e, _ = timed(a.steps, S, graph=use_graph, h2d=h2d, d2h=d2h)
-        e2e = {"value": round(world * total_bytes / (ms_e / 1e3) / 1e9, 3), "unit": "GB/s",
+        e2e = {"value": round(aggregate_gbs(total_bytes, world, ms_e), 3), "unit": "GB/s",
                "h2d_bytes_per_step": total_bytes,
                "d2h_bytes_per_step": total_bytes + F * fpsnr.STATS_BYTES,
                "ms_per_step": round(ms_e, 4)}
