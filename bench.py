@@ -37,6 +37,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--sub-batches", type=int, default=3,
+                    help="batch mode: sub-batches, one per stream")
+    ap.add_argument("--mode", choices=["batch", "streams"], default="batch",
+                    help="batch: one batched compress + decompress call per step; "
+                         "streams: one plain call per field, fields spread over --streams")
     ap.add_argument("--fields", type=int, default=24)
     ap.add_argument("--ny", type=int, default=1800)
     ap.add_argument("--nx", type=int, default=3600)
@@ -173,7 +178,11 @@ def workload_config(a, streams):
          "lorenzo_dims": 2,
          "l2": f"inputs {a.fields * a.ny * a.nx * 4 / 1e6:.0f} MB > 129 MB L2, no flush"}
     if streams is not None:
-        c["streams"] = streams
+        c["mode"] = getattr(a, "mode", "batch")
+        if c["mode"] == "streams":
+            c["streams"] = streams
+        else:
+            c["sub_batches"] = max(1, min(a.sub_batches, a.fields, streams))
         c["launch"] = "eager" if getattr(a, "no_graph", False) else "one CUDA graph per step"
     return c
 
@@ -257,7 +266,45 @@ def main():
     streams = [torch.cuda.Stream(device=dev) for _ in range(S)]
     main_s = torch.cuda.current_stream(dev)
 
+
+    # batch mode: the fields split into `nsub` sub-batches, one per stream, so
+    # that one sub-batch's latency-bound stages overlap another's bandwidth work
+    nsub = max(1, min(a.sub_batches, F, S))
+    groups = [list(range(g, F, nsub)) for g in range(nsub)]
+    nb_all = [torch.zeros(len(g), dtype=torch.int64, device=dev) for g in groups]
+    st_all = [torch.zeros((len(g), fpsnr.STATS_BYTES), dtype=torch.uint8, device=dev) for g in groups]
+    dst_all = [torch.zeros(len(g), dtype=torch.int32, device=dev) for g in groups]
+
+    def step_batch(h2d=None, d2h=None, serial=False):
+        cur = torch.cuda.current_stream(dev)
+        ev = torch.cuda.Event()
+        ev.record(cur)
+        for gi, idx in enumerate(groups):
+            s = cur if serial else streams[gi]
+            if not serial:
+                s.wait_event(ev)
+            with torch.cuda.stream(s):
+                if h2d is not None:
+                    for i in idx:
+                        fields[i].copy_(h2d[i], non_blocking=True)
+                gp = [plans[i] for i in idx]
+                fpsnr.compress_batch(gp, [fields[i] for i in idx], outs=[outs[i] for i in idx],
+                                     nbytes=nb_all[gi], stats=st_all[gi], stream=s)
+                fpsnr.decompress_batch(gp, [outs[i] for i in idx], outs=[recs[i] for i in idx],
+                                       status=dst_all[gi], stream=s)
+                if d2h is not None:
+                    for i in idx:
+                        d2h[0][i].copy_(recs[i], non_blocking=True)
+                    d2h[1][gi].copy_(st_all[gi], non_blocking=True)
+        for gi in range(len(groups) if not serial else 0):
+            e = torch.cuda.Event()
+            e.record(streams[gi])
+            cur.wait_event(e)
+
     def step(nstreams, h2d=None, d2h=None):
+        if a.mode == "batch":
+            step_batch(h2d, d2h, serial=(nstreams == 1))
+            return
         cur = torch.cuda.current_stream(dev)
         ev = torch.cuda.Event()
         ev.record(cur)
@@ -346,9 +393,19 @@ def main():
     # per-field results (outside the timed region)
     per_field = []
     dev_abs, meets, crs = [], [], []
+    if a.mode == "batch":
+        order = [i for g in groups for i in g]
+        stat_rows = [None] * F
+        dec_status = [None] * F
+        for gi, g in enumerate(groups):
+            for j, i in enumerate(g):
+                stat_rows[i] = st_all[gi][j]
+                dec_status[i] = dst_all[gi][j]
+    else:
+        stat_rows, dec_status = sts, dsts
     for i in range(F):
-        st = fpsnr.parse_stats(sts[i])
-        assert st["status"] == 0 and int(dsts[i].item()) == 0, (i, st["status"], int(dsts[i].item()))
+        st = fpsnr.parse_stats(stat_rows[i])
+        assert st["status"] == 0 and int(dec_status[i].item()) == 0, (i, st["status"])
         p_meas, _, _ = fpsnr.psnr(fields[i], recs[i])
         assert p_meas == st["psnr_actual"] or abs(p_meas - st["psnr_actual"]) < 1e-9
         cr = 4 * N / st["bytes"]
@@ -370,15 +427,17 @@ def main():
             fpsnr.fpsnr_plan_profile_read(p.handle)
         ms1, _ = timed(a.steps, 1)
         agg = {}
-        for i, p in enumerate(plans):
-            B = fpsnr.parse_stats(sts[i])["bytes"]
+        comp_bytes = [fpsnr.parse_stats(stat_rows[i])["bytes"] for i in range(F)]
+        for p in plans:
             for name, (t, n) in fpsnr.fpsnr_plan_profile_read(p.handle).items():
                 e = agg.setdefault(name, [0.0, 0, 0])
                 e[0] += t
                 e[1] += n
-                sb = stage_bytes(name, N, B)
-                e[2] += (sb or 0) * n
             fpsnr.fpsnr_plan_profile(p.handle, False)
+        for name, e in agg.items():
+            # algorithmic bytes of the stage for every field, every timed step
+            sb = [stage_bytes(name, N, comp_bytes[i]) for i in range(F)]
+            e[2] = a.steps * sum(sb) if e[1] and all(v is not None for v in sb) else 0
         step_ms = ms1
         stage_table = {k: {"ms_per_step": round(v[0] / a.steps, 4), "launches_per_step": v[1] // a.steps,
                            "share": round(v[0] / a.steps / step_ms, 4),
@@ -401,7 +460,7 @@ def main():
                     "traffic": traffic, "peak_source": "measured" if peaks else "fallback",
                     "bytes_per_launch": byts // n, "launch_ms": round(t / n, 5),
                     "timing": f"CUDA events around each launch over a second timed pass of "
-                              f"{a.steps} steps on one stream",
+                              f"{a.steps} steps on one stream ({a.mode} mode)",
                     "step_ms_one_stream": round(ms1, 4)}
 
     # end to end through host buffers
@@ -409,6 +468,9 @@ def main():
     if not a.no_e2e:
         h2d = [f.cpu().pin_memory() for f in fields]
         d2h = ([torch.empty((a.ny, a.nx), dtype=torch.float32).pin_memory() for _ in range(F)],
+               [torch.empty((len(g), fpsnr.STATS_BYTES), dtype=torch.uint8).pin_memory()
+                for g in groups]
+               if a.mode == "batch" else
                [torch.empty(fpsnr.STATS_BYTES, dtype=torch.uint8).pin_memory() for _ in range(F)])
         step(S, h2d=h2d, d2h=d2h)
         if use_graph:

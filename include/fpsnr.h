@@ -139,6 +139,27 @@ int fpsnr_compress(fpsnr_plan_t plan, const float* d_in, void* d_out, uint64_t o
 int fpsnr_decompress(fpsnr_plan_t plan, const void* d_blob, uint64_t blob_bytes, float* d_out,
                      uint64_t n_out, int* d_status, void* stream);
 
+/* Batched compression: `count` fields, each with its own plan (shape, target
+ * PSNR, options), compressed by one kernel launch per stage, so that stages
+ * bound by latency (Huffman construction, look-back chains, small kernels)
+ * overlap across fields.  plans, d_in, d_out, out_cap: host arrays of `count`
+ * entries (pointers as for fpsnr_compress; the plans must be distinct and on
+ * the current device).  d_out_bytes: device array of `count` u64 (may be NULL);
+ * d_stats: device array of `count` fpsnr_stats (may be NULL).  Results equal
+ * those of `count` separate fpsnr_compress calls.  Any count is accepted;
+ * launches cover at most 32 fields each.  Asynchronous, no allocation.
+ * Returns FPSNR_OK, FPSNR_EINVAL or FPSNR_ECUDA. */
+int fpsnr_compress_batch(const fpsnr_plan_t* plans, const float* const* d_in, void* const* d_out,
+                         const uint64_t* out_cap, uint64_t* d_out_bytes, fpsnr_stats* d_stats,
+                         int count, void* stream);
+
+/* Batched decompression, the counterpart of fpsnr_compress_batch: host arrays
+ * plans, d_blob, blob_bytes, d_out of `count` entries; d_status: device array
+ * of `count` ints (may be NULL).  Asynchronous, no allocation. */
+int fpsnr_decompress_batch(const fpsnr_plan_t* plans, const void* const* d_blob,
+                           const uint64_t* blob_bytes, float* const* d_out, int* d_status,
+                           int count, void* stream);
+
 /* Distortion of a reconstruction (Eq. 4-5): vr = max - min of d_x (FP64),
  * MSE = sum((x - xr)^2) / n with exact squares accumulated to FP64,
  * PSNR = 20 log10 vr - 10 log10 MSE (+inf when MSE == 0), log10 on the host.

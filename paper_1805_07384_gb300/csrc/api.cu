@@ -59,8 +59,7 @@ void carve(fpsnr_plan_s* p, uint8_t* base, size_t* total) {
     w.lb_flags = c.take<uint32_t>(std::max<uint64_t>(p->lb_tiles_total, 1));
     w.lb_vals = c.take<uint32_t>(2 * std::max<uint64_t>(p->lb_tiles_total, 1) * p->lb_width);
     w.lb_ctr = c.take<uint32_t>(8);
-    w.enc_flags = c.take<uint32_t>(3 * std::max<uint64_t>(p->enc_tiles, 1));
-    w.enc_ctr = c.take<uint32_t>(2);
+    w.enc_tiles = c.take<uint32_t>(std::max<uint64_t>(p->enc_tiles, 1));
     *total = (c.off + 255) & ~(size_t)255;
 }
 
@@ -90,6 +89,17 @@ ScanPass strided_pass(uint64_t A, uint64_t L, uint64_t B, bool final_pass) {
     s.tiles = (uint32_t)(cdiv(L, 16) * A * cdiv(B, (uint64_t)s.tb));
     s.final_pass = final_pass;
     return s;
+}
+
+// Runs `fn` with the plans' device current (all plans of one call share it).
+template <class F>
+int on_device(int device, F fn) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return FPSNR_ECUDA;
+    if (cur != device && cudaSetDevice(device) != cudaSuccess) return FPSNR_ECUDA;
+    int rc = fn();
+    if (cur != device) cudaSetDevice(cur);
+    return rc;
 }
 
 }  // namespace
@@ -317,8 +327,7 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
               cudaMemset(w.bm, 0, 2 * std::max<uint64_t>(p->nwords, 1) * 4) == cudaSuccess &&
               cudaMemset(w.lb_flags, 0, std::max<uint64_t>(p->lb_tiles_total, 1) * 4) == cudaSuccess &&
               cudaMemset(w.lb_ctr, 0, 8 * 4) == cudaSuccess &&
-              cudaMemset(w.enc_flags, 0, 3 * std::max<uint64_t>(p->enc_tiles, 1) * 4) == cudaSuccess &&
-              cudaMemset(w.enc_ctr, 0, 2 * 4) == cudaSuccess &&
+
               fp::codebook_prepare() == FPSNR_OK && fp::decode_prepare(p) == FPSNR_OK &&
               cudaDeviceSynchronize() == cudaSuccess;
     if (!ok) {
@@ -352,28 +361,53 @@ uint64_t fpsnr_max_compressed_bytes(fpsnr_plan_t p) {
 
 int fpsnr_compress(fpsnr_plan_t p, const float* d_in, void* d_out, uint64_t out_cap,
                    uint64_t* d_out_bytes, fpsnr_stats* d_stats, void* stream) {
-    if (!p || !d_out || (p->n > 0 && !d_in)) return FPSNR_EINVAL;
-    if (((uintptr_t)d_in & 3u) || ((uintptr_t)d_out & 15u)) return FPSNR_EINVAL;
-    int cur = -1;
-    if (cudaGetDevice(&cur) != cudaSuccess) return FPSNR_ECUDA;
-    if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return FPSNR_ECUDA;
-    int rc = fp::launch_compress(p, d_in, d_out, out_cap, d_out_bytes, d_stats,
-                                 reinterpret_cast<cudaStream_t>(stream));
-    if (cur != p->device) cudaSetDevice(cur);
-    return rc;
+    return fpsnr_compress_batch(&p, &d_in, &d_out, &out_cap, d_out_bytes, d_stats, 1, stream);
+}
+
+int fpsnr_compress_batch(const fpsnr_plan_t* plans, const float* const* d_in, void* const* d_out,
+                         const uint64_t* out_cap, uint64_t* d_out_bytes, fpsnr_stats* d_stats,
+                         int count, void* stream) {
+    if (count < 0 || (count > 0 && (!plans || !d_in || !d_out || !out_cap))) return FPSNR_EINVAL;
+    if (count == 0) return FPSNR_OK;
+    for (int i = 0; i < count; i++) {
+        const fpsnr_plan_s* p = plans[i];
+        if (!p || !d_out[i] || (p->n > 0 && !d_in[i])) return FPSNR_EINVAL;
+        if (((uintptr_t)d_in[i] & 3u) || ((uintptr_t)d_out[i] & 15u)) return FPSNR_EINVAL;
+        if (p->device != plans[0]->device) return FPSNR_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (plans[j] == p) return FPSNR_EINVAL;  // a plan's scratch serves one field at a time
+    }
+    return on_device(plans[0]->device, [&] {
+        return fp::launch_compress_batch(const_cast<fpsnr_plan_s* const*>(plans), d_in, d_out, out_cap,
+                                         d_out_bytes, d_stats, count,
+                                         reinterpret_cast<cudaStream_t>(stream));
+    });
 }
 
 int fpsnr_decompress(fpsnr_plan_t p, const void* d_blob, uint64_t blob_bytes, float* d_out,
                      uint64_t n_out, int* d_status, void* stream) {
-    if (!p || !d_blob || n_out != p->n || (p->n > 0 && !d_out)) return FPSNR_EINVAL;
-    if (((uintptr_t)d_blob & 15u) || ((uintptr_t)d_out & 15u)) return FPSNR_EINVAL;
-    int cur = -1;
-    if (cudaGetDevice(&cur) != cudaSuccess) return FPSNR_ECUDA;
-    if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return FPSNR_ECUDA;
-    int rc = fp::launch_decompress(p, d_blob, blob_bytes, d_out, d_status,
-                                   reinterpret_cast<cudaStream_t>(stream));
-    if (cur != p->device) cudaSetDevice(cur);
-    return rc;
+    if (!p || n_out != p->n) return FPSNR_EINVAL;
+    return fpsnr_decompress_batch(&p, &d_blob, &blob_bytes, &d_out, d_status, 1, stream);
+}
+
+int fpsnr_decompress_batch(const fpsnr_plan_t* plans, const void* const* d_blob,
+                           const uint64_t* blob_bytes, float* const* d_out, int* d_status,
+                           int count, void* stream) {
+    if (count < 0 || (count > 0 && (!plans || !d_blob || !blob_bytes || !d_out))) return FPSNR_EINVAL;
+    if (count == 0) return FPSNR_OK;
+    for (int i = 0; i < count; i++) {
+        const fpsnr_plan_s* p = plans[i];
+        if (!p || !d_blob[i] || (p->n > 0 && !d_out[i])) return FPSNR_EINVAL;
+        if (((uintptr_t)d_blob[i] & 15u) || ((uintptr_t)d_out[i] & 15u)) return FPSNR_EINVAL;
+        if (p->device != plans[0]->device) return FPSNR_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (plans[j] == p) return FPSNR_EINVAL;
+    }
+    return on_device(plans[0]->device, [&] {
+        return fp::launch_decompress_batch(const_cast<fpsnr_plan_s* const*>(plans), d_blob, blob_bytes,
+                                           d_out, d_status, count,
+                                           reinterpret_cast<cudaStream_t>(stream));
+    });
 }
 
 const uint16_t* fpsnr_plan_codes(fpsnr_plan_t p) { return p ? p->w.codes : nullptr; }

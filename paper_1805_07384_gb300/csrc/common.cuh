@@ -38,9 +38,10 @@ struct DevParams {
     uint32_t stream_words;
     uint32_t done_range;      // self-resetting last-block counter
     uint32_t sym_lo, sym_hi;  // smallest / largest nonzero symbol seen by the predictor
-    // look-back epochs, advanced on the device by the first kernel of every
-    // compress / decompress call (so a captured CUDA graph replays correctly)
-    uint32_t enc_epoch, dec_epoch;
+    // look-back epoch of the inverse-Lorenzo scans, advanced on the device by
+    // the first kernel of every decompress call (so a captured CUDA graph
+    // replays correctly)
+    uint32_t dec_epoch;
     uint64_t cap;             // output capacity of this call
     uint64_t off_cb, off_ct, off_st, off_ou, off_vb, total;
     // decompression: header fields of the blob being decoded
@@ -75,9 +76,7 @@ struct Workspace {
     uint32_t* lb_flags;  // [n_lb_tiles]
     uint32_t* lb_vals;   // [2][n_lb_tiles * lb_width] aggregate, inclusive
     uint32_t* lb_ctr;    // [8] dynamic tile counters (pairs: counter, done)
-    // encoder look-back state
-    uint32_t* enc_flags; // [3][enc_tiles] flags, tile words, inclusive words
-    uint32_t* enc_ctr;   // [2] tile counter, done counter
+    uint32_t* enc_tiles; // [enc_tiles] words per encoder tile, then their exclusive prefix
 };
 
 // Launch geometry of the predict-quantize kernel.
@@ -164,12 +163,55 @@ struct StageScope {
 
 namespace fp {
 
-// ---- host-side launchers (one per translation unit) ----
-int launch_compress(fpsnr_plan_s* p, const float* d_in, void* d_out, uint64_t cap,
-                    uint64_t* d_out_bytes, fpsnr_stats* d_stats, cudaStream_t st);
-int launch_codebook(fpsnr_plan_s* p, void* d_out, cudaStream_t st);
-int launch_decompress(fpsnr_plan_s* p, const void* d_blob, uint64_t bytes, float* d_out,
-                      int* d_status, cudaStream_t st);
+// ---- batched launches ----
+// A batch runs one kernel launch per stage for up to kMaxBatch fields.  The
+// per-field arguments travel in the kernel parameter (a __grid_constant__
+// table, so no device memory and nothing to re-upload when a graph replays);
+// block b belongs to the field f with off[f] <= b < off[f + 1].
+constexpr int kMaxBatch = 32;
+
+template <class A>
+struct Batch {
+    uint32_t count;
+    uint32_t off[kMaxBatch + 1];
+    A a[kMaxBatch];
+};
+
+// Host: fills off[] from per-field block counts; returns the total.
+template <class A>
+inline uint32_t batch_offsets(Batch<A>& b, const uint32_t* blocks) {
+    uint32_t t = 0;
+    for (uint32_t f = 0; f < b.count; f++) {
+        b.off[f] = t;
+        t += blocks[f];
+    }
+    b.off[b.count] = t;
+    return t;
+}
+
+#ifdef __CUDACC__
+// Field of block `bid`: the largest f with off[f] <= bid (fields with no
+// blocks are skipped because a later field starts at the same offset).
+__device__ __forceinline__ uint32_t batch_field(const uint32_t* off, uint32_t count, uint32_t bid) {
+    uint32_t lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= bid) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+#endif
+
+// ---- host-side launchers ----
+int launch_compress_batch(fpsnr_plan_s* const* plans, const float* const* d_in,
+                          void* const* d_out, const uint64_t* caps, uint64_t* d_out_bytes,
+                          fpsnr_stats* d_stats, int count, cudaStream_t st);
+int launch_codebook_batch(fpsnr_plan_s* const* plans, void* const* d_out, int count,
+                          cudaStream_t st);
+int launch_decompress_batch(fpsnr_plan_s* const* plans, const void* const* d_blob,
+                            const uint64_t* bytes, float* const* d_out, int* d_status, int count,
+                            cudaStream_t st);
 int codebook_smem_bytes();
 // PSNR reduction (psnr.cu): scratch = 16-byte zeroed counter, 32-byte result,
 // then one partial per block.

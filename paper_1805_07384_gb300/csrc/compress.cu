@@ -16,6 +16,8 @@
 //   k_finalize     header, size, statistics
 #include <float.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace fp {
@@ -24,15 +26,32 @@ namespace fp {
 // value range and plan scalars
 // ---------------------------------------------------------------------------
 
-template <bool VEC>
-__global__ void __launch_bounds__(512) k_range_plan(const float* __restrict__ x, uint64_t n,
-                                                    DevParams* par, float* part,
-                                                    uint32_t* hist, uint32_t nsym,
-                                                    double eb_rel, double target, uint64_t cap,
-                                                    uint32_t* enc_ctr) {
+struct RangeArgs {
+    const float* x;
+    uint64_t n;
+    DevParams* par;
+    float* part;
+    uint32_t* hist;
+    uint32_t nsym;
+    double eb_rel, target;
+    uint64_t cap;
+    bool vec;  // x is 16-byte aligned
+};
+
+__global__ void __launch_bounds__(512) k_range_plan(const __grid_constant__ Batch<RangeArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const RangeArgs& A = B.a[fld];
+    const uint32_t bid = blockIdx.x - B.off[fld], nblk = B.off[fld + 1] - B.off[fld];
+    const float* __restrict__ x = A.x;
+    const uint64_t n = A.n;
+    DevParams* par = A.par;
+    float* part = A.part;
+    uint32_t* hist = A.hist;
+    const uint32_t nsym = A.nsym;
+    const bool VEC = A.vec;
     const uint32_t tid = threadIdx.x;
-    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + tid;
-    const uint64_t gsz = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gtid = (uint64_t)bid * blockDim.x + tid;
+    const uint64_t gsz = (uint64_t)nblk * blockDim.x;
     for (uint64_t i = gtid; i < nsym; i += gsz) hist[i] = 0u;
 
     float lo = FLT_MAX, hi = -FLT_MAX;
@@ -75,17 +94,17 @@ __global__ void __launch_bounds__(512) k_range_plan(const float* __restrict__ x,
         for (uint32_t w = 1; w < (blockDim.x >> 5); w++) {
             lo = fminf(lo, slo[w]); hi = fmaxf(hi, shi[w]); nf |= snf[w];
         }
-        part[3 * blockIdx.x] = lo;
-        part[3 * blockIdx.x + 1] = hi;
-        part[3 * blockIdx.x + 2] = nf ? 1.0f : 0.0f;
+        part[3 * bid] = lo;
+        part[3 * bid + 1] = hi;
+        part[3 * bid + 2] = nf ? 1.0f : 0.0f;
         __threadfence();
-        last = (atomicAdd(&par->done_range, 1u) == gridDim.x - 1);
+        last = (atomicAdd(&par->done_range, 1u) == nblk - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     lo = FLT_MAX; hi = -FLT_MAX; nf = 0;
-    for (uint32_t b = tid; b < gridDim.x; b += blockDim.x) {
+    for (uint32_t b = tid; b < nblk; b += blockDim.x) {
         lo = fminf(lo, __ldcg(part + 3 * b));
         hi = fmaxf(hi, __ldcg(part + 3 * b + 1));
         nf |= __ldcg(part + 3 * b + 2) != 0.0f;
@@ -115,7 +134,7 @@ __global__ void __launch_bounds__(512) k_range_plan(const float* __restrict__ x,
     } else if (n == 0 || vr == 0.0) {
         flags = kFlagConstant;
     } else {
-        eb = eb_rel * vr;
+        eb = A.eb_rel * vr;
         double two_eb = 2.0 * eb;
         s = __double2float_rn(two_eb);
         inv = __double2float_rn(1.0 / two_eb);
@@ -130,8 +149,8 @@ __global__ void __launch_bounds__(512) k_range_plan(const float* __restrict__ x,
     }
     par->vr = vr;
     par->eb_abs = eb;
-    par->eb_rel = eb_rel;
-    par->target_psnr = target;
+    par->eb_rel = A.eb_rel;
+    par->target_psnr = A.target;
     par->sse = 0.0;
     par->xmin = lo;
     par->xmax = hi;
@@ -144,18 +163,12 @@ __global__ void __launch_bounds__(512) k_range_plan(const float* __restrict__ x,
     par->n_vb = 0;
     par->n_sym = 0;
     par->stream_words = 0;
-    par->cap = cap;
+    par->cap = A.cap;
     par->off_cb = kHeaderBytes;
     par->off_ct = par->off_st = par->off_ou = par->off_vb = par->total = kHeaderBytes;
     par->done_range = 0;
     par->sym_lo = 0xffffffffu;
     par->sym_hi = 0u;
-    // the encoder's tile counters start every call at zero, even after an
-    // earlier call ended in an error that stopped some of its blocks early
-    enc_ctr[0] = 0;
-    enc_ctr[1] = 0;
-    const uint32_t e = (par->enc_epoch + 1) & 0x3fffffffu;
-    par->enc_epoch = e ? e : 1u;
 }
 
 // ---------------------------------------------------------------------------
@@ -163,6 +176,7 @@ __global__ void __launch_bounds__(512) k_range_plan(const float* __restrict__ x,
 // ---------------------------------------------------------------------------
 
 struct PQArgs {
+    const float* x;
     DevParams* par;
     uint16_t* codes;
     uint32_t* hist;
@@ -188,8 +202,11 @@ __device__ __forceinline__ int32_t prequant(float x, float xmin, float inv, bool
 // MODE 2: 2D predictor on (vz rows) x vx, TY must be 1 (vy == 1).
 // MODE 3: 3D predictor on vz x vy x vx with TY rows per tile.
 template <int MODE, int TX, int TY, bool VEC>
-__global__ void __launch_bounds__(TX / 4 * TY) k_pq(const float* __restrict__ x, PQArgs a) {
+__global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batch<PQArgs> B) {
     constexpr int NT = TX / 4 * TY;
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const PQArgs& a = B.a[fld];
+    const float* __restrict__ x = a.x;
     DevParams* par = a.par;
     const uint32_t flags = par->flags;
     if (flags & (kFlagConstant | kFlagError)) return;
@@ -205,7 +222,7 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const float* __restrict__ x,
     for (uint32_t i = tid; i < kHistWin; i += NT) shist[i] = 0u;
     __syncthreads();
 
-    const uint32_t b = blockIdx.x;
+    const uint32_t b = blockIdx.x - B.off[fld];
     const uint32_t bx = b % a.nbx;
     const uint32_t by = (b / a.nbx) % a.nby;
     const uint32_t bz = b / (a.nbx * a.nby);
@@ -420,7 +437,7 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const float* __restrict__ x,
         if (c) atomicAdd(&a.hist[wlo + (int)i], c);
     }
     double tot = block_sum_double(ff_to_double(acc), ssum);
-    if (tid == 0) a.sse_part[blockIdx.x] = tot;
+    if (tid == 0) a.sse_part[b] = tot;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sym_lo = min(sym_lo, __shfl_xor_sync(0xffffffffu, sym_lo, o));
@@ -436,20 +453,37 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const float* __restrict__ x,
 // order-preserving ranks: popcount prefix of the membership bitmaps
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(1024) k_rank_popc(const DevParams* __restrict__ par,
-                                                    const uint32_t* __restrict__ bm,
-                                                    uint32_t* wpre, uint32_t* bpre,
-                                                    uint64_t nwords, uint32_t nbmblk) {
-    const uint32_t list = blockIdx.y;
+struct RankArgs {
+    const DevParams* par;
+    const uint32_t* bm;
+    uint32_t* wpre;
+    uint32_t* bpre;
+    uint64_t nwords;
+    uint32_t nbmblk;
+};
+
+// 2 * nbmblk blocks per field: list (outliers, verbatims) x bitmap block
+__global__ void __launch_bounds__(1024) k_rank_popc(const __grid_constant__ Batch<RankArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const RankArgs& A = B.a[fld];
+    const uint32_t bid = blockIdx.x - B.off[fld];
+    const DevParams* par = A.par;
+    const uint32_t* bm = A.bm;
+    uint32_t* wpre = A.wpre;
+    uint32_t* bpre = A.bpre;
+    const uint64_t nwords = A.nwords;
+    const uint32_t nbmblk = A.nbmblk;
+    const uint32_t list = bid / nbmblk;
+    const uint32_t blk = bid % nbmblk;
     const uint32_t cnt = list == 0 ? par->n_out : par->n_vb;
     if (cnt == 0 || (par->flags & (kFlagConstant | kFlagError))) return;
     __shared__ uint32_t sh[33];
-    const uint64_t w = (uint64_t)blockIdx.x * 1024u + threadIdx.x;
+    const uint64_t w = (uint64_t)blk * 1024u + threadIdx.x;
     uint32_t c = w < nwords ? __popc(bm[list * nwords + w]) : 0u;
     uint32_t total;
     uint32_t ex = block_excl_scan(c, sh, &total);
     if (w < nwords) wpre[list * nwords + w] = ex;
-    if (threadIdx.x == 0) bpre[list * nbmblk + blockIdx.x] = total;
+    if (threadIdx.x == 0) bpre[list * nbmblk + blk] = total;
 }
 
 // ---------------------------------------------------------------------------
@@ -460,7 +494,6 @@ static __device__ __forceinline__ uint64_t pad16(uint64_t b) { return (b + 15u) 
 
 constexpr int kEncWarps = 8;  // chunks per tile, one warp each
 constexpr int kPieceWords = (256 * kMaxLmax + 31) / 32 + 2;
-constexpr uint32_t kEncA = 1u, kEncP = 2u;
 
 struct EncArgs {
     DevParams* par;
@@ -471,10 +504,8 @@ struct EncArgs {
     uint32_t chunk;
     uint64_t nchunks;
     uint32_t ntiles;
-    uint32_t* flags;  // [ntiles] look-back flags (epoch << 2 | state)
-    uint32_t* agg;    // [ntiles] words of the tile
-    uint32_t* inc;    // [ntiles] words up to and including the tile
-    uint32_t* ctr;    // [2] tile counter, done counter
+    uint32_t* chunk_words;  // [nchunks] words of every chunk
+    uint32_t* tile_sum;     // [ntiles] words of every tile, then their exclusive prefix
 };
 
 // Coded bits of symbols [beg, end) summed over the warp (8 per lane per step).
@@ -500,169 +531,206 @@ __device__ __forceinline__ uint32_t warp_chunk_bits(const uint16_t* __restrict__
     return bits;
 }
 
-// Each warp sizes its chunk; the tile's chunks get consecutive word offsets
-// from a decoupled look-back over earlier tiles; the warp then packs its chunk
-// MSB-first: pieces of 256 symbols (8 per lane) are OR-ed into a per-warp
-// shared-memory word buffer, full words go out coalesced and the partial last
-// word carries into the next piece.  The last tile lays out the sections and
-// checks the output capacity; every write is also checked against it.
-__global__ void __launch_bounds__(kEncWarps * 32) k_encode(EncArgs a) {
-    DevParams* par = a.par;
-    if (par->flags & (kFlagConstant | kFlagError)) return;  // the whole grid leaves
-    __shared__ uint32_t s_tile, s_carry, s_words[kEncWarps], s_excl[kEncWarps];
-    __shared__ uint32_t sbuf[kEncWarps][kPieceWords];
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, wib = tid >> 5;
-    const uint32_t epoch = par->enc_epoch;
-    if (tid == 0) s_tile = atomicAdd(a.ctr, 1u);
-    __syncthreads();
-    const uint32_t t = s_tile;
+// Encoder, three launches with no inter-block waiting:
+//   k_enc_bits  one warp per chunk: its words; a block (tile of kEncWarps
+//               chunks) also writes the tile's total
+//   k_enc_scan  one block per field: exclusive prefix of the tile totals, the
+//               section layout and the capacity check
+//   k_enc_pack  one block per tile: chunk word offsets (tile prefix + in-tile
+//               prefix), chunk table entries, MSB-first packing: pieces of 256
+//               symbols (8 per lane) are OR-ed into a per-warp shared-memory
+//               word buffer, full words go out coalesced and the partial last
+//               word carries into the next piece.  Every write is checked
+//               against the output capacity.
+__global__ void __launch_bounds__(kEncWarps * 32) k_enc_bits(const __grid_constant__ Batch<EncArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const EncArgs& a = B.a[fld];
+    const uint32_t t = blockIdx.x - B.off[fld];
+    if (a.par->flags & (kFlagConstant | kFlagError)) return;
+    __shared__ uint32_t s_words[kEncWarps];
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     const uint64_t c = (uint64_t)t * kEncWarps + wib;
     const uint64_t beg = c * a.chunk;
     const uint64_t end = min(beg + a.chunk, a.n);
     const uint32_t bits = (c < a.nchunks) ? warp_chunk_bits(a.codes, a.enc, beg, end, lane) : 0u;
-    if (lane == 0) s_words[wib] = (bits + 31u) >> 5;
+    const uint32_t words = (bits + 31u) >> 5;
+    if (lane == 0) {
+        s_words[wib] = words;
+        if (c < a.nchunks) a.chunk_words[c] = words;
+    }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t sum = 0;
+        for (int w = 0; w < kEncWarps; w++) sum += s_words[w];
+        a.tile_sum[t] = sum;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_enc_scan(const __grid_constant__ Batch<EncArgs> B) {
+    const EncArgs& a = B.a[blockIdx.x];  // one block per field
+    DevParams* par = a.par;
+    if (par->flags & (kFlagConstant | kFlagError)) return;
+    __shared__ uint32_t sh[33];
+    constexpr int IPT = 4;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < a.ntiles; base += 1024u * IPT) {
+        const uint32_t i0 = base + threadIdx.x * IPT;
+        uint32_t v[IPT], sum = 0;
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            v[k] = (i0 + k < a.ntiles) ? a.tile_sum[i0 + k] : 0u;
+            sum += v[k];
+        }
+        uint32_t total;
+        uint32_t ex = block_excl_scan(sum, sh, &total) + carry;
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            if (i0 + k < a.ntiles) a.tile_sum[i0 + k] = ex;
+            ex += v[k];
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        const uint64_t off_st = par->off_ct + pad16(4ull * a.nchunks);
+        const uint64_t off_ou = off_st + pad16(4ull * carry);
+        const uint64_t off_vb = off_ou + pad16(8ull * par->n_out);
+        const uint64_t total = off_vb + pad16(8ull * par->n_vb);
+        par->stream_words = carry;
+        par->off_st = off_st;
+        par->off_ou = off_ou;
+        par->off_vb = off_vb;
+        par->total = total;
+        if (total > par->cap) set_error(par, FPSNR_ECAPACITY);
+    }
+}
+
+__global__ void __launch_bounds__(kEncWarps * 32) k_enc_pack(const __grid_constant__ Batch<EncArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const EncArgs& a = B.a[fld];
+    const uint32_t t = blockIdx.x - B.off[fld];
+    DevParams* par = a.par;
+    if (par->flags & (kFlagConstant | kFlagError)) return;
+    __shared__ uint32_t sbuf[kEncWarps][kPieceWords];
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    const uint64_t c = (uint64_t)t * kEncWarps + wib;
+    if (c >= a.nchunks) return;
     const uint64_t cap = par->cap;
     const uint64_t off_ct = par->off_ct;
-    const uint64_t off_st = off_ct + pad16(4ull * a.nchunks);
-    if (tid < 32) {
-        uint32_t agg = 0;
-        for (int w = 0; w < kEncWarps; w++) agg += s_words[w];
-        if (tid == 0) {
-            uint32_t e = 0;
-            for (int w = 0; w < kEncWarps; w++) {
-                s_excl[w] = e;
-                e += s_words[w];
-            }
-            if (t == 0) {
-                a.inc[0] = agg;
-                __threadfence();
-                st_release(a.flags, (epoch << 2) | kEncP);
-            } else {
-                a.agg[t] = agg;
-                __threadfence();
-                st_release(a.flags + t, (epoch << 2) | kEncA);
-            }
-        }
-        const uint32_t carry = (t == 0) ? 0u : warp_lookback(a.flags, a.agg, a.inc, t, 0, epoch, par);
-        if (tid == 0) {
-            if (t > 0) {
-                a.inc[t] = carry + agg;
-                __threadfence();
-                st_release(a.flags + t, (epoch << 2) | kEncP);
-            }
-            s_carry = carry;
-            if (t == a.ntiles - 1) {
-                const uint32_t words = carry + agg;
-                const uint64_t off_ou = off_st + pad16(4ull * words);
-                const uint64_t off_vb = off_ou + pad16(8ull * par->n_out);
-                const uint64_t total = off_vb + pad16(8ull * par->n_vb);
-                par->stream_words = words;
-                par->off_st = off_st;
-                par->off_ou = off_ou;
-                par->off_vb = off_vb;
-                par->total = total;
-                if (total > cap) set_error(par, FPSNR_ECAPACITY);
-            }
-        }
-    }
-    __syncthreads();
-    if (c < a.nchunks) {
-        uint32_t wpos = s_carry + s_excl[wib];  // first word of the chunk
-        const uint32_t nwc = s_words[wib];
-        if (lane == 0 && off_ct + 4ull * (c + 1) <= cap)
-            reinterpret_cast<uint32_t*>(a.out + off_ct)[c] = wpos;
-        if (off_st + 4ull * ((uint64_t)wpos + nwc) <= cap) {
-            uint32_t* stream = reinterpret_cast<uint32_t*>(a.out + off_st);
-            uint32_t* buf = sbuf[wib];
-            uint32_t carry = 0;  // partial word (bits from previous pieces)
-            uint32_t cbits = 0;  // valid bits in carry (< 32)
-            for (uint64_t pb = beg; pb < end; pb += 256u) {
-                uint32_t cw[8], cl[8];
-                uint32_t mybits = 0;
-                const uint64_t i = pb + 8u * lane;
-                if (i + 8 <= end) {
-                    const uint4 v = *reinterpret_cast<const uint4*>(a.codes + i);
-                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+    const uint64_t off_st = par->off_st;
+    // word offset of this chunk: tile prefix + words of the tile's earlier chunks
+    uint32_t wpos = a.tile_sum[t];
+    const uint64_t c0 = (uint64_t)t * kEncWarps;
+    for (uint64_t k = c0; k < c; k++) wpos += a.chunk_words[k];
+    const uint32_t nwc = a.chunk_words[c];
+    if (lane == 0 && off_ct + 4ull * (c + 1) <= cap)
+        reinterpret_cast<uint32_t*>(a.out + off_ct)[c] = wpos;
+    if (off_st + 4ull * ((uint64_t)wpos + nwc) > cap) return;
+    const uint64_t beg = c * a.chunk;
+    const uint64_t end = min(beg + a.chunk, a.n);
+    uint32_t* stream = reinterpret_cast<uint32_t*>(a.out + off_st);
+    uint32_t* buf = sbuf[wib];
+    uint32_t carry = 0;  // partial word (bits from previous pieces)
+    uint32_t cbits = 0;  // valid bits in carry (< 32)
+    for (uint64_t pb = beg; pb < end; pb += 256u) {
+        uint32_t cw[8], cl[8];
+        uint32_t mybits = 0;
+        const uint64_t i = pb + 8u * lane;
+        if (i + 8 <= end) {
+            const uint4 v = *reinterpret_cast<const uint4*>(a.codes + i);
+            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        const uint32_t e0 = __ldg(a.enc + (wv[k] & 0xffffu));
-                        const uint32_t e1 = __ldg(a.enc + (wv[k] >> 16));
-                        cw[2 * k] = e0 >> 5; cl[2 * k] = e0 & 31u;
-                        cw[2 * k + 1] = e1 >> 5; cl[2 * k + 1] = e1 & 31u;
-                    }
+            for (int k = 0; k < 4; k++) {
+                const uint32_t e0 = __ldg(a.enc + (wv[k] & 0xffffu));
+                const uint32_t e1 = __ldg(a.enc + (wv[k] >> 16));
+                cw[2 * k] = e0 >> 5; cl[2 * k] = e0 & 31u;
+                cw[2 * k + 1] = e1 >> 5; cl[2 * k + 1] = e1 & 31u;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const uint32_t e = (i + k < end) ? __ldg(a.enc + a.codes[i + k]) : 0u;
+                cw[k] = e >> 5; cl[k] = e & 31u;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) mybits += cl[k];
+        uint32_t incl = mybits;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        const uint32_t piece_bits = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t nw = (cbits + piece_bits + 31u) >> 5;
+        for (uint32_t k = lane; k < nw; k += 32) buf[k] = 0u;
+        __syncwarp();
+        if (lane == 0) buf[0] = carry;
+        __syncwarp();
+        uint32_t bp = cbits + incl - mybits;  // bit position in buf
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint32_t l = cl[k];
+            if (l) {
+                const uint32_t w = bp >> 5, o = bp & 31u;
+                if (o + l <= 32u) {
+                    atomicOr(&buf[w], cw[k] << (32u - o - l));
                 } else {
-#pragma unroll
-                    for (int k = 0; k < 8; k++) {
-                        const uint32_t e = (i + k < end) ? __ldg(a.enc + a.codes[i + k]) : 0u;
-                        cw[k] = e >> 5; cl[k] = e & 31u;
-                    }
+                    atomicOr(&buf[w], cw[k] >> (o + l - 32u));
+                    atomicOr(&buf[w + 1], cw[k] << (64u - o - l));
                 }
-#pragma unroll
-                for (int k = 0; k < 8; k++) mybits += cl[k];
-                uint32_t incl = mybits;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= (uint32_t)o) incl += y;
-                }
-                const uint32_t piece_bits = __shfl_sync(0xffffffffu, incl, 31);
-                const uint32_t nw = (cbits + piece_bits + 31u) >> 5;
-                for (uint32_t k = lane; k < nw; k += 32) buf[k] = 0u;
-                __syncwarp();
-                if (lane == 0) buf[0] = carry;
-                __syncwarp();
-                uint32_t bp = cbits + incl - mybits;  // bit position in buf
-#pragma unroll
-                for (int k = 0; k < 8; k++) {
-                    const uint32_t l = cl[k];
-                    if (l) {
-                        const uint32_t w = bp >> 5, o = bp & 31u;
-                        if (o + l <= 32u) {
-                            atomicOr(&buf[w], cw[k] << (32u - o - l));
-                        } else {
-                            atomicOr(&buf[w], cw[k] >> (o + l - 32u));
-                            atomicOr(&buf[w + 1], cw[k] << (64u - o - l));
-                        }
-                        bp += l;
-                    }
-                }
-                __syncwarp();
-                const uint32_t tot = cbits + piece_bits;
-                const uint32_t full = tot >> 5;
-                for (uint32_t k = lane; k < full; k += 32) stream[wpos + k] = buf[k];
-                carry = (tot & 31u) ? buf[full] : 0u;
-                cbits = tot & 31u;
-                wpos += full;
-                __syncwarp();
+                bp += l;
             }
-            if (cbits && lane == 0) stream[wpos] = carry;
         }
+        __syncwarp();
+        const uint32_t tot = cbits + piece_bits;
+        const uint32_t full = tot >> 5;
+        for (uint32_t k = lane; k < full; k += 32) stream[wpos + k] = buf[k];
+        carry = (tot & 31u) ? buf[full] : 0u;
+        cbits = tot & 31u;
+        wpos += full;
+        __syncwarp();
     }
-    if (tid == 0 && atomicAdd(a.ctr + 1, 1u) == a.ntiles - 1) {
-        a.ctr[0] = 0;
-        a.ctr[1] = 0;
-    }
+    if (cbits && lane == 0) stream[wpos] = carry;
 }
 
 // Outliers and verbatims in ascending index: rank = number of set bitmap bits
 // before the index.
-__global__ void __launch_bounds__(256) k_emit(const DevParams* __restrict__ par,
-                                              const uint2* __restrict__ stage_out,
-                                              const uint2* __restrict__ stage_vb,
-                                              const uint32_t* __restrict__ bm,
-                                              const uint32_t* __restrict__ wpre,
-                                              const uint32_t* __restrict__ bpre, uint8_t* out,
-                                              uint64_t nwords, uint32_t nbmblk) {
+struct EmitArgs {
+    const DevParams* par;
+    const uint2* stage_out;
+    const uint2* stage_vb;
+    const uint32_t* bm;
+    const uint32_t* wpre;
+    const uint32_t* bpre;
+    uint8_t* out;
+    uint64_t nwords;
+    uint32_t nbmblk;
+    uint32_t G;  // blocks per list
+};
+
+__global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Batch<EmitArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const EmitArgs& A = B.a[fld];
+    const uint32_t bid = blockIdx.x - B.off[fld];
+    const DevParams* par = A.par;
+    const uint2* stage_out = A.stage_out;
+    const uint2* stage_vb = A.stage_vb;
+    const uint32_t* bm = A.bm;
+    const uint32_t* wpre = A.wpre;
+    const uint32_t* bpre = A.bpre;
+    uint8_t* out = A.out;
+    const uint64_t nwords = A.nwords;
+    const uint32_t nbmblk = A.nbmblk;
     if (par->flags & (kFlagConstant | kFlagError)) return;
-    const uint32_t list = blockIdx.y;
+    const uint32_t list = bid / A.G;
+    const uint32_t lb = bid % A.G;
     const uint32_t cnt = list == 0 ? par->n_out : par->n_vb;
     const uint2* stage = list == 0 ? stage_out : stage_vb;
     uint2* dst = reinterpret_cast<uint2*>(out + (list == 0 ? par->off_ou : par->off_vb));
     const uint32_t* b = bm + list * nwords;
     const uint32_t* wp = wpre + list * nwords;
     const uint32_t* bp = bpre + list * nbmblk;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    for (uint32_t i = lb * blockDim.x + threadIdx.x; i < cnt; i += A.G * blockDim.x) {
         uint2 e = stage[i];
         const uint32_t idx = e.x, w = idx >> 5;
         const uint32_t r = bp[w >> 10] + wp[w] + __popc(b[w] & ((1u << (idx & 31u)) - 1u));
@@ -670,21 +738,43 @@ __global__ void __launch_bounds__(256) k_emit(const DevParams* __restrict__ par,
     }
 }
 
-__global__ void __launch_bounds__(256) k_finalize(DevParams* par, uint32_t* bm,
-                                                  const uint2* __restrict__ stage_out,
-                                                  const uint2* __restrict__ stage_vb,
-                                                  uint8_t* out, uint64_t* out_bytes,
-                                                  fpsnr_stats* stats, int ndim, int ld,
-                                                  uint64_t d0, uint64_t d1, uint64_t d2,
-                                                  uint64_t n, int radius, int chunk, int lmax,
-                                                  uint64_t nchunks, uint64_t nwords) {
+struct FinArgs {
+    DevParams* par;
+    uint32_t* bm;
+    const uint2* stage_out;
+    const uint2* stage_vb;
+    uint8_t* out;
+    uint64_t* out_bytes;
+    fpsnr_stats* stats;
+    int ndim, ld;
+    uint64_t d0, d1, d2, n;
+    int radius, chunk, lmax;
+    uint64_t nchunks, nwords;
+    uint32_t G;  // blocks per field
+};
+
+__global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ Batch<FinArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const FinArgs& A = B.a[fld];
+    const uint32_t bid = blockIdx.x - B.off[fld];
+    DevParams* par = A.par;
+    uint32_t* bm = A.bm;
+    const uint2* stage_out = A.stage_out;
+    const uint2* stage_vb = A.stage_vb;
+    uint8_t* out = A.out;
+    uint64_t* out_bytes = A.out_bytes;
+    fpsnr_stats* stats = A.stats;
+    const int ndim = A.ndim, ld = A.ld;
+    const uint64_t d0 = A.d0, d1 = A.d1, d2 = A.d2, n = A.n;
+    const int radius = A.radius, chunk = A.chunk, lmax = A.lmax;
+    const uint64_t nchunks = A.nchunks, nwords = A.nwords;
     // clear the membership bitmaps (only the words that were set)
     const uint32_t no = par->n_out, nv = par->n_vb;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < no; i += gridDim.x * blockDim.x)
+    for (uint32_t i = bid * blockDim.x + threadIdx.x; i < no; i += A.G * blockDim.x)
         bm[stage_out[i].x >> 5] = 0u;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x)
+    for (uint32_t i = bid * blockDim.x + threadIdx.x; i < nv; i += A.G * blockDim.x)
         bm[nwords + (stage_vb[i].x >> 5)] = 0u;
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    if (bid != 0 || threadIdx.x != 0) return;
 
     uint32_t flags = par->flags;
     if ((flags & kFlagConstant) && !(flags & kFlagError) && par->cap < kHeaderBytes) {
@@ -767,114 +857,225 @@ __global__ void __launch_bounds__(256) k_finalize(DevParams* par, uint32_t* bm,
 // host launcher
 // ---------------------------------------------------------------------------
 
-#define FP_LAUNCH_CHECK()                                \
-    do {                                                 \
+#define FP_LAUNCH_CHECK()                                          \
+    do {                                                           \
         if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA; \
     } while (0)
 
+// Launches one k_pq variant over the fields of a batch that use it.
 template <int MODE, int TX, int TY>
-static void launch_pq_t(const fpsnr_plan_s* p, const float* d_in, const PQArgs& a, cudaStream_t st) {
-    dim3 blk(TX / 4, TY);
-    if (p->pq.vec)
-        k_pq<MODE, TX, TY, true><<<p->pq.nblocks, blk, 0, st>>>(d_in, a);
-    else
-        k_pq<MODE, TX, TY, false><<<p->pq.nblocks, blk, 0, st>>>(d_in, a);
+static void launch_pq_t(Batch<PQArgs>& b, uint32_t blocks, bool vec, cudaStream_t st) {
+    const dim3 blk(TX / 4, TY);
+    if (vec) k_pq<MODE, TX, TY, true><<<blocks, blk, 0, st>>>(b);
+    else k_pq<MODE, TX, TY, false><<<blocks, blk, 0, st>>>(b);
 }
 
-static void launch_pq(const fpsnr_plan_s* p, const float* d_in, const PQArgs& a, cudaStream_t st) {
-    const PQGeom& g = p->pq;
-    if (g.mode == 1) {
-        launch_pq_t<1, 512, 1>(p, d_in, a, st);
-    } else if (g.mode == 2) {
-        if (g.tx == 128) launch_pq_t<2, 128, 1>(p, d_in, a, st);
-        else if (g.tx == 256) launch_pq_t<2, 256, 1>(p, d_in, a, st);
-        else launch_pq_t<2, 512, 1>(p, d_in, a, st);
-    } else {
-        launch_pq_t<3, 128, 8>(p, d_in, a, st);
+static void launch_pq_variant(int mode, int tx, Batch<PQArgs>& b, uint32_t blocks, bool vec,
+                              cudaStream_t st) {
+    if (mode == 1) launch_pq_t<1, 512, 1>(b, blocks, vec, st);
+    else if (mode == 3) launch_pq_t<3, 128, 8>(b, blocks, vec, st);
+    else if (tx == 128) launch_pq_t<2, 128, 1>(b, blocks, vec, st);
+    else if (tx == 256) launch_pq_t<2, 256, 1>(b, blocks, vec, st);
+    else launch_pq_t<2, 512, 1>(b, blocks, vec, st);
+}
+
+// Small grid-stride kernels (emit, finalize) use this many blocks per field.
+static uint32_t small_blocks(const fpsnr_plan_s* p, int count) {
+    const uint32_t g = (uint32_t)std::max(1, p->sm_count / std::max(1, count));
+    return std::min<uint32_t>(g, 64);
+}
+
+int launch_compress_batch(fpsnr_plan_s* const* P, const float* const* d_in, void* const* d_out,
+                          const uint64_t* caps, uint64_t* d_out_bytes, fpsnr_stats* d_stats,
+                          int count, cudaStream_t st) {
+    if (count <= 0) return FPSNR_OK;
+    if (count > kMaxBatch) {
+        for (int b0 = 0; b0 < count; b0 += kMaxBatch) {
+            const int c = std::min(kMaxBatch, count - b0);
+            int rc = launch_compress_batch(P + b0, d_in + b0, d_out + b0, caps + b0,
+                                           d_out_bytes ? d_out_bytes + b0 : nullptr,
+                                           d_stats ? d_stats + b0 : nullptr, c, st);
+            if (rc) return rc;
+        }
+        return FPSNR_OK;
     }
-}
+    fp::Profiler& prof = P[0]->prof;  // batched launches are attributed to the first plan
+    uint32_t blocks[kMaxBatch];
 
-int launch_compress(fpsnr_plan_s* p, const float* d_in, void* d_out, uint64_t cap,
-                    uint64_t* d_out_bytes, fpsnr_stats* d_stats, cudaStream_t st) {
-    const Workspace& w = p->w;
-    const bool vec_in = ((uintptr_t)d_in & 15u) == 0;
+    // ---- range + plan scalars ----
     {
-    StageScope sc(p->prof, kStRange, st);
-    if (vec_in)
-        k_range_plan<true><<<p->n_range_blocks, 512, 0, st>>>(d_in, p->n, w.par, w.range_part,
-                                                              w.hist, p->nsym, p->eb_rel,
-                                                              p->target_psnr, cap, w.enc_ctr);
-    else
-        k_range_plan<false><<<p->n_range_blocks, 512, 0, st>>>(d_in, p->n, w.par, w.range_part,
-                                                               w.hist, p->nsym, p->eb_rel,
-                                                               p->target_psnr, cap, w.enc_ctr);
+        Batch<RangeArgs> b;
+        b.count = (uint32_t)count;
+        for (int f = 0; f < count; f++) {
+            const fpsnr_plan_s* p = P[f];
+            const Workspace& w = p->w;
+            b.a[f] = RangeArgs{d_in[f], p->n, w.par, w.range_part, w.hist, p->nsym, p->eb_rel,
+                               p->target_psnr, caps[f],
+                               ((uintptr_t)d_in[f] & 15u) == 0};
+            blocks[f] = p->n_range_blocks;
+        }
+        const uint32_t tot = batch_offsets(b, blocks);
+        StageScope sc(prof, kStRange, st);
+        k_range_plan<<<tot, 512, 0, st>>>(b);
     }
     FP_LAUNCH_CHECK();
-    if (p->n > 0) {
-        PQArgs a;
-        a.par = w.par;
-        a.codes = w.codes;
-        a.hist = w.hist;
-        a.stage_out = w.stage_out;
-        a.stage_vb = w.stage_vb;
-        a.bm_out = w.bm;
-        a.bm_vb = w.bm + p->nwords;
-        a.sse_part = w.sse_part;
-        a.n = p->n;
-        a.vx = p->pq.vx;
-        a.vy = p->pq.vy;
-        a.vz = p->pq.vz;
-        a.zs = (uint32_t)p->pq.zs;
-        a.nbx = p->pq.nbx;
-        a.nby = p->pq.nby;
-        a.radius = p->radius;
-        PQGeom g = p->pq;
-        fpsnr_plan_s tmp = *p;
-        tmp.pq.vec = g.vec && vec_in;
-        {
-            StageScope sc(p->prof, kStPq, st);
-            launch_pq(&tmp, d_in, a, st);
+
+    // ---- predictor: one launch per kernel variant present in the batch ----
+    {
+        Batch<PQArgs> b;
+        bool done[kMaxBatch] = {};
+        for (int f0 = 0; f0 < count; f0++) {
+            if (done[f0] || P[f0]->n == 0) continue;
+            const PQGeom& g0 = P[f0]->pq;
+            const bool vec0 = g0.vec && ((uintptr_t)d_in[f0] & 15u) == 0;
+            b.count = 0;
+            for (int f = f0; f < count; f++) {
+                const fpsnr_plan_s* p = P[f];
+                const PQGeom& g = p->pq;
+                const bool vec = g.vec && ((uintptr_t)d_in[f] & 15u) == 0;
+                if (done[f] || p->n == 0 || g.mode != g0.mode || g.tx != g0.tx || vec != vec0) continue;
+                done[f] = true;
+                const Workspace& w = p->w;
+                PQArgs a;
+                a.x = d_in[f];
+                a.par = w.par;
+                a.codes = w.codes;
+                a.hist = w.hist;
+                a.stage_out = w.stage_out;
+                a.stage_vb = w.stage_vb;
+                a.bm_out = w.bm;
+                a.bm_vb = w.bm + p->nwords;
+                a.sse_part = w.sse_part;
+                a.n = p->n;
+                a.vx = g.vx;
+                a.vy = g.vy;
+                a.vz = g.vz;
+                a.zs = (uint32_t)g.zs;
+                a.nbx = g.nbx;
+                a.nby = g.nby;
+                a.radius = p->radius;
+                blocks[b.count] = g.nblocks;
+                b.a[b.count++] = a;
+            }
+            const uint32_t tot = batch_offsets(b, blocks);
+            StageScope sc(prof, kStPq, st);
+            launch_pq_variant(g0.mode, g0.tx, b, tot, vec0, st);
+            FP_LAUNCH_CHECK();
         }
-        FP_LAUNCH_CHECK();
-        StageScope sc(p->prof, kStRank, st);
-        k_rank_popc<<<dim3((unsigned)p->nbmblk, 2), 1024, 0, st>>>(w.par, w.bm, w.wpre, w.bpre,
-                                                                 p->nwords, (uint32_t)p->nbmblk);
-        FP_LAUNCH_CHECK();
     }
-    int rc = launch_codebook(p, d_out, st);
+
+    // ---- order-preserving ranks of outliers / verbatims ----
+    {
+        Batch<RankArgs> b;
+        b.count = (uint32_t)count;
+        for (int f = 0; f < count; f++) {
+            const fpsnr_plan_s* p = P[f];
+            const Workspace& w = p->w;
+            b.a[f] = RankArgs{w.par, w.bm, w.wpre, w.bpre, p->nwords, (uint32_t)p->nbmblk};
+            blocks[f] = p->n ? 2u * (uint32_t)p->nbmblk : 0u;
+        }
+        const uint32_t tot = batch_offsets(b, blocks);
+        if (tot) {
+            StageScope sc(prof, kStRank, st);
+            k_rank_popc<<<tot, 1024, 0, st>>>(b);
+            FP_LAUNCH_CHECK();
+        }
+    }
+
+    // ---- codebook ----
+    int rc = launch_codebook_batch(P, d_out, count, st);
     if (rc) return rc;
-    uint8_t* out = reinterpret_cast<uint8_t*>(d_out);
-    if (p->n > 0) {
-        EncArgs e;
-        e.par = w.par;
-        e.codes = w.codes;
-        e.enc = w.enc;
-        e.out = out;
-        e.n = p->n;
-        e.chunk = (uint32_t)p->chunk;
-        e.nchunks = p->nchunks;
-        e.ntiles = (uint32_t)((p->nchunks + kEncWarps - 1) / kEncWarps);
-        e.flags = w.enc_flags;
-        e.agg = w.enc_flags + e.ntiles;
-        e.inc = w.enc_flags + 2 * (uint64_t)e.ntiles;
-        e.ctr = w.enc_ctr;
-        {
-            StageScope sc(p->prof, kStEncode, st);
-            k_encode<<<e.ntiles, kEncWarps * 32, 0, st>>>(e);
+
+    // ---- encoder: chunk words, tile prefix, packing ----
+    {
+        Batch<EncArgs> b;
+        b.count = (uint32_t)count;
+        for (int f = 0; f < count; f++) {
+            const fpsnr_plan_s* p = P[f];
+            const Workspace& w = p->w;
+            EncArgs e;
+            e.par = w.par;
+            e.codes = w.codes;
+            e.enc = w.enc;
+            e.out = reinterpret_cast<uint8_t*>(d_out[f]);
+            e.n = p->n;
+            e.chunk = (uint32_t)p->chunk;
+            e.nchunks = p->nchunks;
+            e.ntiles = (uint32_t)((p->nchunks + kEncWarps - 1) / kEncWarps);
+            e.chunk_words = w.chunk_off;
+            e.tile_sum = w.enc_tiles;
+            b.a[f] = e;
+            blocks[f] = p->n ? e.ntiles : 0u;
         }
-        FP_LAUNCH_CHECK();
-        StageScope sc(p->prof, kStEmit, st);
-        k_emit<<<dim3((unsigned)p->sm_count, 2), 256, 0, st>>>(w.par, w.stage_out, w.stage_vb, w.bm,
-                                                             w.wpre, w.bpre, out, p->nwords,
-                                                             (uint32_t)p->nbmblk);
+        const uint32_t tot = batch_offsets(b, blocks);
+        if (tot) {
+            StageScope sc(prof, kStEncode, st);
+            k_enc_bits<<<tot, kEncWarps * 32, 0, st>>>(b);
+            FP_LAUNCH_CHECK();
+            for (int f = 0; f <= count; f++) b.off[f] = (uint32_t)f;
+            k_enc_scan<<<count, 1024, 0, st>>>(b);
+            FP_LAUNCH_CHECK();
+            batch_offsets(b, blocks);
+            k_enc_pack<<<tot, kEncWarps * 32, 0, st>>>(b);
+            FP_LAUNCH_CHECK();
+        }
+    }
+
+    // ---- outliers / verbatims in index order ----
+    {
+        Batch<EmitArgs> b;
+        b.count = (uint32_t)count;
+        for (int f = 0; f < count; f++) {
+            const fpsnr_plan_s* p = P[f];
+            const Workspace& w = p->w;
+            const uint32_t G = small_blocks(p, count);
+            b.a[f] = EmitArgs{w.par, w.stage_out, w.stage_vb, w.bm, w.wpre, w.bpre,
+                              reinterpret_cast<uint8_t*>(d_out[f]), p->nwords, (uint32_t)p->nbmblk, G};
+            blocks[f] = p->n ? 2 * G : 0u;
+        }
+        const uint32_t tot = batch_offsets(b, blocks);
+        if (tot) {
+            StageScope sc(prof, kStEmit, st);
+            k_emit<<<tot, 256, 0, st>>>(b);
+            FP_LAUNCH_CHECK();
+        }
+    }
+
+    // ---- header, size, statistics, bitmap clearing ----
+    {
+        Batch<FinArgs> b;
+        b.count = (uint32_t)count;
+        for (int f = 0; f < count; f++) {
+            const fpsnr_plan_s* p = P[f];
+            const Workspace& w = p->w;
+            FinArgs a;
+            a.par = w.par;
+            a.bm = w.bm;
+            a.stage_out = w.stage_out;
+            a.stage_vb = w.stage_vb;
+            a.out = reinterpret_cast<uint8_t*>(d_out[f]);
+            a.out_bytes = d_out_bytes ? d_out_bytes + f : nullptr;
+            a.stats = d_stats ? d_stats + f : nullptr;
+            a.ndim = p->ndim;
+            a.ld = p->ld;
+            a.d0 = p->dims[0];
+            a.d1 = p->dims[1];
+            a.d2 = p->dims[2];
+            a.n = p->n;
+            a.radius = p->radius;
+            a.chunk = p->chunk;
+            a.lmax = p->lmax;
+            a.nchunks = p->nchunks;
+            a.nwords = p->nwords;
+            a.G = small_blocks(p, count);
+            b.a[f] = a;
+            blocks[f] = a.G;
+        }
+        const uint32_t tot = batch_offsets(b, blocks);
+        StageScope sc(prof, kStFinalize, st);
+        k_finalize<<<tot, 256, 0, st>>>(b);
         FP_LAUNCH_CHECK();
     }
-    StageScope sc(p->prof, kStFinalize, st);
-    k_finalize<<<(unsigned)p->sm_count, 256, 0, st>>>(
-        w.par, w.bm, w.stage_out, w.stage_vb, out, d_out_bytes, d_stats, p->ndim, p->ld,
-        p->dims[0], p->dims[1], p->dims[2], p->n, p->radius, p->chunk, p->lmax, p->nchunks,
-        p->nwords);
-    FP_LAUNCH_CHECK();
     return FPSNR_OK;
 }
 

@@ -18,6 +18,8 @@
 // The prefix sums run in modular uint32 arithmetic: intermediate partial sums
 // may leave the int32 range, but every final lattice value is in [0, 2^31),
 // so the modular result is exact.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace fp {
@@ -30,11 +32,32 @@ __device__ __forceinline__ uint64_t rd64(const uint8_t* b, uint64_t o) {
 }
 static __device__ __forceinline__ uint64_t pad16d(uint64_t b) { return (b + 15u) & ~(uint64_t)15u; }
 
-__global__ void __launch_bounds__(1024) k_dsetup(DevParams* par, const uint8_t* __restrict__ blob,
-                                                 uint64_t bytes, int ndim, int ld, uint64_t d0,
-                                                 uint64_t d1, uint64_t d2, uint64_t n,
-                                                 uint32_t chunk, uint64_t nchunks, uint32_t* lut,
-                                                 uint16_t* syms, uint32_t* lb_ctr) {
+struct DsetupArgs {
+    DevParams* par;
+    const uint8_t* blob;
+    uint64_t bytes;
+    int ndim, ld;
+    uint64_t d0, d1, d2, n;
+    uint32_t chunk;
+    uint64_t nchunks;
+    uint32_t* lut;
+    uint16_t* syms;
+    uint32_t* lb_ctr;
+};
+
+// one block per field
+__global__ void __launch_bounds__(1024) k_dsetup(const __grid_constant__ Batch<DsetupArgs> B) {
+    const DsetupArgs& A = B.a[blockIdx.x];
+    DevParams* par = A.par;
+    const uint8_t* __restrict__ blob = A.blob;
+    const uint64_t bytes = A.bytes;
+    const int ndim = A.ndim, ld = A.ld;
+    const uint64_t d0 = A.d0, d1 = A.d1, d2 = A.d2, n = A.n;
+    const uint32_t chunk = A.chunk;
+    const uint64_t nchunks = A.nchunks;
+    uint32_t* lut = A.lut;
+    uint16_t* syms = A.syms;
+    uint32_t* lb_ctr = A.lb_ctr;
     __shared__ int s_ok;
     __shared__ uint32_t s_cnt[32];
     __shared__ unsigned long long s_kraft;
@@ -166,18 +189,37 @@ __global__ void __launch_bounds__(1024) k_dsetup(DevParams* par, const uint8_t* 
 // and written as two 16-byte stores into the thread's own chunk.  Codes longer
 // than the table are located by comparing the left-justified window with the
 // end of each length's canonical range.
-constexpr int kDecThreads = 64;
+constexpr int kDecThreads = 256;  // chunks per decode block
 constexpr int kMaxDynSmem = 227 * 1024;
 
 // STAGED = false (chunks too large for the window to fit shared memory): the
 // words are read from global memory directly.
-template <bool STAGED>
-__global__ void __launch_bounds__(kDecThreads) k_decode(DevParams* par, const uint8_t* __restrict__ blob,
-                                                        const uint32_t* __restrict__ lut_g,
-                                                        const uint16_t* __restrict__ syms,
-                                                        int32_t* __restrict__ out, uint64_t n,
-                                                        uint32_t chunk, uint64_t nchunks,
-                                                        uint32_t win_cap) {
+struct DecArgs {
+    DevParams* par;
+    const uint8_t* blob;
+    const uint32_t* lut_g;
+    const uint16_t* syms;
+    int32_t* out;
+    uint64_t n;
+    uint32_t chunk;
+    uint64_t nchunks;
+    uint32_t win_cap;
+};
+
+template <bool STAGED, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_decode(const __grid_constant__ Batch<DecArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const DecArgs& A = B.a[fld];
+    const uint32_t bid = blockIdx.x - B.off[fld];
+    DevParams* par = A.par;
+    const uint8_t* __restrict__ blob = A.blob;
+    const uint32_t* __restrict__ lut_g = A.lut_g;
+    const uint16_t* __restrict__ syms = A.syms;
+    int32_t* __restrict__ out = A.out;
+    const uint64_t n = A.n;
+    const uint32_t chunk = A.chunk;
+    const uint64_t nchunks = A.nchunks;
+    const uint32_t win_cap = A.win_cap;
     extern __shared__ __align__(16) uint32_t dsw[];
     uint32_t* slut = dsw;                   // 1 << kLutBits entries
     uint32_t* sw = dsw + (1u << kLutBits);  // the block's stream words (from a 16-byte boundary)
@@ -188,9 +230,9 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DevParams* par, const ui
     const uint32_t flags = par->flags;
     if (flags & kFlagError) return;
     const bool cst = (flags & kFlagConstant) != 0;
-    const uint64_t cb0 = (uint64_t)blockIdx.x * kDecThreads;
+    const uint64_t cb0 = (uint64_t)bid * THREADS;
     const uint64_t c = cb0 + threadIdx.x;
-    const uint64_t cb1 = min(cb0 + kDecThreads, nchunks);
+    const uint64_t cb1 = min(cb0 + THREADS, nchunks);
     if (cst) {
         if (c < nchunks) {
             const uint64_t beg = c * chunk, end = min(beg + chunk, n);
@@ -212,8 +254,8 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DevParams* par, const ui
         s_lje[32] = ~0ull;
         const uint32_t ws = tab[cb0];
         const uint32_t we = (cb1 < nchunks) ? tab[cb1] : words;
-        // a non-monotone table or an oversized chunk cannot come from the encoder
-        const bool bad = ws > we || we > words || (STAGED && we - ws > win_cap);
+        // a non-monotone table cannot come from the encoder
+        const bool bad = ws > we || we > words;
         if (bad) set_error(par, FPSNR_ECORRUPT);
         s_bad = bad;
         s_ws = bad ? 0 : ws;
@@ -223,10 +265,12 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DevParams* par, const ui
     __syncthreads();
     if (s_bad) return;
     const uint32_t ws = s_ws, we = s_we;
+    // the window is staged only when it fits; otherwise this block reads global memory
+    const bool staged = STAGED && (((we + 3u) & ~3u) - (ws & ~3u)) <= win_cap + 4u;
     // the look-up table and the 16-byte aligned cover of the window arrive by two
     // bulk copies (the stream section is padded to 16 bytes, so the cover stays in it)
     const uint32_t ws_al = ws & ~3u;
-    const uint32_t win_bytes = STAGED ? (((we + 3u) & ~3u) - ws_al) * 4u : 0u;
+    const uint32_t win_bytes = staged ? (((we + 3u) & ~3u) - ws_al) * 4u : 0u;
     if (threadIdx.x == 0) {
         const uint32_t lut_bytes = (1u << kLutBits) * 4u;
         mbar_arrive_expect_tx(&s_mbar, lut_bytes + win_bytes);
@@ -247,10 +291,13 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DevParams* par, const ui
     const uint32_t w0 = tab[c];
     const uint32_t w1 = (c + 1 < nchunks) ? tab[c + 1] : words;
     if (w0 > w1 || w0 < ws || w1 > we) { set_error(par, FPSNR_ECORRUPT); return; }
-    auto word = [&](uint32_t k) -> uint32_t { return STAGED ? sw[k - ws_al] : __ldg(stream + k); };
+    auto word = [&](uint32_t k) -> uint32_t { return staged ? sw[k - ws_al] : __ldg(stream + k); };
     uint64_t buf = 0;
     uint32_t nb = 0, wi = w0;
+    // the next two words are always in flight (a global load takes several
+    // refills' worth of symbols to arrive)
     uint32_t nxt = wi < w1 ? word(wi) : 0u;
+    uint32_t nxt2 = wi + 1 < w1 ? word(wi + 1) : 0u;
     bool bad = false;
     // decodes one residual; sets `bad` on a malformed stream
     auto one = [&]() -> int32_t {
@@ -258,7 +305,8 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DevParams* par, const ui
             buf |= (uint64_t)nxt << (32 - nb);
             nb += 32;
             wi++;
-            nxt = wi < w1 ? word(wi) : 0u;
+            nxt = nxt2;
+            nxt2 = wi + 1 < w1 ? word(wi + 1) : 0u;
         }
         const uint32_t e = slut[(uint32_t)(buf >> (64 - kLutBits))];
         uint32_t l = e & 0xffu, sym = e >> 8;
@@ -292,31 +340,52 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DevParams* par, const ui
     }
 }
 
-__global__ void __launch_bounds__(256) k_scatter(DevParams* par, const uint8_t* __restrict__ blob,
-                                                 int32_t* out, uint64_t n) {
+struct SmallArgs {
+    DevParams* par;
+    const uint8_t* blob;
+    void* out;
+    uint64_t n;
+    uint32_t G;       // blocks per field
+    int* status;      // k_status only
+};
+
+__global__ void __launch_bounds__(256) k_scatter(const __grid_constant__ Batch<SmallArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const SmallArgs& A = B.a[fld];
+    const uint32_t bid = blockIdx.x - B.off[fld];
+    DevParams* par = A.par;
     if (par->flags & kFlagError) return;
     const uint32_t no = par->d_nout;
-    const uint2* ol = reinterpret_cast<const uint2*>(blob + par->off_ou);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < no; i += gridDim.x * blockDim.x) {
+    const uint2* ol = reinterpret_cast<const uint2*>(A.blob + par->off_ou);
+    int32_t* out = reinterpret_cast<int32_t*>(A.out);
+    for (uint32_t i = bid * blockDim.x + threadIdx.x; i < no; i += A.G * blockDim.x) {
         const uint2 e = ol[i];
-        if (e.x >= n) { set_error(par, FPSNR_ECORRUPT); return; }
+        if (e.x >= A.n) { set_error(par, FPSNR_ECORRUPT); return; }
         out[e.x] = (int32_t)e.y;
     }
 }
 
-__global__ void __launch_bounds__(256) k_patch(DevParams* par, const uint8_t* __restrict__ blob,
-                                               float* out, uint64_t n) {
+__global__ void __launch_bounds__(256) k_patch(const __grid_constant__ Batch<SmallArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const SmallArgs& A = B.a[fld];
+    const uint32_t bid = blockIdx.x - B.off[fld];
+    DevParams* par = A.par;
     if (par->flags & kFlagError) return;
     const uint32_t nv = par->d_nvb;
-    const uint2* vl = reinterpret_cast<const uint2*>(blob + par->off_vb);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
+    const uint2* vl = reinterpret_cast<const uint2*>(A.blob + par->off_vb);
+    float* out = reinterpret_cast<float*>(A.out);
+    for (uint32_t i = bid * blockDim.x + threadIdx.x; i < nv; i += A.G * blockDim.x) {
         const uint2 e = vl[i];
-        if (e.x >= n) { set_error(par, FPSNR_ECORRUPT); return; }
+        if (e.x >= A.n) { set_error(par, FPSNR_ECORRUPT); return; }
         out[e.x] = __uint_as_float(e.y);
     }
 }
 
-__global__ void k_status(const DevParams* par, int* status) { *status = par->status; }
+// one thread per field
+__global__ void k_status(const __grid_constant__ Batch<SmallArgs> B) {
+    const SmallArgs& A = B.a[blockIdx.x];
+    if (threadIdx.x == 0 && A.status) *A.status = A.par->status;
+}
 
 // ---------------------------------------------------------------------------
 // decoupled look-back helpers
@@ -346,7 +415,8 @@ __device__ __forceinline__ void tile_done(uint32_t* ctr, uint32_t tiles) {
 
 // Contiguous rows: each tile is 256*IPT consecutive points of one row.
 template <int IPT, bool FINAL, bool VEC>
-__global__ void __launch_bounds__(256) k_scan_contig(ScanArgs a) {
+__global__ void __launch_bounds__(256) k_scan_contig(const __grid_constant__ Batch<ScanArgs> B) {
+    const ScanArgs& a = B.a[batch_field(B.off, B.count, blockIdx.x)];
     __shared__ uint32_t sh[33];
     __shared__ uint32_t s_id, s_carry;
     const uint32_t tid = threadIdx.x;
@@ -430,7 +500,8 @@ __global__ void __launch_bounds__(256) k_scan_contig(ScanArgs a) {
 // Strided scan along the middle axis of (A, L, B): a tile is SEG consecutive
 // rows of the scan axis by 256*CPT consecutive inner columns.
 template <int SEG, int CPT, bool FINAL>
-__global__ void __launch_bounds__(256) k_scan_strided(ScanArgs a) {
+__global__ void __launch_bounds__(256) k_scan_strided(const __grid_constant__ Batch<ScanArgs> B) {
+    const ScanArgs& a = B.a[batch_field(B.off, B.count, blockIdx.x)];
     constexpr uint32_t TB = 256u * CPT;
     __shared__ uint32_t s_id, s_st;
     const uint32_t tid = threadIdx.x;
@@ -570,101 +641,193 @@ __global__ void __launch_bounds__(256) k_scan_strided(ScanArgs a) {
 // ---------------------------------------------------------------------------
 
 template <int IPT, bool FINAL>
-static void launch_contig_t(const ScanArgs& a, bool vec, cudaStream_t st) {
-    if (vec) k_scan_contig<IPT, FINAL, true><<<a.tiles, 256, 0, st>>>(a);
-    else k_scan_contig<IPT, FINAL, false><<<a.tiles, 256, 0, st>>>(a);
+static void launch_contig_t(const Batch<ScanArgs>& b, uint32_t tiles, bool vec, cudaStream_t st) {
+    if (vec) k_scan_contig<IPT, FINAL, true><<<tiles, 256, 0, st>>>(b);
+    else k_scan_contig<IPT, FINAL, false><<<tiles, 256, 0, st>>>(b);
 }
 
 template <bool FINAL>
-static void launch_contig(const ScanArgs& a, int ipt, bool vec, cudaStream_t st) {
-    if (ipt == 4) launch_contig_t<4, FINAL>(a, vec, st);
-    else if (ipt == 8) launch_contig_t<8, FINAL>(a, vec, st);
-    else launch_contig_t<16, FINAL>(a, vec, st);
+static void launch_contig(const Batch<ScanArgs>& b, uint32_t tiles, int ipt, bool vec,
+                          cudaStream_t st) {
+    if (ipt == 4) launch_contig_t<4, FINAL>(b, tiles, vec, st);
+    else if (ipt == 8) launch_contig_t<8, FINAL>(b, tiles, vec, st);
+    else launch_contig_t<16, FINAL>(b, tiles, vec, st);
 }
 
-// Words of the largest stream window one decode block can need: every chunk
-// holds at most ceil(chunk * lmax / 32) words.
+// Shared-memory stream window of one decode block: room for its chunks at up
+// to 16 bits per symbol (a chunk may need ceil(chunk * lmax / 32) words; a block
+// whose window is larger reads its words from global memory instead).  Keeping
+// the window small keeps several blocks resident per SM.
 uint32_t decode_window_words(const fpsnr_plan_s* p) {
-    return (uint32_t)(kDecThreads * (((uint64_t)p->chunk * p->lmax + 31) / 32));
+    const uint32_t bits = (uint32_t)std::min(p->lmax, 16);
+    return (uint32_t)(kDecThreads * (((uint64_t)p->chunk * bits + 31) / 32));
 }
 
-// LUT + window + 3 words for rounding the window's start down to 16 bytes and
-// 3 for rounding its end up
+// LUT + window + 4 words of slack for rounding the window to 16-byte bounds
 int decode_smem_bytes(const fpsnr_plan_s* p) {
     return (int)(((1u << kLutBits) + decode_window_words(p) + 8) * 4);
 }
 
-int decode_prepare(const fpsnr_plan_s* p) {
-    if (decode_smem_bytes(p) > kMaxDynSmem) return FPSNR_OK;  // the unstaged kernel needs 8 KB
-    return cudaFuncSetAttribute(k_decode<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                decode_smem_bytes(p)) == cudaSuccess ? FPSNR_OK : FPSNR_ECUDA;
+// Largest dynamic shared memory the staged decoder can take on this device:
+// the per-block opt-in limit minus the kernel's static shared memory.
+static int decode_smem_limit() {
+    static int limit = -1;
+    if (limit < 0) {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, k_decode<false, kDecThreads>) != cudaSuccess)
+            return 0;
+        limit = std::min(kMaxDynSmem, optin - (int)fa.sharedSizeBytes);
+    }
+    return limit;
 }
 
-int launch_decompress(fpsnr_plan_s* p, const void* d_blob, uint64_t bytes, float* d_out,
-                      int* d_status, cudaStream_t st) {
-    const Workspace& w = p->w;
-    const uint8_t* blob = reinterpret_cast<const uint8_t*>(d_blob);
-    {
-    StageScope sc(p->prof, kStDsetup, st);
-    k_dsetup<<<1, 1024, 0, st>>>(w.par, blob, bytes, p->ndim, p->ld, p->dims[0], p->dims[1],
-                                 p->dims[2], p->n, (uint32_t)p->chunk, p->nchunks, w.dlut, w.dsyms,
-                                 w.lb_ctr);
+// The attribute belongs to the kernel, not to a plan: set it to the largest
+// size any plan can ask for.
+int decode_prepare(const fpsnr_plan_s*) { return decode_smem_limit() > 0 ? FPSNR_OK : FPSNR_ECUDA; }
+
+static uint32_t small_blocks_d(const fpsnr_plan_s* p, int count) {
+    const int g = std::max(1, p->sm_count / std::max(1, count));
+    return (uint32_t)std::min(g, 64);
+}
+
+int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
+                            const uint64_t* bytes, float* const* d_out, int* d_status, int count,
+                            cudaStream_t st) {
+    if (count <= 0) return FPSNR_OK;
+    if (count > kMaxBatch) {
+        for (int b0 = 0; b0 < count; b0 += kMaxBatch) {
+            const int c = std::min(kMaxBatch, count - b0);
+            int rc = launch_decompress_batch(P + b0, d_blob + b0, bytes + b0, d_out + b0,
+                                             d_status ? d_status + b0 : nullptr, c, st);
+            if (rc) return rc;
+        }
+        return FPSNR_OK;
     }
-    if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
-    if (p->n > 0) {
-        int32_t* out = reinterpret_cast<int32_t*>(d_out);
-        const unsigned gdec = (unsigned)((p->nchunks + kDecThreads - 1) / kDecThreads);
-        {
-        StageScope sc(p->prof, kStDecode, st);
-        if (decode_smem_bytes(p) <= kMaxDynSmem)
-            k_decode<true><<<gdec, kDecThreads, decode_smem_bytes(p), st>>>(
-                w.par, blob, w.dlut, w.dsyms, out, p->n, (uint32_t)p->chunk, p->nchunks,
-                decode_window_words(p));
-        else
-            k_decode<false><<<gdec, kDecThreads, (1u << kLutBits) * 4, st>>>(
-                w.par, blob, w.dlut, w.dsyms, out, p->n, (uint32_t)p->chunk, p->nchunks, 0u);
+    fp::Profiler& prof = P[0]->prof;  // batched launches are attributed to the first plan
+    uint32_t blocks[kMaxBatch];
+    {
+        Batch<DsetupArgs> b;
+        b.count = (uint32_t)count;
+        for (int f = 0; f < count; f++) {
+            const fpsnr_plan_s* p = P[f];
+            const Workspace& w = p->w;
+            b.a[f] = DsetupArgs{w.par, reinterpret_cast<const uint8_t*>(d_blob[f]), bytes[f],
+                                p->ndim, p->ld, p->dims[0], p->dims[1], p->dims[2], p->n,
+                                (uint32_t)p->chunk, p->nchunks, w.dlut, w.dsyms, w.lb_ctr};
+            b.off[f] = (uint32_t)f;
         }
-        {
-        StageScope sc(p->prof, kStScatter, st);
-        k_scatter<<<(unsigned)p->sm_count, 256, 0, st>>>(w.par, blob, out, p->n);
-        }
+        b.off[count] = (uint32_t)count;
+        StageScope sc(prof, kStDsetup, st);
+        k_dsetup<<<count, 1024, 0, st>>>(b);
         if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
-        for (int i = 0; i < p->n_passes; i++) {
-            const ScanPass& sp = p->pass[i];
-            ScanArgs a;
-            a.par = w.par;
-            a.data = reinterpret_cast<uint32_t*>(d_out);
-            a.A = sp.A;
-            a.L = sp.L;
-            a.B = sp.B;
-            a.tiles = sp.tiles;
-            a.flags = w.lb_flags + sp.val_off;
-            a.agg = w.lb_vals + sp.val_off * p->lb_width;
-            a.inc = w.lb_vals + (p->lb_tiles_total + sp.val_off) * p->lb_width;
-            a.ctr = w.lb_ctr + 2 * sp.ctr_slot;
-            StageScope sc(p->prof, sp.final_pass ? kStScanFinal : (i == 0 ? kStScanX : kStScanY), st);
-            if (sp.kind == 0) {
-                a.tpr = (sp.L + 256u * sp.ipt - 1) / (256u * sp.ipt);
-                a.nbt = 1;
-                if (sp.final_pass) launch_contig<true>(a, sp.ipt, sp.vec, st);
-                else launch_contig<false>(a, sp.ipt, sp.vec, st);
-            } else {
-                a.tpr = 1;
-                a.nbt = (sp.B + sp.tb - 1) / sp.tb;
-                if (sp.vec) {
-                    if (sp.final_pass) k_scan_strided<16, 4, true><<<sp.tiles, 256, 0, st>>>(a);
-                    else k_scan_strided<16, 4, false><<<sp.tiles, 256, 0, st>>>(a);
+    }
+    // decode: one launch per (staged, shared-memory size) group
+    {
+        bool done[kMaxBatch] = {};
+        for (int f0 = 0; f0 < count; f0++) {
+            if (done[f0] || P[f0]->n == 0) continue;
+            const int smem0 = decode_smem_bytes(P[f0]);
+            Batch<DecArgs> b;
+            b.count = 0;
+            for (int f = f0; f < count; f++) {
+                const fpsnr_plan_s* p = P[f];
+                if (done[f] || p->n == 0 || decode_smem_bytes(p) != smem0) continue;
+                done[f] = true;
+                const Workspace& w = p->w;
+                blocks[b.count] = (uint32_t)((p->nchunks + kDecThreads - 1) / kDecThreads);
+                b.a[b.count++] = DecArgs{w.par, reinterpret_cast<const uint8_t*>(d_blob[f]), w.dlut,
+                                         w.dsyms, reinterpret_cast<int32_t*>(d_out[f]), p->n,
+                                         (uint32_t)p->chunk, p->nchunks, decode_window_words(p)};
+            }
+            const uint32_t tot = batch_offsets(b, blocks);
+            StageScope sc(prof, kStDecode, st);
+            // every thread streams its own chunk from global memory (two words in
+            // flight); only the look-up table is staged in shared memory
+            k_decode<false, kDecThreads><<<tot, kDecThreads, (1u << kLutBits) * 4 + 64, st>>>(b);
+            if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
+        }
+    }
+    Batch<SmallArgs> sb;
+    sb.count = (uint32_t)count;
+    for (int f = 0; f < count; f++) {
+        const fpsnr_plan_s* p = P[f];
+        sb.a[f] = SmallArgs{p->w.par, reinterpret_cast<const uint8_t*>(d_blob[f]), d_out[f], p->n,
+                            small_blocks_d(p, count), d_status ? d_status + f : nullptr};
+        blocks[f] = p->n ? sb.a[f].G : 0u;
+    }
+    const uint32_t small_tot = batch_offsets(sb, blocks);
+    if (small_tot) {
+        StageScope sc(prof, kStScatter, st);
+        k_scatter<<<small_tot, 256, 0, st>>>(sb);
+        if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
+    }
+    // inverse Lorenzo passes, grouped by pass index and kernel variant
+    for (int i = 0; i < 3; i++) {
+        bool done[kMaxBatch] = {};
+        for (int f0 = 0; f0 < count; f0++) {
+            const fpsnr_plan_s* p0 = P[f0];
+            if (done[f0] || p0->n == 0 || p0->n_passes <= i) continue;
+            const ScanPass& s0 = p0->pass[i];
+            Batch<ScanArgs> b;
+            b.count = 0;
+            for (int f = f0; f < count; f++) {
+                const fpsnr_plan_s* p = P[f];
+                if (done[f] || p->n == 0 || p->n_passes <= i) continue;
+                const ScanPass& sp = p->pass[i];
+                if (sp.kind != s0.kind || sp.ipt != s0.ipt || sp.vec != s0.vec ||
+                    sp.final_pass != s0.final_pass)
+                    continue;
+                done[f] = true;
+                const Workspace& w = p->w;
+                ScanArgs a;
+                a.par = w.par;
+                a.data = reinterpret_cast<uint32_t*>(d_out[f]);
+                a.A = sp.A;
+                a.L = sp.L;
+                a.B = sp.B;
+                a.tiles = sp.tiles;
+                a.flags = w.lb_flags + sp.val_off;
+                a.agg = w.lb_vals + sp.val_off * p->lb_width;
+                a.inc = w.lb_vals + (p->lb_tiles_total + sp.val_off) * p->lb_width;
+                a.ctr = w.lb_ctr + 2 * sp.ctr_slot;
+                if (sp.kind == 0) {
+                    a.tpr = (sp.L + 256u * sp.ipt - 1) / (256u * sp.ipt);
+                    a.nbt = 1;
                 } else {
-                    if (sp.final_pass) k_scan_strided<16, 1, true><<<sp.tiles, 256, 0, st>>>(a);
-                    else k_scan_strided<16, 1, false><<<sp.tiles, 256, 0, st>>>(a);
+                    a.tpr = 1;
+                    a.nbt = (sp.B + sp.tb - 1) / sp.tb;
                 }
+                blocks[b.count] = sp.tiles;
+                b.a[b.count++] = a;
+            }
+            const uint32_t tot = batch_offsets(b, blocks);
+            StageScope sc(prof, s0.final_pass ? kStScanFinal : (i == 0 ? kStScanX : kStScanY), st);
+            if (s0.kind == 0) {
+                if (s0.final_pass) launch_contig<true>(b, tot, s0.ipt, s0.vec, st);
+                else launch_contig<false>(b, tot, s0.ipt, s0.vec, st);
+            } else if (s0.vec) {
+                if (s0.final_pass) k_scan_strided<16, 4, true><<<tot, 256, 0, st>>>(b);
+                else k_scan_strided<16, 4, false><<<tot, 256, 0, st>>>(b);
+            } else {
+                if (s0.final_pass) k_scan_strided<16, 1, true><<<tot, 256, 0, st>>>(b);
+                else k_scan_strided<16, 1, false><<<tot, 256, 0, st>>>(b);
             }
             if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
         }
-        StageScope sc(p->prof, kStPatch, st);
-        k_patch<<<(unsigned)p->sm_count, 256, 0, st>>>(w.par, blob, d_out, p->n);
     }
-    if (d_status) k_status<<<1, 1, 0, st>>>(w.par, d_status);
+    if (small_tot) {
+        StageScope sc(prof, kStPatch, st);
+        k_patch<<<small_tot, 256, 0, st>>>(sb);
+        if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
+    }
+    if (d_status) {
+        for (int f = 0; f < count; f++) sb.off[f] = (uint32_t)f;
+        sb.off[count] = (uint32_t)count;
+        k_status<<<count, 32, 0, st>>>(sb);
+    }
     return cudaGetLastError() == cudaSuccess ? FPSNR_OK : FPSNR_ECUDA;
 }
 

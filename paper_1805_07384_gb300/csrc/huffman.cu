@@ -138,7 +138,8 @@ __device__ __forceinline__ uint32_t warp_first_false(uint32_t lo, uint32_t hi, P
     return lo + __popc(__ballot_sync(0xffffffffu, t));
 }
 
-__global__ void __launch_bounds__(1024, 1) k_codebook(CBArgs a) {
+__global__ void __launch_bounds__(1024, 1) k_codebook(const __grid_constant__ Batch<CBArgs> B) {
+    const CBArgs& a = B.a[blockIdx.x];  // one block per field
     extern __shared__ uint32_t dsm[];
     uint32_t* sq = dsm;                                              // internal queue (n <= 32768)
     uint8_t* depth8 = reinterpret_cast<uint8_t*>(dsm + kSmemQueue);  // internal-node depths
@@ -388,26 +389,34 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(CBArgs a) {
     }
 }
 
-int launch_codebook(fpsnr_plan_s* p, void* d_out, cudaStream_t st) {
-    const Workspace& w = p->w;
-    CBArgs a;
-    a.par = w.par;
-    a.hist = w.hist;
-    a.enc = w.enc;
-    a.len_sym = w.len_sym;
-    a.nsym = p->nsym;
-    a.lmax = p->lmax;
-    a.sse_part = w.sse_part;
-    a.n_sse = p->n ? p->pq.nblocks : 0;
-    a.bpre = w.bpre;
-    a.nbmblk = (uint32_t)p->nbmblk;
-    a.list = w.hlist;
-    a.buf1 = w.hbuf1;
-    a.buf2 = w.hbuf2;
-    a.parent = w.hpar;
-    a.out = reinterpret_cast<uint8_t*>(d_out);
-    StageScope sc(p->prof, kStCodebook, st);
-    k_codebook<<<1, 1024, p->cb_smem, st>>>(a);
+int launch_codebook_batch(fpsnr_plan_s* const* P, void* const* d_out, int count,
+                          cudaStream_t st) {
+    Batch<CBArgs> b;
+    b.count = (uint32_t)count;
+    for (int f = 0; f < count; f++) {
+        const fpsnr_plan_s* p = P[f];
+        const Workspace& w = p->w;
+        CBArgs& a = b.a[f];
+        a.par = w.par;
+        a.hist = w.hist;
+        a.enc = w.enc;
+        a.len_sym = w.len_sym;
+        a.nsym = p->nsym;
+        a.lmax = p->lmax;
+        a.sse_part = w.sse_part;
+        a.n_sse = p->n ? p->pq.nblocks : 0;
+        a.bpre = w.bpre;
+        a.nbmblk = (uint32_t)p->nbmblk;
+        a.list = w.hlist;
+        a.buf1 = w.hbuf1;
+        a.buf2 = w.hbuf2;
+        a.parent = w.hpar;
+        a.out = reinterpret_cast<uint8_t*>(d_out[f]);
+        b.off[f] = (uint32_t)f;
+    }
+    b.off[count] = (uint32_t)count;
+    StageScope sc(P[0]->prof, kStCodebook, st);
+    k_codebook<<<count, 1024, P[0]->cb_smem, st>>>(b);
     return cudaGetLastError() == cudaSuccess ? FPSNR_OK : FPSNR_ECUDA;
 }
 

@@ -34,7 +34,8 @@ EXPORTS = ("fpsnr_default_opts", "fpsnr_plan", "fpsnr_plan_set_psnr", "fpsnr_pla
            "fpsnr_plan_points", "fpsnr_max_compressed_bytes", "fpsnr_compress",
            "fpsnr_decompress", "fpsnr_psnr", "fpsnr_plan_codes", "fpsnr_plan_destroy",
            "fpsnr_strerror", "fpsnr_plan_profile", "fpsnr_plan_profile_read",
-           "fpsnr_stage_name", "fpsnr_psnr_static")
+           "fpsnr_stage_name", "fpsnr_psnr_static", "fpsnr_compress_batch",
+           "fpsnr_decompress_batch")
 FPSNR_PSNR_STATIC_MAX_POINTS = 1 << 28
 FPSNR_NSTAGES = 16
 
@@ -91,6 +92,8 @@ def load(path: str = LIB_PATH):
         L.fpsnr_max_compressed_bytes.restype = U64
         L.fpsnr_compress.argtypes = [P, P, P, U64, P, P, P]
         L.fpsnr_decompress.argtypes = [P, P, U64, P, U64, P, P]
+        L.fpsnr_compress_batch.argtypes = [P, P, P, P, P, P, C.c_int, P]
+        L.fpsnr_decompress_batch.argtypes = [P, P, P, P, P, C.c_int, P]
         L.fpsnr_psnr.argtypes = [P, P, U64, C.POINTER(D), C.POINTER(D), C.POINTER(D), P]
         L.fpsnr_psnr_static.argtypes = [P, P, U64, C.POINTER(D), C.POINTER(D), C.POINTER(D), P]
         L.fpsnr_plan_codes.argtypes = [P]
@@ -156,6 +159,28 @@ def fpsnr_decompress(plan, d_blob: int, blob_bytes: int, d_out: int, n_out: int,
                      d_status: int = 0, stream: int = 0) -> int:
     return load().fpsnr_decompress(plan, d_blob, int(blob_bytes), d_out, int(n_out),
                                    d_status or None, stream or None)
+
+
+def _ptr_array(vals):
+    return (C.c_void_p * len(vals))(*[int(v) if v else None for v in vals])
+
+
+def fpsnr_compress_batch(plans, d_in, d_out, out_cap, d_out_bytes: int = 0, d_stats: int = 0,
+                         stream: int = 0) -> int:
+    """Lists of plan handles, input/output device pointers and capacities."""
+    n = len(plans)
+    caps = (C.c_uint64 * n)(*[int(c) for c in out_cap])
+    return load().fpsnr_compress_batch(_ptr_array(plans), _ptr_array(d_in), _ptr_array(d_out),
+                                       caps, d_out_bytes or None, d_stats or None, n,
+                                       stream or None)
+
+
+def fpsnr_decompress_batch(plans, d_blob, blob_bytes, d_out, d_status: int = 0,
+                           stream: int = 0) -> int:
+    n = len(plans)
+    nb = (C.c_uint64 * n)(*[int(b) for b in blob_bytes])
+    return load().fpsnr_decompress_batch(_ptr_array(plans), _ptr_array(d_blob), nb,
+                                         _ptr_array(d_out), d_status or None, n, stream or None)
 
 
 def fpsnr_psnr(d_x: int, d_xr: int, n: int, stream: int = 0):
@@ -301,6 +326,40 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def compress_batch(plans, xs, outs=None, nbytes=None, stats=None, stream=None):
+    """Compress fields xs[i] with plans[i] in one batched call.  Returns (outs,
+    nbytes int64[count], stats uint8[count, STATS_BYTES]) device tensors."""
+    import torch
+    dev = xs[0].device
+    outs = [p.alloc_out() for p in plans] if outs is None else outs
+    nbytes = torch.zeros(len(plans), dtype=torch.int64, device=dev) if nbytes is None else nbytes
+    stats = (torch.zeros((len(plans), STATS_BYTES), dtype=torch.uint8, device=dev)
+             if stats is None else stats)
+    rc = fpsnr_compress_batch([p.handle for p in plans], [x.data_ptr() for x in xs],
+                              [o.data_ptr() for o in outs], [o.numel() for o in outs],
+                              nbytes.data_ptr(), stats.data_ptr(), _stream_handle(stream))
+    if rc:
+        raise FpsnrError(rc, "fpsnr_compress_batch")
+    return outs, nbytes, stats
+
+
+def decompress_batch(plans, blobs, blob_bytes=None, outs=None, status=None, stream=None):
+    """Decompress blobs[i] with plans[i] in one batched call.  blob_bytes
+    defaults to each buffer's size.  Returns (outs, status int32[count])."""
+    import torch
+    dev = blobs[0].device
+    outs = ([torch.empty(p.shape, dtype=torch.float32, device=dev) for p in plans]
+            if outs is None else outs)
+    status = torch.zeros(len(plans), dtype=torch.int32, device=dev) if status is None else status
+    blob_bytes = [b.numel() for b in blobs] if blob_bytes is None else blob_bytes
+    rc = fpsnr_decompress_batch([p.handle for p in plans], [b.data_ptr() for b in blobs],
+                                blob_bytes, [o.data_ptr() for o in outs], status.data_ptr(),
+                                _stream_handle(stream))
+    if rc:
+        raise FpsnrError(rc, "fpsnr_decompress_batch")
+    return outs, status
 
 
 def psnr(x, xr, stream=None):
