@@ -290,7 +290,7 @@ __device__ __forceinline__ void ff_add_sq_diff(FF& acc, float a, float b) {
     // d^2 = p + e (+ 2 dh dl + dl^2, both far below the float-float precision needed)
     float p = __fmul_rn(dh, dh);
     float e = __fmaf_rn(dh, dh, -p);
-    e = __fadd_rn(e, __fmul_rn(__fmul_rn(2.0f, dh), dl));
+    e = __fmaf_rn(__fadd_rn(dh, dh), dl, e);
     // acc += p + e
     float t = __fadd_rn(acc.hi, p);
     float tb = __fsub_rn(t, acc.hi);
