@@ -231,73 +231,82 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batc
     const uint32_t xb = x0 + 4u * threadIdx.x;
     const uint32_t y = y0 + threadIdx.y;
     const uint32_t lane = tid & 31u;
-    const int wlo = R - kHistWin / 2;
+    const uint32_t vx = a.vx;
+    const bool yin = (MODE == 3) ? (y < a.vy) : true;
+    // histogram window [wlo, wlo + kHistWin) around the zero residual; the
+    // unsigned difference code - wlo wraps for codes below the window
+    const uint32_t wlo = (uint32_t)(R - kHistWin / 2);
+
+    // A row of the tile: 4 points per thread and, for lane 0, the left
+    // neighbour of its first point.  Rows are fetched one ahead of their use.
+    struct Row {
+        float v[4];
+        float l;
+        bool hl;
+    };
+    auto row_limit = [&](uint64_t rowbase) -> uint32_t {
+        // MODE 1 rows are consecutive runs of vx points; only the last is short
+        return (MODE == 1) ? (uint32_t)min((uint64_t)vx, a.n - rowbase) : vx;
+    };
+    auto load_row = [&](const float* xrow, uint64_t rowbase, bool rowin, uint32_t lim, Row& r) {
+        if (VEC && rowin && xb + 3 < lim) {
+            const float4 v = __ldcs(reinterpret_cast<const float4*>(xrow + xb));
+            r.v[0] = v.x; r.v[1] = v.y; r.v[2] = v.z; r.v[3] = v.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) r.v[k] = (rowin && xb + k < lim) ? xrow[xb + k] : 0.0f;
+        }
+        r.l = 0.0f;
+        r.hl = false;
+        if (lane == 0 && rowin) {
+            if (xb > 0) {
+                // a warp that starts past the row end needs nothing: its points are outside
+                if (xb <= lim) {
+                    r.l = xrow[xb - 1];
+                    r.hl = true;
+                }
+            } else if (MODE == 1 && rowbase > 0) {
+                r.l = x[rowbase - 1];
+                r.hl = true;
+            }
+        }
+    };
+    auto fetch = [&](uint32_t z, Row& r, Row& h) {
+        const uint64_t rowbase = ((uint64_t)z * a.vy + y) * vx;
+        load_row(x + rowbase, rowbase, yin, row_limit(rowbase), r);
+        if (MODE == 3 && threadIdx.y == 0 && y0 > 0) {
+            // halo row y0 - 1 of plane z
+            const uint64_t hb = ((uint64_t)z * a.vy + (y0 - 1)) * vx;
+            load_row(x + hb, hb, true, vx, h);
+        }
+    };
 
     int32_t L2prev[4] = {0, 0, 0, 0};
     FF acc = {0.0f, 0.0f};
-    uint32_t sym_lo = 0xffffffffu, sym_hi = 0u;
+    uint32_t glo = 0xffffffffu, ghi = 0u;  // nonzero symbols counted outside the window
     int buf = 0;
     const uint32_t zstart = (MODE != 1 && z0 > 0) ? z0 - 1 : z0;
+    Row nxt, hnxt;
+    hnxt.v[0] = hnxt.v[1] = hnxt.v[2] = hnxt.v[3] = hnxt.l = 0.0f;
+    hnxt.hl = false;
+    fetch(zstart, nxt, hnxt);
+    for (uint32_t z = zstart; z < z1; z++) {
+        const Row cur = nxt;
+        const Row hcur = hnxt;
+        if (z + 1 < z1) fetch(z + 1, nxt, hnxt);
 
-    // rows are loaded G at a time ahead of their processing so that several
-    // 16-byte loads per thread are in flight (the walk is otherwise latency bound)
-    constexpr int G = (MODE == 3) ? 1 : 4;
-    for (uint32_t zg = zstart; zg < z1; zg += G) {
-        float xg[G][4];
-        float xlg[G];
-        bool hlg[G];
-#pragma unroll
-        for (int g = 0; g < G; g++) {
-            const uint32_t z = zg + g;
-            const uint64_t rowbase = ((uint64_t)z * a.vy + y) * a.vx;
-            const float* xrow = x + rowbase;
-            const bool rowin = (z < z1) && ((MODE == 3) ? (y < a.vy) : true);
-            const uint64_t rowend = (MODE == 1) ? a.n - min(a.n, rowbase) : 0xffffffffull;
-            bool inb[4];
-#pragma unroll
-            for (int k = 0; k < 4; k++) inb[k] = rowin && (xb + k < a.vx) && (xb + k < rowend);
-            if (VEC && inb[3]) {
-                const float4 v = __ldcs(reinterpret_cast<const float4*>(xrow + xb));
-                xg[g][0] = v.x; xg[g][1] = v.y; xg[g][2] = v.z; xg[g][3] = v.w;
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; k++) xg[g][k] = inb[k] ? xrow[xb + k] : 0.0f;
-            }
-            // left neighbour of the lane's first point (lane 0 only; a warp that
-            // starts past the row end needs nothing: its points are out of the field)
-            hlg[g] = false;
-            xlg[g] = 0.0f;
-            if (lane == 0 && rowin) {
-                if (xb > 0) {
-                    if (xb <= a.vx && xb - 1 < rowend) {
-                        xlg[g] = xrow[xb - 1];
-                        hlg[g] = true;
-                    }
-                } else if (MODE == 1 && rowbase > 0 && rowbase - 1 < a.n) {
-                    xlg[g] = x[rowbase - 1];
-                    hlg[g] = true;
-                }
-            }
-        }
-#pragma unroll
-    for (int g = 0; g < G; g++) {
-        const uint32_t z = zg + g;
-        if (z >= z1) break;  // uniform across the block
         // ---- own row: lattice q, row difference L1 ----
-        const uint64_t rowbase = ((uint64_t)z * a.vy + y) * a.vx;
-        const bool rowin = (MODE == 3) ? (y < a.vy) : true;
-        const uint64_t rowend = (MODE == 1) ? a.n - min(a.n, rowbase) : 0xffffffffull;
-        float xv[4];
-        int32_t q[4];
+        const uint64_t rowbase = ((uint64_t)z * a.vy + y) * vx;
+        const uint32_t lim = row_limit(rowbase);
         bool in[4];
+        int32_t q[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            in[k] = rowin && (xb + k < a.vx) && (xb + k < rowend);
-            xv[k] = xg[g][k];
-            q[k] = in[k] ? prequant(xv[k], xmin, inv, off) : 0;
+            in[k] = yin && (xb + k < lim);
+            q[k] = in[k] ? prequant(cur.v[k], xmin, inv, off) : 0;
         }
         int32_t qleft = __shfl_up_sync(0xffffffffu, q[3], 1);
-        if (lane == 0) qleft = hlg[g] ? prequant(xlg[g], xmin, inv, off) : 0;
+        if (lane == 0) qleft = cur.hl ? prequant(cur.l, xmin, inv, off) : 0;
         int32_t L1[4];
         L1[0] = q[0] - qleft;
 #pragma unroll
@@ -308,24 +317,14 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batc
 #pragma unroll
             for (int k = 0; k < 4; k++) sL1[buf][threadIdx.y + 1][4 * threadIdx.x + k] = L1[k];
             if (threadIdx.y == 0) {
-                // halo row y0 - 1 of this plane
                 int32_t h[4] = {0, 0, 0, 0};
                 int32_t hl = 0;
                 if (y0 > 0) {
-                    const float* hrow = x + ((uint64_t)z * a.vy + (y0 - 1)) * a.vx;
-                    float hv[4];
-                    if (VEC && xb + 3 < a.vx) {
-                        float4 v = *reinterpret_cast<const float4*>(hrow + xb);
-                        hv[0] = v.x; hv[1] = v.y; hv[2] = v.z; hv[3] = v.w;
-                    } else {
 #pragma unroll
-                        for (int k = 0; k < 4; k++) hv[k] = (xb + k < a.vx) ? hrow[xb + k] : 0.0f;
-                    }
-#pragma unroll
-                    for (int k = 0; k < 4; k++) h[k] = (xb + k < a.vx) ? prequant(hv[k], xmin, inv, off) : 0;
-                    if (lane == 0 && xb > 0 && xb <= a.vx) hl = prequant(hrow[xb - 1], xmin, inv, off);
+                    for (int k = 0; k < 4; k++) h[k] = (xb + k < vx) ? prequant(hcur.v[k], xmin, inv, off) : 0;
+                    if (hcur.hl) hl = prequant(hcur.l, xmin, inv, off);
                 }
-                int32_t hs = __shfl_up_sync(0xffffffffu, h[3], 1);
+                const int32_t hs = __shfl_up_sync(0xffffffffu, h[3], 1);
                 if (lane != 0) hl = hs;
                 sL1[buf][0][4 * threadIdx.x] = h[0] - hl;
 #pragma unroll
@@ -346,9 +345,10 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batc
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 d[k] = (MODE == 1) ? L2[k] : L2[k] - L2prev[k];
-                code[k] = (d[k] > -R && d[k] < R) ? (uint32_t)(d[k] + R) : 0u;
+                // |d| < R  <=>  d + R - 1 in [0, 2R - 2]
+                const uint32_t u = (uint32_t)(d[k] + (R - 1));
+                code[k] = u < (uint32_t)(2 * R - 1) ? u + 1u : 0u;
             }
-            // symbols
             uint16_t* crow = a.codes + rowbase;
             if (VEC && in[3]) {
                 uint2 pk;
@@ -360,26 +360,19 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batc
                 for (int k = 0; k < 4; k++)
                     if (in[k]) crow[xb + k] = (uint16_t)code[k];
             }
+            // histogram: shared-memory window, global counters outside it
 #pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (in[k] && code[k]) { sym_lo = min(sym_lo, code[k]); sym_hi = max(sym_hi, code[k]); }
-            // histogram: warp-uniform fast path, else per point
-            const bool all4 = in[0] && in[1] && in[2] && in[3] && code[0] == code[1] &&
-                              code[1] == code[2] && code[2] == code[3];
-            const uint32_t c0 = __shfl_sync(0xffffffffu, code[0], 0);
-            if (__all_sync(0xffffffffu, all4 && code[0] == c0)) {
-                if (lane == 0) {
-                    int bin = (int)c0 - wlo;
-                    if (bin >= 0 && bin < kHistWin) atomicAdd(&shist[bin], 128u);
-                    else atomicAdd(&a.hist[c0], 128u);
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    if (!in[k]) continue;
-                    int bin = (int)code[k] - wlo;
-                    if (bin >= 0 && bin < kHistWin) atomicAdd(&shist[bin], 1u);
-                    else atomicAdd(&a.hist[code[k]], 1u);
+            for (int k = 0; k < 4; k++) {
+                if (!in[k]) continue;
+                const uint32_t bin = code[k] - wlo;
+                if (bin < (uint32_t)kHistWin) {
+                    atomicAdd(&shist[bin], 1u);
+                } else {
+                    atomicAdd(&a.hist[code[k]], 1u);
+                    if (code[k]) {
+                        glo = min(glo, code[k]);
+                        ghi = max(ghi, code[k]);
+                    }
                 }
             }
             // reconstruction, verbatim test, exact squared error
@@ -388,10 +381,10 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batc
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const float xr = __fmaf_rn(__int2float_rn(q[k]), s, xmin);
-                const float df = __fsub_rn(xv[k], xr);
+                const float df = __fsub_rn(cur.v[k], xr);
                 vb[k] = in[k] && !(fabsf(df) <= thr);
                 ol[k] = in[k] && code[k] == 0u;
-                if (in[k] && !vb[k]) ff_add_sq_diff(acc, xv[k], xr);
+                if (in[k] && !vb[k]) ff_add_sq_diff(acc, cur.v[k], xr);
                 rare |= vb[k] | ol[k];
             }
             // outliers and verbatims are rare: one vote per row decides whether any
@@ -418,7 +411,7 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batc
                         base = __shfl_sync(0xffffffffu, base, leader);
                         if (vb[k]) {
                             const uint32_t slot = base + __popc(mv & lanemask_lt());
-                            a.stage_vb[slot] = make_uint2(gi, __float_as_uint(xv[k]));
+                            a.stage_vb[slot] = make_uint2(gi, __float_as_uint(cur.v[k]));
                             atomicOr(&a.bm_vb[gi >> 5], 1u << (gi & 31u));
                         }
                     }
@@ -428,24 +421,31 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batc
 #pragma unroll
         for (int k = 0; k < 4; k++) L2prev[k] = L2[k];
     }
-    }
 
-    // flush histogram window and squared-error partial
+    // flush the histogram window (and take the block's symbol range from it)
+    // and the squared-error partial
     __syncthreads();
     for (uint32_t i = tid; i < kHistWin; i += NT) {
-        uint32_t c = shist[i];
-        if (c) atomicAdd(&a.hist[wlo + (int)i], c);
+        const uint32_t c = shist[i];
+        if (c) {
+            const uint32_t sym = wlo + i;
+            atomicAdd(&a.hist[sym], c);
+            if (sym) {
+                glo = min(glo, sym);
+                ghi = max(ghi, sym);
+            }
+        }
     }
     double tot = block_sum_double(ff_to_double(acc), ssum);
     if (tid == 0) a.sse_part[b] = tot;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        sym_lo = min(sym_lo, __shfl_xor_sync(0xffffffffu, sym_lo, o));
-        sym_hi = max(sym_hi, __shfl_xor_sync(0xffffffffu, sym_hi, o));
+        glo = min(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+        ghi = max(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
     }
-    if (lane == 0 && sym_lo <= sym_hi) {
-        atomicMin(&par->sym_lo, sym_lo);
-        atomicMax(&par->sym_hi, sym_hi);
+    if (lane == 0 && glo <= ghi) {
+        atomicMin(&par->sym_lo, glo);
+        atomicMax(&par->sym_hi, ghi);
     }
 }
 
