@@ -295,6 +295,27 @@ def test_config0_psnr_within_model(oracle):
     assert vr == pytest.approx(2.0, rel=1e-6)
 
 
+def test_sse_exact_sum(oracle):
+    """Eq. 4's sum of squared errors against exact rational arithmetic: errors
+    spread over eight decades, pairs far apart (inexact float differences)
+    and 40000 terms, where a plain running FP64 sum drifts visibly."""
+    from fractions import Fraction
+    rng = np.random.default_rng(11)
+    n = 40000
+    x = (rng.standard_normal(n) * 10.0 ** rng.uniform(-3, 3, n)).astype(np.float32)
+    xr = (x.astype(np.float64) + rng.standard_normal(n) * 10.0 ** rng.uniform(-8, 0, n)).astype(np.float32)
+    xr[:50] = -x[:50] * 1e7  # differences not representable in float32
+    exact = sum((Fraction(float(a)) - Fraction(float(b))) ** 2 for a, b in zip(x, xr))
+    got = oracle.sse(x, xr)
+    assert abs(Fraction(got) - exact) <= exact * Fraction(1, 10 ** 15)
+    # the same accumulation runs inside compress: the stats' SSE is exact too
+    f = synth.smooth_1d(30000, 5)
+    blob, st = oracle.compress(f, 40.0)
+    fr = oracle.decompress(blob, f.shape)
+    exact = sum((Fraction(float(a)) - Fraction(float(b))) ** 2 for a, b in zip(f, fr))
+    assert abs(Fraction(st["sse"]) - exact) <= exact * Fraction(1, 10 ** 15)
+
+
 @pytest.mark.parametrize("psnr", [40.0, 60.0, 100.0, 120.0])
 def test_psnr_model_tracks_target(oracle, psnr):
     """Sec. V trend: deviation from the target shrinks as the target rises;
