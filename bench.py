@@ -217,9 +217,10 @@ def rank_seed(rank: int) -> int:
 
 # algorithmic bytes per launch of each stage (N points, B compressed bytes of one field)
 def stage_bytes(stage, N, B):
+    # 2D fields: decode writes 16-bit symbols; the band pass reads them and the
+    # final band scan reads them again and writes the floats
     return {"range_plan": 4 * N, "predict_quantize": 6 * N, "encode": 2 * N + B,
-            "decode": B + 4 * N, "scan_x": 8 * N,
-            "scan_final_dequant": 8 * N, "scan_y": 8 * N}.get(stage)
+            "decode": B + 2 * N, "band_sum": 2 * N, "scan_final_dequant": 6 * N}.get(stage)
 
 
 def main():

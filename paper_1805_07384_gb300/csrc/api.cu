@@ -60,6 +60,7 @@ void carve(fpsnr_plan_s* p, uint8_t* base, size_t* total) {
     w.lb_vals = c.take<uint32_t>(2 * std::max<uint64_t>(p->lb_tiles_total, 1) * p->lb_width);
     w.lb_ctr = c.take<uint32_t>(8);
     w.enc_tiles = c.take<uint32_t>(std::max<uint64_t>(p->enc_tiles, 1));
+    w.bsum = c.take<uint32_t>(p->band.on ? (uint64_t)p->band.nbands * p->band.nx : 1);
     *total = (c.off + 255) & ~(size_t)255;
 }
 
@@ -73,6 +74,7 @@ ScanPass contig_pass(uint64_t rows, uint64_t W, bool final_pass) {
     s.tiles = (uint32_t)(rows * cdiv(W, 256ull * s.ipt));
     s.tb = 1;
     s.vec = (W % 4) == 0;
+    s.vec16 = rows == 1 || (W % 8) == 0;
     s.final_pass = final_pass;
     return s;
 }
@@ -157,8 +159,8 @@ void Profiler::release() {
 extern "C" {
 
 static const char* kStageNames[FPSNR_NSTAGES] = {
-    "range_plan", "predict_quantize", "rank_popc", "codebook", "unused4", "unused5",
-    "encode", "emit", "finalize", "decode_setup", "decode", "scatter", "scan_x", "scan_y",
+    "range_plan", "predict_quantize", "rank_popc", "codebook", "band_sum", "band_carry",
+    "encode", "emit", "finalize", "decode_setup", "decode", "unused11", "scan_x", "scan_y",
     "scan_final_dequant", "patch"};
 
 const char* fpsnr_stage_name(int stage) {
@@ -289,9 +291,20 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
 
     // inverse-Lorenzo passes
     p->n_passes = 0;
+    p->band = fp::BandGeom{};
     if (n > 0) {
         if (ld == 1) {
             p->pass[p->n_passes++] = contig_pass(1, n, true);
+        } else if (ld == 2 && d[0] <= fp::kBandMaxNx) {
+            const uint64_t nx = d[0], rows = n / nx;
+            fp::BandGeom& b = p->band;
+            b.on = true;
+            b.nx = (uint32_t)nx;
+            b.rows = (uint32_t)rows;
+            b.tr = fp::kBandRows;
+            b.nbands = (uint32_t)cdiv(rows, b.tr);
+            b.g = nx <= 2048 ? 1 : (nx <= 4096 ? 2 : 4);
+            b.vec = (nx % 8) == 0;
         } else if (ld == 2) {
             const uint64_t nx = d[0], rows = n / nx;
             p->pass[p->n_passes++] = contig_pass(rows, nx, false);

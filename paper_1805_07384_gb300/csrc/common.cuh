@@ -77,6 +77,7 @@ struct Workspace {
     uint32_t* lb_vals;   // [2][n_lb_tiles * lb_width] aggregate, inclusive
     uint32_t* lb_ctr;    // [8] dynamic tile counters (pairs: counter, done)
     uint32_t* enc_tiles; // [enc_tiles] words per encoder tile, then their exclusive prefix
+    uint32_t* bsum;      // [nbands * nx] 2D band column sums (band geometry only)
 };
 
 // Launch geometry of the predict-quantize kernel.
@@ -90,13 +91,24 @@ struct PQGeom {
 };
 
 // Geometry of one inverse-Lorenzo scan pass.
+// 2D inverse Lorenzo by bands of rows, used when a row fits one block.
+constexpr uint32_t kBandMaxNx = 8192;  // 256 threads x 8 columns x G (G <= 4)
+constexpr uint32_t kBandRows = 32;     // rows per band
+struct BandGeom {
+    bool on;
+    uint32_t nx, rows, tr, nbands;
+    int g;     // 8 * g columns per thread
+    bool vec;  // nx % 8 == 0: symbol rows and output rows start on 16-byte boundaries
+};
+
 struct ScanPass {
     int kind;          // 0: contiguous rows, 1: strided (middle axis)
     uint32_t A, L, B;  // outer count, scan length, inner count (B = 1 for contiguous)
     uint32_t tiles;
     int ipt;           // contiguous: items per thread; strided: rows per tile
     int tb;            // strided: columns per tile
-    bool vec;
+    bool vec;          // rows of int32 values start on 16-byte boundaries
+    bool vec16;        // rows of 16-bit symbols start on 16-byte boundaries
     bool final_pass;
     int ctr_slot;      // which lb_ctr pair
     uint64_t val_off;  // offset (in tiles) into the look-back arrays
@@ -106,8 +118,8 @@ struct ScanPass {
 
 namespace fp {
 enum Stage {
-    kStRange = 0, kStPq, kStRank, kStCodebook, kStUnused4, kStUnused5, kStEncode, kStEmit,
-    kStFinalize, kStDsetup, kStDecode, kStScatter, kStScanX, kStScanY, kStScanFinal, kStPatch
+    kStRange = 0, kStPq, kStRank, kStCodebook, kStBandSum, kStBandCarry, kStEncode, kStEmit,
+    kStFinalize, kStDsetup, kStDecode, kStUnused11, kStScanX, kStScanY, kStScanFinal, kStPatch
 };
 
 // Host-side launch counters and optional per-launch CUDA events.
@@ -139,6 +151,7 @@ struct fpsnr_plan_s {
     uint32_t n_range_blocks;
     int n_passes;
     fp::ScanPass pass[3];
+    fp::BandGeom band;
     uint64_t lb_tiles_total, lb_width;
     uint64_t enc_tiles;
     void* slab;
@@ -223,7 +236,6 @@ constexpr size_t kPsnrResultOffset = 16;
 constexpr size_t kPsnrResultBytes = 24;
 int codebook_prepare();
 int decode_prepare(const fpsnr_plan_s* p);
-int decode_smem_bytes(const fpsnr_plan_s* p);
 
 // ---- device helpers ----
 #ifdef __CUDACC__

@@ -3,21 +3,28 @@
 // reproduced exactly).
 //
 //   k_dsetup        header validation against the plan, canonical decoding
-//                   tables and an 11-bit look-up table
-//   k_decode        one thread per chunk, canonical Huffman decode into int32
-//                   residuals (written into the output buffer)
-//   k_scatter       outlier residuals put back
-//   k_scan_contig   inclusive prefix sum along x (rows), decoupled look-back
-//                   between tiles of one row
-//   k_scan_strided  inclusive prefix sum along y or z, decoupled look-back
-//                   between row segments; the last pass also dequantizes:
-//                   x' = fmaf((float)q, s, xmin) (midpoint reconstruction,
-//                   Sec. IV)
+//                   tables and a look-up table over the next kLutBits bits
+//   k_decode        one thread per chunk, canonical Huffman decode into the
+//                   16-bit symbols (the plan's symbol buffer)
+//   2D fields up to kBandMaxNx columns (reduce, then scan, over bands of rows):
+//     k_band_sum    column sums of the residuals of every band
+//     k_band_carry  exclusive prefix of those sums over the bands
+//     k_band_scan   per band: the carry row's prefix along x seeds the column
+//                   sums, then every row's prefix along x is added to them;
+//                   dequantization x' = fmaf((float)q, s, xmin) (midpoint
+//                   reconstruction, Sec. IV) is fused into the write
+//   other shapes (1D, 3D, wider 2D):
+//     k_scan_contig   inclusive prefix sum along x (rows), decoupled look-back
+//                     between tiles of one row; the first pass reads symbols
+//     k_scan_strided  inclusive prefix sum along y or z, decoupled look-back
+//                     between row segments; the last pass dequantizes
 //   k_patch         verbatim points restored
 //
-// The prefix sums run in modular uint32 arithmetic: intermediate partial sums
-// may leave the int32 range, but every final lattice value is in [0, 2^31),
-// so the modular result is exact.
+// Symbol 0 marks an outlier: every pass that turns symbols into residuals
+// finds its residual in the outlier list (sorted by point index) by binary
+// search.  The prefix sums run in modular uint32 arithmetic: intermediate
+// partial sums may leave the int32 range, but every final lattice value is in
+// [0, 2^31), so the modular result is exact.
 #include <algorithm>
 
 #include "common.cuh"
@@ -180,69 +187,47 @@ __global__ void __launch_bounds__(1024) k_dsetup(const __grid_constant__ Batch<D
     }
 }
 
-// One thread decodes one chunk of `chunk` symbols into int32 residuals.  The
-// block's chunks are consecutive, so their words form one contiguous range of
-// the stream: the block copies it into shared memory with coalesced loads and
-// every thread then reads its bits from there.  The serial chain per symbol is
-// one look-up-table read plus a few shifts: the next stream word is fetched
-// into a register ahead of the refill, 8 residuals are decoded into registers
-// and written as two 16-byte stores into the thread's own chunk.  Codes longer
-// than the table are located by comparing the left-justified window with the
-// end of each length's canonical range.
+// One thread decodes one chunk of `chunk` symbols.  The bit window is 64 bits
+// held as two 32-bit halves (hi holds the next bits, left-justified); a stream
+// word is appended whenever 32 or fewer valid bits remain, and the two words
+// after it are always in flight.  Every symbol is one look-up-table read and a
+// funnel shift; codes longer than the table are located by comparing the
+// left-justified window with the end of each length's canonical range.  Past
+// the chunk's last word the window fills with zeros; a chunk that consumes
+// more bits than it owns, or meets a prefix no code has, is corrupt.
 constexpr int kDecThreads = 256;  // chunks per decode block
-constexpr int kMaxDynSmem = 227 * 1024;
 
-// STAGED = false (chunks too large for the window to fit shared memory): the
-// words are read from global memory directly.
 struct DecArgs {
     DevParams* par;
     const uint8_t* blob;
     const uint32_t* lut_g;
     const uint16_t* syms;
-    int32_t* out;
+    uint16_t* out;  // [n] decoded symbols
     uint64_t n;
     uint32_t chunk;
     uint64_t nchunks;
-    uint32_t win_cap;
 };
 
-template <bool STAGED, int THREADS>
+template <int THREADS>
 __global__ void __launch_bounds__(THREADS) k_decode(const __grid_constant__ Batch<DecArgs> B) {
     const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
     const DecArgs& A = B.a[fld];
     const uint32_t bid = blockIdx.x - B.off[fld];
     DevParams* par = A.par;
-    const uint8_t* __restrict__ blob = A.blob;
     const uint32_t* __restrict__ lut_g = A.lut_g;
     const uint16_t* __restrict__ syms = A.syms;
-    int32_t* __restrict__ out = A.out;
     const uint64_t n = A.n;
     const uint32_t chunk = A.chunk;
     const uint64_t nchunks = A.nchunks;
-    const uint32_t win_cap = A.win_cap;
-    extern __shared__ __align__(16) uint32_t dsw[];
-    uint32_t* slut = dsw;                   // 1 << kLutBits entries
-    uint32_t* sw = dsw + (1u << kLutBits);  // the block's stream words (from a 16-byte boundary)
+    extern __shared__ __align__(16) uint32_t slut[];  // 1 << kLutBits entries
     __shared__ uint32_t s_fc[32], s_fi[32];
     __shared__ unsigned long long s_lje[33];
-    __shared__ uint32_t s_ws, s_we, s_bad;
     __shared__ __align__(8) unsigned long long s_mbar;
-    const uint32_t flags = par->flags;
-    if (flags & kFlagError) return;
-    const bool cst = (flags & kFlagConstant) != 0;
-    const uint64_t cb0 = (uint64_t)bid * THREADS;
-    const uint64_t c = cb0 + threadIdx.x;
-    const uint64_t cb1 = min(cb0 + THREADS, nchunks);
-    if (cst) {
-        if (c < nchunks) {
-            const uint64_t beg = c * chunk, end = min(beg + chunk, n);
-            for (uint64_t i = beg; i < end; i++) out[i] = 0;
-        }
-        return;
-    }
+    // constant fields have no stream: their residuals are all zero
+    if (par->flags & (kFlagError | kFlagConstant)) return;
     const uint32_t words = par->d_words;
-    const uint32_t* tab = reinterpret_cast<const uint32_t*>(blob + par->off_ct);
-    const uint32_t* stream = reinterpret_cast<const uint32_t*>(blob + par->off_st);
+    const uint32_t* __restrict__ tab = reinterpret_cast<const uint32_t*>(A.blob + par->off_ct);
+    const uint32_t* __restrict__ stream = reinterpret_cast<const uint32_t*>(A.blob + par->off_st);
     if (threadIdx.x < 32) {
         const uint32_t l = threadIdx.x;
         s_fc[l] = par->d_first_code[l];
@@ -252,91 +237,113 @@ __global__ void __launch_bounds__(THREADS) k_decode(const __grid_constant__ Batc
     }
     if (threadIdx.x == 0) {
         s_lje[32] = ~0ull;
-        const uint32_t ws = tab[cb0];
-        const uint32_t we = (cb1 < nchunks) ? tab[cb1] : words;
-        // a non-monotone table cannot come from the encoder
-        const bool bad = ws > we || we > words;
-        if (bad) set_error(par, FPSNR_ECORRUPT);
-        s_bad = bad;
-        s_ws = bad ? 0 : ws;
-        s_we = bad ? 0 : we;
         mbar_init(&s_mbar, 1);
     }
     __syncthreads();
-    if (s_bad) return;
-    const uint32_t ws = s_ws, we = s_we;
-    // the window is staged only when it fits; otherwise this block reads global memory
-    const bool staged = STAGED && (((we + 3u) & ~3u) - (ws & ~3u)) <= win_cap + 4u;
-    // the look-up table and the 16-byte aligned cover of the window arrive by two
-    // bulk copies (the stream section is padded to 16 bytes, so the cover stays in it)
-    const uint32_t ws_al = ws & ~3u;
-    const uint32_t win_bytes = staged ? (((we + 3u) & ~3u) - ws_al) * 4u : 0u;
     if (threadIdx.x == 0) {
         const uint32_t lut_bytes = (1u << kLutBits) * 4u;
-        mbar_arrive_expect_tx(&s_mbar, lut_bytes + win_bytes);
+        mbar_arrive_expect_tx(&s_mbar, lut_bytes);
         bulk_g2s(slut, lut_g, lut_bytes, &s_mbar);
-        if (win_bytes) bulk_g2s(sw, stream + ws_al, win_bytes, &s_mbar);
     }
     if (!mbar_wait_bounded(&s_mbar, 0)) {
-        // never expected; record it, let the copies land, then leave
+        // never expected; record it, let the copy land, then leave
         set_error(par, FPSNR_ETIMEOUT);
         mbar_wait_bounded(&s_mbar, 0);
         return;
     }
+    const uint64_t c = (uint64_t)bid * THREADS + threadIdx.x;
     if (c >= nchunks) return;
     const uint64_t beg = c * chunk;
     const uint32_t cnt = (uint32_t)(min(beg + chunk, n) - beg);
-    const int32_t R = (int32_t)par->d_radius;
     const uint32_t lmax = par->d_lmax;
     const uint32_t w0 = tab[c];
     const uint32_t w1 = (c + 1 < nchunks) ? tab[c + 1] : words;
-    if (w0 > w1 || w0 < ws || w1 > we) { set_error(par, FPSNR_ECORRUPT); return; }
-    auto word = [&](uint32_t k) -> uint32_t { return staged ? sw[k - ws_al] : __ldg(stream + k); };
-    uint64_t buf = 0;
-    uint32_t nb = 0, wi = w0;
-    // the next two words are always in flight (a global load takes several
-    // refills' worth of symbols to arrive)
-    uint32_t nxt = wi < w1 ? word(wi) : 0u;
-    uint32_t nxt2 = wi + 1 < w1 ? word(wi + 1) : 0u;
+    if (w0 > w1 || w1 > words) {
+        set_error(par, FPSNR_ECORRUPT);
+        return;
+    }
+    uint32_t hi = 0u, lo = 0u;  // window; bits past the valid ones are zero
+    uint32_t nb = 0u;           // valid bits in the window
+    uint32_t wi = w0;           // words appended so far (past w1 they are zero)
+    uint32_t nxt = wi < w1 ? __ldg(stream + wi) : 0u;
+    uint32_t nxt2 = wi + 1 < w1 ? __ldg(stream + wi + 1) : 0u;
     bool bad = false;
-    // decodes one residual; sets `bad` on a malformed stream
-    auto one = [&]() -> int32_t {
-        if (nb <= 32 && wi < w1) {
-            buf |= (uint64_t)nxt << (32 - nb);
-            nb += 32;
+    auto one = [&]() -> uint32_t {
+        if (nb <= 32u) {
+            hi |= __funnelshift_rc(nxt, 0u, nb);        // nxt >> nb (0 when nb == 32)
+            lo = __funnelshift_lc(0u, nxt, 32u - nb);   // nxt << (32 - nb) (0 when nb == 0)
+            nb += 32u;
             wi++;
             nxt = nxt2;
-            nxt2 = wi + 1 < w1 ? word(wi + 1) : 0u;
+            nxt2 = wi + 1 < w1 ? __ldg(stream + wi + 1) : 0u;
         }
-        const uint32_t e = slut[(uint32_t)(buf >> (64 - kLutBits))];
+        const uint32_t e = slut[hi >> (32 - kLutBits)];
         uint32_t l = e & 0xffu, sym = e >> 8;
-        if (l == 0) {
-            const uint32_t w32 = (uint32_t)(buf >> 32);
+        if (l == 0u) {
             l = kLutBits + 1;
-            while (l <= lmax && (unsigned long long)w32 >= s_lje[l]) l++;
-            if (l > lmax) { bad = true; l = 0; sym = 0; }
-            else sym = syms[s_fi[l] + ((w32 >> (32 - l)) - s_fc[l])];
+            while (l <= lmax && (unsigned long long)hi >= s_lje[l]) l++;
+            if (l > lmax) {
+                bad = true;
+                l = 1u;
+                sym = 0u;
+            } else {
+                sym = syms[s_fi[l] + ((hi >> (32 - l)) - s_fc[l])];
+            }
         }
-        if (l > nb) { bad = true; l = 0; }
-        buf <<= l;
+        hi = __funnelshift_l(lo, hi, l);
+        lo <<= l;
         nb -= l;
-        return sym ? (int32_t)sym - R : 0;
+        return sym;
     };
-    int32_t* dst = out + beg;
+    uint16_t* __restrict__ dst = A.out + beg;
     const uint32_t cnt8 = cnt & ~7u;
     for (uint32_t i = 0; i < cnt8; i += 8) {
-        int32_t o[8];
+        uint32_t s[8];
 #pragma unroll
-        for (int k = 0; k < 8; k++) o[k] = one();
-        if (bad) { set_error(par, FPSNR_ECORRUPT); return; }
-        int4* d4 = reinterpret_cast<int4*>(dst + i);
-        d4[0] = make_int4(o[0], o[1], o[2], o[3]);
-        d4[1] = make_int4(o[4], o[5], o[6], o[7]);
+        for (int k = 0; k < 8; k++) s[k] = one();
+        *reinterpret_cast<uint4*>(dst + i) =
+            make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16), s[6] | (s[7] << 16));
     }
-    for (uint32_t i = cnt8; i < cnt; i++) {
-        const int32_t v = one();
-        if (bad) { set_error(par, FPSNR_ECORRUPT); return; }
-        dst[i] = v;
+    for (uint32_t i = cnt8; i < cnt; i++) dst[i] = (uint16_t)one();
+    // bits consumed = appended - still valid; the chunk owns (w1 - w0) words
+    const uint64_t used = 32ull * (wi - w0) - nb;
+    if (bad || used > 32ull * (w1 - w0)) set_error(par, FPSNR_ECORRUPT);
+}
+
+// Residual of point `idx` from its symbol: code - R, or for symbol 0 (an
+// outlier) the residual stored for idx in the outlier list, which is sorted by
+// point index.  A missing entry means the blob is corrupt.
+__device__ __forceinline__ uint32_t residual_of(uint32_t code, uint32_t R, uint32_t idx,
+                                                const uint2* __restrict__ ol, uint32_t no,
+                                                DevParams* par) {
+    if (code) return code - R;
+    uint32_t lo = 0u, hi = no;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(&ol[mid].x) < idx) lo = mid + 1u;
+        else hi = mid;
+    }
+    if (lo < no && __ldg(&ol[lo].x) == idx) return __ldg(&ol[lo].y);
+    set_error(par, FPSNR_ECORRUPT);
+    return 0u;
+}
+
+// Loads IPT consecutive symbols (IPT a multiple of 4; p 8-byte aligned, and
+// 16-byte aligned when IPT >= 8).
+template <int IPT>
+__device__ __forceinline__ void load_syms(const uint16_t* __restrict__ p, uint32_t (&v)[IPT]) {
+    if constexpr (IPT == 4) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        v[0] = q.x & 0xffffu; v[1] = q.x >> 16; v[2] = q.y & 0xffffu; v[3] = q.y >> 16;
+    } else {
+#pragma unroll
+        for (int k = 0; k < IPT; k += 8) {
+            const uint4 q = *reinterpret_cast<const uint4*>(p + k);
+            v[k] = q.x & 0xffffu; v[k + 1] = q.x >> 16;
+            v[k + 2] = q.y & 0xffffu; v[k + 3] = q.y >> 16;
+            v[k + 4] = q.z & 0xffffu; v[k + 5] = q.z >> 16;
+            v[k + 6] = q.w & 0xffffu; v[k + 7] = q.w >> 16;
+        }
     }
 }
 
@@ -348,22 +355,6 @@ struct SmallArgs {
     uint32_t G;       // blocks per field
     int* status;      // k_status only
 };
-
-__global__ void __launch_bounds__(256) k_scatter(const __grid_constant__ Batch<SmallArgs> B) {
-    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
-    const SmallArgs& A = B.a[fld];
-    const uint32_t bid = blockIdx.x - B.off[fld];
-    DevParams* par = A.par;
-    if (par->flags & kFlagError) return;
-    const uint32_t no = par->d_nout;
-    const uint2* ol = reinterpret_cast<const uint2*>(A.blob + par->off_ou);
-    int32_t* out = reinterpret_cast<int32_t*>(A.out);
-    for (uint32_t i = bid * blockDim.x + threadIdx.x; i < no; i += A.G * blockDim.x) {
-        const uint2 e = ol[i];
-        if (e.x >= A.n) { set_error(par, FPSNR_ECORRUPT); return; }
-        out[e.x] = (int32_t)e.y;
-    }
-}
 
 __global__ void __launch_bounds__(256) k_patch(const __grid_constant__ Batch<SmallArgs> B) {
     const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
@@ -395,7 +386,9 @@ constexpr uint32_t kStA = 1u, kStP = 2u;
 
 struct ScanArgs {
     DevParams* par;
-    uint32_t* data;
+    uint32_t* data;         // int32 lattice values in the output buffer (later passes)
+    const uint16_t* syms;   // decoded symbols (first pass)
+    const uint8_t* blob;    // outlier list (first pass)
     uint32_t A, L, B;       // (outer, scan length, inner)
     uint32_t nbt;           // strided: column tiles
     uint32_t tpr;           // contiguous: tiles per row
@@ -413,14 +406,16 @@ __device__ __forceinline__ void tile_done(uint32_t* ctr, uint32_t tiles) {
     }
 }
 
-// Contiguous rows: each tile is 256*IPT consecutive points of one row.
-template <int IPT, bool FINAL, bool VEC>
+// Contiguous rows: each tile is 256*IPT consecutive points of one row.  SYM:
+// the input is the decoded symbols (first pass), else int32 values in place.
+template <int IPT, bool FINAL, bool VEC, bool SYM>
 __global__ void __launch_bounds__(256) k_scan_contig(const __grid_constant__ Batch<ScanArgs> B) {
     const ScanArgs& a = B.a[batch_field(B.off, B.count, blockIdx.x)];
     __shared__ uint32_t sh[33];
     __shared__ uint32_t s_id, s_carry;
     const uint32_t tid = threadIdx.x;
-    const uint32_t epoch = a.par->dec_epoch;
+    DevParams* par = a.par;
+    const uint32_t epoch = par->dec_epoch;
     if (tid == 0) s_id = atomicAdd(a.ctr, 1u);
     __syncthreads();
     const uint32_t id = s_id;
@@ -429,7 +424,24 @@ __global__ void __launch_bounds__(256) k_scan_contig(const __grid_constant__ Bat
     const uint64_t rbase = (uint64_t)row * W;
     const uint32_t c0 = t * (256u * IPT) + tid * IPT;
     uint32_t v[IPT];
-    if (VEC && c0 + IPT <= W) {
+    if (SYM) {
+        const uint32_t flags = par->flags;
+        if (flags & kFlagConstant) {
+#pragma unroll
+            for (int k = 0; k < IPT; k++) v[k] = 0u;
+        } else {
+            const uint32_t R = par->d_radius, no = par->d_nout;
+            const uint2* __restrict__ ol = reinterpret_cast<const uint2*>(a.blob + par->off_ou);
+            if (VEC && c0 + IPT <= W) {
+                load_syms<IPT>(a.syms + rbase + c0, v);
+            } else {
+#pragma unroll
+                for (int k = 0; k < IPT; k++) v[k] = (c0 + k < W) ? a.syms[rbase + c0 + k] : R;
+            }
+#pragma unroll
+            for (int k = 0; k < IPT; k++) v[k] = residual_of(v[k], R, (uint32_t)(rbase + c0 + k), ol, no, par);
+        }
+    } else if (VEC && c0 + IPT <= W) {
 #pragma unroll
         for (int k = 0; k < IPT; k += 4) {
             uint4 q = *reinterpret_cast<const uint4*>(a.data + rbase + c0 + k);
@@ -453,7 +465,7 @@ __global__ void __launch_bounds__(256) k_scan_contig(const __grid_constant__ Bat
                 st_release(a.flags + id, (epoch << 2) | (t == 0 ? kStP : kStA));
             }
             if (t > 0) {
-                carry = warp_lookback(a.flags, a.agg, a.inc, id, id - t, epoch, a.par);
+                carry = warp_lookback(a.flags, a.agg, a.inc, id, id - t, epoch, par);
                 if (tid == 0) {
                     a.inc[id] = carry + agg;
                     __threadfence();
@@ -467,7 +479,6 @@ __global__ void __launch_bounds__(256) k_scan_contig(const __grid_constant__ Bat
     }
     const uint32_t add = ex + carry;
     if (FINAL) {
-        const DevParams* par = a.par;
         const float s = par->s, xmin = par->xmin;
         float* outf = reinterpret_cast<float*>(a.data);
         float f[IPT];
@@ -637,61 +648,233 @@ __global__ void __launch_bounds__(256) k_scan_strided(const __grid_constant__ Ba
 }
 
 // ---------------------------------------------------------------------------
+// 2D inverse Lorenzo over bands of rows: reduce, then scan
+// ---------------------------------------------------------------------------
+//
+// With S the 2D inclusive prefix sum of the residuals, band b (rows r0..r1-1)
+// needs only S(r0 - 1, .), which is the prefix along x of E_b, the sum of the
+// residuals of all rows above r0 per column.  E_b is the exclusive prefix over
+// bands of every band's column sums, so three launches with no waiting between
+// blocks give the exact 2D sum: column sums per band, their prefix over bands,
+// then per band the row prefixes added on top of the carry row.  Each thread
+// owns 8*G consecutive columns; a row of up to 2048*G columns is one block.
+
+struct BandArgs {
+    DevParams* par;
+    const uint16_t* syms;  // [rows * nx] decoded symbols
+    const uint8_t* blob;   // outlier list
+    uint32_t* bsum;        // [nbands * nx] column sums, then their exclusive prefix over bands
+    float* out;            // [rows * nx]
+    uint32_t nx, rows, tr, nbands;
+};
+
+// Residuals of columns c0 .. c0 + 8G - 1 of row r (zero past the row end).
+template <int G, bool VEC>
+__device__ __forceinline__ void band_row_residuals(const BandArgs& a, uint32_t r, uint32_t c0,
+                                                   uint32_t R, const uint2* __restrict__ ol,
+                                                   uint32_t no, uint32_t (&d)[8 * G]) {
+    const uint64_t base = (uint64_t)r * a.nx;
+    if (VEC) {
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            uint32_t v[8];
+            if (c0 + 8u * g < a.nx) load_syms<8>(a.syms + base + c0 + 8u * g, v);
+            else {
+#pragma unroll
+                for (int k = 0; k < 8; k++) v[k] = R;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) d[8 * g + k] = v[k];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8 * G; k++) d[k] = (c0 + k < a.nx) ? a.syms[base + c0 + k] : R;
+    }
+#pragma unroll
+    for (int k = 0; k < 8 * G; k++)
+        d[k] = residual_of(d[k], R, (uint32_t)(base + c0 + k), ol, no, a.par);
+}
+
+// one block per band: column sums of the band's residuals
+template <int G, bool VEC>
+__global__ void __launch_bounds__(256) k_band_sum(const __grid_constant__ Batch<BandArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const BandArgs& a = B.a[fld];
+    const uint32_t band = blockIdx.x - B.off[fld];
+    DevParams* par = a.par;
+    const uint32_t flags = par->flags;
+    if (flags & kFlagError) return;
+    const uint32_t c0 = threadIdx.x * 8u * G;
+    if (c0 >= a.nx) return;
+    uint32_t acc[8 * G];
+#pragma unroll
+    for (int k = 0; k < 8 * G; k++) acc[k] = 0u;
+    if (!(flags & kFlagConstant)) {
+        const uint32_t R = par->d_radius, no = par->d_nout;
+        const uint2* __restrict__ ol = reinterpret_cast<const uint2*>(a.blob + par->off_ou);
+        const uint32_t r0 = band * a.tr, r1 = min(r0 + a.tr, a.rows);
+        for (uint32_t r = r0; r < r1; r++) {
+            uint32_t d[8 * G];
+            band_row_residuals<G, VEC>(a, r, c0, R, ol, no, d);
+#pragma unroll
+            for (int k = 0; k < 8 * G; k++) acc[k] += d[k];
+        }
+    }
+    uint32_t* dst = a.bsum + (uint64_t)band * a.nx;
+#pragma unroll
+    for (int k = 0; k < 8 * G; k++)
+        if (c0 + k < a.nx) dst[c0 + k] = acc[k];
+}
+
+// one thread per column: exclusive prefix over the bands, in place
+__global__ void __launch_bounds__(256) k_band_carry(const __grid_constant__ Batch<BandArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const BandArgs& a = B.a[fld];
+    if (a.par->flags & kFlagError) return;
+    const uint32_t col = (blockIdx.x - B.off[fld]) * blockDim.x + threadIdx.x;
+    if (col >= a.nx) return;
+    uint32_t* p = a.bsum + col;
+    const uint64_t st = a.nx;
+    uint32_t acc = 0u;
+    uint32_t b = 0;
+    for (; b + 8 <= a.nbands; b += 8) {
+        uint32_t t[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) t[k] = p[(uint64_t)(b + k) * st];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            p[(uint64_t)(b + k) * st] = acc;
+            acc += t[k];
+        }
+    }
+    for (; b < a.nbands; b++) {
+        const uint32_t t = p[(uint64_t)b * st];
+        p[(uint64_t)b * st] = acc;
+        acc += t;
+    }
+}
+
+// Inclusive prefix along the block's columns of one row given per thread:
+// thread-local prefix plus the block's exclusive scan of the thread totals.
+template <int G>
+__device__ __forceinline__ void band_row_prefix(uint32_t (&d)[8 * G], uint32_t* sh) {
+#pragma unroll
+    for (int k = 1; k < 8 * G; k++) d[k] += d[k - 1];
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(d[8 * G - 1], sh, &tot);
+#pragma unroll
+    for (int k = 0; k < 8 * G; k++) d[k] += ex;
+}
+
+// one block per band: carry row, then every row's prefix, dequantized
+template <int G, bool VEC>
+__global__ void __launch_bounds__(256) k_band_scan(const __grid_constant__ Batch<BandArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const BandArgs& a = B.a[fld];
+    const uint32_t band = blockIdx.x - B.off[fld];
+    DevParams* par = a.par;
+    __shared__ uint32_t sh[33];
+    const uint32_t flags = par->flags;
+    if (flags & kFlagError) return;
+    const bool cst = (flags & kFlagConstant) != 0;
+    const uint32_t c0 = threadIdx.x * 8u * G;
+    const float s = par->s, xmin = par->xmin;
+    const uint32_t R = par->d_radius, no = par->d_nout;
+    const uint2* __restrict__ ol = reinterpret_cast<const uint2*>(a.blob + par->off_ou);
+    // S(r0 - 1, .) = prefix along x of the carry row
+    uint32_t col[8 * G];
+    {
+        const uint32_t* e = a.bsum + (uint64_t)band * a.nx;
+#pragma unroll
+        for (int k = 0; k < 8 * G; k++) col[k] = (c0 + k < a.nx) ? e[c0 + k] : 0u;
+        band_row_prefix<G>(col, sh);
+    }
+    const uint32_t r0 = band * a.tr, r1 = min(r0 + a.tr, a.rows);
+    for (uint32_t r = r0; r < r1; r++) {
+        uint32_t d[8 * G];
+        if (cst || c0 >= a.nx) {
+#pragma unroll
+            for (int k = 0; k < 8 * G; k++) d[k] = 0u;
+        } else {
+            band_row_residuals<G, VEC>(a, r, c0, R, ol, no, d);
+        }
+        band_row_prefix<G>(d, sh);
+        float f[8 * G];
+#pragma unroll
+        for (int k = 0; k < 8 * G; k++) {
+            col[k] += d[k];
+            f[k] = __fmaf_rn(__int2float_rn((int32_t)col[k]), s, xmin);
+        }
+        float* o = a.out + (uint64_t)r * a.nx + c0;
+        if (VEC) {
+#pragma unroll
+            for (int g = 0; g < 2 * G; g++)
+                if (c0 + 4u * g < a.nx)
+                    *reinterpret_cast<float4*>(o + 4 * g) =
+                        make_float4(f[4 * g], f[4 * g + 1], f[4 * g + 2], f[4 * g + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8 * G; k++)
+                if (c0 + k < a.nx) o[k] = f[k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host launcher
 // ---------------------------------------------------------------------------
 
-template <int IPT, bool FINAL>
+template <int IPT, bool FINAL, bool SYM>
 static void launch_contig_t(const Batch<ScanArgs>& b, uint32_t tiles, bool vec, cudaStream_t st) {
-    if (vec) k_scan_contig<IPT, FINAL, true><<<tiles, 256, 0, st>>>(b);
-    else k_scan_contig<IPT, FINAL, false><<<tiles, 256, 0, st>>>(b);
+    if (vec) k_scan_contig<IPT, FINAL, true, SYM><<<tiles, 256, 0, st>>>(b);
+    else k_scan_contig<IPT, FINAL, false, SYM><<<tiles, 256, 0, st>>>(b);
 }
 
-template <bool FINAL>
+template <bool FINAL, bool SYM>
 static void launch_contig(const Batch<ScanArgs>& b, uint32_t tiles, int ipt, bool vec,
                           cudaStream_t st) {
-    if (ipt == 4) launch_contig_t<4, FINAL>(b, tiles, vec, st);
-    else if (ipt == 8) launch_contig_t<8, FINAL>(b, tiles, vec, st);
-    else launch_contig_t<16, FINAL>(b, tiles, vec, st);
+    if (ipt == 4) launch_contig_t<4, FINAL, SYM>(b, tiles, vec, st);
+    else if (ipt == 8) launch_contig_t<8, FINAL, SYM>(b, tiles, vec, st);
+    else launch_contig_t<16, FINAL, SYM>(b, tiles, vec, st);
 }
 
-// Shared-memory stream window of one decode block: room for its chunks at up
-// to 16 bits per symbol (a chunk may need ceil(chunk * lmax / 32) words; a block
-// whose window is larger reads its words from global memory instead).  Keeping
-// the window small keeps several blocks resident per SM.
-uint32_t decode_window_words(const fpsnr_plan_s* p) {
-    const uint32_t bits = (uint32_t)std::min(p->lmax, 16);
-    return (uint32_t)(kDecThreads * (((uint64_t)p->chunk * bits + 31) / 32));
-}
-
-// LUT + window + 4 words of slack for rounding the window to 16-byte bounds
-int decode_smem_bytes(const fpsnr_plan_s* p) {
-    return (int)(((1u << kLutBits) + decode_window_words(p) + 8) * 4);
-}
-
-// Largest dynamic shared memory the staged decoder can take on this device:
-// the per-block opt-in limit minus the kernel's static shared memory.
-static int decode_smem_limit() {
-    static int limit = -1;
-    if (limit < 0) {
-        int dev = 0, optin = 0;
-        cudaFuncAttributes fa;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-            cudaFuncGetAttributes(&fa, k_decode<false, kDecThreads>) != cudaSuccess)
-            return 0;
-        limit = std::min(kMaxDynSmem, optin - (int)fa.sharedSizeBytes);
+template <int G, bool VEC>
+static void launch_band_t(const Batch<BandArgs>& b, const uint32_t* nb, const uint32_t* ncol,
+                          fp::Profiler& prof, cudaStream_t st) {
+    Batch<BandArgs> bb = b;
+    const uint32_t tb = batch_offsets(bb, nb);
+    {
+        StageScope sc(prof, kStBandSum, st);
+        k_band_sum<G, VEC><<<tb, 256, 0, st>>>(bb);
     }
-    return limit;
+    Batch<BandArgs> bc = b;
+    const uint32_t tc = batch_offsets(bc, ncol);
+    {
+        StageScope sc(prof, kStBandCarry, st);
+        k_band_carry<<<tc, 256, 0, st>>>(bc);
+    }
+    {
+        StageScope sc(prof, kStScanFinal, st);
+        k_band_scan<G, VEC><<<tb, 256, 0, st>>>(bb);
+    }
 }
 
-// The attribute belongs to the kernel, not to a plan: set it to the largest
-// size any plan can ask for.
-int decode_prepare(const fpsnr_plan_s*) { return decode_smem_limit() > 0 ? FPSNR_OK : FPSNR_ECUDA; }
+template <bool VEC>
+static void launch_band(const Batch<BandArgs>& b, const uint32_t* nb, const uint32_t* ncol, int g,
+                        fp::Profiler& prof, cudaStream_t st) {
+    if (g == 1) launch_band_t<1, VEC>(b, nb, ncol, prof, st);
+    else if (g == 2) launch_band_t<2, VEC>(b, nb, ncol, prof, st);
+    else launch_band_t<4, VEC>(b, nb, ncol, prof, st);
+}
+
+int decode_prepare(const fpsnr_plan_s*) { return FPSNR_OK; }
 
 static uint32_t small_blocks_d(const fpsnr_plan_s* p, int count) {
     const int g = std::max(1, p->sm_count / std::max(1, count));
     return (uint32_t)std::min(g, 64);
 }
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
                             const uint64_t* bytes, float* const* d_out, int* d_status, int count,
@@ -724,60 +907,72 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
         k_dsetup<<<count, 1024, 0, st>>>(b);
         if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
     }
-    // decode: one launch per (staged, shared-memory size) group
+    // decode every field into its plan's symbol buffer
     {
-        bool done[kMaxBatch] = {};
-        for (int f0 = 0; f0 < count; f0++) {
-            if (done[f0] || P[f0]->n == 0) continue;
-            const int smem0 = decode_smem_bytes(P[f0]);
-            Batch<DecArgs> b;
-            b.count = 0;
-            for (int f = f0; f < count; f++) {
-                const fpsnr_plan_s* p = P[f];
-                if (done[f] || p->n == 0 || decode_smem_bytes(p) != smem0) continue;
-                done[f] = true;
-                const Workspace& w = p->w;
-                blocks[b.count] = (uint32_t)((p->nchunks + kDecThreads - 1) / kDecThreads);
-                b.a[b.count++] = DecArgs{w.par, reinterpret_cast<const uint8_t*>(d_blob[f]), w.dlut,
-                                         w.dsyms, reinterpret_cast<int32_t*>(d_out[f]), p->n,
-                                         (uint32_t)p->chunk, p->nchunks, decode_window_words(p)};
-            }
+        Batch<DecArgs> b;
+        b.count = 0;
+        for (int f = 0; f < count; f++) {
+            const fpsnr_plan_s* p = P[f];
+            if (p->n == 0) continue;
+            const Workspace& w = p->w;
+            blocks[b.count] = (uint32_t)((p->nchunks + kDecThreads - 1) / kDecThreads);
+            b.a[b.count++] = DecArgs{w.par, reinterpret_cast<const uint8_t*>(d_blob[f]), w.dlut,
+                                     w.dsyms, w.codes, p->n, (uint32_t)p->chunk, p->nchunks};
+        }
+        if (b.count) {
             const uint32_t tot = batch_offsets(b, blocks);
             StageScope sc(prof, kStDecode, st);
-            // every thread streams its own chunk from global memory (two words in
-            // flight); only the look-up table is staged in shared memory
-            k_decode<false, kDecThreads><<<tot, kDecThreads, (1u << kLutBits) * 4 + 64, st>>>(b);
+            k_decode<kDecThreads><<<tot, kDecThreads, (1u << kLutBits) * 4, st>>>(b);
             if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
         }
     }
-    Batch<SmallArgs> sb;
-    sb.count = (uint32_t)count;
-    for (int f = 0; f < count; f++) {
-        const fpsnr_plan_s* p = P[f];
-        sb.a[f] = SmallArgs{p->w.par, reinterpret_cast<const uint8_t*>(d_blob[f]), d_out[f], p->n,
-                            small_blocks_d(p, count), d_status ? d_status + f : nullptr};
-        blocks[f] = p->n ? sb.a[f].G : 0u;
+    // 2D fields whose rows fit one block: bands of rows, grouped by kernel variant
+    {
+        bool done[kMaxBatch] = {};
+        for (int f0 = 0; f0 < count; f0++) {
+            const fpsnr_plan_s* p0 = P[f0];
+            if (done[f0] || p0->n == 0 || !p0->band.on) continue;
+            const bool vec0 = p0->band.vec && aligned16(d_out[f0]);
+            Batch<BandArgs> b;
+            b.count = 0;
+            uint32_t nb[kMaxBatch], ncol[kMaxBatch];
+            for (int f = f0; f < count; f++) {
+                const fpsnr_plan_s* p = P[f];
+                if (done[f] || p->n == 0 || !p->band.on) continue;
+                const bool vec = p->band.vec && aligned16(d_out[f]);
+                if (p->band.g != p0->band.g || vec != vec0) continue;
+                done[f] = true;
+                const BandGeom& g = p->band;
+                nb[b.count] = g.nbands;
+                ncol[b.count] = (g.nx + 255u) / 256u;
+                b.a[b.count++] = BandArgs{p->w.par, p->w.codes,
+                                          reinterpret_cast<const uint8_t*>(d_blob[f]), p->w.bsum,
+                                          d_out[f], g.nx, g.rows, g.tr, g.nbands};
+            }
+            if (vec0) launch_band<true>(b, nb, ncol, p0->band.g, prof, st);
+            else launch_band<false>(b, nb, ncol, p0->band.g, prof, st);
+            if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
+        }
     }
-    const uint32_t small_tot = batch_offsets(sb, blocks);
-    if (small_tot) {
-        StageScope sc(prof, kStScatter, st);
-        k_scatter<<<small_tot, 256, 0, st>>>(sb);
-        if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
-    }
-    // inverse Lorenzo passes, grouped by pass index and kernel variant
+    // other shapes: inverse Lorenzo passes, grouped by pass index and kernel variant
     for (int i = 0; i < 3; i++) {
         bool done[kMaxBatch] = {};
+        auto vec_of = [&](const fpsnr_plan_s* p, int f) {
+            const ScanPass& sp = p->pass[i];
+            return (i == 0 ? sp.vec16 : sp.vec) && aligned16(d_out[f]);
+        };
         for (int f0 = 0; f0 < count; f0++) {
             const fpsnr_plan_s* p0 = P[f0];
             if (done[f0] || p0->n == 0 || p0->n_passes <= i) continue;
             const ScanPass& s0 = p0->pass[i];
+            const bool vec0 = vec_of(p0, f0);
             Batch<ScanArgs> b;
             b.count = 0;
             for (int f = f0; f < count; f++) {
                 const fpsnr_plan_s* p = P[f];
                 if (done[f] || p->n == 0 || p->n_passes <= i) continue;
                 const ScanPass& sp = p->pass[i];
-                if (sp.kind != s0.kind || sp.ipt != s0.ipt || sp.vec != s0.vec ||
+                if (sp.kind != s0.kind || sp.ipt != s0.ipt || vec_of(p, f) != vec0 ||
                     sp.final_pass != s0.final_pass)
                     continue;
                 done[f] = true;
@@ -785,6 +980,8 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
                 ScanArgs a;
                 a.par = w.par;
                 a.data = reinterpret_cast<uint32_t*>(d_out[f]);
+                a.syms = w.codes;
+                a.blob = reinterpret_cast<const uint8_t*>(d_blob[f]);
                 a.A = sp.A;
                 a.L = sp.L;
                 a.B = sp.B;
@@ -806,9 +1003,15 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
             const uint32_t tot = batch_offsets(b, blocks);
             StageScope sc(prof, s0.final_pass ? kStScanFinal : (i == 0 ? kStScanX : kStScanY), st);
             if (s0.kind == 0) {
-                if (s0.final_pass) launch_contig<true>(b, tot, s0.ipt, s0.vec, st);
-                else launch_contig<false>(b, tot, s0.ipt, s0.vec, st);
-            } else if (s0.vec) {
+                // the first pass of every shape is contiguous and reads the symbols
+                if (i == 0) {
+                    if (s0.final_pass) launch_contig<true, true>(b, tot, s0.ipt, vec0, st);
+                    else launch_contig<false, true>(b, tot, s0.ipt, vec0, st);
+                } else {
+                    if (s0.final_pass) launch_contig<true, false>(b, tot, s0.ipt, vec0, st);
+                    else launch_contig<false, false>(b, tot, s0.ipt, vec0, st);
+                }
+            } else if (vec0) {
                 if (s0.final_pass) k_scan_strided<16, 4, true><<<tot, 256, 0, st>>>(b);
                 else k_scan_strided<16, 4, false><<<tot, 256, 0, st>>>(b);
             } else {
@@ -818,6 +1021,15 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
             if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
         }
     }
+    Batch<SmallArgs> sb;
+    sb.count = (uint32_t)count;
+    for (int f = 0; f < count; f++) {
+        const fpsnr_plan_s* p = P[f];
+        sb.a[f] = SmallArgs{p->w.par, reinterpret_cast<const uint8_t*>(d_blob[f]), d_out[f], p->n,
+                            small_blocks_d(p, count), d_status ? d_status + f : nullptr};
+        blocks[f] = p->n ? sb.a[f].G : 0u;
+    }
+    const uint32_t small_tot = batch_offsets(sb, blocks);
     if (small_tot) {
         StageScope sc(prof, kStPatch, st);
         k_patch<<<small_tot, 256, 0, st>>>(sb);

@@ -96,6 +96,8 @@ SHAPES = [
     ((130, 1031), 2), ((9, 130), 1),
     ((1, 1, 1), 3), ((2, 3, 5), 3), ((17, 33, 65), 3), ((9, 130, 7), 3), ((40, 40, 40), 3),
     ((5, 9, 300), 2), ((4, 6, 33), 1),
+    # 2D rows of 8*G columns per thread (G = 2, 4) and rows wider than one block
+    ((40, 2056), 2), ((37, 5000), 2), ((11, 8200), 2), ((9, 9001), 2),
 ]
 
 
