@@ -54,7 +54,7 @@ void carve(fpsnr_plan_s* p, uint8_t* base, size_t* total) {
     w.hbuf1 = c.take<unsigned long long>(p->nsym);
     w.hbuf2 = c.take<unsigned long long>(p->nsym);
     w.hpar = c.take<uint32_t>(2ull * p->nsym);
-    w.dlut = c.take<uint32_t>(1u << fp::kLutBits);
+    w.dlut = c.take<uint32_t>((1u << fp::kLutBits) + fp::kL2Cap);
     w.dsyms = c.take<uint16_t>(fp::kMaxSym);
     w.lb_flags = c.take<uint32_t>(std::max<uint64_t>(p->lb_tiles_total, 1));
     w.lb_vals = c.take<uint32_t>(2 * std::max<uint64_t>(p->lb_tiles_total, 1) * p->lb_width);

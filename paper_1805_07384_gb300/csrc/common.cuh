@@ -23,7 +23,9 @@ constexpr uint32_t kFlagError = 1u << 31;  // internal: a device-side error occu
 constexpr int kMaxRadius = 32768;
 constexpr int kMaxSym = 2 * kMaxRadius;
 constexpr int kMaxLmax = 27;
-constexpr int kLutBits = 12;  // decode look-up table width
+constexpr int kLutBits = 12;  // decode look-up table width (first level)
+constexpr int kL2Sub = 6;     // second level: up to this many bits past the first level
+constexpr int kL2Cap = 4096;  // second-level entries (shared memory of the decoder)
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 // Per-call device record.  Written by kernels, read by later kernels.
@@ -46,6 +48,7 @@ struct DevParams {
     uint64_t off_cb, off_ct, off_st, off_ou, off_vb, total;
     // decompression: header fields of the blob being decoded
     uint32_t d_radius, d_chunk, d_lmax, d_nsym, d_nchunks, d_words, d_nout, d_nvb;
+    uint32_t d_l2n;  // second-level table entries in use
     uint32_t d_count[32], d_first_code[32], d_first_index[32];
 };
 
@@ -70,7 +73,7 @@ struct Workspace {
     unsigned long long* hbuf2;  // [nsym] sort ping-pong
     uint32_t* hpar;             // [2*nsym] parent of every node
     // decoding tables
-    uint32_t* dlut;  // [1 << kLutBits]
+    uint32_t* dlut;  // [(1 << kLutBits) + kL2Cap] first-level table, then second-level tables
     uint16_t* dsyms; // [kMaxSym]
     // inverse-Lorenzo look-back state
     uint32_t* lb_flags;  // [n_lb_tiles]
