@@ -60,35 +60,97 @@ def parse():
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """SM clock, power and clock-event reasons of this process's GPU, read
+    through NVML (libnvidia-ml, read-only queries) every 2 ms on a thread while
+    the timed region runs; falls back to `nvidia-smi -lms 200` without NVML."""
 
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index = index
-        self.rows = []
+    def __init__(self, device):
+        self.device = device
+        self.rows = []          # (sm_mhz, reasons bitmask, power mW)
+        self.smi_rows = []
+        self.max_mhz = None
         self.proc = None
         self.thread = None
+        self.stop_flag = threading.Event()
+        self.nvml = None
+        self.handle = None
+
+    def _nvml_open(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+        except OSError:
+            return False
+        if lib.nvmlInit_v2() != 0:
+            return False
+        h = ctypes.c_void_p()
+        props = None
+        try:
+            import torch
+            props = torch.cuda.get_device_properties(self.device)
+        except Exception:
+            pass
+        ok = False
+        if props is not None and hasattr(props, "pci_bus_id"):
+            bus = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0".encode()
+            ok = lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) == 0
+        if not ok:
+            idx = self.device.index if hasattr(self.device, "index") and self.device.index is not None else 0
+            ok = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(idx), ctypes.byref(h)) == 0
+        if not ok:
+            return False
+        self.nvml, self.handle = lib, h
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:  # NVML_CLOCK_SM
+            self.max_mhz = float(mx.value)
+        return True
+
+    def _poll(self):
+        import ctypes
+        lib, h = self.nvml, self.handle
+        mhz, rs, mw = ctypes.c_uint(), ctypes.c_ulonglong(), ctypes.c_uint()
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop_flag.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0 and \
+                    get_reasons(h, ctypes.byref(rs)) == 0:
+                p = mw.value if lib.nvmlDeviceGetPowerUsage(h, ctypes.byref(mw)) == 0 else None
+                self.rows.append((float(mhz.value), int(rs.value), p))
+            time.sleep(0.002)
 
     def start(self):
+        if self._nvml_open():
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            t0 = time.perf_counter()
+            while not self.rows and time.perf_counter() - t0 < 1.0:
+                time.sleep(0.001)
+            self.rows.clear()  # samples from here on fall inside the timed region
+            return
         try:
+            idx = self.device.index if self.device.index is not None else 0
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                ["nvidia-smi", "-i", str(idx), f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
-        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread = threading.Thread(target=self._read_smi, daemon=True)
         self.thread.start()
 
-    def _read(self):
+    def _read_smi(self):
         for line in self.proc.stdout:
-            self.rows.append([v.strip() for v in line.split(",")])
+            self.smi_rows.append([v.strip() for v in line.split(",")])
 
     def stop(self):
+        self.stop_flag.set()
         if self.proc:
             self.proc.terminate()
             try:
@@ -97,16 +159,26 @@ class ClockSampler:
                 self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        if not self.rows:
+        if self.nvml is not None:
+            rows = list(self.rows)
+            if not rows:
+                return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples"],
+                        "samples": 0, "source": "nvml"}
+            reasons = sorted({name for _, r, _ in rows for bit, name in self.REASONS.items() if r & bit})
+            pw = [p for _, _, p in rows if p is not None]
+            return {"sm_mhz": statistics.median(m for m, _, _ in rows), "sm_max_mhz": self.max_mhz,
+                    "reasons": reasons, "samples": len(rows), "source": "nvml, 2 ms",
+                    "power_w_max": round(max(pw) / 1000.0, 1) if pw else None}
+        if not self.smi_rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        sm = [float(r[0]) for r in self.smi_rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.smi_rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in self.rows for k in range(4)
+        reasons = sorted({names[k] for r in self.smi_rows for k in range(4)
                           if len(r) > 4 + k and r[4 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.rows)}
+                "samples": len(self.smi_rows), "source": "nvidia-smi, 200 ms"}
 
 
 def oracle_field(args):
@@ -214,6 +286,22 @@ def rank_seed(rank: int) -> int:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+
+def measured_traffic(stage):
+    """DRAM bytes per launch of `stage` from the committed ncu capture, or None
+    when the kernel's source file changed since the counters were taken."""
+    import hashlib
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(tf):
+        return None
+    e = json.load(open(tf)).get(stage)
+    if not e:
+        return None
+    src = os.path.join(ROOT, e["source"])
+    if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != e["source_sha1"]:
+        return None
+    return e["dram_bytes_per_launch"]
+
 
 # algorithmic bytes per launch of each stage (N points, B compressed bytes of one field)
 def stage_bytes(stage, N, B):
@@ -382,7 +470,7 @@ def main():
     for p in plans:
         fpsnr.fpsnr_plan_profile_read(p.handle)  # reset launch counters
 
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(dev)
     clocks.start()
     ms, wall = timed(a.steps, S, graph=use_graph)
     clk = clocks.stop()
@@ -452,10 +540,7 @@ def main():
         if dom:
             name, (t, n, byts) = dom
             achieved = byts / (t / 1e3) / 1e9
-            traffic = None
-            tf = os.path.join(ROOT, "profiles", "traffic.json")
-            if os.path.exists(tf):
-                traffic = json.load(open(tf)).get(name)
+            traffic = measured_traffic(name)
             roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                     "traffic": traffic, "peak_source": "measured" if peaks else "fallback",
