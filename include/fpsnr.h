@@ -196,6 +196,51 @@ int fpsnr_psnr(const float* d_x, const float* d_xr, uint64_t n, double* h_psnr_d
 int fpsnr_psnr_static(const float* d_x, const float* d_xr, uint64_t n, double* h_psnr_db,
                       double* h_mse, double* h_vr, void* stream);
 
+/* Launch shapes and chunk size of a plan.  The paper fixes none of these: the
+ * chunk size C (symbols per independently decodable Huffman chunk, a header
+ * field) trades decoder parallelism against one u32 offset per chunk in the
+ * stream; the tile shapes change only how the work is split over blocks, never
+ * the bytes.
+ *   chunk        symbols per chunk (0: keep the plan's)
+ *   pq_tile_x    2D predictor tile width: 128, 256 or 512 points (0: by row length)
+ *   band_rows    2D decompression band height: 16, 32 or 64 rows (0: 32); only
+ *                for 2D fields with rows of at most 8192 points
+ *   dec_threads  decoder block size: 128 or 512 (0: chosen per launch)
+ *   ms, bytes    filled by fpsnr_autotune: best compress + decompress time of the
+ *                sample (milliseconds) and its compressed size at `chunk` */
+typedef struct {
+    int chunk;
+    int pq_tile_x;
+    int band_rows;
+    int dec_threads;
+    double ms;
+    uint64_t bytes;
+} fpsnr_tuning;
+
+/* Applies the launch shapes of `t` to the plan (t->chunk must be 0 or equal
+ * the plan's chunk; a plan's chunk is fixed when it is created).  Values that
+ * do not apply to the plan's shape, or are not in the lists above, return
+ * FPSNR_EINVAL and leave the plan unchanged.  Not while a call on the plan is
+ * in flight. */
+int fpsnr_plan_set_tuning(fpsnr_plan_t plan, const fpsnr_tuning* t);
+int fpsnr_plan_get_tuning(fpsnr_plan_t plan, fpsnr_tuning* t);
+
+/* Autotuner: picks the chunk size and launch shapes for fields of this shape,
+ * target and options by timing compress + decompress of `d_sample` (a device
+ * field of that shape, 4-byte aligned) on `stream`.  It tries chunk sizes
+ * 64..2048 (and opts->chunk), keeps those whose compressed size is within
+ * (1 + max_size_increase) of the smallest, takes the fastest of them, then
+ * tunes pq_tile_x, band_rows and dec_threads one at a time at that chunk.
+ * Each candidate is timed as the best of 3 runs after a warm-up, with CUDA
+ * events.  Results are cached for the process by (shape, target, options,
+ * max_size_increase); a cached answer returns without touching the device.
+ * Synchronous; allocates temporary device buffers and plans.
+ * Returns FPSNR_OK, FPSNR_EINVAL, FPSNR_ENOMEM or FPSNR_ECUDA (or the status
+ * a sample compression reported, e.g. FPSNR_ENONFINITE). */
+int fpsnr_autotune(int ndim, const uint64_t* dims, double target_psnr_db, const fpsnr_opts* opts,
+                   const float* d_sample, double max_size_increase, fpsnr_tuning* out,
+                   void* stream);
+
 /* Device pointer to the uint16 symbol array (n entries) the last
  * fpsnr_compress on this plan produced; valid until the next call on the plan.
  * For inspection and tests. */

@@ -48,7 +48,7 @@ void carve(fpsnr_plan_s* p, uint8_t* base, size_t* total) {
     w.bm = c.take<uint32_t>(2 * std::max<uint64_t>(p->nwords, 1));
     w.wpre = c.take<uint32_t>(2 * std::max<uint64_t>(p->nwords, 1));
     w.bpre = c.take<uint32_t>(2 * std::max<uint64_t>(p->nbmblk, 1));
-    w.sse_part = c.take<double>(std::max<uint32_t>(p->pq.nblocks, 1));
+    w.sse_part = c.take<double>(std::max<uint32_t>(p->pq_blocks_cap, 1));
     w.range_part = c.take<float>(3 * (uint64_t)p->n_range_blocks);
     w.hlist = c.take<unsigned long long>(p->nsym);
     w.hbuf1 = c.take<unsigned long long>(p->nsym);
@@ -60,8 +60,47 @@ void carve(fpsnr_plan_s* p, uint8_t* base, size_t* total) {
     w.lb_vals = c.take<uint32_t>(2 * std::max<uint64_t>(p->lb_tiles_total, 1) * p->lb_width);
     w.lb_ctr = c.take<uint32_t>(8);
     w.enc_tiles = c.take<uint32_t>(std::max<uint64_t>(p->enc_tiles, 1));
-    w.bsum = c.take<uint32_t>(p->band.on ? (uint64_t)p->band.nbands * p->band.nx : 1);
+    w.bsum = c.take<uint32_t>(p->band.on ? (uint64_t)p->band_cap * p->band.nx : 1);
     *total = (c.off + 255) & ~(size_t)255;
+}
+
+// Predictor geometry.  2D fields take a tile width tx of 128, 256 or 512 points
+// (0: by row length); each block walks max(4, 8192 / tx) rows.  Returns false if
+// the grid would be too large.
+bool pq_geometry(fpsnr_plan_s* p, int tx) {
+    const uint64_t* d = p->dims;
+    const uint64_t n = p->n;
+    PQGeom& g = p->pq;
+    if (p->ld == 1) {
+        g.mode = 1; g.tx = 512; g.ty = 1; g.zs = 16;
+        g.vx = 512; g.vy = 1; g.vz = (uint32_t)std::max<uint64_t>(cdiv(n, 512), 1);
+    } else if (p->ld == 2) {
+        const uint64_t nx = d[0], rows = nx ? n / nx : 0;
+        g.mode = 2; g.ty = 1;
+        g.tx = tx ? tx : (nx <= 128 ? 128 : (nx <= 256 ? 256 : 512));
+        g.zs = std::max(4, 8192 / g.tx);
+        g.vx = (uint32_t)nx; g.vy = 1; g.vz = (uint32_t)rows;
+    } else {
+        g.mode = 3; g.tx = 128; g.ty = 8; g.zs = 16;
+        g.vx = (uint32_t)d[0]; g.vy = (uint32_t)d[1]; g.vz = (uint32_t)d[2];
+    }
+    g.vec = (g.vx % 4) == 0;
+    g.nbx = g.nby = g.nbz = g.nblocks = 0;
+    if (n > 0) {
+        g.nbx = (uint32_t)cdiv(g.vx, g.tx);
+        g.nby = (uint32_t)cdiv(g.vy, g.ty);
+        g.nbz = (uint32_t)cdiv(g.vz, g.zs);
+        const uint64_t nb = (uint64_t)g.nbx * g.nby * g.nbz;
+        if (nb > 0x7FFFFFFFull) return false;
+        g.nblocks = (uint32_t)nb;
+    }
+    return true;
+}
+
+// 2D inverse-Lorenzo band height (16, 32 or 64 rows).
+void band_rows(fpsnr_plan_s* p, uint32_t tr) {
+    p->band.tr = tr;
+    p->band.nbands = (uint32_t)cdiv(p->band.rows, tr);
 }
 
 ScanPass contig_pass(uint64_t rows, uint64_t W, bool final_pass) {
@@ -262,29 +301,16 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
         return FPSNR_ECUDA;
     }
 
-    // predictor geometry
-    PQGeom& g = p->pq;
-    if (ld == 1) {
-        g.mode = 1; g.tx = 512; g.ty = 1; g.zs = 16;
-        g.vx = 512; g.vy = 1; g.vz = (uint32_t)std::max<uint64_t>(cdiv(n, 512), 1);
-    } else if (ld == 2) {
-        const uint64_t nx = d[0], rows = nx ? n / nx : 0;
-        g.mode = 2; g.ty = 1;
-        g.tx = nx <= 128 ? 128 : (nx <= 256 ? 256 : 512);
-        g.zs = std::max(4, 8192 / g.tx);
-        g.vx = (uint32_t)nx; g.vy = 1; g.vz = (uint32_t)rows;
-    } else {
-        g.mode = 3; g.tx = 128; g.ty = 8; g.zs = 16;
-        g.vx = (uint32_t)d[0]; g.vy = (uint32_t)d[1]; g.vz = (uint32_t)d[2];
-    }
-    g.vec = (g.vx % 4) == 0;
-    if (n > 0) {
-        g.nbx = (uint32_t)cdiv(g.vx, g.tx);
-        g.nby = (uint32_t)cdiv(g.vy, g.ty);
-        g.nbz = (uint32_t)cdiv(g.vz, g.zs);
-        const uint64_t nb = (uint64_t)g.nbx * g.nby * g.nbz;
-        if (nb > 0x7FFFFFFFull) { delete p; return FPSNR_EINVAL; }
-        g.nblocks = (uint32_t)nb;
+    // predictor geometry; the workspace holds partials for any 2D tile width
+    if (!pq_geometry(p, 0)) { delete p; return FPSNR_EINVAL; }
+    p->pq_blocks_cap = p->pq.nblocks;
+    if (ld == 2 && n > 0) {
+        const int tx0 = p->pq.tx;
+        for (int tx : {128, 256, 512}) {
+            if (!pq_geometry(p, tx)) { delete p; return FPSNR_EINVAL; }
+            p->pq_blocks_cap = std::max(p->pq_blocks_cap, p->pq.nblocks);
+        }
+        pq_geometry(p, tx0);
     }
     p->n_range_blocks = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(cdiv(n, 512ull * 16),
                                                                             2ull * p->sm_count));
@@ -301,8 +327,8 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
             b.on = true;
             b.nx = (uint32_t)nx;
             b.rows = (uint32_t)rows;
-            b.tr = fp::kBandRows;
-            b.nbands = (uint32_t)cdiv(rows, b.tr);
+            band_rows(p, fp::kBandRows);
+            p->band_cap = (uint32_t)cdiv(rows, 16);
             b.g = nx <= 2048 ? 1 : (nx <= 4096 ? 2 : 4);
             b.vec = (nx % 8) == 0;
         } else if (ld == 2) {
@@ -421,6 +447,37 @@ int fpsnr_decompress_batch(const fpsnr_plan_t* plans, const void* const* d_blob,
                                            d_out, d_status, count,
                                            reinterpret_cast<cudaStream_t>(stream));
     });
+}
+
+int fpsnr_plan_set_tuning(fpsnr_plan_t p, const fpsnr_tuning* t) {
+    if (!p || !t) return FPSNR_EINVAL;
+    if (t->chunk != 0 && t->chunk != p->chunk) return FPSNR_EINVAL;
+    const int tx = t->pq_tile_x, tr = t->band_rows, dt = t->dec_threads;
+    if (tx != 0 && (tx != 128 && tx != 256 && tx != 512)) return FPSNR_EINVAL;
+    if (tx != 0 && p->ld != 2) return FPSNR_EINVAL;
+    if (tr != 0 && (tr != 16 && tr != 32 && tr != 64)) return FPSNR_EINVAL;
+    if (tr != 0 && !p->band.on) return FPSNR_EINVAL;
+    if (dt != 0 && dt != 128 && dt != 512) return FPSNR_EINVAL;
+    if (p->ld == 2 && p->n > 0) {
+        const int keep = p->pq.tx;
+        if (!pq_geometry(p, tx) || p->pq.nblocks > p->pq_blocks_cap) {
+            pq_geometry(p, keep);
+            return FPSNR_EINVAL;
+        }
+    }
+    if (p->band.on) band_rows(p, tr ? (uint32_t)tr : fp::kBandRows);
+    p->dec_threads = dt;
+    return FPSNR_OK;
+}
+
+int fpsnr_plan_get_tuning(fpsnr_plan_t p, fpsnr_tuning* t) {
+    if (!p || !t) return FPSNR_EINVAL;
+    memset(t, 0, sizeof(*t));
+    t->chunk = p->chunk;
+    t->pq_tile_x = p->ld == 2 ? p->pq.tx : 0;
+    t->band_rows = p->band.on ? (int)p->band.tr : 0;
+    t->dec_threads = p->dec_threads;
+    return FPSNR_OK;
 }
 
 const uint16_t* fpsnr_plan_codes(fpsnr_plan_t p) { return p ? p->w.codes : nullptr; }

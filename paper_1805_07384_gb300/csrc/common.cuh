@@ -161,7 +161,10 @@ struct fpsnr_plan_s {
     size_t slab_bytes;
     fp::Workspace w;
     int sm_count;
-    int cb_smem;  // dynamic shared memory of the codebook kernel
+    int cb_smem;               // dynamic shared memory of the codebook kernel
+    int dec_threads;           // decoder block size: 0 chosen per launch, or 128 / 512
+    uint32_t pq_blocks_cap;    // predictor blocks the workspace holds partials for (any tile width)
+    uint32_t band_cap;         // band sums the workspace holds (band height 16)
     fp::Profiler prof;
 };
 

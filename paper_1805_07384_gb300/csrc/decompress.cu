@@ -1069,7 +1069,8 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
     {
         uint64_t chunks = 0;
         for (int f = 0; f < count; f++) chunks += P[f]->n ? P[f]->nchunks : 0;
-        const int T = chunks <= 256ull * (uint64_t)P[0]->sm_count ? 128 : 512;
+        const int T = P[0]->dec_threads ? P[0]->dec_threads
+                                         : (chunks <= 256ull * (uint64_t)P[0]->sm_count ? 128 : 512);
         Batch<DecArgs> b;
         b.count = 0;
         for (int f = 0; f < count; f++) {

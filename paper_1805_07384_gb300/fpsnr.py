@@ -35,7 +35,8 @@ EXPORTS = ("fpsnr_default_opts", "fpsnr_plan", "fpsnr_plan_set_psnr", "fpsnr_pla
            "fpsnr_decompress", "fpsnr_psnr", "fpsnr_plan_codes", "fpsnr_plan_destroy",
            "fpsnr_strerror", "fpsnr_plan_profile", "fpsnr_plan_profile_read",
            "fpsnr_stage_name", "fpsnr_psnr_static", "fpsnr_compress_batch",
-           "fpsnr_decompress_batch")
+           "fpsnr_decompress_batch", "fpsnr_plan_set_tuning", "fpsnr_plan_get_tuning",
+           "fpsnr_autotune")
 FPSNR_PSNR_STATIC_MAX_POINTS = 1 << 28
 FPSNR_NSTAGES = 16
 
@@ -68,6 +69,14 @@ class fpsnr_stats(C.Structure):
 
 
 STATS_BYTES = C.sizeof(fpsnr_stats)
+
+
+class fpsnr_tuning(C.Structure):
+    _fields_ = [("chunk", C.c_int), ("pq_tile_x", C.c_int), ("band_rows", C.c_int),
+                ("dec_threads", C.c_int), ("ms", C.c_double), ("bytes", C.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def load(path: str = LIB_PATH):
@@ -106,6 +115,10 @@ def load(path: str = LIB_PATH):
         L.fpsnr_plan_profile_read.argtypes = [P, C.POINTER(D), C.POINTER(U64), C.c_int]
         L.fpsnr_stage_name.argtypes = [C.c_int]
         L.fpsnr_stage_name.restype = C.c_char_p
+        L.fpsnr_plan_set_tuning.argtypes = [P, C.POINTER(fpsnr_tuning)]
+        L.fpsnr_plan_get_tuning.argtypes = [P, C.POINTER(fpsnr_tuning)]
+        L.fpsnr_autotune.argtypes = [C.c_int, C.POINTER(U64), D, C.POINTER(fpsnr_opts), P, D,
+                                     C.POINTER(fpsnr_tuning), P]
         _lib = L
         return L
 
@@ -242,6 +255,45 @@ def _stream_handle(stream) -> int:
     return int(s.cuda_stream)
 
 
+def fpsnr_plan_set_tuning(plan, t: fpsnr_tuning) -> int:
+    return load().fpsnr_plan_set_tuning(plan, C.byref(t))
+
+
+def fpsnr_plan_get_tuning(plan) -> fpsnr_tuning:
+    t = fpsnr_tuning()
+    rc = load().fpsnr_plan_get_tuning(plan, C.byref(t))
+    if rc:
+        raise FpsnrError(rc, "fpsnr_plan_get_tuning")
+    return t
+
+
+def fpsnr_autotune(ndim: int, dims, target_psnr_db: float, opts, d_sample: int,
+                   max_size_increase: float, stream: int) -> fpsnr_tuning:
+    """dims x-fastest; d_sample a device pointer; returns fpsnr_tuning or raises."""
+    vals = [int(d) for d in dims] + [1] * max(0, 3 - len(dims))
+    arr = (C.c_uint64 * len(vals))(*vals)
+    t = fpsnr_tuning()
+    rc = load().fpsnr_autotune(int(ndim), arr, float(target_psnr_db),
+                               C.byref(opts) if opts is not None else None, d_sample,
+                               float(max_size_increase), C.byref(t), stream)
+    if rc:
+        raise FpsnrError(rc, "fpsnr_autotune")
+    return t
+
+
+def autotune(sample, target_psnr_db: float, max_size_increase: float = 0.01, radius: int = 32768,
+             chunk: int = 256, lmax: int = 27, lorenzo_dims: int = 0, stream=None) -> dict:
+    """Chunk size and launch shapes for fields shaped like `sample` (a float32
+    CUDA tensor, numpy C-order shape) at this target; see fpsnr_autotune."""
+    import torch
+    assert sample.dtype == torch.float32 and sample.is_cuda and sample.is_contiguous()
+    o = fpsnr_default_opts()
+    o.radius, o.chunk, o.lmax, o.lorenzo_dims = radius, chunk, lmax, lorenzo_dims
+    shape = tuple(sample.shape)
+    return fpsnr_autotune(len(shape), list(reversed(shape)), target_psnr_db, o, sample.data_ptr(),
+                          max_size_increase, _stream_handle(stream)).as_dict()
+
+
 def parse_stats(raw) -> dict:
     """fpsnr_stats from a uint8 tensor/bytes of STATS_BYTES bytes."""
     b = bytes(raw.cpu().numpy().tobytes()) if hasattr(raw, "cpu") else bytes(raw)
@@ -301,6 +353,19 @@ class Plan:
         if rc:
             raise FpsnrError(rc, "fpsnr_decompress")
         return out, status
+
+    def set_tuning(self, t: dict) -> None:
+        """Launch shapes from a tuning dict (autotune's, or hand-written); the
+        chunk must match the plan's (pass chunk=... at construction)."""
+        tt = fpsnr_tuning()
+        for k in ("chunk", "pq_tile_x", "band_rows", "dec_threads"):
+            setattr(tt, k, int(t.get(k, 0)))
+        rc = fpsnr_plan_set_tuning(self.handle, tt)
+        if rc:
+            raise FpsnrError(rc, "fpsnr_plan_set_tuning")
+
+    def get_tuning(self) -> dict:
+        return fpsnr_plan_get_tuning(self.handle).as_dict()
 
     def codes(self):
         """Copy of the uint16 symbols of the last compression (int16 tensor)."""
