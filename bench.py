@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--ny", type=int, default=1800)
     ap.add_argument("--nx", type=int, default=3600)
     ap.add_argument("--chunk", type=int, default=256)
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick chunk size and tile shapes per target PSNR with fpsnr_autotune "
+                         "(timed on the first field of each target, outside the timed region)")
+    ap.add_argument("--tune-tol", type=float, default=0.01,
+                    help="autotune: largest accepted compressed-size increase over the smallest")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true")
@@ -346,7 +351,21 @@ def main():
     fields, meta = synth.climate_batch(F, a.ny, a.nx, seed=rank_seed(rank), device=dev)
     psnrs = [synth.mixed_psnr(i) for i in range(F)]
     N = a.ny * a.nx
-    plans = [fpsnr.Plan((a.ny, a.nx), psnrs[i], chunk=a.chunk) for i in range(F)]
+    tuning = None
+    if a.autotune:
+        tuning = {}
+        for ps in sorted(set(psnrs)):
+            i0 = psnrs.index(ps)
+            tuning[ps] = fpsnr.autotune(fields[i0], ps, max_size_increase=a.tune_tol, chunk=a.chunk)
+        plans = []
+        for i in range(F):
+            t = tuning[psnrs[i]]
+            p = fpsnr.Plan((a.ny, a.nx), psnrs[i], chunk=t["chunk"])
+            # the decoder's block size is left to each batched launch
+            p.set_tuning({"pq_tile_x": t["pq_tile_x"], "band_rows": t["band_rows"]})
+            plans.append(p)
+    else:
+        plans = [fpsnr.Plan((a.ny, a.nx), psnrs[i], chunk=a.chunk) for i in range(F)]
     outs = [p.alloc_out() for p in plans]
     nbs = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(F)]
     sts = [torch.zeros(fpsnr.STATS_BYTES, dtype=torch.uint8, device=dev) for _ in range(F)]
@@ -584,7 +603,11 @@ def main():
             "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
             "steps": a.steps, "warmup": max(3, a.warmup), "ms_per_step": round(ms, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": workload_config(a, S),
+            "data": "synthetic",
+            "config": dict(workload_config(a, S),
+                           **({"chunk": "autotuned per target",
+                               "tuning": {str(k): {kk: v[kk] for kk in ("chunk", "pq_tile_x", "band_rows")}
+                                          for k, v in tuning.items()}} if tuning else {})),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
             "hbm_frac_of_step": round(value / (6775.6 if roof is None else roof["peak"]), 4),
