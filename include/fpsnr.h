@@ -60,6 +60,7 @@ extern "C" {
 #define FPSNR_ECAPACITY (-5)  /* (device status) compressed size exceeds out_cap */
 #define FPSNR_ECORRUPT (-6)   /* (device status) blob malformed or mismatched */
 #define FPSNR_ETIMEOUT (-7)   /* (device status) an inter-block wait gave up */
+#define FPSNR_EAGAIN (-8)     /* (server) the request has not completed yet */
 
 /* Limits on the target PSNR: 0 < target <= FPSNR_MAX_PSNR dB.  Above 180 dB
  * the integer lattice of a 3D residual could overflow int32. */
@@ -240,6 +241,108 @@ int fpsnr_plan_get_tuning(fpsnr_plan_t plan, fpsnr_tuning* t);
 int fpsnr_autotune(int ndim, const uint64_t* dims, double target_psnr_db, const fpsnr_opts* opts,
                    const float* d_sample, double max_size_increase, fpsnr_tuning* out,
                    void* stream);
+
+/* ------------------------------------------------------------------------
+ * Request server (no counterpart in the paper, which compresses one field per
+ * call).  A worker thread takes compress and decompress requests for fields of
+ * any shape and target as they arrive, keeps plans (and so their device
+ * workspace, tables and codebooks) cached per (shape, options), admits a
+ * request only while the plans it needs fit an HBM budget, and fuses the
+ * admitted requests of one kind into batched launches (fpsnr_compress_batch /
+ * fpsnr_decompress_batch) on a few streams, continuously: each stream holds
+ * one batch in flight, and as soon as a stream is free the requests that have
+ * arrived leave together (a batch never waits to fill).  Results are identical
+ * to a plain call on the same field (every kernel is deterministic and per
+ * field).
+ * ------------------------------------------------------------------------ */
+typedef struct fpsnr_server_s* fpsnr_server_t;
+
+/* hbm_budget   bytes of device memory the server's cached plans may hold (the
+ *              caller's input and output buffers are not counted); idle plans
+ *              are evicted least recently used first to admit others; a request
+ *              whose plan alone exceeds the budget fails with FPSNR_ENOMEM
+ * max_batch    requests fused into one launch (1..32)
+ * streams      CUDA streams the worker launches on (1..16) */
+typedef struct {
+    uint64_t hbm_budget;
+    int max_batch;
+    int streams;
+} fpsnr_server_opts;
+
+#define FPSNR_REQ_COMPRESS 0
+#define FPSNR_REQ_DECOMPRESS 1
+
+/* kind         FPSNR_REQ_COMPRESS or FPSNR_REQ_DECOMPRESS
+ * ndim, dims   field shape, x fastest (as fpsnr_plan)
+ * target_psnr_db, opts   as fpsnr_plan (opts.radius 0 means the defaults);
+ *              decompression uses opts and dims to pick the plan, and the blob
+ *              must have been made with them
+ * d_in         compress: float32 field (4-byte aligned); decompress: blob
+ *              (16-byte aligned) of in_bytes bytes
+ * d_out        compress: blob buffer of out_cap bytes; decompress: float32
+ *              output of the field's points (both 16-byte aligned)
+ * arrival_us   when the request may start, in microseconds of the server's
+ *              clock (fpsnr_server_now); 0 or a past time means now.  Latency
+ *              is measured from max(arrival, submission).
+ * Buffers stay owned by the caller and must stay valid until the request
+ * completes. */
+typedef struct {
+    int kind;
+    int ndim;
+    uint64_t dims[3];
+    double target_psnr_db;
+    fpsnr_opts opts;
+    const void* d_in;
+    uint64_t in_bytes;
+    void* d_out;
+    uint64_t out_cap;
+    double arrival_us;
+} fpsnr_request;
+
+/* status       FPSNR_OK or the request's error (launch errors, or the device
+ *              status the compression / decompression reported)
+ * out_bytes    compress: blob size
+ * stats        compress: the field's fpsnr_stats
+ * arrival_us, start_us, done_us   server clock: admitted arrival, launch
+ *              enqueued, completion observed by the worker */
+typedef struct {
+    int status;
+    uint64_t out_bytes;
+    fpsnr_stats stats;
+    double arrival_us, start_us, done_us;
+} fpsnr_result;
+
+/* completed / failed   requests finished since creation (failed: status != 0)
+ * batches              launches (each one batched compress or decompress call)
+ * p50_us, p99_us, max_us   latency (done - arrival) over completed requests
+ * plans, plan_bytes    plans cached now and the device memory they hold
+ * bytes_in             original field bytes of completed requests */
+typedef struct {
+    uint64_t completed, failed, batches;
+    double p50_us, p99_us, max_us;
+    uint64_t plans, plan_bytes;
+    uint64_t bytes_in;
+} fpsnr_server_stats;
+
+/* Creates a server on the current device (its worker thread starts at once).
+ * Returns FPSNR_OK, FPSNR_EINVAL, FPSNR_ENOMEM or FPSNR_ECUDA. */
+int fpsnr_server_create(const fpsnr_server_opts* opts, fpsnr_server_t* out);
+/* Queues a request; *ticket identifies it.  Thread-safe; never blocks on the
+ * GPU.  Returns FPSNR_OK or FPSNR_EINVAL (bad shape, options or alignment). */
+int fpsnr_server_submit(fpsnr_server_t s, const fpsnr_request* r, uint64_t* ticket);
+/* Result of a completed request (each result can be taken once): FPSNR_OK with
+ * *res filled, FPSNR_EAGAIN if it is still pending, FPSNR_EINVAL for a ticket
+ * never issued or already taken. */
+int fpsnr_server_poll(fpsnr_server_t s, uint64_t ticket, fpsnr_result* res);
+/* Blocks until the request completes or timeout_s elapses (FPSNR_ETIMEOUT). */
+int fpsnr_server_wait(fpsnr_server_t s, uint64_t ticket, fpsnr_result* res, double timeout_s);
+/* Blocks until every submitted request has completed. */
+int fpsnr_server_drain(fpsnr_server_t s, double timeout_s);
+int fpsnr_server_get_stats(fpsnr_server_t s, fpsnr_server_stats* st);
+/* Microseconds since the server was created (its clock for arrival times). */
+double fpsnr_server_now(fpsnr_server_t s);
+/* Completes every queued request, then frees the plans, streams and thread. */
+void fpsnr_server_destroy(fpsnr_server_t s);
 
 /* Device pointer to the uint16 symbol array (n entries) the last
  * fpsnr_compress on this plan produced; valid until the next call on the plan.

@@ -254,6 +254,7 @@ const char* fpsnr_strerror(int code) {
         case FPSNR_ECAPACITY: return "output buffer too small";
         case FPSNR_ECORRUPT: return "compressed stream is corrupt or does not match the plan";
         case FPSNR_ETIMEOUT: return "inter-block wait timed out";
+        case FPSNR_EAGAIN: return "request not completed yet";
         default: return "unknown error";
     }
 }

@@ -36,7 +36,12 @@ EXPORTS = ("fpsnr_default_opts", "fpsnr_plan", "fpsnr_plan_set_psnr", "fpsnr_pla
            "fpsnr_strerror", "fpsnr_plan_profile", "fpsnr_plan_profile_read",
            "fpsnr_stage_name", "fpsnr_psnr_static", "fpsnr_compress_batch",
            "fpsnr_decompress_batch", "fpsnr_plan_set_tuning", "fpsnr_plan_get_tuning",
-           "fpsnr_autotune")
+           "fpsnr_autotune", "fpsnr_server_create", "fpsnr_server_submit", "fpsnr_server_poll",
+           "fpsnr_server_wait", "fpsnr_server_drain", "fpsnr_server_get_stats",
+           "fpsnr_server_now", "fpsnr_server_destroy")
+FPSNR_EAGAIN = -8
+FPSNR_REQ_COMPRESS = 0
+FPSNR_REQ_DECOMPRESS = 1
 FPSNR_PSNR_STATIC_MAX_POINTS = 1 << 28
 FPSNR_NSTAGES = 16
 
@@ -69,6 +74,31 @@ class fpsnr_stats(C.Structure):
 
 
 STATS_BYTES = C.sizeof(fpsnr_stats)
+
+
+class fpsnr_server_opts(C.Structure):
+    _fields_ = [("hbm_budget", C.c_uint64), ("max_batch", C.c_int), ("streams", C.c_int)]
+
+
+class fpsnr_request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("ndim", C.c_int), ("dims", C.c_uint64 * 3),
+                ("target_psnr_db", C.c_double), ("opts", fpsnr_opts), ("d_in", C.c_void_p),
+                ("in_bytes", C.c_uint64), ("d_out", C.c_void_p), ("out_cap", C.c_uint64),
+                ("arrival_us", C.c_double)]
+
+
+class fpsnr_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("out_bytes", C.c_uint64), ("stats", fpsnr_stats),
+                ("arrival_us", C.c_double), ("start_us", C.c_double), ("done_us", C.c_double)]
+
+
+class fpsnr_server_stats(C.Structure):
+    _fields_ = [("completed", C.c_uint64), ("failed", C.c_uint64), ("batches", C.c_uint64),
+                ("p50_us", C.c_double), ("p99_us", C.c_double), ("max_us", C.c_double),
+                ("plans", C.c_uint64), ("plan_bytes", C.c_uint64), ("bytes_in", C.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class fpsnr_tuning(C.Structure):
@@ -115,6 +145,16 @@ def load(path: str = LIB_PATH):
         L.fpsnr_plan_profile_read.argtypes = [P, C.POINTER(D), C.POINTER(U64), C.c_int]
         L.fpsnr_stage_name.argtypes = [C.c_int]
         L.fpsnr_stage_name.restype = C.c_char_p
+        L.fpsnr_server_create.argtypes = [C.POINTER(fpsnr_server_opts), C.POINTER(P)]
+        L.fpsnr_server_submit.argtypes = [P, C.POINTER(fpsnr_request), C.POINTER(U64)]
+        L.fpsnr_server_poll.argtypes = [P, U64, C.POINTER(fpsnr_result)]
+        L.fpsnr_server_wait.argtypes = [P, U64, C.POINTER(fpsnr_result), D]
+        L.fpsnr_server_drain.argtypes = [P, D]
+        L.fpsnr_server_get_stats.argtypes = [P, C.POINTER(fpsnr_server_stats)]
+        L.fpsnr_server_now.argtypes = [P]
+        L.fpsnr_server_now.restype = D
+        L.fpsnr_server_destroy.argtypes = [P]
+        L.fpsnr_server_destroy.restype = None
         L.fpsnr_plan_set_tuning.argtypes = [P, C.POINTER(fpsnr_tuning)]
         L.fpsnr_plan_get_tuning.argtypes = [P, C.POINTER(fpsnr_tuning)]
         L.fpsnr_autotune.argtypes = [C.c_int, C.POINTER(U64), D, C.POINTER(fpsnr_opts), P, D,
@@ -431,3 +471,106 @@ def psnr(x, xr, stream=None):
     """(PSNR dB, MSE, vr) of reconstruction xr against x (CUDA float32 tensors)."""
     assert x.numel() == xr.numel()
     return fpsnr_psnr(x.data_ptr(), xr.data_ptr(), x.numel(), _stream_handle(stream))
+
+
+# ---------------------------------------------------------------------------
+# request server
+# ---------------------------------------------------------------------------
+
+def _result_dict(r: fpsnr_result) -> dict:
+    return {"status": r.status, "out_bytes": r.out_bytes, "stats": r.stats.as_dict(),
+            "arrival_us": r.arrival_us, "start_us": r.start_us, "done_us": r.done_us}
+
+
+class Server:
+    """fpsnr_server_* over torch tensors.  Keeps each request's tensors alive
+    until its result has been taken."""
+
+    def __init__(self, hbm_budget: int = 8 << 30, max_batch: int = 16, streams: int = 4):
+        o = fpsnr_server_opts(int(hbm_budget), int(max_batch), int(streams))
+        h = C.c_void_p()
+        rc = load().fpsnr_server_create(C.byref(o), C.byref(h))
+        if rc:
+            raise FpsnrError(rc, "fpsnr_server_create")
+        self.handle = h.value
+        self._keep = {}
+
+    def now(self) -> float:
+        return load().fpsnr_server_now(self.handle)
+
+    def _submit(self, kind, shape, d_in, in_bytes, d_out, out_cap, psnr, arrival_us, keep,
+                radius, chunk, lmax, lorenzo_dims) -> int:
+        r = fpsnr_request()
+        r.kind = kind
+        dims = list(reversed([int(v) for v in shape]))
+        r.ndim = len(dims)
+        for i, d in enumerate(dims):
+            r.dims[i] = d
+        r.target_psnr_db = float(psnr)
+        r.opts.radius, r.opts.chunk, r.opts.lmax, r.opts.lorenzo_dims = radius, chunk, lmax, lorenzo_dims
+        r.d_in, r.in_bytes, r.d_out, r.out_cap = d_in, int(in_bytes), d_out, int(out_cap)
+        r.arrival_us = float(arrival_us)
+        t = C.c_uint64()
+        rc = load().fpsnr_server_submit(self.handle, C.byref(r), C.byref(t))
+        if rc:
+            raise FpsnrError(rc, "fpsnr_server_submit")
+        self._keep[t.value] = keep
+        return t.value
+
+    def submit_compress(self, x, psnr: float, out, arrival_us: float = 0.0, radius: int = 32768,
+                        chunk: int = 256, lmax: int = 27, lorenzo_dims: int = 0) -> int:
+        """Queue compression of x (float32 CUDA tensor) into out (uint8 CUDA tensor)."""
+        return self._submit(FPSNR_REQ_COMPRESS, x.shape, x.data_ptr(), 0, out.data_ptr(),
+                            out.numel(), psnr, arrival_us, (x, out), radius, chunk, lmax,
+                            lorenzo_dims)
+
+    def submit_decompress(self, blob, nbytes: int, out, arrival_us: float = 0.0,
+                          radius: int = 32768, chunk: int = 256, lmax: int = 27,
+                          lorenzo_dims: int = 0) -> int:
+        """Queue decompression of blob (uint8 CUDA tensor) into out (float32
+        CUDA tensor of the field's shape)."""
+        return self._submit(FPSNR_REQ_DECOMPRESS, out.shape, blob.data_ptr(), nbytes,
+                            out.data_ptr(), 4 * out.numel(), 60.0, arrival_us, (blob, out),
+                            radius, chunk, lmax, lorenzo_dims)
+
+    def poll(self, ticket: int):
+        r = fpsnr_result()
+        rc = load().fpsnr_server_poll(self.handle, ticket, C.byref(r))
+        if rc == FPSNR_EAGAIN:
+            return None
+        if rc:
+            raise FpsnrError(rc, "fpsnr_server_poll")
+        self._keep.pop(ticket, None)
+        return _result_dict(r)
+
+    def wait(self, ticket: int, timeout: float = 120.0) -> dict:
+        r = fpsnr_result()
+        rc = load().fpsnr_server_wait(self.handle, ticket, C.byref(r), float(timeout))
+        if rc:
+            raise FpsnrError(rc, "fpsnr_server_wait")
+        self._keep.pop(ticket, None)
+        return _result_dict(r)
+
+    def drain(self, timeout: float = 600.0) -> None:
+        rc = load().fpsnr_server_drain(self.handle, float(timeout))
+        if rc:
+            raise FpsnrError(rc, "fpsnr_server_drain")
+
+    def stats(self) -> dict:
+        st = fpsnr_server_stats()
+        rc = load().fpsnr_server_get_stats(self.handle, C.byref(st))
+        if rc:
+            raise FpsnrError(rc, "fpsnr_server_get_stats")
+        return st.as_dict()
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            load().fpsnr_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
