@@ -49,6 +49,14 @@ def parse():
     ap.add_argument("--autotune", action="store_true",
                     help="pick chunk size and tile shapes per target PSNR with fpsnr_autotune "
                          "(timed on the first field of each target, outside the timed region)")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving workload instead of the batch: requests of mixed shapes and "
+                         "targets with Poisson arrivals through the request server")
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rates", type=str, default="1000,5000,10000,20000",
+                    help="arrival rates (requests per second), one run each")
+    ap.add_argument("--serve-serial", type=int, default=1000,
+                    help="requests of the serial plain-call baseline")
     ap.add_argument("--tune-tol", type=float, default=0.01,
                     help="autotune: largest accepted compressed-size increase over the smallest")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -316,10 +324,184 @@ def stage_bytes(stage, N, B):
             "decode": B + 2 * N, "band_sum": 2 * N, "scan_final_dequant": 6 * N}.get(stage)
 
 
+# ---------------------------------------------------------------------------
+# serving workload
+# ---------------------------------------------------------------------------
+
+SERVE_SHAPES = [(64, 64), (512, 512), (1800, 3600), (64, 64, 64), (100, 500, 500), (256, 256, 256)]
+SERVE_BUCKETS = [30.0 + 10.0 * k for k in range(10)]
+
+
+def serve_field(shape, seed, device):
+    """The workload generators by shape: 512^2-style isotropic GRF, climate-like
+    field with an affine offset, hurricane-like anisotropic 3D GRF (z stretched
+    4x), cosmology-like 3D velocity GRF; float32 on `device`."""
+    import torch
+    from paper_1805_07384_gb300 import synth
+    if len(shape) == 2 and shape != (1800, 3600):
+        g = synth.grf_torch(shape, 3.0, seed, device)
+    elif len(shape) == 2:
+        g = synth.grf_torch(shape, 3.0, seed, device) * 1e2 + 5e3
+    elif shape == (100, 500, 500):
+        g = synth.grf_torch(shape, 3.0, seed, device, stretch=(4.0, 1.0, 1.0))
+    else:
+        g = synth.grf_torch(shape, 3.0, seed, device)
+    return g.to(torch.float32).contiguous()
+
+
+def run_serve(a):
+    import numpy as np
+    import torch
+    from paper_1805_07384_gb300 import build as fbuild
+    fbuild.build()
+    from paper_1805_07384_gb300 import fpsnr
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    K = 2  # pre-staged fields per shape
+    fields = {s: [serve_field(s, 100 * i + j, dev) for j in range(K)] for i, s in enumerate(SERVE_SHAPES)}
+    nbytes = {s: 4 * int(np.prod(s)) for s in SERVE_SHAPES}
+    # blobs for the decompression requests: every field at every target bucket
+    blobs = {}
+    for s in SERVE_SHAPES:
+        p = fpsnr.Plan(s, 60.0)
+        for j in range(K):
+            for b in SERVE_BUCKETS:
+                p.set_psnr(b)
+                out, nb, st = p.compress(fields[s][j])
+                torch.cuda.synchronize()
+                n = int(nb.item())
+                assert fpsnr.parse_stats(st)["status"] == 0
+                blobs[(s, j, b)] = (out[:n].clone(), n)
+        p.close()
+    # output buffers per shape (a compressed blob may take up to 4n + 1 MiB)
+    pool_n = {s: (64 if nbytes[s] <= (4 << 20) else (16 if nbytes[s] <= (64 << 20) else 8))
+              for s in SERVE_SHAPES}
+    cap = {s: nbytes[s] + (1 << 20) for s in SERVE_SHAPES}
+    bufs = {s: [torch.empty(cap[s], dtype=torch.uint8, device=dev) for _ in range(pool_n[s])]
+            for s in SERVE_SHAPES}
+
+    def requests(n, rate, seed):
+        rng = np.random.default_rng(seed)
+        gaps = rng.exponential(1e6 / rate, size=n)
+        out = []
+        t = 0.0
+        for i in range(n):
+            t += gaps[i]
+            s = SERVE_SHAPES[int(rng.integers(len(SERVE_SHAPES)))]
+            psnr = float(rng.uniform(30.0, 120.0))
+            kind = int(rng.integers(2))
+            out.append((t, s, psnr, kind, i % K))
+        return out
+
+    srv = fpsnr.Server(hbm_budget=40 << 30, max_batch=16, streams=4)
+    # warm the plan cache: one request of each kind per shape
+    for s in SERVE_SHAPES:
+        srv.wait(srv.submit_compress(fields[s][0], 60.0, bufs[s][0]))
+        blob, n = blobs[(s, 0, 60.0)]
+        srv.wait(srv.submit_decompress(blob, n, bufs[s][0][:nbytes[s]].view(torch.float32).view(s)))
+
+    runs = []
+    for rate in [float(r) for r in a.serve_rates.split(",")]:
+        reqs = requests(a.serve_requests, rate, seed=int(rate))
+        free = {s: list(range(pool_n[s])) for s in SERVE_SHAPES}
+        owner, lat, done_t, total_bytes, failed = {}, [], [], 0, 0
+        st0 = srv.stats()
+
+        def collect(block):
+            nonlocal total_bytes, failed
+            while True:
+                item = srv.take_any()
+                if item is None:
+                    if not block:
+                        return
+                    time.sleep(20e-6)
+                    continue
+                t, r = item
+                s, bi = owner.pop(t)
+                free[s].append(bi)
+                if r["status"]:
+                    failed += 1
+                else:
+                    lat.append(r["done_us"] - r["arrival_us"])
+                    total_bytes += nbytes[s]
+                done_t.append(r["done_us"])
+                return
+
+        t0 = srv.now() + 20000.0
+        for (ta, s, psnr, kind, j) in reqs:
+            while not free[s]:
+                collect(True)
+            collect(False)
+            bi = free[s].pop()
+            buf = bufs[s][bi]
+            if kind == 0:
+                t = srv.submit_compress(fields[s][j], psnr, buf, arrival_us=t0 + ta)
+            else:
+                b = min(SERVE_BUCKETS, key=lambda v: abs(v - psnr))
+                blob, n = blobs[(s, j, b)]
+                t = srv.submit_decompress(blob, n, buf[:nbytes[s]].view(torch.float32).view(s),
+                                          arrival_us=t0 + ta)
+            owner[t] = (s, bi)
+        while owner:
+            collect(True)
+        st1 = srv.stats()
+        span = (max(done_t) - t0) / 1e6
+        lat_ms = sorted(v / 1e3 for v in lat)
+        q = lambda f: lat_ms[min(len(lat_ms) - 1, int(f * (len(lat_ms) - 1) + 0.5))]
+        nb = st1["batches"] - st0["batches"]
+        runs.append({"rate_rps": rate, "requests": len(reqs), "failed": failed,
+                     "p50_ms": round(q(0.5), 3), "p99_ms": round(q(0.99), 3),
+                     "max_ms": round(lat_ms[-1], 3), "gbs": round(total_bytes / span / 1e9, 2),
+                     "offered_gbs": round(sum(nbytes[s] for _, s, _, _, _ in reqs) /
+                                          (reqs[-1][0] / 1e6) / 1e9, 2),
+                     "batches": nb, "mean_batch": round(len(reqs) / max(nb, 1), 2)})
+    pst = srv.stats()
+    srv.close()
+
+    # serial plain calls on the first requests of the lowest rate's list
+    reqs = requests(a.serve_serial, float(a.serve_rates.split(",")[0]), seed=1)
+    plans = {s: fpsnr.Plan(s, 60.0) for s in SERVE_SHAPES}
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    tot = 0
+    for (ta, s, psnr, kind, j) in reqs:
+        p = plans[s]
+        buf = bufs[s][0]
+        if kind == 0:
+            p.set_psnr(psnr)
+            p.compress(fields[s][j], out=buf)
+        else:
+            b = min(SERVE_BUCKETS, key=lambda v: abs(v - psnr))
+            blob, n = blobs[(s, j, b)]
+            p.decompress(blob, n, out=buf[:nbytes[s]].view(torch.float32).view(s))
+        torch.cuda.synchronize()
+        tot += nbytes[s]
+    serial_gbs = tot / (time.perf_counter() - w0) / 1e9
+    for p in plans.values():
+        p.close()
+    line = {"metric": "served compress/decompress requests: p50/p99 latency and aggregate GB/s",
+            "unit": "ms / GB/s", "n_gpus": 1, "data": "synthetic", "impl": "ours",
+            "config": {"workload": "requests with Poisson arrivals; shape uniform over "
+                                   + ", ".join("x".join(map(str, s)) for s in SERVE_SHAPES)
+                                   + "; target PSNR U[30,120] dB; half compress, half decompress "
+                                   "of a blob made beforehand at the nearest 10 dB target; inputs "
+                                   f"pre-staged on the device ({K} fields per shape)",
+                       "server": {"hbm_budget": 40 << 30, "max_batch": 16, "streams": 4},
+                       "latency": "completion observed by the server minus scheduled arrival"},
+            "runs": runs,
+            "serial_plain": {"gbs": round(serial_gbs, 2), "requests": len(reqs),
+                             "note": "one plain call per request, synchronized after each"},
+            "plans_cached": pst["plans"], "plan_bytes": pst["plan_bytes"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.serve:
+        run_serve(a)
         return
     import torch
     import torch.distributed as dist

@@ -282,8 +282,10 @@ typedef struct {
  * d_out        compress: blob buffer of out_cap bytes; decompress: float32
  *              output of the field's points (both 16-byte aligned)
  * arrival_us   when the request may start, in microseconds of the server's
- *              clock (fpsnr_server_now); 0 or a past time means now.  Latency
- *              is measured from max(arrival, submission).
+ *              clock (fpsnr_server_now); 0 means at submission.  Latency is
+ *              measured from arrival_us when it is set (a request submitted
+ *              after its arrival time counts the lateness), else from
+ *              submission.
  * Buffers stay owned by the caller and must stay valid until the request
  * completes. */
 typedef struct {
@@ -334,6 +336,9 @@ int fpsnr_server_submit(fpsnr_server_t s, const fpsnr_request* r, uint64_t* tick
  * *res filled, FPSNR_EAGAIN if it is still pending, FPSNR_EINVAL for a ticket
  * never issued or already taken. */
 int fpsnr_server_poll(fpsnr_server_t s, uint64_t ticket, fpsnr_result* res);
+/* The oldest completed result not yet taken, in completion order: FPSNR_OK
+ * with *ticket and *res filled, or FPSNR_EAGAIN when none is waiting. */
+int fpsnr_server_take_any(fpsnr_server_t s, uint64_t* ticket, fpsnr_result* res);
 /* Blocks until the request completes or timeout_s elapses (FPSNR_ETIMEOUT). */
 int fpsnr_server_wait(fpsnr_server_t s, uint64_t ticket, fpsnr_result* res, double timeout_s);
 /* Blocks until every submitted request has completed. */

@@ -50,7 +50,8 @@ struct Req {
     uint64_t ticket;
     fpsnr_request r;
     std::string key;
-    double arrival;
+    double arrival;  // when it may start: max(requested arrival, submission)
+    double origin;   // latency is measured from here: the requested arrival, else submission
 };
 
 struct Slot {
@@ -96,6 +97,7 @@ struct fpsnr_server_s {
     std::vector<cudaStream_t> streams;
     int next_stream = 0;
     std::unordered_map<uint64_t, fpsnr_result> results;
+    std::deque<uint64_t> done_order;  // completion order (tickets taken by poll are skipped)
     uint64_t next_ticket = 1;
     uint64_t outstanding = 0;  // submitted and not yet completed
     std::vector<double> lat;
@@ -113,6 +115,7 @@ struct fpsnr_server_s {
 
 void fpsnr_server_s::finish(const Req& q, const fpsnr_result& res) {
     results[q.ticket] = res;
+    done_order.push_back(q.ticket);
     completed++;
     if (res.status) failed++;
     else lat.push_back(res.done_us - res.arrival_us);
@@ -184,7 +187,7 @@ void fpsnr_server_s::harvest() {
             } else {
                 res.status = s.h_status[i];
             }
-            res.arrival_us = s.reqs[i].arrival;
+            res.arrival_us = s.reqs[i].origin;
             res.start_us = s.start;
             res.done_us = t;
             finish(s.reqs[i], res);
@@ -224,7 +227,7 @@ bool fpsnr_server_s::launch_next(double now_us) {
             fpsnr_result res;
             memset(&res, 0, sizeof(res));
             res.status = err;
-            res.arrival_us = it->arrival;
+            res.arrival_us = it->origin;
             res.start_us = res.done_us = now();
             finish(*it, res);
             it = pending.erase(it);
@@ -301,7 +304,7 @@ bool fpsnr_server_s::launch_next(double now_us) {
             fpsnr_result res;
             memset(&res, 0, sizeof(res));
             res.status = rc;
-            res.arrival_us = take[i].arrival;
+            res.arrival_us = take[i].origin;
             res.start_us = res.done_us = t;
             finish(take[i], res);
             got[i]->busy = false;
@@ -398,7 +401,9 @@ int fpsnr_server_submit(fpsnr_server_t s, const fpsnr_request* r, uint64_t* tick
     {
         std::lock_guard<std::mutex> lk(s->mu);
         q.ticket = s->next_ticket++;
-        q.arrival = std::max(r->arrival_us, s->now());
+        const double t = s->now();
+        q.arrival = std::max(r->arrival_us, t);
+        q.origin = r->arrival_us > 0.0 ? r->arrival_us : t;
         // keep arrival order (submissions are usually already in order)
         auto it = s->pending.end();
         while (it != s->pending.begin() && std::prev(it)->arrival > q.arrival) --it;
@@ -426,6 +431,22 @@ int fpsnr_server_poll(fpsnr_server_t s, uint64_t ticket, fpsnr_result* res) {
         for (auto& q : sl.reqs)
             if (sl.used && q.ticket == ticket) return FPSNR_EAGAIN;
     return FPSNR_EINVAL;  // already taken
+}
+
+int fpsnr_server_take_any(fpsnr_server_t s, uint64_t* ticket, fpsnr_result* res) {
+    if (!s || !ticket || !res) return FPSNR_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    while (!s->done_order.empty()) {
+        const uint64_t t = s->done_order.front();
+        s->done_order.pop_front();
+        auto it = s->results.find(t);
+        if (it == s->results.end()) continue;  // taken by ticket already
+        *ticket = t;
+        *res = it->second;
+        s->results.erase(it);
+        return FPSNR_OK;
+    }
+    return FPSNR_EAGAIN;
 }
 
 int fpsnr_server_wait(fpsnr_server_t s, uint64_t ticket, fpsnr_result* res, double timeout_s) {

@@ -38,7 +38,7 @@ EXPORTS = ("fpsnr_default_opts", "fpsnr_plan", "fpsnr_plan_set_psnr", "fpsnr_pla
            "fpsnr_decompress_batch", "fpsnr_plan_set_tuning", "fpsnr_plan_get_tuning",
            "fpsnr_autotune", "fpsnr_server_create", "fpsnr_server_submit", "fpsnr_server_poll",
            "fpsnr_server_wait", "fpsnr_server_drain", "fpsnr_server_get_stats",
-           "fpsnr_server_now", "fpsnr_server_destroy")
+           "fpsnr_server_now", "fpsnr_server_destroy", "fpsnr_server_take_any")
 FPSNR_EAGAIN = -8
 FPSNR_REQ_COMPRESS = 0
 FPSNR_REQ_DECOMPRESS = 1
@@ -149,6 +149,7 @@ def load(path: str = LIB_PATH):
         L.fpsnr_server_submit.argtypes = [P, C.POINTER(fpsnr_request), C.POINTER(U64)]
         L.fpsnr_server_poll.argtypes = [P, U64, C.POINTER(fpsnr_result)]
         L.fpsnr_server_wait.argtypes = [P, U64, C.POINTER(fpsnr_result), D]
+        L.fpsnr_server_take_any.argtypes = [P, C.POINTER(U64), C.POINTER(fpsnr_result)]
         L.fpsnr_server_drain.argtypes = [P, D]
         L.fpsnr_server_get_stats.argtypes = [P, C.POINTER(fpsnr_server_stats)]
         L.fpsnr_server_now.argtypes = [P]
@@ -542,6 +543,18 @@ class Server:
             raise FpsnrError(rc, "fpsnr_server_poll")
         self._keep.pop(ticket, None)
         return _result_dict(r)
+
+    def take_any(self):
+        """(ticket, result) of the oldest completed request not yet taken, or None."""
+        r = fpsnr_result()
+        t = C.c_uint64()
+        rc = load().fpsnr_server_take_any(self.handle, C.byref(t), C.byref(r))
+        if rc == FPSNR_EAGAIN:
+            return None
+        if rc:
+            raise FpsnrError(rc, "fpsnr_server_take_any")
+        self._keep.pop(t.value, None)
+        return t.value, _result_dict(r)
 
     def wait(self, ticket: int, timeout: float = 120.0) -> dict:
         r = fpsnr_result()

@@ -141,5 +141,16 @@ def test_server_arrival_and_errors(env):
     with pytest.raises(fpsnr.FpsnrError):
         srv._submit(fpsnr.FPSNR_REQ_DECOMPRESS, shape, good.data_ptr() + 4, 100, rec.data_ptr(),
                     rec.numel() * 4, 60.0, 0.0, None, 32768, 256, 27, 0)
+    # results in completion order
+    ts = {srv.submit_compress(x, 50.0 + 10 * i, torch.empty(cap, dtype=torch.uint8, device="cuda")): i
+          for i in range(5)}
     srv.drain()
+    got = []
+    while True:
+        item = srv.take_any()
+        if item is None:
+            break
+        got.append(item)
+    assert sorted(t for t, _ in got) == sorted(ts) and all(r["status"] == 0 for _, r in got)
+    assert [r["done_us"] for _, r in got] == sorted(r["done_us"] for _, r in got)
     srv.close()
