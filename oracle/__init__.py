@@ -93,6 +93,14 @@ def lib():
             L.or_canonical_codes.argtypes = [P, C.c_uint32, P, P]
             L.or_compress.argtypes = [P, C.c_int, P, C.c_int, C.c_double, C.c_int, C.c_int,
                                       C.c_int, C.POINTER(C.c_void_p), P, P]
+            L.or_compress_mode.argtypes = [P, C.c_int, P, C.c_int, C.c_double, C.c_int, C.c_int,
+                                           C.c_int, C.c_int, C.POINTER(C.c_void_p), P, P]
+            L.or_fine_hist.restype = None
+            L.or_fine_hist.argtypes = [P, C.c_uint64, C.c_float, C.c_double, P]
+            L.or_pred_mse.restype = C.c_double
+            L.or_pred_mse.argtypes = [P, C.c_uint64, C.c_double, C.c_double]
+            L.or_refine_eb.restype = C.c_double
+            L.or_refine_eb.argtypes = [P, C.c_uint64, C.c_double, C.c_double, C.c_double]
             L.or_decompress.argtypes = [P, C.c_uint64, P, C.c_uint64]
             L.or_blob_info.argtypes = [P, C.c_uint64, P, P]
             L.or_free.restype = None
@@ -192,16 +200,17 @@ def canonical_codes(lens):
 
 
 def compress(x: np.ndarray, psnr_db: float, radius: int = 32768, chunk: int = 256,
-             lmax: int = 27, lorenzo_dims: int = 0):
-    """Returns (blob bytes, stats dict); raises on a nonzero status."""
+             lmax: int = 27, lorenzo_dims: int = 0, psnr_mode: int = 0):
+    """Returns (blob bytes, stats dict); raises on a nonzero status.  psnr_mode
+    1 refines eb from the fine histogram (or_refine_eb)."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     dims = _dims(x.shape)
     out = C.c_void_p()
     nbytes = C.c_uint64()
     st = Stats()
-    rc = lib().or_compress(_ptr(x), x.ndim, _ptr(dims), int(lorenzo_dims), float(psnr_db),
-                           int(radius), int(chunk), int(lmax), C.byref(out), C.byref(nbytes),
-                           C.byref(st))
+    rc = lib().or_compress_mode(_ptr(x), x.ndim, _ptr(dims), int(lorenzo_dims), float(psnr_db),
+                                int(psnr_mode), int(radius), int(chunk), int(lmax), C.byref(out),
+                                C.byref(nbytes), C.byref(st))
     if rc:
         raise ValueError(f"or_compress failed with status {rc}")
     try:
@@ -295,3 +304,23 @@ def parse_blob(blob: bytes) -> dict:
     h["total"] = end
     del b
     return h
+
+
+FINE_BINS = 4096
+
+
+def fine_hist(x: np.ndarray, xmin: float, vr: float) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float32).ravel()
+    h = np.zeros(FINE_BINS, np.uint32)
+    lib().or_fine_hist(_ptr(x), x.size, C.c_float(xmin), float(vr), _ptr(h))
+    return h
+
+
+def pred_mse(h: np.ndarray, n: int, vr: float, eb: float) -> float:
+    h = np.ascontiguousarray(h, dtype=np.uint32)
+    return lib().or_pred_mse(_ptr(h), int(n), float(vr), float(eb))
+
+
+def refine_eb(h: np.ndarray, n: int, vr: float, eb0: float, mse_target: float) -> float:
+    h = np.ascontiguousarray(h, dtype=np.uint32)
+    return lib().or_refine_eb(_ptr(h), int(n), float(vr), float(eb0), float(mse_target))

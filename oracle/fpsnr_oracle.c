@@ -30,6 +30,13 @@
  *   or_compress / or_decompress ... the whole pipeline and its inverse
  *                          (Sec. III: decompression rebuilds the prediction
  *                          errors, then the data point by point, Eq. 1)
+ *   or_fine_hist / or_pred_mse / or_refine_eb ... optional eb refinement:
+ *                          Eq. 3 evaluated on the field's empirical PDF (a
+ *                          fine histogram) instead of a PDF taken constant
+ *                          over each quantization bin, then the largest eb
+ *                          whose predicted MSE meets the target (Sec. V notes
+ *                          the constant-PDF estimate degrades as bins widen;
+ *                          Sec. VI leaves low targets to future work)
  *   or_sse / or_psnr ..... MSE, NRMSE and PSNR definitions (Eq. 4-5, with the
  *                          sign of Eq. 5 read as PSNR = 20 log10 vr - 10 log10 MSE)
  *   or_classic_sz ........ comparison path: the classic sequential predictor
@@ -104,19 +111,10 @@ static float round_down_to_float(double v) {
     return f;
 }
 
-void or_plan_scalars(double eb_rel, float xmin, float xmax, uint64_t n, or_scalars* p) {
-    memset(p, 0, sizeof(*p));
-    p->eb_rel = eb_rel;
-    p->xmin = xmin;
-    p->xmax = xmax;
-    p->vr = (double)xmax - (double)xmin;
-    if (n == 0 || p->vr == 0.0) {
-        /* constant (or empty) field: nothing to quantize, exact reconstruction */
-        p->flags = OR_FLAG_CONSTANT;
-        p->eb_abs = 0.0;
-        return;
-    }
-    p->eb_abs = eb_rel * p->vr;
+/* Bin width, its inverse and the verbatim threshold for absolute bound eb_abs
+ * (the caller has checked that the field is not constant). */
+static void scalars_for_eb(double eb_abs, or_scalars* p) {
+    p->eb_abs = eb_abs;
     double two_eb = 2.0 * p->eb_abs;
     float s = (float)two_eb;
     float inv = (float)(1.0 / two_eb);
@@ -131,6 +129,86 @@ void or_plan_scalars(double eb_rel, float xmin, float xmax, uint64_t n, or_scala
     float f = round_down_to_float(p->eb_abs);
     float t = (f > 0.0f) ? nextafterf(f, 0.0f) : 0.0f;
     p->thr = t > 0.0f ? t : 0.0f;
+}
+
+void or_plan_scalars(double eb_rel, float xmin, float xmax, uint64_t n, or_scalars* p) {
+    memset(p, 0, sizeof(*p));
+    p->eb_rel = eb_rel;
+    p->xmin = xmin;
+    p->xmax = xmax;
+    p->vr = (double)xmax - (double)xmin;
+    if (n == 0 || p->vr == 0.0) {
+        /* constant (or empty) field: nothing to quantize, exact reconstruction */
+        p->flags = OR_FLAG_CONSTANT;
+        p->eb_abs = 0.0;
+        return;
+    }
+    scalars_for_eb(eb_rel * p->vr, p);
+}
+
+/* ------------------------------------------------------------------------ */
+/* optional eb refinement from the empirical PDF (Eq. 3)                     */
+/* ------------------------------------------------------------------------ */
+
+#define OR_FINE_BINS 4096   /* bins of the fine histogram over [xmin, xmax] */
+#define OR_SUM_GROUPS 1024  /* the predicted MSE sums 4 bins per group, then pairs of groups */
+#define OR_BISECT_STEPS 16
+
+/* Fine histogram of the field: bin = trunc((x - xmin) * kinv) in float32,
+ * kinv = (float)(K / vr), clamped to [0, K - 1]. */
+void or_fine_hist(const float* x, uint64_t n, float xmin, double vr, uint32_t* h) {
+    const float kinv = (float)((double)OR_FINE_BINS / vr);
+    memset(h, 0, OR_FINE_BINS * sizeof(uint32_t));
+    for (uint64_t i = 0; i < n; i++) {
+        float u = (x[i] - xmin) * kinv;
+        int b = (int)u; /* truncation toward zero; u >= 0 */
+        if (b < 0) b = 0;
+        if (b > OR_FINE_BINS - 1) b = OR_FINE_BINS - 1;
+        h[b]++;
+    }
+}
+
+/* Eq. 3 with the PDF taken constant over each fine bin of width w = vr / K
+ * rather than over each quantization bin: with midpoint reconstruction on the
+ * lattice of step 2eb anchored at xmin, a fine bin centred at c (relative to
+ * xmin) contributes h (e^2 + w^2 / 12), e = c - 2eb round(c / 2eb).  Per-bin
+ * terms in float32; their sum in FP64, 4 bins per group in order, then the
+ * OR_SUM_GROUPS group sums added pairwise (group i += group i + s for s =
+ * 512, 256, ..., 1).  Returns the predicted MSE. */
+double or_pred_mse(const uint32_t* h, uint64_t n, double vr, double eb) {
+    const double w = vr / (double)OR_FINE_BINS;
+    const float df = (float)(2.0 * eb);
+    const float w212 = (float)(w * w / 12.0);
+    double part[OR_SUM_GROUPS];
+    for (int t = 0; t < OR_SUM_GROUPS; t++) {
+        double acc = 0.0;
+        for (int k = 0; k < OR_FINE_BINS / OR_SUM_GROUPS; k++) {
+            int j = t * (OR_FINE_BINS / OR_SUM_GROUPS) + k;
+            float c = (float)(((double)j + 0.5) * w);
+            float q = rintf(c / df);
+            float e = c - q * df;
+            float term = e * e + w212;
+            acc = acc + (double)h[j] * (double)term;
+        }
+        part[t] = acc;
+    }
+    for (int s2 = OR_SUM_GROUPS / 2; s2 >= 1; s2 >>= 1)
+        for (int i = 0; i < s2; i++) part[i] = part[i] + part[i + s2];
+    return part[0] / (double)n;
+}
+
+/* Largest eb in [eb0 / 4, 64 eb0] whose predicted MSE does not exceed
+ * mse_target, by OR_BISECT_STEPS bisections on the geometric midpoint. */
+double or_refine_eb(const uint32_t* h, uint64_t n, double vr, double eb0, double mse_target) {
+    double lo = eb0 * 0.25, hi = eb0 * 64.0;
+    if (or_pred_mse(h, n, vr, lo) > mse_target) return lo;
+    if (or_pred_mse(h, n, vr, hi) <= mse_target) return hi;
+    for (int it = 0; it < OR_BISECT_STEPS; it++) {
+        double mid = sqrt(lo * hi);
+        if (or_pred_mse(h, n, vr, mid) <= mse_target) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -435,16 +513,19 @@ static double psnr_from(double vr, double mse) {
 
 /* Compress a float32 field at a target PSNR.  dims are x fastest.  On success
  * *out receives a malloc'd blob of *out_bytes bytes (free with or_free). */
-int or_compress(const float* x, int ndim, const uint64_t* dims_in, int lorenzo_dims,
-                double target_psnr, int radius, int chunk, int lmax, uint8_t** out,
-                uint64_t* out_bytes, or_stats* st) {
+/* psnr_mode 0: eb from Eq. 8; 1: eb refined from the fine histogram (above)
+ * when Eq. 8's quantization bin spans at least 16 fine bins. */
+int or_compress_mode(const float* x, int ndim, const uint64_t* dims_in, int lorenzo_dims,
+                     double target_psnr, int psnr_mode, int radius, int chunk, int lmax,
+                     uint8_t** out, uint64_t* out_bytes, or_stats* st) {
     or_stats dummy;
     if (!st) st = &dummy;
     memset(st, 0, sizeof(*st));
     *out = NULL;
     *out_bytes = 0;
     if (ndim < 1 || ndim > 3 || !(target_psnr > 0.0) || !(target_psnr <= 180.0) ||
-        radius < 1 || radius > 32768 || chunk < 1 || lmax < 1 || lmax > 27)
+        radius < 1 || radius > 32768 || chunk < 1 || lmax < 1 || lmax > 27 ||
+        psnr_mode < 0 || psnr_mode > 1)
         return st->status = OR_EINVAL;
     int ld = lorenzo_dims ? lorenzo_dims : ndim;
     if (ld < 1 || ld > ndim) return st->status = OR_EINVAL;
@@ -459,6 +540,21 @@ int or_compress(const float* x, int ndim, const uint64_t* dims_in, int lorenzo_d
     if (or_range(x, n, &xmin, &xmax) != OR_OK) return st->status = OR_ENONFINITE;
     or_scalars p;
     or_plan_scalars(or_eb_rel_from_psnr(target_psnr), xmin, xmax, n, &p);
+    /* the fine histogram resolves the PDF inside a quantization bin only when
+     * the bin spans at least 16 fine bins (2 eb >= 16 vr / K); narrower bins
+     * are Eq. 6's setting and keep Eq. 8's eb */
+    if (psnr_mode == 1 && !(p.flags & OR_FLAG_CONSTANT) &&
+        p.eb_abs * (double)OR_FINE_BINS >= 8.0 * p.vr) {
+        uint32_t* fh = (uint32_t*)malloc(OR_FINE_BINS * sizeof(uint32_t));
+        if (!fh) return st->status = OR_ENOMEM;
+        or_fine_hist(x, n, xmin, p.vr, fh);
+        const double mse_target = p.vr * p.vr * pow(10.0, -target_psnr / 10.0);
+        const double eb = or_refine_eb(fh, n, p.vr, p.eb_abs, mse_target);
+        free(fh);
+        p.flags = 0;
+        p.eb_rel = eb / p.vr;
+        scalars_for_eb(eb, &p);
+    }
 
     uint16_t* codes = (uint16_t*)malloc((n ? n : 1) * sizeof(uint16_t));
     uint32_t* oi = (uint32_t*)malloc((n ? n : 1) * 4);
@@ -575,6 +671,13 @@ done:
     free(hist); free(len); free(code); free(order);
     st->status = rc;
     return rc;
+}
+
+int or_compress(const float* x, int ndim, const uint64_t* dims_in, int lorenzo_dims,
+                double target_psnr, int radius, int chunk, int lmax, uint8_t** out,
+                uint64_t* out_bytes, or_stats* st) {
+    return or_compress_mode(x, ndim, dims_in, lorenzo_dims, target_psnr, 0, radius, chunk, lmax,
+                            out, out_bytes, st);
 }
 
 /* Parse a blob's header (first 128 bytes): dims and counts.  Returns OR_OK or

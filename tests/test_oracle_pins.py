@@ -330,6 +330,90 @@ def test_psnr_model_tracks_target(oracle, psnr):
         assert p > psnr - 1.0
 
 
+# ---------------------------------------------------------------------------
+# histogram-refined eb (Eq. 3 on the empirical PDF)
+# ---------------------------------------------------------------------------
+
+def _lattice_sse(oracle, x, psnr, mode):
+    blob, st = oracle.compress(x, psnr, psnr_mode=mode)
+    xr = oracle.decompress(blob, x.shape)
+    return st, oracle.psnr(x, xr)[0]
+
+
+def test_pred_mse_matches_lattice_sse(oracle):
+    """The predicted MSE of a trial eb against the exact SSE of compressing at
+    that eb (verbatim points aside): smooth and skewed fields, several bounds."""
+    rng = np.random.default_rng(5)
+    fields = [synth.single_2d(256, seed=2),
+              np.exp(2.0 * rng.standard_normal(200000)).astype(np.float32),
+              rng.uniform(0.0, 1.0, 200000).astype(np.float32)]
+    for x in fields:
+        for psnr in (25.0, 35.0, 50.0):
+            blob, st = oracle.compress(x, psnr)
+            h = oracle.fine_hist(x, st["xmin"], st["vr"])
+            assert int(h.sum()) == x.size
+            pred = oracle.pred_mse(h, x.size, st["vr"], st["eb_abs"])
+            assert pred == pytest.approx(st["mse"], rel=0.02), (psnr, pred, st["mse"])
+
+
+def test_refine_eb_reduces_to_eq8_on_flat_pdf(oracle):
+    """Uniform data is Eq. 6's setting (error uniform in every bin): the refined
+    eb stays at Eq. 8's to within a few per cent; above ~59 dB (a bin narrower
+    than 16 fine bins) Eq. 8's eb is kept exactly."""
+    x = np.random.default_rng(6).uniform(-3.0, 5.0, 300000).astype(np.float32)
+    for psnr in (30.0, 40.0, 50.0):
+        _, st0 = oracle.compress(x, psnr)
+        _, st1 = oracle.compress(x, psnr, psnr_mode=1)
+        assert st1["eb_abs"] == pytest.approx(st0["eb_abs"], rel=0.03)
+        assert abs(st1["psnr_actual"] - psnr) < 0.1
+    for psnr in (60.0, 70.0, 100.0):
+        b0, st0 = oracle.compress(x, psnr)
+        b1, st1 = oracle.compress(x, psnr, psnr_mode=1)
+        assert st1["eb_abs"] == st0["eb_abs"] and b0 == b1
+
+
+def test_refine_eb_bracket(oracle):
+    """The result is feasible (predicted MSE within the target) and, inside the
+    bracket, the bisection end is tight: 1% more eb breaks the target.  At the
+    upper end of the bracket the target is out of reach (every point
+    reconstructed as xmin is already closer than the target asks)."""
+    x = np.exp(1.5 * np.random.default_rng(7).standard_normal(150000)).astype(np.float32)
+    rc, lo, hi = oracle.value_range(x)
+    vr = float(np.float64(hi) - np.float64(lo))
+    h = oracle.fine_hist(x, lo, vr)
+    for psnr in (30.0, 40.0, 50.0):
+        eb0 = oracle.eb_rel_from_psnr(psnr) * vr
+        tgt = vr * vr * 10.0 ** (-psnr / 10.0)
+        eb = oracle.refine_eb(h, x.size, vr, eb0, tgt)
+        assert eb0 * 0.25 <= eb <= eb0 * 64.0
+        assert oracle.pred_mse(h, x.size, vr, eb) <= tgt
+        if eb < eb0 * 64.0:
+            assert oracle.pred_mse(h, x.size, vr, eb * 1.01) > tgt
+        else:
+            assert float(np.mean((x.astype(np.float64) - lo) ** 2)) < tgt
+
+
+def test_refined_eb_meets_skewed_targets(oracle):
+    """Lognormal densities (the NYX-like stand-in) overshoot the target by
+    10-20 dB under Eq. 8 at low targets; the refinement lands within 0.5 dB of
+    it, or, when no bound can reach it (reconstructing every point as xmin is
+    already closer than the target asks), at that floor."""
+    fields, kinds = synth.cosmology_fields(40, seed=3)
+    for x, k in zip(fields, kinds):
+        if k != "density":
+            continue
+        xd = x.astype(np.float64).ravel()
+        vr = xd.max() - xd.min()
+        floor = 20 * math.log10(vr) - 10 * math.log10(np.mean((xd - xd.min()) ** 2))
+        for psnr in (30.0, 40.0, 50.0):
+            st0, p0 = _lattice_sse(oracle, x, psnr, 0)
+            st1, p1 = _lattice_sse(oracle, x, psnr, 1)
+            assert p0 - psnr > 5.0
+            assert abs(p1 - max(psnr, floor)) < 0.5, (psnr, p0, p1, floor)
+            assert st1["eb_abs"] > st0["eb_abs"]
+            assert p1 == pytest.approx(st1["psnr_actual"], abs=1e-9)
+
+
 def test_constant_and_empty_fields(oracle):
     x = np.full((17, 9), 3.25, np.float32)
     blob, st = oracle.compress(x, 80.0)
