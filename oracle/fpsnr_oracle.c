@@ -542,9 +542,9 @@ int or_compress_mode(const float* x, int ndim, const uint64_t* dims_in, int lore
     or_plan_scalars(or_eb_rel_from_psnr(target_psnr), xmin, xmax, n, &p);
     /* the fine histogram resolves the PDF inside a quantization bin only when
      * the bin spans at least 16 fine bins (2 eb >= 16 vr / K); narrower bins
-     * are Eq. 6's setting and keep Eq. 8's eb */
-    if (psnr_mode == 1 && !(p.flags & OR_FLAG_CONSTANT) &&
-        p.eb_abs * (double)OR_FINE_BINS >= 8.0 * p.vr) {
+     * are Eq. 6's setting and keep Eq. 8's eb.  A constant field, or one whose
+     * lattice is off (x - xmin may overflow float), is left as it is. */
+    if (psnr_mode == 1 && p.flags == 0 && p.eb_abs * (double)OR_FINE_BINS >= 8.0 * p.vr) {
         uint32_t* fh = (uint32_t*)malloc(OR_FINE_BINS * sizeof(uint32_t));
         if (!fh) return st->status = OR_ENOMEM;
         or_fine_hist(x, n, xmin, p.vr, fh);
