@@ -75,6 +75,16 @@ typedef struct {
     int lmax;         /* longest Huffman code in bits, 1..27, 2^lmax >= 2R (27) */
     int lorenzo_dims; /* predictor dimension d, 0 = ndim; d < ndim merges the
                          slowest axes into the slowest predictor axis */
+    int psnr_mode;    /* 0: eb from Eq. 8 (0).  1: refine eb on the field's
+                         empirical PDF: Eq. 3 evaluated on a 4096-bin histogram
+                         of the values (each fine bin contributes its count x
+                         (e^2 + w^2/12), e the lattice error of its centre, w
+                         its width), and the largest eb in [eb8/4, 64 eb8] whose
+                         predicted MSE meets the target, by 16 geometric
+                         bisections; only when Eq. 8's bin 2 eb8 spans at least
+                         16 fine bins (targets below about 59 dB), else eb8.
+                         Costs one more pass over the input.  The blob records
+                         the eb used; decompression is unchanged. */
 } fpsnr_opts;
 
 /* Per-call statistics, written by fpsnr_compress to device memory. */

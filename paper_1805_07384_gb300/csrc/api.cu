@@ -61,6 +61,7 @@ void carve(fpsnr_plan_s* p, uint8_t* base, size_t* total) {
     w.lb_ctr = c.take<uint32_t>(8);
     w.enc_tiles = c.take<uint32_t>(std::max<uint64_t>(p->enc_tiles, 1));
     w.bsum = c.take<uint32_t>(p->band.on ? (uint64_t)p->band_cap * p->band.nx : 1);
+    w.fine_hist = c.take<uint32_t>(fp::kFineBins);
     *total = (c.off + 255) & ~(size_t)255;
 }
 
@@ -199,7 +200,7 @@ extern "C" {
 
 static const char* kStageNames[FPSNR_NSTAGES] = {
     "range_plan", "predict_quantize", "rank_popc", "codebook", "band_sum", "band_carry",
-    "encode", "emit", "finalize", "decode_setup", "decode", "unused11", "scan_x", "scan_y",
+    "encode", "emit", "finalize", "decode_setup", "decode", "eb_refine", "scan_x", "scan_y",
     "scan_final_dequant", "patch"};
 
 const char* fpsnr_stage_name(int stage) {
@@ -241,6 +242,7 @@ int fpsnr_default_opts(fpsnr_opts* o) {
     o->chunk = 256;
     o->lmax = 27;
     o->lorenzo_dims = 0;
+    o->psnr_mode = 0;
     return FPSNR_OK;
 }
 
@@ -272,6 +274,7 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
     if (o.radius < 1 || o.radius > fp::kMaxRadius) return FPSNR_EINVAL;
     if (o.chunk < 32 || o.chunk > 65536 || (o.chunk % 32) != 0) return FPSNR_EINVAL;
     if (o.lmax < 1 || o.lmax > fp::kMaxLmax || (1ull << o.lmax) < 2ull * o.radius) return FPSNR_EINVAL;
+    if (o.psnr_mode != 0 && o.psnr_mode != 1) return FPSNR_EINVAL;
     uint64_t d[3] = {1, 1, 1};
     uint64_t n = 1;
     for (int i = 0; i < ndim; i++) {
@@ -288,6 +291,8 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
     p->n = n;
     p->target_psnr = target_psnr_db;
     p->eb_rel = eb_rel_of(target_psnr_db);
+    p->mse_rel = pow(10.0, -target_psnr_db / 10.0);
+    p->psnr_mode = o.psnr_mode;
     p->radius = o.radius;
     p->chunk = o.chunk;
     p->lmax = o.lmax;
@@ -367,6 +372,7 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
               cudaMemset(w.bm, 0, 2 * std::max<uint64_t>(p->nwords, 1) * 4) == cudaSuccess &&
               cudaMemset(w.lb_flags, 0, std::max<uint64_t>(p->lb_tiles_total, 1) * 4) == cudaSuccess &&
               cudaMemset(w.lb_ctr, 0, 8 * 4) == cudaSuccess &&
+              cudaMemset(w.fine_hist, 0, fp::kFineBins * 4) == cudaSuccess &&
 
               fp::codebook_prepare() == FPSNR_OK && fp::decode_prepare(p) == FPSNR_OK &&
               cudaDeviceSynchronize() == cudaSuccess;
@@ -384,6 +390,7 @@ int fpsnr_plan_set_psnr(fpsnr_plan_t p, double target_psnr_db) {
     if (!p || !psnr_ok(target_psnr_db)) return FPSNR_EINVAL;
     p->target_psnr = target_psnr_db;
     p->eb_rel = eb_rel_of(target_psnr_db);
+    p->mse_rel = pow(10.0, -target_psnr_db / 10.0);
     return FPSNR_OK;
 }
 

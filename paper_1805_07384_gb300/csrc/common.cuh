@@ -23,6 +23,7 @@ constexpr uint32_t kFlagError = 1u << 31;  // internal: a device-side error occu
 constexpr int kMaxRadius = 32768;
 constexpr int kMaxSym = 2 * kMaxRadius;
 constexpr int kMaxLmax = 27;
+constexpr int kFineBins = 4096;  // fine histogram of the bound refinement (psnr_mode 1)
 constexpr int kLutBits = 12;  // decode look-up table width (first level)
 constexpr int kL2Sub = 6;     // second level: up to this many bits past the first level
 constexpr int kL2Cap = 4096;  // second-level entries (shared memory of the decoder)
@@ -44,6 +45,7 @@ struct DevParams {
     // the first kernel of every decompress call (so a captured CUDA graph
     // replays correctly)
     uint32_t dec_epoch;
+    float kinv;               // (float)(kFineBins / vr): fine-histogram bin scale
     uint64_t cap;             // output capacity of this call
     uint64_t off_cb, off_ct, off_st, off_ou, off_vb, total;
     // decompression: header fields of the blob being decoded
@@ -81,6 +83,7 @@ struct Workspace {
     uint32_t* lb_ctr;    // [8] dynamic tile counters (pairs: counter, done)
     uint32_t* enc_tiles; // [enc_tiles] words per encoder tile, then their exclusive prefix
     uint32_t* bsum;      // [nbands * nx] 2D band column sums (band geometry only)
+    uint32_t* fine_hist; // [kFineBins] bound refinement histogram (kept zero between calls)
 };
 
 // Launch geometry of the predict-quantize kernel.
@@ -122,7 +125,7 @@ struct ScanPass {
 namespace fp {
 enum Stage {
     kStRange = 0, kStPq, kStRank, kStCodebook, kStBandSum, kStBandCarry, kStEncode, kStEmit,
-    kStFinalize, kStDsetup, kStDecode, kStUnused11, kStScanX, kStScanY, kStScanFinal, kStPatch
+    kStFinalize, kStDsetup, kStDecode, kStRefine, kStScanX, kStScanY, kStScanFinal, kStPatch
 };
 
 // Host-side launch counters and optional per-launch CUDA events.
@@ -148,6 +151,8 @@ struct fpsnr_plan_s {
     uint64_t n;
     double target_psnr, eb_rel;
     int radius, chunk, lmax;
+    int psnr_mode;    // 0: eb from Eq. 8; 1: refined from the fine histogram
+    double mse_rel;   // 10^(-target / 10) (the target MSE over vr^2)
     uint32_t nsym;
     uint64_t nchunks, nwords, nbmblk;
     fp::PQGeom pq;

@@ -26,6 +26,27 @@ namespace fp {
 // value range and plan scalars
 // ---------------------------------------------------------------------------
 
+// Bin width s = (float)(2 eb), its inverse, the verbatim threshold (the float
+// just below rd(eb)) and the lattice-off flag for absolute bound eb on a
+// non-constant field of range vr.
+__device__ void scalars_for_eb(double eb, double vr, float* s_out, float* inv_out, float* thr_out,
+                               uint32_t* flags) {
+    const double two_eb = __dmul_rn(2.0, eb);
+    float s = __double2float_rn(two_eb);
+    float inv = __double2float_rn(__ddiv_rn(1.0, two_eb));
+    *flags = 0;
+    if (!(s > 0.0f) || isinf(inv) || !(vr <= (double)FLT_MAX)) {
+        *flags = kFlagLatticeOff;
+        s = 0.0f;
+        inv = 0.0f;
+    }
+    const float f = __double2float_rd(eb);
+    const float t = f > 0.0f ? __int_as_float(__float_as_int(f) - 1) : 0.0f;
+    *s_out = s;
+    *inv_out = inv;
+    *thr_out = t > 0.0f ? t : 0.0f;
+}
+
 struct RangeArgs {
     const float* x;
     uint64_t n;
@@ -134,19 +155,10 @@ __global__ void __launch_bounds__(512) k_range_plan(const __grid_constant__ Batc
     } else if (n == 0 || vr == 0.0) {
         flags = kFlagConstant;
     } else {
-        eb = A.eb_rel * vr;
-        double two_eb = 2.0 * eb;
-        s = __double2float_rn(two_eb);
-        inv = __double2float_rn(1.0 / two_eb);
-        if (!(s > 0.0f) || isinf(inv) || !(vr <= (double)FLT_MAX)) {
-            flags = kFlagLatticeOff;
-            s = 0.0f;
-            inv = 0.0f;
-        }
-        float f = __double2float_rd(eb);
-        float t = f > 0.0f ? __int_as_float(__float_as_int(f) - 1) : 0.0f;
-        thr = t > 0.0f ? t : 0.0f;
+        eb = __dmul_rn(A.eb_rel, vr);
+        scalars_for_eb(eb, vr, &s, &inv, &thr, &flags);
     }
+    par->kinv = vr > 0.0 ? __double2float_rn(__ddiv_rn((double)kFineBins, vr)) : 0.0f;
     par->vr = vr;
     par->eb_abs = eb;
     par->eb_rel = A.eb_rel;
@@ -169,6 +181,145 @@ __global__ void __launch_bounds__(512) k_range_plan(const __grid_constant__ Batc
     par->done_range = 0;
     par->sym_lo = 0xffffffffu;
     par->sym_hi = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// optional error-bound refinement from the field's empirical PDF (Eq. 3)
+// ---------------------------------------------------------------------------
+//
+// Eq. 8 takes the quantization error as uniform over every bin (Eq. 6).  With
+// psnr_mode 1 the bound is refined on a kFineBins-bin histogram of the field:
+// every fine bin contributes h (e^2 + w^2/12), e the lattice error of its
+// centre, and a fixed bisection finds the largest eb whose predicted MSE meets
+// the target.  Only when Eq. 8's bin spans at least 16 fine bins.  The order of
+// every operation is fixed (float per-bin terms, FP64 sums over 1024 groups of
+// 4 bins, a pairwise tree), and explicit round-to-nearest intrinsics keep the
+// compiler from fusing any of them, so the result is the same bit for bit
+// wherever it is computed.
+
+__device__ __forceinline__ bool refine_applies(const DevParams* par) {
+    return par->flags == 0 && __dmul_rn(par->eb_abs, (double)kFineBins) >= __dmul_rn(8.0, par->vr);
+}
+
+struct FineArgs {
+    const float* x;
+    DevParams* par;
+    uint32_t* fh;
+    uint64_t n;
+    bool vec;
+};
+
+// Fine histogram: bin = trunc((x - xmin) * kinv) in float, clamped to [0, K - 1].
+__global__ void __launch_bounds__(512) k_fine_hist(const __grid_constant__ Batch<FineArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const FineArgs& A = B.a[fld];
+    const uint32_t bid = blockIdx.x - B.off[fld], nblk = B.off[fld + 1] - B.off[fld];
+    const DevParams* par = A.par;
+    if (!refine_applies(par)) return;
+    __shared__ uint32_t sh[kFineBins];
+    for (uint32_t i = threadIdx.x; i < (uint32_t)kFineBins; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
+    const float xmin = par->xmin, kinv = par->kinv;
+    auto bin = [&](float v) {
+        const float u = __fmul_rn(__fsub_rn(v, xmin), kinv);
+        const int b = __float2int_rz(u);
+        atomicAdd(&sh[min(max(b, 0), kFineBins - 1)], 1u);
+    };
+    const uint64_t gtid = (uint64_t)bid * blockDim.x + threadIdx.x;
+    const uint64_t gsz = (uint64_t)nblk * blockDim.x;
+    const float* __restrict__ x = A.x;
+    if (A.vec) {
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        const uint64_t n4 = A.n >> 2;
+        for (uint64_t i = gtid; i < n4; i += gsz) {
+            const float4 v = __ldcs(x4 + i);
+            bin(v.x); bin(v.y); bin(v.z); bin(v.w);
+        }
+        for (uint64_t i = (n4 << 2) + gtid; i < A.n; i += gsz) bin(x[i]);
+    } else {
+        for (uint64_t i = gtid; i < A.n; i += gsz) bin(x[i]);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < (uint32_t)kFineBins; i += blockDim.x)
+        if (sh[i]) atomicAdd(&A.fh[i], sh[i]);
+}
+
+struct RefineArgs {
+    DevParams* par;
+    uint32_t* fh;
+    uint64_t n;
+    double mse_rel;  // 10^(-target / 10), from the host
+};
+
+constexpr int kRefineThreads = 1024;
+constexpr int kBisectSteps = 16;
+
+// One block per field: the bisection of Eq. 3's predicted MSE, then the plan
+// scalars for the refined bound.  Clears the fine histogram for the next call.
+__global__ void __launch_bounds__(kRefineThreads) k_eb_refine(const __grid_constant__ Batch<RefineArgs> B) {
+    const RefineArgs& A = B.a[blockIdx.x];
+    DevParams* par = A.par;
+    if (!refine_applies(par)) return;
+    static_assert(kFineBins == 4 * kRefineThreads, "4 fine bins per thread");
+    __shared__ double part[kRefineThreads];
+    const uint32_t t = threadIdx.x;
+    uint32_t h[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        h[k] = A.fh[4 * t + k];
+        A.fh[4 * t + k] = 0u;
+    }
+    const double vr = par->vr, eb0 = par->eb_abs;
+    const double w = __ddiv_rn(vr, (double)kFineBins);
+    const float w212 = __double2float_rn(__ddiv_rn(__dmul_rn(w, w), 12.0));
+    float c[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) c[k] = __double2float_rn(__dmul_rn(__dadd_rn((double)(4 * t + k), 0.5), w));
+    const double nd = (double)A.n;
+    auto pred = [&](double eb) -> double {
+        const float df = __double2float_rn(__dmul_rn(2.0, eb));
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float q = rintf(__fdiv_rn(c[k], df));
+            const float e = __fsub_rn(c[k], __fmul_rn(q, df));
+            const float term = __fadd_rn(__fmul_rn(e, e), w212);
+            acc = __dadd_rn(acc, __dmul_rn((double)h[k], (double)term));
+        }
+        __syncthreads();  // the previous evaluation's result has been read
+        part[t] = acc;
+        __syncthreads();
+        for (uint32_t s2 = kRefineThreads / 2; s2 >= 1; s2 >>= 1) {
+            if (t < s2) part[t] = __dadd_rn(part[t], part[t + s2]);
+            __syncthreads();
+        }
+        return __ddiv_rn(part[0], nd);
+    };
+    const double target = __dmul_rn(__dmul_rn(vr, vr), A.mse_rel);
+    double lo = __dmul_rn(eb0, 0.25), hi = __dmul_rn(eb0, 64.0), eb;
+    if (pred(lo) > target) {
+        eb = lo;
+    } else if (pred(hi) <= target) {
+        eb = hi;
+    } else {
+        for (int it = 0; it < kBisectSteps; it++) {
+            const double mid = __dsqrt_rn(__dmul_rn(lo, hi));
+            if (pred(mid) <= target) lo = mid;
+            else hi = mid;
+        }
+        eb = lo;
+    }
+    if (t == 0) {
+        float s, inv, thr;
+        uint32_t flags;
+        scalars_for_eb(eb, vr, &s, &inv, &thr, &flags);
+        par->eb_abs = eb;
+        par->eb_rel = __ddiv_rn(eb, vr);
+        par->s = s;
+        par->inv = inv;
+        par->thr = thr;
+        par->flags = flags;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -917,6 +1068,31 @@ int launch_compress_batch(fpsnr_plan_s* const* P, const float* const* d_in, void
         const uint32_t tot = batch_offsets(b, blocks);
         StageScope sc(prof, kStRange, st);
         k_range_plan<<<tot, 512, 0, st>>>(b);
+    }
+    FP_LAUNCH_CHECK();
+
+    // ---- optional bound refinement (psnr_mode 1) ----
+    {
+        Batch<FineArgs> bf;
+        Batch<RefineArgs> br;
+        bf.count = br.count = 0;
+        uint32_t fblocks[kMaxBatch], rblocks[kMaxBatch];
+        for (int f = 0; f < count; f++) {
+            const fpsnr_plan_s* p = P[f];
+            if (p->psnr_mode != 1 || p->n == 0) continue;
+            fblocks[bf.count] = p->n_range_blocks;
+            rblocks[br.count] = 1;
+            bf.a[bf.count++] = FineArgs{d_in[f], p->w.par, p->w.fine_hist, p->n,
+                                        ((uintptr_t)d_in[f] & 15u) == 0};
+            br.a[br.count++] = RefineArgs{p->w.par, p->w.fine_hist, p->n, p->mse_rel};
+        }
+        if (bf.count) {
+            const uint32_t tf = batch_offsets(bf, fblocks);
+            const uint32_t tr = batch_offsets(br, rblocks);
+            StageScope sc(prof, kStRefine, st);
+            k_fine_hist<<<tf, 512, 0, st>>>(bf);
+            k_eb_refine<<<tr, kRefineThreads, 0, st>>>(br);
+        }
     }
     FP_LAUNCH_CHECK();
 

@@ -29,10 +29,10 @@ def env(oracle):
     return torch, fpsnr, oracle
 
 
-def run_gpu(env, x, psnr, radius=32768, chunk=256, lmax=27, ld=0, plan=None):
+def run_gpu(env, x, psnr, radius=32768, chunk=256, lmax=27, ld=0, plan=None, psnr_mode=0):
     torch, fpsnr, _ = env
     plan = plan or fpsnr.Plan(x.shape, psnr, radius=radius, chunk=chunk, lmax=lmax,
-                              lorenzo_dims=ld)
+                              lorenzo_dims=ld, psnr_mode=psnr_mode)
     plan.set_psnr(psnr)
     xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     out, nb, st = plan.compress(xt)
@@ -43,13 +43,14 @@ def run_gpu(env, x, psnr, radius=32768, chunk=256, lmax=27, ld=0, plan=None):
     return plan, xt, out, nbytes, stats, blob
 
 
-def check_case(env, x, psnr, radius=32768, chunk=256, lmax=27, ld=0, plan=None):
+def check_case(env, x, psnr, radius=32768, chunk=256, lmax=27, ld=0, plan=None, psnr_mode=0):
     torch, fpsnr, oracle = env
-    plan, xt, out, nbytes, st, blob = run_gpu(env, x, psnr, radius, chunk, lmax, ld, plan)
+    plan, xt, out, nbytes, st, blob = run_gpu(env, x, psnr, radius, chunk, lmax, ld, plan, psnr_mode)
     assert st["status"] == 0, fpsnr.fpsnr_strerror(st["status"])
-    ob, ost = oracle.compress(x, psnr, radius=radius, chunk=chunk, lmax=lmax, lorenzo_dims=ld)
+    ob, ost = oracle.compress(x, psnr, radius=radius, chunk=chunk, lmax=lmax, lorenzo_dims=ld,
+                              psnr_mode=psnr_mode)
     # symbols
-    if x.size and not (ost["flags"] & oracle.FLAG_CONSTANT):
+    if x.size and not (ost["flags"] & oracle.FLAG_CONSTANT) and psnr_mode == 0:
         s = oracle.plan_scalars(ost["eb_rel"], ost["xmin"], ost["xmax"], x.size)
         lat = oracle.lattice(x, s, radius, lorenzo_dims=ld)
         gcodes = plan.codes().cpu().numpy().view(np.uint16)
@@ -84,6 +85,43 @@ def check_case(env, x, psnr, radius=32768, chunk=256, lmax=27, ld=0, plan=None):
     assert st["n_outlier"] == ost["n_outlier"] and st["n_verbatim"] == ost["n_verbatim"]
     assert st["eb_abs"] == ost["eb_abs"] and st["vr"] == ost["vr"]
     return plan, st, ost
+
+
+# ---------------------------------------------------------------------------
+# histogram-refined bound (psnr_mode 1)
+# ---------------------------------------------------------------------------
+
+def _refine_fields():
+    dens, kinds = synth.cosmology_fields(40, seed=3)
+    rng = np.random.default_rng(12)
+    return [("density", dens[0]), ("temperature", dens[5]), ("velocity", dens[2]),
+            ("climate", field_for((300, 700), 13)),
+            ("lognormal1d", np.exp(1.5 * rng.standard_normal(100003)).astype(np.float32)),
+            ("uniform", rng.uniform(-2.0, 7.0, (64, 1000)).astype(np.float32))]
+
+
+@pytest.mark.parametrize("psnr", [30.0, 40.0, 50.0, 80.0])
+def test_parity_refined_eb(env, psnr):
+    """Bytes, floats and PSNR with the refined bound: the device must reach the
+    oracle's eb bit for bit (same histogram, same fixed-order sums)."""
+    for name, x in _refine_fields():
+        _, st, ost = check_case(env, x, psnr, psnr_mode=1)
+        assert st["eb_abs"] == ost["eb_abs"] and st["eb_rel"] == ost["eb_rel"], name
+
+
+def test_refined_eb_batch_and_constant(env):
+    """Refined and plain fields mixed in one batch; a constant field is left alone."""
+    torch, fpsnr, oracle = env
+    fields = [x for _, x in _refine_fields()] + [np.full((40, 50), 3.5, np.float32)]
+    modes = [1, 0, 1, 1, 0, 1, 1]
+    plans = [fpsnr.Plan(x.shape, 35.0, psnr_mode=m) for x, m in zip(fields, modes)]
+    xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in fields]
+    outs, nb, st = fpsnr.compress_batch(plans, xs)
+    torch.cuda.synchronize()
+    for i, (x, m) in enumerate(zip(fields, modes)):
+        ob, _ = oracle.compress(x, 35.0, psnr_mode=m)
+        n = int(nb[i].item())
+        assert outs[i][:n].cpu().numpy().tobytes() == ob, i
 
 
 # ---------------------------------------------------------------------------
