@@ -94,7 +94,9 @@ def lib():
             L.or_compress.argtypes = [P, C.c_int, P, C.c_int, C.c_double, C.c_int, C.c_int,
                                       C.c_int, C.POINTER(C.c_void_p), P, P]
             L.or_compress_mode.argtypes = [P, C.c_int, P, C.c_int, C.c_double, C.c_int, C.c_int,
-                                           C.c_int, C.c_int, C.POINTER(C.c_void_p), P, P]
+                                           C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p), P, P]
+            L.or_zrle_wrap.argtypes = [P, C.c_uint64, C.POINTER(C.c_void_p), P]
+            L.or_zrle_unwrap.argtypes = [P, C.c_uint64, C.POINTER(C.c_void_p), P]
             L.or_fine_hist.restype = None
             L.or_fine_hist.argtypes = [P, C.c_uint64, C.c_float, C.c_double, P]
             L.or_pred_mse.restype = C.c_double
@@ -200,16 +202,18 @@ def canonical_codes(lens):
 
 
 def compress(x: np.ndarray, psnr_db: float, radius: int = 32768, chunk: int = 256,
-             lmax: int = 27, lorenzo_dims: int = 0, psnr_mode: int = 0):
+             lmax: int = 27, lorenzo_dims: int = 0, psnr_mode: int = 0, lossless: int = 0):
     """Returns (blob bytes, stats dict); raises on a nonzero status.  psnr_mode
-    1 refines eb from the fine histogram (or_refine_eb)."""
+    1 refines eb from the fine histogram (or_refine_eb); lossless 1 wraps the
+    blob in the zero-run container when that is smaller (or_zrle_wrap)."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     dims = _dims(x.shape)
     out = C.c_void_p()
     nbytes = C.c_uint64()
     st = Stats()
     rc = lib().or_compress_mode(_ptr(x), x.ndim, _ptr(dims), int(lorenzo_dims), float(psnr_db),
-                                int(psnr_mode), int(radius), int(chunk), int(lmax), C.byref(out),
+                                int(psnr_mode), int(lossless), int(radius), int(chunk), int(lmax),
+                                C.byref(out),
                                 C.byref(nbytes), C.byref(st))
     if rc:
         raise ValueError(f"or_compress failed with status {rc}")
@@ -324,3 +328,24 @@ def pred_mse(h: np.ndarray, n: int, vr: float, eb: float) -> float:
 def refine_eb(h: np.ndarray, n: int, vr: float, eb0: float, mse_target: float) -> float:
     h = np.ascontiguousarray(h, dtype=np.uint32)
     return lib().or_refine_eb(_ptr(h), int(n), float(vr), float(eb0), float(mse_target))
+
+
+def _zcall(fn, data: bytes) -> bytes:
+    buf = np.frombuffer(data, dtype=np.uint8).copy() if data else np.zeros(1, np.uint8)
+    out = C.c_void_p()
+    nb = C.c_uint64()
+    rc = fn(_ptr(buf), len(data), C.byref(out), C.byref(nb))
+    if rc:
+        raise ValueError(f"lossless layer failed with status {rc}")
+    try:
+        return C.string_at(out.value, nb.value)
+    finally:
+        lib().or_free(out)
+
+
+def zrle_wrap(raw: bytes) -> bytes:
+    return _zcall(lib().or_zrle_wrap, raw)
+
+
+def zrle_unwrap(data: bytes) -> bytes:
+    return _zcall(lib().or_zrle_unwrap, data)

@@ -37,6 +37,10 @@
  *                          whose predicted MSE meets the target (Sec. V notes
  *                          the constant-PDF estimate degrades as bins widen;
  *                          Sec. VI leaves low targets to future work)
+ *   or_zrle_wrap / or_zrle_unwrap ... optional lossless layer over the finished
+ *                          blob, standing in for SZ's lossless step 3 (Sec. II-A,
+ *                          "optional"; the paper names GZIP): zero-byte runs
+ *                          coded per 1 KiB segment
  *   or_sse / or_psnr ..... MSE, NRMSE and PSNR definitions (Eq. 4-5, with the
  *                          sign of Eq. 5 read as PSNR = 20 log10 vr - 10 log10 MSE)
  *   or_classic_sz ........ comparison path: the classic sequential predictor
@@ -513,11 +517,171 @@ static double psnr_from(double vr, double mse) {
 
 /* Compress a float32 field at a target PSNR.  dims are x fastest.  On success
  * *out receives a malloc'd blob of *out_bytes bytes (free with or_free). */
+/* ------------------------------------------------------------------------ */
+/* optional lossless layer (SZ step 3)                                       */
+/* ------------------------------------------------------------------------ */
+/* Container "FPZ1" around a finished blob:
+ *   0  u32 magic 0x315A5046 ("FPZ1")    4  u32 version 1
+ *   8  u64 raw blob bytes              16  u32 segment bytes (1024)
+ *  20  u32 segments                    24  8 zero bytes
+ *  32  u32 offsets[segments + 1]: start of every segment's data relative to
+ *      the data section (bit 31: the segment is stored raw); the last entry
+ *      is the data length; zero-padded to 16 bytes
+ *      data section: every segment coded on its own, zero-padded to 16 bytes
+ * A segment is coded byte by byte: a nonzero byte is copied; a run of k zero
+ * bytes (k >= 1, as long as it lasts inside the segment) becomes 0x00 and
+ * k - 1 in LEB128 (7 bits per byte, low first, bit 7 = more).  A segment whose
+ * code is not shorter than the segment is stored raw.  The container is used
+ * only when it is smaller than the blob; otherwise the blob stays as it is. */
+
+#define OR_ZMAGIC 0x315A5046u
+#define OR_ZSEG 1024u
+
+static uint64_t zrle_code(const uint8_t* in, uint64_t len, uint8_t* out) {
+    uint64_t o = 0, i = 0;
+    while (i < len) {
+        if (in[i] != 0) {
+            if (out) out[o] = in[i];
+            o++;
+            i++;
+            continue;
+        }
+        uint64_t k = 0;
+        while (i + k < len && in[i + k] == 0) k++;
+        if (out) out[o] = 0;
+        o++;
+        uint64_t v = k - 1;
+        while (v >= 128) {
+            if (out) out[o] = (uint8_t)((v & 127u) | 128u);
+            o++;
+            v >>= 7;
+        }
+        if (out) out[o] = (uint8_t)v;
+        o++;
+        i += k;
+    }
+    return o;
+}
+
+static uint64_t pad16o(uint64_t b) { return (b + 15u) & ~(uint64_t)15u; }
+
+/* Wraps `raw` in the container when that is smaller; *out is malloc'd (free
+ * with or_free) and holds either the container or a copy of raw. */
+int or_zrle_wrap(const uint8_t* raw, uint64_t raw_bytes, uint8_t** out, uint64_t* out_bytes) {
+    uint64_t nseg = (raw_bytes + OR_ZSEG - 1) / OR_ZSEG;
+    uint64_t* off = (uint64_t*)malloc((nseg + 1) * sizeof(uint64_t));
+    uint8_t* rawflag = (uint8_t*)malloc(nseg ? nseg : 1);
+    if (!off || !rawflag) { free(off); free(rawflag); return OR_ENOMEM; }
+    uint64_t data = 0;
+    for (uint64_t sg = 0; sg < nseg; sg++) {
+        uint64_t b = sg * OR_ZSEG, len = raw_bytes - b < OR_ZSEG ? raw_bytes - b : OR_ZSEG;
+        uint64_t c = zrle_code(raw + b, len, NULL);
+        rawflag[sg] = c >= len;
+        off[sg] = data;
+        data += rawflag[sg] ? len : c;
+    }
+    off[nseg] = data;
+    uint64_t dstart = 32 + pad16o(4 * (nseg + 1));
+    uint64_t total = dstart + pad16o(data);
+    uint8_t* o;
+    if (total >= raw_bytes) {
+        o = (uint8_t*)malloc(raw_bytes ? raw_bytes : 1);
+        if (!o) { free(off); free(rawflag); return OR_ENOMEM; }
+        memcpy(o, raw, raw_bytes);
+        *out = o;
+        *out_bytes = raw_bytes;
+        free(off);
+        free(rawflag);
+        return OR_OK;
+    }
+    o = (uint8_t*)calloc(total, 1);
+    if (!o) { free(off); free(rawflag); return OR_ENOMEM; }
+    put32(o, 0, OR_ZMAGIC);
+    put32(o, 4, 1u);
+    put64(o, 8, raw_bytes);
+    put32(o, 16, OR_ZSEG);
+    put32(o, 20, (uint32_t)nseg);
+    for (uint64_t sg = 0; sg <= nseg; sg++)
+        put32(o, 32 + 4 * sg, (uint32_t)off[sg] | ((sg < nseg && rawflag[sg]) ? 0x80000000u : 0u));
+    for (uint64_t sg = 0; sg < nseg; sg++) {
+        uint64_t b = sg * OR_ZSEG, len = raw_bytes - b < OR_ZSEG ? raw_bytes - b : OR_ZSEG;
+        if (rawflag[sg]) memcpy(o + dstart + off[sg], raw + b, len);
+        else zrle_code(raw + b, len, o + dstart + off[sg]);
+    }
+    free(off);
+    free(rawflag);
+    *out = o;
+    *out_bytes = total;
+    return OR_OK;
+}
+
+/* Inverse of or_zrle_wrap for a container (magic "FPZ1"); a buffer without
+ * the magic is returned as a copy.  OR_ECORRUPT on any inconsistency. */
+int or_zrle_unwrap(const uint8_t* c, uint64_t bytes, uint8_t** raw, uint64_t* raw_bytes) {
+    *raw = NULL;
+    *raw_bytes = 0;
+    if (bytes < 4 || get32(c, 0) != OR_ZMAGIC) {
+        uint8_t* o = (uint8_t*)malloc(bytes ? bytes : 1);
+        if (!o) return OR_ENOMEM;
+        memcpy(o, c, bytes);
+        *raw = o;
+        *raw_bytes = bytes;
+        return OR_OK;
+    }
+    if (bytes < 32 || get32(c, 4) != 1u || get32(c, 16) != OR_ZSEG) return OR_ECORRUPT;
+    uint64_t rb = get64(c, 8), nseg = get32(c, 20);
+    if (nseg != (rb + OR_ZSEG - 1) / OR_ZSEG) return OR_ECORRUPT;
+    uint64_t dstart = 32 + pad16o(4 * (nseg + 1));
+    if (dstart > bytes) return OR_ECORRUPT;
+    uint64_t dlen = get32(c, 32 + 4 * nseg) & 0x7FFFFFFFu;
+    if (dstart + dlen > bytes) return OR_ECORRUPT;
+    uint8_t* o = (uint8_t*)malloc(rb ? rb : 1);
+    if (!o) return OR_ENOMEM;
+    for (uint64_t sg = 0; sg < nseg; sg++) {
+        uint32_t e0 = get32(c, 32 + 4 * sg), e1 = get32(c, 32 + 4 * (sg + 1));
+        uint64_t a = e0 & 0x7FFFFFFFu, z = e1 & 0x7FFFFFFFu;
+        uint64_t b = sg * OR_ZSEG, len = rb - b < OR_ZSEG ? rb - b : OR_ZSEG;
+        if (a > z || z > dlen) { free(o); return OR_ECORRUPT; }
+        const uint8_t* in = c + dstart + a;
+        if (e0 & 0x80000000u) {
+            if (z - a != len) { free(o); return OR_ECORRUPT; }
+            memcpy(o + b, in, len);
+            continue;
+        }
+        uint64_t i = 0, w = 0;
+        while (i < z - a) {
+            uint8_t v = in[i++];
+            if (v != 0) {
+                if (w >= len) { free(o); return OR_ECORRUPT; }
+                o[b + w++] = v;
+                continue;
+            }
+            uint64_t k = 0;
+            int sh = 0;
+            for (;;) {
+                if (i >= z - a || sh > 28) { free(o); return OR_ECORRUPT; }
+                uint8_t t = in[i++];
+                k |= (uint64_t)(t & 127u) << sh;
+                sh += 7;
+                if (!(t & 128u)) break;
+            }
+            k += 1;
+            if (w + k > len) { free(o); return OR_ECORRUPT; }
+            memset(o + b + w, 0, k);
+            w += k;
+        }
+        if (w != len) { free(o); return OR_ECORRUPT; }
+    }
+    *raw = o;
+    *raw_bytes = rb;
+    return OR_OK;
+}
+
 /* psnr_mode 0: eb from Eq. 8; 1: eb refined from the fine histogram (above)
  * when Eq. 8's quantization bin spans at least 16 fine bins. */
 int or_compress_mode(const float* x, int ndim, const uint64_t* dims_in, int lorenzo_dims,
-                     double target_psnr, int psnr_mode, int radius, int chunk, int lmax,
-                     uint8_t** out, uint64_t* out_bytes, or_stats* st) {
+                     double target_psnr, int psnr_mode, int lossless, int radius, int chunk,
+                     int lmax, uint8_t** out, uint64_t* out_bytes, or_stats* st) {
     or_stats dummy;
     if (!st) st = &dummy;
     memset(st, 0, sizeof(*st));
@@ -525,7 +689,7 @@ int or_compress_mode(const float* x, int ndim, const uint64_t* dims_in, int lore
     *out_bytes = 0;
     if (ndim < 1 || ndim > 3 || !(target_psnr > 0.0) || !(target_psnr <= 180.0) ||
         radius < 1 || radius > 32768 || chunk < 1 || lmax < 1 || lmax > 27 ||
-        psnr_mode < 0 || psnr_mode > 1)
+        psnr_mode < 0 || psnr_mode > 1 || lossless < 0 || lossless > 1)
         return st->status = OR_EINVAL;
     int ld = lorenzo_dims ? lorenzo_dims : ndim;
     if (ld < 1 || ld > ndim) return st->status = OR_EINVAL;
@@ -662,6 +826,16 @@ int or_compress_mode(const float* x, int ndim, const uint64_t* dims_in, int lore
     st->n_sym = nused;
     st->xmin = p.xmin; st->xmax = p.xmax; st->s = p.s; st->inv = p.inv; st->thr = p.thr;
     st->flags = p.flags;
+    if (lossless) {
+        uint8_t* wrapped = NULL;
+        uint64_t wb = 0;
+        rc = or_zrle_wrap(blob, total, &wrapped, &wb);
+        if (rc) goto done;
+        free(blob);
+        blob = wrapped;
+        total = wb;
+        st->bytes = wb;
+    }
     *out = blob;
     *out_bytes = total;
     blob = NULL;
@@ -676,8 +850,8 @@ done:
 int or_compress(const float* x, int ndim, const uint64_t* dims_in, int lorenzo_dims,
                 double target_psnr, int radius, int chunk, int lmax, uint8_t** out,
                 uint64_t* out_bytes, or_stats* st) {
-    return or_compress_mode(x, ndim, dims_in, lorenzo_dims, target_psnr, 0, radius, chunk, lmax,
-                            out, out_bytes, st);
+    return or_compress_mode(x, ndim, dims_in, lorenzo_dims, target_psnr, 0, 0, radius, chunk,
+                            lmax, out, out_bytes, st);
 }
 
 /* Parse a blob's header (first 128 bytes): dims and counts.  Returns OR_OK or
@@ -693,7 +867,22 @@ int or_blob_info(const uint8_t* blob, uint64_t bytes, uint64_t* dims, uint32_t* 
 /* Decompress a blob into n floats.  Bit-serial canonical Huffman decoding,
  * outlier deltas put back, prefix sums, midpoint reconstruction, verbatim
  * values restored. */
+static int decompress_raw(const uint8_t* blob, uint64_t bytes, float* out, uint64_t n_out);
+
+/* A container (or_zrle_wrap) is unwrapped first. */
 int or_decompress(const uint8_t* blob, uint64_t bytes, float* out, uint64_t n_out) {
+    if (bytes >= 4 && get32(blob, 0) == OR_ZMAGIC) {
+        uint8_t* raw = NULL;
+        uint64_t rb = 0;
+        int rc = or_zrle_unwrap(blob, bytes, &raw, &rb);
+        if (rc == OR_OK) rc = decompress_raw(raw, rb, out, n_out);
+        free(raw);
+        return rc;
+    }
+    return decompress_raw(blob, bytes, out, n_out);
+}
+
+static int decompress_raw(const uint8_t* blob, uint64_t bytes, float* out, uint64_t n_out) {
     if (bytes < OR_HEADER_BYTES || get32(blob, 0) != OR_MAGIC || get32(blob, 4) != OR_VERSION)
         return OR_ECORRUPT;
     int ndim = (int)get32(blob, 8);

@@ -414,6 +414,73 @@ def test_refined_eb_meets_skewed_targets(oracle):
             assert p1 == pytest.approx(st1["psnr_actual"], abs=1e-9)
 
 
+# ---------------------------------------------------------------------------
+# optional lossless layer
+# ---------------------------------------------------------------------------
+
+def test_zrle_golden(oracle):
+    cases, cur = {}, None
+    for key, toks in read_golden("zrle_tiny.txt"):
+        if key == "case":
+            cur = cases.setdefault(toks[0], {})
+        elif key == "raw":
+            raw = b""
+            for t in toks:
+                cnt, hx = t.split("*")
+                raw += bytes([int(hx, 16)]) * int(cnt)
+            cur["raw"] = raw
+        elif key == "container":
+            cur["container"] = None if toks == ["same"] else bytes(int(t, 16) for t in toks)
+    assert len(cases) == 3
+    for name, c in cases.items():
+        want = c["raw"] if c["container"] is None else c["container"]
+        assert oracle.zrle_wrap(c["raw"]) == want, name
+        assert oracle.zrle_unwrap(want) == c["raw"], name
+
+
+def test_zrle_roundtrip_and_corruption(oracle):
+    rng = np.random.default_rng(13)
+    for n in (0, 1, 1023, 1024, 1025, 5000, 70000):
+        raw = rng.integers(0, 256, n, dtype=np.uint8)
+        raw[rng.uniform(size=n) < 0.7] = 0  # zero runs of every length
+        raw = raw.tobytes()
+        w = oracle.zrle_wrap(raw)
+        assert oracle.zrle_unwrap(w) == raw
+        assert len(w) <= len(raw)
+    raw = bytes(3000) + bytes(range(1, 200)) * 5
+    w = bytearray(oracle.zrle_wrap(raw))
+    assert w[:4] == b"FPZ1"
+    for off in (8, 16, 20, 36, len(w) - 30):
+        b = bytearray(w)
+        b[off] ^= 0x41
+        try:
+            out = oracle.zrle_unwrap(bytes(b))
+        except ValueError:
+            continue
+        assert len(out) == len(raw)  # a flipped literal byte survives decoding
+    with pytest.raises(ValueError):
+        oracle.zrle_unwrap(bytes(w[:40]))
+
+
+def test_lossless_compress_roundtrip(oracle):
+    """The wrapped blob decompresses to the same floats.  A field with a flat
+    region (long runs of the zero residual, each still one Huffman bit) shrinks;
+    a field without zero runs comes back unchanged."""
+    x = synth.single_2d(256, seed=1).copy()
+    x[:, :128] = x.min()
+    for psnr in (30.0, 40.0, 60.0):
+        b0, s0 = oracle.compress(x, psnr)
+        b1, s1 = oracle.compress(x, psnr, lossless=1)
+        assert b1[:4] == b"FPZ1" and len(b1) < len(b0) and s1["bytes"] == len(b1)
+        assert np.array_equal(oracle.decompress(b1, x.shape).view(np.uint32),
+                              oracle.decompress(b0, x.shape).view(np.uint32))
+        assert oracle.zrle_unwrap(b1) == b0
+    y = synth.single_2d(256, seed=1)
+    c0, _ = oracle.compress(y, 40.0)
+    c1, _ = oracle.compress(y, 40.0, lossless=1)
+    assert c1 == c0
+
+
 def test_constant_and_empty_fields(oracle):
     x = np.full((17, 9), 3.25, np.float32)
     blob, st = oracle.compress(x, 80.0)
