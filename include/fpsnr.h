@@ -85,6 +85,22 @@ typedef struct {
                          16 fine bins (targets below about 59 dB), else eb8.
                          Costs one more pass over the input.  The blob records
                          the eb used; decompression is unchanged. */
+    int lossless;     /* 0: none (0).  1: optional lossless layer (the paper's
+                         optional lossless step, Sec. II-A): the finished blob
+                         is wrapped in the container below when that is
+                         smaller, else left as it is.  A plan with lossless 1
+                         decompresses both forms; a plan with 0 only plain
+                         blobs.  Its workspace grows by about the largest blob.
+                         Container "FPZ1": u32 magic 0x315A5046, u32 version 1,
+                         u64 blob bytes, u32 segment bytes (1024), u32 segments
+                         S, 8 zero bytes; u32 offsets[S + 1] (start of every
+                         segment's data in the data section, bit 31 = stored
+                         raw; the last entry is the data length), zero-padded
+                         to 16 bytes; the data section, zero-padded to 16 bytes.
+                         A segment is coded byte by byte: a nonzero byte is
+                         copied, a run of k zero bytes becomes 0x00 and k - 1
+                         in LEB128; it is stored raw when the code is not
+                         shorter. */
 } fpsnr_opts;
 
 /* Per-call statistics, written by fpsnr_compress to device memory. */
@@ -373,7 +389,7 @@ const uint16_t* fpsnr_plan_codes(fpsnr_plan_t plan);
  * entries, either may be NULL), and resets the counters.  Recording adds one
  * event pair per launch; it does not change what the kernels compute.
  * Returns FPSNR_OK, FPSNR_EINVAL or FPSNR_ECUDA. */
-#define FPSNR_NSTAGES 16
+#define FPSNR_NSTAGES 18
 int fpsnr_plan_profile(fpsnr_plan_t plan, int enable);
 int fpsnr_plan_profile_read(fpsnr_plan_t plan, double* ms, uint64_t* launches, int nstages);
 const char* fpsnr_stage_name(int stage);

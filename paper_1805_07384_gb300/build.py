@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfpsnr.so")
 SOURCES = ["api.cu", "compress.cu", "huffman.cu", "decompress.cu", "psnr.cu", "psnr_static.cu",
-           "tune.cu", "serve.cu"]
+           "tune.cu", "serve.cu", "lossless.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

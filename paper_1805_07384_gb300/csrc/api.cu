@@ -62,6 +62,8 @@ void carve(fpsnr_plan_s* p, uint8_t* base, size_t* total) {
     w.enc_tiles = c.take<uint32_t>(std::max<uint64_t>(p->enc_tiles, 1));
     w.bsum = c.take<uint32_t>(p->band.on ? (uint64_t)p->band_cap * p->band.nx : 1);
     w.fine_hist = c.take<uint32_t>(fp::kFineBins);
+    w.zr_scratch = c.take<uint8_t>(p->lossless ? p->zr_scratch_cap : 16);
+    w.zr_seg = c.take<uint32_t>(p->lossless ? p->zr_seg_cap : 1);
     *total = (c.off + 255) & ~(size_t)255;
 }
 
@@ -201,7 +203,7 @@ extern "C" {
 static const char* kStageNames[FPSNR_NSTAGES] = {
     "range_plan", "predict_quantize", "rank_popc", "codebook", "band_sum", "band_carry",
     "encode", "emit", "finalize", "decode_setup", "decode", "eb_refine", "scan_x", "scan_y",
-    "scan_final_dequant", "patch"};
+    "scan_final_dequant", "patch", "lossless_wrap", "lossless_unwrap"};
 
 const char* fpsnr_stage_name(int stage) {
     return (stage >= 0 && stage < FPSNR_NSTAGES) ? kStageNames[stage] : "unknown";
@@ -243,6 +245,7 @@ int fpsnr_default_opts(fpsnr_opts* o) {
     o->lmax = 27;
     o->lorenzo_dims = 0;
     o->psnr_mode = 0;
+    o->lossless = 0;
     return FPSNR_OK;
 }
 
@@ -275,6 +278,7 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
     if (o.chunk < 32 || o.chunk > 65536 || (o.chunk % 32) != 0) return FPSNR_EINVAL;
     if (o.lmax < 1 || o.lmax > fp::kMaxLmax || (1ull << o.lmax) < 2ull * o.radius) return FPSNR_EINVAL;
     if (o.psnr_mode != 0 && o.psnr_mode != 1) return FPSNR_EINVAL;
+    if (o.lossless != 0 && o.lossless != 1) return FPSNR_EINVAL;
     uint64_t d[3] = {1, 1, 1};
     uint64_t n = 1;
     for (int i = 0; i < ndim; i++) {
@@ -293,6 +297,7 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
     p->eb_rel = eb_rel_of(target_psnr_db);
     p->mse_rel = pow(10.0, -target_psnr_db / 10.0);
     p->psnr_mode = o.psnr_mode;
+    p->lossless = o.lossless;
     p->radius = o.radius;
     p->chunk = o.chunk;
     p->lmax = o.lmax;
@@ -356,6 +361,10 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
         p->lb_width = std::max<uint64_t>(p->lb_width, (uint64_t)p->pass[i].tb);
     }
 
+    if (p->lossless) {
+        p->zr_scratch_cap = (fpsnr_max_compressed_bytes(p) + 15) & ~(uint64_t)15;
+        p->zr_seg_cap = cdiv(p->zr_scratch_cap, fp::kZrSeg) + 1;
+    }
     size_t bytes = 0;
     carve(p, nullptr, &bytes);
     void* slab = nullptr;

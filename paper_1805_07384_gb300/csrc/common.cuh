@@ -24,6 +24,8 @@ constexpr int kMaxRadius = 32768;
 constexpr int kMaxSym = 2 * kMaxRadius;
 constexpr int kMaxLmax = 27;
 constexpr int kFineBins = 4096;  // fine histogram of the bound refinement (psnr_mode 1)
+constexpr uint32_t kZrSeg = 1024;          // lossless container: bytes per segment
+constexpr uint32_t kZrMagic = 0x315A5046u;  // bytes "FPZ1"
 constexpr int kLutBits = 12;  // decode look-up table width (first level)
 constexpr int kL2Sub = 6;     // second level: up to this many bits past the first level
 constexpr int kL2Cap = 4096;  // second-level entries (shared memory of the decoder)
@@ -46,6 +48,9 @@ struct DevParams {
     // replays correctly)
     uint32_t dec_epoch;
     float kinv;               // (float)(kFineBins / vr): fine-histogram bin scale
+    // lossless container: wrap decision and sizes; unwrap verdict and raw length
+    uint32_t zr_use, zr_bad;
+    uint64_t zr_total, zr_dstart, zr_raw;
     uint64_t cap;             // output capacity of this call
     uint64_t off_cb, off_ct, off_st, off_ou, off_vb, total;
     // decompression: header fields of the blob being decoded
@@ -84,6 +89,8 @@ struct Workspace {
     uint32_t* enc_tiles; // [enc_tiles] words per encoder tile, then their exclusive prefix
     uint32_t* bsum;      // [nbands * nx] 2D band column sums (band geometry only)
     uint32_t* fine_hist; // [kFineBins] bound refinement histogram (kept zero between calls)
+    uint8_t* zr_scratch; // lossless plans: container (compress) / expanded blob (decompress)
+    uint32_t* zr_seg;    // lossless plans: per-segment lengths, then offsets
 };
 
 // Launch geometry of the predict-quantize kernel.
@@ -125,7 +132,8 @@ struct ScanPass {
 namespace fp {
 enum Stage {
     kStRange = 0, kStPq, kStRank, kStCodebook, kStBandSum, kStBandCarry, kStEncode, kStEmit,
-    kStFinalize, kStDsetup, kStDecode, kStRefine, kStScanX, kStScanY, kStScanFinal, kStPatch
+    kStFinalize, kStDsetup, kStDecode, kStRefine, kStScanX, kStScanY, kStScanFinal, kStPatch,
+    kStZrWrap, kStZrUnwrap
 };
 
 // Host-side launch counters and optional per-launch CUDA events.
@@ -152,6 +160,8 @@ struct fpsnr_plan_s {
     double target_psnr, eb_rel;
     int radius, chunk, lmax;
     int psnr_mode;    // 0: eb from Eq. 8; 1: refined from the fine histogram
+    int lossless;     // 1: wrap blobs in the zero-run container when smaller
+    uint64_t zr_scratch_cap, zr_seg_cap;
     double mse_rel;   // 10^(-target / 10) (the target MSE over vr^2)
     uint32_t nsym;
     uint64_t nchunks, nwords, nbmblk;
@@ -247,6 +257,11 @@ constexpr size_t kPsnrResultOffset = 16;
 constexpr size_t kPsnrResultBytes = 24;
 int codebook_prepare();
 int decode_prepare(const fpsnr_plan_s* p);
+// lossless container (lossless.cu)
+int launch_zr_wrap(fpsnr_plan_s* const* plans, void* const* d_out, uint64_t* d_out_bytes,
+                   fpsnr_stats* d_stats, int count, cudaStream_t st);
+int launch_zr_unwrap(fpsnr_plan_s* const* plans, const void* const* d_blob, const uint64_t* bytes,
+                     int count, cudaStream_t st);
 
 // ---- device helpers ----
 #ifdef __CUDACC__

@@ -1252,7 +1252,8 @@ int launch_compress_batch(fpsnr_plan_s* const* P, const float* const* d_in, void
         k_finalize<<<tot, 256, 0, st>>>(b);
         FP_LAUNCH_CHECK();
     }
-    return FPSNR_OK;
+    // optional lossless container around the finished blobs
+    return launch_zr_wrap(P, d_out, d_out_bytes, d_stats, count, st);
 }
 
 }  // namespace fp

@@ -43,6 +43,7 @@ struct DsetupArgs {
     DevParams* par;
     const uint8_t* blob;
     uint64_t bytes;
+    bool zr;  // the blob is the plan's unwrapped copy: its length and verdict are on the device
     int ndim, ld;
     uint64_t d0, d1, d2, n;
     uint32_t chunk;
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(1024) k_dsetup(const __grid_constant__ Batch<D
     const DsetupArgs& A = B.a[blockIdx.x];
     DevParams* par = A.par;
     const uint8_t* __restrict__ blob = A.blob;
-    const uint64_t bytes = A.bytes;
+    const uint64_t bytes = A.zr ? par->zr_raw : A.bytes;
     const int ndim = A.ndim, ld = A.ld;
     const uint64_t d0 = A.d0, d1 = A.d1, d2 = A.d2, n = A.n;
     const uint32_t chunk = A.chunk;
@@ -77,7 +78,10 @@ __global__ void __launch_bounds__(1024) k_dsetup(const __grid_constant__ Batch<D
     if (tid == 0) {
         const uint32_t e = (par->dec_epoch + 1) & 0x3fffffffu;
         par->dec_epoch = e ? e : 1u;
-        int ok = bytes >= kHeaderBytes;
+        // a container that failed to expand is corrupt whatever the copy holds
+        const bool zr_bad = A.zr && par->zr_bad != 0u;
+        if (A.zr) par->zr_bad = 0u;
+        int ok = bytes >= kHeaderBytes && !zr_bad;
         uint32_t flags = 0, radius = 0, ch = 0, lmax = 0, nsym = 0, nck = 0, words = 0, no = 0, nv = 0;
         if (ok) {
             ok = rd32(blob, 0) == kMagic && rd32(blob, 4) == kVersion &&
@@ -1049,6 +1053,12 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
     }
     fp::Profiler& prof = P[0]->prof;  // batched launches are attributed to the first plan
     uint32_t blocks[kMaxBatch];
+    // lossless plans: expand the container (or copy the plain blob) into the
+    // plan's scratch; every later kernel reads that copy
+    if (launch_zr_unwrap(P, d_blob, bytes, count, st) != FPSNR_OK) return FPSNR_ECUDA;
+    const void* blob_of[kMaxBatch];
+    for (int f = 0; f < count; f++) blob_of[f] = P[f]->lossless ? (const void*)P[f]->w.zr_scratch : d_blob[f];
+    d_blob = blob_of;
     {
         Batch<DsetupArgs> b;
         b.count = (uint32_t)count;
@@ -1056,8 +1066,9 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
             const fpsnr_plan_s* p = P[f];
             const Workspace& w = p->w;
             b.a[f] = DsetupArgs{w.par, reinterpret_cast<const uint8_t*>(d_blob[f]), bytes[f],
-                                p->ndim, p->ld, p->dims[0], p->dims[1], p->dims[2], p->n,
-                                (uint32_t)p->chunk, p->nchunks, w.dlut, w.dsyms, w.lb_ctr};
+                                p->lossless != 0, p->ndim, p->ld, p->dims[0], p->dims[1],
+                                p->dims[2], p->n, (uint32_t)p->chunk, p->nchunks, w.dlut,
+                                w.dsyms, w.lb_ctr};
             b.off[f] = (uint32_t)f;
         }
         b.off[count] = (uint32_t)count;

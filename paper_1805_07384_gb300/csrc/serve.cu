@@ -72,9 +72,9 @@ struct Slot {
 
 std::string key_of(const fpsnr_request& r) {
     char b[160];
-    snprintf(b, sizeof(b), "%d|%llu,%llu,%llu|%d,%d,%d,%d,%d", r.ndim, (unsigned long long)r.dims[0],
+    snprintf(b, sizeof(b), "%d|%llu,%llu,%llu|%d,%d,%d,%d,%d,%d", r.ndim, (unsigned long long)r.dims[0],
              (unsigned long long)r.dims[1], (unsigned long long)r.dims[2], r.opts.radius,
-             r.opts.chunk, r.opts.lmax, r.opts.lorenzo_dims, r.opts.psnr_mode);
+             r.opts.chunk, r.opts.lmax, r.opts.lorenzo_dims, r.opts.psnr_mode, r.opts.lossless);
     return b;
 }
 

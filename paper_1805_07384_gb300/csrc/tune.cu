@@ -106,9 +106,9 @@ extern "C" int fpsnr_autotune(int ndim, const uint64_t* dims, double target_psnr
         n *= d[i];
     }
     char key[256];
-    snprintf(key, sizeof(key), "%d|%d|%llu,%llu,%llu|%.17g|%d,%d,%d,%d,%d|%.17g", dev, ndim,
+    snprintf(key, sizeof(key), "%d|%d|%llu,%llu,%llu|%.17g|%d,%d,%d,%d,%d,%d|%.17g", dev, ndim,
              (unsigned long long)d[0], (unsigned long long)d[1], (unsigned long long)d[2],
-             target_psnr_db, o.radius, o.chunk, o.lmax, o.lorenzo_dims, o.psnr_mode,
+             target_psnr_db, o.radius, o.chunk, o.lmax, o.lorenzo_dims, o.psnr_mode, o.lossless,
              max_size_increase);
     {
         std::lock_guard<std::mutex> lk(g_mu);

@@ -43,7 +43,7 @@ FPSNR_EAGAIN = -8
 FPSNR_REQ_COMPRESS = 0
 FPSNR_REQ_DECOMPRESS = 1
 FPSNR_PSNR_STATIC_MAX_POINTS = 1 << 28
-FPSNR_NSTAGES = 16
+FPSNR_NSTAGES = 18
 
 _lock = threading.Lock()
 _lib = None
@@ -58,7 +58,7 @@ class FpsnrError(RuntimeError):
 
 class fpsnr_opts(C.Structure):
     _fields_ = [("radius", C.c_int), ("chunk", C.c_int), ("lmax", C.c_int),
-                ("lorenzo_dims", C.c_int), ("psnr_mode", C.c_int)]
+                ("lorenzo_dims", C.c_int), ("psnr_mode", C.c_int), ("lossless", C.c_int)]
 
 
 class fpsnr_stats(C.Structure):
@@ -345,13 +345,13 @@ class Plan:
     """Owns one C plan for fields of one shape (numpy/torch C-order shape)."""
 
     def __init__(self, shape, target_psnr_db: float, radius: int = 32768, chunk: int = 256,
-                 lmax: int = 27, lorenzo_dims: int = 0, psnr_mode: int = 0):
+                 lmax: int = 27, lorenzo_dims: int = 0, psnr_mode: int = 0, lossless: int = 0):
         import torch
         self.shape = tuple(int(s) for s in shape)
         self.n = int(math.prod(self.shape))
         o = fpsnr_default_opts()
         o.radius, o.chunk, o.lmax, o.lorenzo_dims = radius, chunk, lmax, lorenzo_dims
-        o.psnr_mode = psnr_mode
+        o.psnr_mode, o.lossless = psnr_mode, lossless
         self.opts = o
         self.handle = fpsnr_plan(len(self.shape), list(reversed(self.shape)), target_psnr_db, o)
         self.target = float(target_psnr_db)

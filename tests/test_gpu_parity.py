@@ -332,3 +332,76 @@ def test_cosmology_like_reduced(env):
     fields, kinds = synth.cosmology_fields(n=48)
     for i, x in enumerate(fields):
         check_case(env, x, (40.0, 60.0, 80.0)[i % 3])
+
+
+# ---------------------------------------------------------------------------
+# optional lossless container
+# ---------------------------------------------------------------------------
+
+def _flat_field(shape, seed):
+    x = field_for(shape, seed).copy()
+    x[:, : shape[1] // 2] = x.min()  # a flat region: long runs of the zero residual
+    return x
+
+
+@pytest.mark.parametrize("case", [((300, 700), 30.0), ((300, 700), 40.0), ((257, 511), 60.0),
+                                  ((300, 700), 100.0), ((12, 20, 36), 40.0)])
+def test_parity_lossless(env, case):
+    torch, fpsnr, oracle = env
+    shape, psnr = case
+    x = synth.smooth_3d(shape, 4) if len(shape) == 3 else _flat_field(shape, 17)
+    ob, ost = oracle.compress(x, psnr, lossless=1)
+    plain, _ = oracle.compress(x, psnr)
+    plan = fpsnr.Plan(shape, psnr, lossless=1)
+    xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    out, nb, st = plan.compress(xt)
+    torch.cuda.synchronize()
+    n = int(nb.item())
+    s = fpsnr.parse_stats(st)
+    assert s["status"] == 0 and s["bytes"] == n == len(ob)
+    assert out[:n].cpu().numpy().tobytes() == ob
+    oxr = oracle.decompress(ob, x.shape)
+    xr, status = plan.decompress(out, n)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert np.array_equal(xr.cpu().numpy().view(np.uint32), oxr.view(np.uint32))
+    # a lossless plan also reads plain blobs; a plain plan refuses containers
+    pb = torch.from_numpy(np.frombuffer(plain, np.uint8).copy()).cuda()
+    xr2, status = plan.decompress(pb, len(plain))
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0 and torch.equal(xr2, xr)
+    if ob[:4] == b"FPZ1":
+        assert len(ob) < len(plain)
+        xr3, status = fpsnr.Plan(shape, psnr).decompress(out, n)
+        torch.cuda.synchronize()
+        assert int(status.item()) == fpsnr.FPSNR_ECORRUPT
+        # damaged containers are caught, never a fault
+        for off in (4, 16, 20, 33, 40):
+            b = out[:n].clone()
+            b[off] ^= 0x5A
+            _, status = plan.decompress(b, n)
+            torch.cuda.synchronize()
+            assert int(status.item()) == fpsnr.FPSNR_ECORRUPT, off
+        _, status = plan.decompress(out, n)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+    else:
+        assert ob == plain
+
+
+def test_lossless_batch_mixed(env):
+    torch, fpsnr, oracle = env
+    fields = [_flat_field((200, 400), 21), field_for((200, 400), 22), _flat_field((150, 300), 23)]
+    flags = [1, 0, 1]
+    plans = [fpsnr.Plan(x.shape, 40.0, lossless=f) for x, f in zip(fields, flags)]
+    xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in fields]
+    outs, nb, st = fpsnr.compress_batch(plans, xs)
+    recs, status = fpsnr.decompress_batch(plans, outs)
+    torch.cuda.synchronize()
+    for i, (x, f) in enumerate(zip(fields, flags)):
+        ob, _ = oracle.compress(x, 40.0, lossless=f)
+        n = int(nb[i].item())
+        assert outs[i][:n].cpu().numpy().tobytes() == ob, i
+        assert int(status[i].item()) == 0
+        assert np.array_equal(recs[i].cpu().numpy().view(np.uint32),
+                              oracle.decompress(ob, x.shape).view(np.uint32)), i
