@@ -1,0 +1,76 @@
+"""The 3D workloads at their full sizes, through the batched calls the
+benchmark uses.
+
+Hurricane-like fields (100 x 500 x 500, 25 M points): three of them (the
+vortex field and two spiked ones) in one batch, bytes and floats checked
+against the oracle.  NYX-like fields (512^3, 134 M points): two of them in one
+batch; every point satisfies |x - x'| <= eb and the reported PSNR equals the
+standalone reduction's; the velocity field is also checked byte for byte
+against the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1805_07384_gb300 import synth
+from test_gpu_parity import env  # noqa: F401  (fixture)
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(env, fields, psnrs):
+    torch, fpsnr, _ = env
+    plans = [fpsnr.Plan(tuple(x.shape), p) for x, p in zip(fields, psnrs)]
+    xs = [x if hasattr(x, "is_cuda") else torch.from_numpy(np.ascontiguousarray(x)).cuda()
+          for x in fields]
+    outs, nb, st = fpsnr.compress_batch(plans, xs)
+    recs, status = fpsnr.decompress_batch(plans, outs)
+    torch.cuda.synchronize()
+    stats = [fpsnr.parse_stats(st[i]) for i in range(len(fields))]
+    assert all(s["status"] == 0 for s in stats)
+    assert all(int(status[i].item()) == 0 for i in range(len(fields)))
+    return plans, xs, outs, nb, stats, recs
+
+
+def _properties(env, x, xr, st):
+    torch, fpsnr, _ = env
+    err = (x.double() - xr.double()).abs().max().item()
+    assert err <= st["eb_abs"]
+    p, _, vr = fpsnr.psnr(x, xr)
+    assert vr == st["vr"]
+    assert (math.isinf(p) and math.isinf(st["psnr_actual"])) or abs(p - st["psnr_actual"]) < 1e-9
+
+
+def test_hurricane_full_size(env):
+    torch, fpsnr, oracle = env
+    fields, meta = synth.hurricane_batch(count=3)
+    assert fields[0].shape == (100, 500, 500) and meta[0]["vortex"] and meta[1]["spikes"] > 0
+    psnrs = [m["psnr"] for m in meta]
+    plans, xs, outs, nb, stats, recs = _batch(env, fields, psnrs)
+    for i, x in enumerate(fields):
+        ob, ost = oracle.compress(x, psnrs[i])
+        n = int(nb[i].item())
+        assert n == len(ob) and outs[i][:n].cpu().numpy().tobytes() == ob, i
+        oxr = oracle.decompress(ob, x.shape)
+        assert np.array_equal(recs[i].cpu().numpy().view(np.uint32), oxr.view(np.uint32)), i
+        assert stats[i]["n_outlier"] == ost["n_outlier"] and stats[i]["n_verbatim"] == ost["n_verbatim"]
+        _properties(env, xs[i], recs[i], stats[i])
+
+
+def test_cosmology_full_size(env):
+    torch, fpsnr, oracle = env
+    fields, kinds = synth.cosmology_fields(512, device=torch.device("cuda"))
+    pick = [kinds.index("density"), kinds.index("velocity")]
+    xs = [fields[i] for i in pick]
+    del fields
+    psnrs = [40.0, 80.0]
+    plans, xs, outs, nb, stats, recs = _batch(env, xs, psnrs)
+    for i in range(2):
+        _properties(env, xs[i], recs[i], stats[i])
+    # the velocity field byte for byte against the oracle
+    xv = xs[1].cpu().numpy()
+    ob, ost = oracle.compress(xv, psnrs[1])
+    n = int(nb[1].item())
+    assert n == len(ob) and outs[1][:n].cpu().numpy().tobytes() == ob
+    assert stats[1]["sse"] == pytest.approx(ost["sse"], rel=1e-12, abs=0)
