@@ -68,6 +68,12 @@ def parse():
     ap.add_argument("--cpu-workers", type=int, default=0, help="0 = all host cores")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every call eagerly instead of replaying one CUDA graph per step")
+    ap.add_argument("--write-traffic", metavar="CSV",
+                    help="read an ncu --csv log of dram__bytes_{read,write}.sum and write "
+                         "profiles/traffic.json (no GPU work)")
+    ap.add_argument("--launch-table", metavar="CSV",
+                    help="print the per-kernel launch table of an ncu --csv log of "
+                         "gpu__time_duration.sum (no GPU work)")
     return ap.parse_args()
 
 
@@ -319,6 +325,94 @@ def measured_traffic(stage):
     return e["dram_bytes_per_launch"]
 
 
+# ncu --csv logs -> per-launch figures (profiles/ summaries and traffic.json)
+_UNITS = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9,
+          "ns": 1e-3, "nsecond": 1e-3, "us": 1, "usecond": 1, "ms": 1e3, "msecond": 1e3}
+# benchmark stages by kernel-name prefix, with the source file that holds them
+_STAGE_KERNELS = [("range_plan", ("k_range_plan",), "compress.cu"),
+                  ("predict_quantize", ("k_pq",), "compress.cu"),
+                  ("encode", ("k_enc_bits", "k_enc_scan", "k_enc_pack"), "compress.cu"),
+                  ("decode", ("k_decode",), "decompress.cu"),
+                  ("band_sum", ("k_band_sum",), "decompress.cu"),
+                  ("scan_final_dequant", ("k_band_scan",), "decompress.cu")]
+
+
+def _ncu_rows(path):
+    """(launch id, short kernel name, metric, value in bytes or microseconds)."""
+    import csv
+    lines = open(path).read().splitlines()
+    start = next(i for i, l in enumerate(lines) if l.startswith('"ID"'))
+    out = []
+    for r in csv.DictReader(lines[start:]):
+        name = r["Kernel Name"]
+        short = name.split("(")[0].replace("void ", "").strip()
+        if short.startswith("fp::"):
+            short = short[4:]
+        elif not short.startswith("k_"):
+            continue  # not one of the library's kernels (input generation, torch)
+        v = float(r["Metric Value"].replace(",", "")) * _UNITS.get(r["Metric Unit"], 1)
+        out.append((int(r["ID"]), short, r["Metric Name"], v))
+    return out
+
+
+def launch_table(path):
+    """Markdown table: launches, total device time and share per kernel."""
+    per = {}
+    for lid, k, m, v in _ncu_rows(path):
+        if m == "gpu__time_duration.sum":
+            n, t = per.get(k, (0, 0.0))
+            per[k] = (n + 1, t + v)
+    tot = sum(t for _, t in per.values()) or 1.0
+    rows = ["| kernel | launches | total us | share |", "|---|---:|---:|---:|"]
+    for k, (n, t) in sorted(per.items(), key=lambda kv: -kv[1][1]):
+        rows.append(f"| `{k}` | {n} | {t:.1f} | {100 * t / tot:.1f}% |")
+    return "\n".join(rows)
+
+
+def write_traffic(path):
+    """profiles/traffic.json: DRAM bytes per launch of every stage, with the
+    SHA-1 of the source file the counters were taken from."""
+    import hashlib
+    launches = {}
+    for lid, k, m, v in _ncu_rows(path):
+        if m in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            launches.setdefault((lid, k), {})[m] = v
+    out = {"_about": "DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each "
+                     "benchmark stage (one launch = one sub-batch of the benchmark's batch), averaged "
+                     "over the launches of the capture; bench.py reports it as roofline.traffic only "
+                     "while the kernel's source file still has the recorded SHA-1.",
+           "_command": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                       "--clock-control none -k regex:\"k_pq|k_decode|k_band_scan|k_band_sum|k_enc_bits|"
+                       "k_enc_pack|k_enc_scan|k_range_plan\" --csv --log-file traffic.csv python bench.py "
+                       "--steps 2 --warmup 3 --no-cpu-baseline --no-e2e --no-roofline; "
+                       "python bench.py --write-traffic traffic.csv"}
+    for stage, prefixes, src in _STAGE_KERNELS:
+        rd = wr = 0.0
+        kernels = set()
+        first = [0]
+        for (lid, k), mv in launches.items():
+            if k.startswith(prefixes):
+                rd += mv.get("dram__bytes_read.sum", 0.0)
+                wr += mv.get("dram__bytes_write.sum", 0.0)
+                kernels.add(k)
+                if k.startswith(prefixes[0]):
+                    first[0] += 1
+        if not first[0]:
+            continue
+        n = first[0]
+        rel = os.path.join("paper_1805_07384_gb300", "csrc", src)
+        out[stage] = {"kernels": sorted(kernels), "launches": n,
+                      "dram_bytes_per_launch": int(round((rd + wr) / n)),
+                      "dram_read": int(round(rd / n)), "dram_write": int(round(wr / n)),
+                      "source": rel,
+                      "source_sha1": hashlib.sha1(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()}
+    dst = os.path.join(ROOT, "profiles", "traffic.json")
+    with open(dst, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(dst)
+
+
 # algorithmic bytes per launch of each stage (N points, B compressed bytes of one field)
 def stage_bytes(stage, N, B):
     # 2D fields: decode writes 16-bit symbols; the band pass reads them and the
@@ -500,6 +594,12 @@ def run_serve(a):
 
 def main():
     a = parse()
+    if a.write_traffic:
+        write_traffic(a.write_traffic)
+        return
+    if a.launch_table:
+        print(launch_table(a.launch_table))
+        return
     if a.impl == "reference":
         run_reference(a)
         return

@@ -229,7 +229,7 @@ int fpsnr_psnr_static(const float* d_x, const float* d_xr, uint64_t n, double* h
  * stream; the tile shapes change only how the work is split over blocks, never
  * the bytes.
  *   chunk        symbols per chunk (0: keep the plan's)
- *   pq_tile_x    2D predictor tile width: 128, 256 or 512 points (0: by row length)
+ *   pq_tile_x    2D predictor tile width: 128, 256, 512 or 1024 points (0: by row length)
  *   band_rows    2D decompression band height: 16, 32 or 64 rows (0: 32); only
  *                for 2D fields with rows of at most 8192 points
  *   dec_threads  decoder block size: 128 or 512 (0: chosen per launch)

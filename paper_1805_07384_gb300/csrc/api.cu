@@ -75,13 +75,13 @@ bool pq_geometry(fpsnr_plan_s* p, int tx) {
     const uint64_t n = p->n;
     PQGeom& g = p->pq;
     if (p->ld == 1) {
-        g.mode = 1; g.tx = 512; g.ty = 1; g.zs = 16;
-        g.vx = 512; g.vy = 1; g.vz = (uint32_t)std::max<uint64_t>(cdiv(n, 512), 1);
+        g.mode = 1; g.tx = 1024; g.ty = 1; g.zs = 16;
+        g.vx = 1024; g.vy = 1; g.vz = (uint32_t)std::max<uint64_t>(cdiv(n, 1024), 1);
     } else if (p->ld == 2) {
         const uint64_t nx = d[0], rows = nx ? n / nx : 0;
         g.mode = 2; g.ty = 1;
-        g.tx = tx ? tx : (nx <= 128 ? 128 : (nx <= 256 ? 256 : 512));
-        g.zs = std::max(4, 8192 / g.tx);
+        g.tx = tx ? tx : (nx <= 128 ? 128 : (nx <= 256 ? 256 : (nx <= 512 ? 512 : 1024)));
+        g.zs = std::max(32, 16384 / g.tx);
         g.vx = (uint32_t)nx; g.vy = 1; g.vz = (uint32_t)rows;
     } else {
         g.mode = 3; g.tx = 128; g.ty = 8; g.zs = 16;
@@ -317,7 +317,7 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
     p->pq_blocks_cap = p->pq.nblocks;
     if (ld == 2 && n > 0) {
         const int tx0 = p->pq.tx;
-        for (int tx : {128, 256, 512}) {
+        for (int tx : {128, 256, 512, 1024}) {
             if (!pq_geometry(p, tx)) { delete p; return FPSNR_EINVAL; }
             p->pq_blocks_cap = std::max(p->pq_blocks_cap, p->pq.nblocks);
         }
@@ -470,7 +470,7 @@ int fpsnr_plan_set_tuning(fpsnr_plan_t p, const fpsnr_tuning* t) {
     if (!p || !t) return FPSNR_EINVAL;
     if (t->chunk != 0 && t->chunk != p->chunk) return FPSNR_EINVAL;
     const int tx = t->pq_tile_x, tr = t->band_rows, dt = t->dec_threads;
-    if (tx != 0 && (tx != 128 && tx != 256 && tx != 512)) return FPSNR_EINVAL;
+    if (tx != 0 && (tx != 128 && tx != 256 && tx != 512 && tx != 1024)) return FPSNR_EINVAL;
     if (tx != 0 && p->ld != 2) return FPSNR_EINVAL;
     if (tr != 0 && (tr != 16 && tr != 32 && tr != 64)) return FPSNR_EINVAL;
     if (tr != 0 && !p->band.on) return FPSNR_EINVAL;

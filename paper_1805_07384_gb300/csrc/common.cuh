@@ -339,6 +339,45 @@ __device__ __forceinline__ void ff_add_sq_diff(FF& acc, float a, float b) {
 
 __device__ __forceinline__ double ff_to_double(const FF& a) { return (double)a.hi + (double)a.lo; }
 
+// Two independent float-float accumulators in the packed f32x2 lanes.  The
+// subtractions are fma(x, -1, y): the product is exact, so each is the single
+// rounding of y - x, as a subtraction would be.
+struct FF2 {
+    float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 f2_sub(float2 y, float2 x) {
+    return __ffma2_rn(x, make_float2(-1.0f, -1.0f), y);
+}
+
+// acc += (a - b)^2 in each lane, given nb = -b and dh = fl(a + nb); a lane
+// whose keep flag is false adds exactly zero (whatever a and b hold).
+__device__ __forceinline__ void ff2_add_sq_diff(FF2& acc, float2 a, float2 nb, float2 dh, bool keep0,
+                                                bool keep1) {
+    // exact a - b = dh + dl (TwoSum)
+    const float2 bb = f2_sub(dh, a);
+    const float2 dl = __fadd2_rn(f2_sub(a, f2_sub(dh, bb)), f2_sub(nb, bb));
+    // d^2 = p + e with np = -p (FMA TwoProd, plus the 2 dh dl cross term)
+    const float2 ndh = __fmul2_rn(dh, make_float2(-1.0f, -1.0f));
+    float2 np = __fmul2_rn(dh, ndh);
+    float2 e = __ffma2_rn(dh, dh, np);
+    e = __ffma2_rn(__fadd2_rn(dh, dh), dl, e);
+    np.x = keep0 ? np.x : 0.0f;
+    np.y = keep1 ? np.y : 0.0f;
+    e.x = keep0 ? e.x : 0.0f;
+    e.y = keep1 ? e.y : 0.0f;
+    // acc.hi + p = t + err (TwoSum; p - tb is formed as -(np + tb))
+    const float2 t = f2_sub(acc.hi, np);
+    const float2 tb = f2_sub(t, acc.hi);
+    const float2 err = f2_sub(f2_sub(acc.hi, f2_sub(t, tb)), __fadd2_rn(np, tb));
+    acc.hi = t;
+    acc.lo = __fadd2_rn(acc.lo, __fadd2_rn(err, e));
+}
+
+__device__ __forceinline__ double ff2_to_double(const FF2& a) {
+    return ((double)a.hi.x + (double)a.lo.x) + ((double)a.hi.y + (double)a.lo.y);
+}
+
 // Deterministic block reduction of one double per thread (fixed tree order).
 // `sh` needs blockDim.x/32 doubles.  Result valid in thread 0.
 __device__ __forceinline__ double block_sum_double(double v, double* sh) {

@@ -17,6 +17,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -352,9 +353,20 @@ __device__ __forceinline__ int32_t prequant(float x, float xmin, float inv, bool
 //         row start is the previous row's last point, no upper-row term.
 // MODE 2: 2D predictor on (vz rows) x vx, TY must be 1 (vy == 1).
 // MODE 3: 3D predictor on vz x vy x vx with TY rows per tile.
-template <int MODE, int TX, int TY, bool VEC>
-__global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batch<PQArgs> B) {
-    constexpr int NT = TX / 4 * TY;
+// A warp covers SEG consecutive segments of 128 columns of a tile row, 4
+// points per lane in each, so a thread handles 4 * SEG points of every row.
+// Register budget: the two-segment kernel keeps all of its state (124
+// registers, 4 blocks per SM: capping it spills inside the row loop); the
+// one-segment kernels are held to 7 blocks of 128 threads per SM (2D) or
+// 4 blocks of 256 (3D).
+template <int MODE, int TX, int TY, bool VEC, int SEG>
+__global__ void __launch_bounds__(TX / (4 * SEG) * TY,
+                                  SEG == 2 ? 1 : (MODE == 3 ? 1024 : 896) / (TX / (4 * SEG) * TY))
+    k_pq(const __grid_constant__ Batch<PQArgs> B) {
+    constexpr int TPR = TX / (4 * SEG);  // threads per tile row
+    constexpr int NT = TPR * TY;
+    constexpr int NP = 4 * SEG;          // points per thread per row
+    static_assert(TPR % 32 == 0, "whole warps per tile row");
     const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
     const PQArgs& a = B.a[fld];
     const float* __restrict__ x = a.x;
@@ -362,15 +374,19 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batc
     const uint32_t flags = par->flags;
     if (flags & (kFlagConstant | kFlagError)) return;
     const float xmin = par->xmin, inv = par->inv, s = par->s, thr = par->thr;
+    // -x' = fma(q, -s, -xmin) rounds to exactly the negated reconstruction
+    const float ns = -s, nxmin = -xmin;
     const bool off = (flags & kFlagLatticeOff) != 0;
     const int R = a.radius;
 
-    __shared__ uint32_t shist[kHistWin];
+    // histogram window, then one spill slot per lane for points counted elsewhere
+    __shared__ __align__(16) uint32_t shist[kHistWin + 32];
     __shared__ int32_t sL1[(MODE == 3) ? 2 : 1][(MODE == 3) ? TY + 1 : 1][(MODE == 3) ? TX : 1];
     __shared__ double ssum[NT / 32];
 
-    const uint32_t tid = threadIdx.y * (TX / 4) + threadIdx.x;
-    for (uint32_t i = tid; i < kHistWin; i += NT) shist[i] = 0u;
+    const uint32_t tid = threadIdx.y * TPR + threadIdx.x;
+    for (uint32_t i = tid; i < (kHistWin + 32) / 4; i += NT)
+        reinterpret_cast<uint4*>(shist)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
 
     const uint32_t b = blockIdx.x - B.off[fld];
@@ -379,19 +395,22 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batc
     const uint32_t bz = b / (a.nbx * a.nby);
     const uint32_t x0 = bx * TX, y0 = by * TY, z0 = bz * a.zs;
     const uint32_t z1 = min(z0 + a.zs, a.vz);
-    const uint32_t xb = x0 + 4u * threadIdx.x;
-    const uint32_t y = y0 + threadIdx.y;
     const uint32_t lane = tid & 31u;
+    // column of the thread's first point within the tile; segment j adds 128 j
+    const uint32_t cb = (threadIdx.x >> 5) * (128u * SEG) + 4u * lane;
+    const uint32_t xb = x0 + cb;
+    const uint32_t xw = xb - 4u * lane;  // the warp's first column
+    const uint32_t y = y0 + threadIdx.y;
     const uint32_t vx = a.vx;
     const bool yin = (MODE == 3) ? (y < a.vy) : true;
     // histogram window [wlo, wlo + kHistWin) around the zero residual; the
     // unsigned difference code - wlo wraps for codes below the window
     const uint32_t wlo = (uint32_t)(R - kHistWin / 2);
 
-    // A row of the tile: 4 points per thread and, for lane 0, the left
+    // A row of the tile: 4 * SEG points per thread and, for lane 0, the left
     // neighbour of its first point.  Rows are fetched one ahead of their use.
     struct Row {
-        float v[4];
+        float v[NP];
         float l;
         bool hl;
     };
@@ -400,12 +419,16 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batc
         return (MODE == 1) ? (uint32_t)min((uint64_t)vx, a.n - rowbase) : vx;
     };
     auto load_row = [&](const float* xrow, uint64_t rowbase, bool rowin, uint32_t lim, Row& r) {
-        if (VEC && rowin && xb + 3 < lim) {
-            const float4 v = __ldcs(reinterpret_cast<const float4*>(xrow + xb));
-            r.v[0] = v.x; r.v[1] = v.y; r.v[2] = v.z; r.v[3] = v.w;
-        } else {
 #pragma unroll
-            for (int k = 0; k < 4; k++) r.v[k] = (rowin && xb + k < lim) ? xrow[xb + k] : 0.0f;
+        for (int j = 0; j < SEG; j++) {
+            const uint32_t xj = xb + 128u * j;
+            if (VEC && rowin && xj + 3 < lim) {
+                const float4 v = __ldcs(reinterpret_cast<const float4*>(xrow + xj));
+                r.v[4 * j] = v.x; r.v[4 * j + 1] = v.y; r.v[4 * j + 2] = v.z; r.v[4 * j + 3] = v.w;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) r.v[4 * j + k] = (rowin && xj + k < lim) ? xrow[xj + k] : 0.0f;
+            }
         }
         r.l = 0.0f;
         r.hl = false;
@@ -431,138 +454,166 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batc
             load_row(x + hb, hb, true, vx, h);
         }
     };
-
-    int32_t L2prev[4] = {0, 0, 0, 0};
-    FF acc = {0.0f, 0.0f};
-    uint32_t glo = 0xffffffffu, ghi = 0u;  // nonzero symbols counted outside the window
-    int buf = 0;
-    const uint32_t zstart = (MODE != 1 && z0 > 0) ? z0 - 1 : z0;
-    Row nxt, hnxt;
-    hnxt.v[0] = hnxt.v[1] = hnxt.v[2] = hnxt.v[3] = hnxt.l = 0.0f;
-    hnxt.hl = false;
-    fetch(zstart, nxt, hnxt);
-    for (uint32_t z = zstart; z < z1; z++) {
-        const Row cur = nxt;
-        const Row hcur = hnxt;
-        if (z + 1 < z1) fetch(z + 1, nxt, hnxt);
-
-        // ---- own row: lattice q, row difference L1 ----
-        const uint64_t rowbase = ((uint64_t)z * a.vy + y) * vx;
-        const uint32_t lim = row_limit(rowbase);
-        bool in[4];
-        int32_t q[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            in[k] = yin && (xb + k < lim);
-            q[k] = in[k] ? prequant(cur.v[k], xmin, inv, off) : 0;
-        }
-        int32_t qleft = __shfl_up_sync(0xffffffffu, q[3], 1);
-        if (lane == 0) qleft = cur.hl ? prequant(cur.l, xmin, inv, off) : 0;
-        int32_t L1[4];
-        L1[0] = q[0] - qleft;
+    // row differences of 4 * SEG lattice values whose left neighbour (of the
+    // warp's first point) is ql0: segment j > 0 of lane 0 continues from lane
+    // 31's segment j - 1
+    auto row_diff = [&](const int32_t (&q)[NP], int32_t ql0, int32_t (&L1)[NP]) {
+        int32_t ql = __shfl_up_sync(0xffffffffu, q[3], 1);
+        if (lane == 0) ql = ql0;
+        L1[0] = q[0] - ql;
 #pragma unroll
         for (int k = 1; k < 4; k++) L1[k] = q[k] - q[k - 1];
+#pragma unroll
+        for (int j = 1; j < SEG; j++) {
+            const int32_t send = lane == 31u ? q[4 * j - 1] : q[4 * j + 3];
+            const int32_t qj = __shfl_sync(0xffffffffu, send, (lane + 31u) & 31u);
+            L1[4 * j] = q[4 * j] - qj;
+#pragma unroll
+            for (int k = 1; k < 4; k++) L1[4 * j + k] = q[4 * j + k] - q[4 * j + k - 1];
+        }
+    };
 
-        int32_t L2[4];
+    int32_t L2prev[NP];
+#pragma unroll
+    for (int i = 0; i < NP; i++) L2prev[i] = 0;
+    FF2 acc = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+    uint32_t glo = 0xffffffffu, ghi = 0u;  // nonzero symbols counted outside the window
+    int buf = 0;
+    Row cur, nxt, hcur, hnxt;
+
+    // One row.  FULL: every point of the warp lies inside the row (a uniform
+    // branch per warp), so no point needs a bounds flag.
+    auto row = [&](uint32_t z, auto full_tag) {
+        constexpr bool FULL = decltype(full_tag)::value;
+        const uint64_t rowbase = ((uint64_t)z * a.vy + y) * vx;
+        const uint32_t lim = row_limit(rowbase);
+        bool in[NP];
+        int32_t q[NP];
+#pragma unroll
+        for (int i = 0; i < NP; i++) {
+            in[i] = FULL || (yin && (xb + 128u * (i / 4) + (i % 4) < lim));
+            q[i] = in[i] ? prequant(cur.v[i], xmin, inv, off) : 0;
+        }
+        int32_t L1[NP];
+        row_diff(q, cur.hl ? prequant(cur.l, xmin, inv, off) : 0, L1);
+
+        int32_t L2[NP];
         if (MODE == 3) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) sL1[buf][threadIdx.y + 1][4 * threadIdx.x + k] = L1[k];
+            for (int i = 0; i < NP; i++) sL1[buf][threadIdx.y + 1][cb + 128u * (i / 4) + (i % 4)] = L1[i];
             if (threadIdx.y == 0) {
-                int32_t h[4] = {0, 0, 0, 0};
+                int32_t h[NP], hd[NP];
                 int32_t hl = 0;
+#pragma unroll
+                for (int i = 0; i < NP; i++) h[i] = 0;
                 if (y0 > 0) {
 #pragma unroll
-                    for (int k = 0; k < 4; k++) h[k] = (xb + k < vx) ? prequant(hcur.v[k], xmin, inv, off) : 0;
+                    for (int i = 0; i < NP; i++)
+                        h[i] = (xb + 128u * (i / 4) + (i % 4) < vx) ? prequant(hcur.v[i], xmin, inv, off) : 0;
                     if (hcur.hl) hl = prequant(hcur.l, xmin, inv, off);
                 }
-                const int32_t hs = __shfl_up_sync(0xffffffffu, h[3], 1);
-                if (lane != 0) hl = hs;
-                sL1[buf][0][4 * threadIdx.x] = h[0] - hl;
+                row_diff(h, hl, hd);
 #pragma unroll
-                for (int k = 1; k < 4; k++) sL1[buf][0][4 * threadIdx.x + k] = h[k] - h[k - 1];
+                for (int i = 0; i < NP; i++) sL1[buf][0][cb + 128u * (i / 4) + (i % 4)] = hd[i];
             }
             __syncthreads();
 #pragma unroll
-            for (int k = 0; k < 4; k++) L2[k] = L1[k] - sL1[buf][threadIdx.y][4 * threadIdx.x + k];
+            for (int i = 0; i < NP; i++) L2[i] = L1[i] - sL1[buf][threadIdx.y][cb + 128u * (i / 4) + (i % 4)];
             buf ^= 1;
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; k++) L2[k] = L1[k];
+            for (int i = 0; i < NP; i++) L2[i] = L1[i];
         }
 
         if (z >= z0) {
-            int32_t d[4];
-            uint32_t code[4];
+            int32_t d[NP];
+            uint32_t code[NP];
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                d[k] = (MODE == 1) ? L2[k] : L2[k] - L2prev[k];
+            for (int i = 0; i < NP; i++) {
+                d[i] = (MODE == 1) ? L2[i] : L2[i] - L2prev[i];
                 // |d| < R  <=>  d + R - 1 in [0, 2R - 2]
-                const uint32_t u = (uint32_t)(d[k] + (R - 1));
-                code[k] = u < (uint32_t)(2 * R - 1) ? u + 1u : 0u;
+                const uint32_t u = (uint32_t)(d[i] + (R - 1));
+                code[i] = u < (uint32_t)(2 * R - 1) ? u + 1u : 0u;
             }
             uint16_t* crow = a.codes + rowbase;
-            if (VEC && in[3]) {
-                uint2 pk;
-                pk.x = code[0] | (code[1] << 16);
-                pk.y = code[2] | (code[3] << 16);
-                *reinterpret_cast<uint2*>(crow + xb) = pk;
-            } else {
 #pragma unroll
-                for (int k = 0; k < 4; k++)
-                    if (in[k]) crow[xb + k] = (uint16_t)code[k];
-            }
-            // histogram: shared-memory window, global counters outside it
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                if (!in[k]) continue;
-                const uint32_t bin = code[k] - wlo;
-                if (bin < (uint32_t)kHistWin) {
-                    atomicAdd(&shist[bin], 1u);
+            for (int j = 0; j < SEG; j++) {
+                const uint32_t xj = xb + 128u * j;
+                if (VEC && in[4 * j + 3]) {
+                    uint2 pk;
+                    pk.x = code[4 * j] | (code[4 * j + 1] << 16);
+                    pk.y = code[4 * j + 2] | (code[4 * j + 3] << 16);
+                    *reinterpret_cast<uint2*>(crow + xj) = pk;
                 } else {
-                    atomicAdd(&a.hist[code[k]], 1u);
-                    if (code[k]) {
-                        glo = min(glo, code[k]);
-                        ghi = max(ghi, code[k]);
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        if (in[4 * j + k]) crow[xj + k] = (uint16_t)code[4 * j + k];
+                }
+            }
+            // histogram: every point adds to its window bin, or to the lane's
+            // spill slot when it is outside the window (or outside the row);
+            // codes outside the window then go to the global counters
+            bool spill = false;
+#pragma unroll
+            for (int i = 0; i < NP; i++) {
+                const uint32_t bin = code[i] - wlo;
+                const bool win = in[i] && bin < (uint32_t)kHistWin;
+                atomicAdd(&shist[win ? bin : kHistWin + lane], 1u);
+                spill |= in[i] && !win;
+            }
+            if (__any_sync(0xffffffffu, spill)) {
+#pragma unroll
+                for (int i = 0; i < NP; i++) {
+                    if (in[i] && code[i] - wlo >= (uint32_t)kHistWin) {
+                        atomicAdd(&a.hist[code[i]], 1u);
+                        if (code[i]) {
+                            glo = min(glo, code[i]);
+                            ghi = max(ghi, code[i]);
+                        }
                     }
                 }
             }
-            // reconstruction, verbatim test, exact squared error
-            bool vb[4], ol[4];
+            // reconstruction, verbatim test, exact squared error, two points at a time
+            bool vb[NP], ol[NP];
             bool rare = false;
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const float xr = __fmaf_rn(__int2float_rn(q[k]), s, xmin);
-                const float df = __fsub_rn(cur.v[k], xr);
-                vb[k] = in[k] && !(fabsf(df) <= thr);
-                ol[k] = in[k] && code[k] == 0u;
-                if (in[k] && !vb[k]) ff_add_sq_diff(acc, cur.v[k], xr);
-                rare |= vb[k] | ol[k];
+            for (int i = 0; i < NP; i += 2) {
+                const float2 xv = make_float2(cur.v[i], cur.v[i + 1]);
+                const float2 nxr = make_float2(__fmaf_rn(__int2float_rn(q[i]), ns, nxmin),
+                                               __fmaf_rn(__int2float_rn(q[i + 1]), ns, nxmin));
+                const float2 df = __fadd2_rn(xv, nxr);  // fl(x - x') per point
+                vb[i] = in[i] && !(fabsf(df.x) <= thr);
+                vb[i + 1] = in[i + 1] && !(fabsf(df.y) <= thr);
+                ol[i] = in[i] && code[i] == 0u;
+                ol[i + 1] = in[i + 1] && code[i + 1] == 0u;
+                ff2_add_sq_diff(acc, xv, nxr, df, in[i] && !vb[i], in[i + 1] && !vb[i + 1]);
+                rare |= vb[i] | ol[i] | vb[i + 1] | ol[i + 1];
             }
             // outliers and verbatims are rare: one vote per row decides whether any
             // lane of the warp needs the order-preserving staging below
             if (__any_sync(0xffffffffu, rare)) {
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const uint32_t gi = (uint32_t)rowbase + xb + k;
-                    const uint32_t mo = __ballot_sync(0xffffffffu, ol[k]);
+                for (int i = 0; i < NP; i++) {
+                    const uint32_t gi = (uint32_t)rowbase + xb + 128u * (i / 4) + (i % 4);
+                    const uint32_t mo = __ballot_sync(0xffffffffu, ol[i]);
                     if (mo) {
                         uint32_t leader = __ffs(mo) - 1, base = 0;
                         if (lane == leader) base = atomicAdd(&par->n_out, __popc(mo));
                         base = __shfl_sync(0xffffffffu, base, leader);
-                        if (ol[k]) {
+                        if (ol[i]) {
                             const uint32_t slot = base + __popc(mo & lanemask_lt());
-                            a.stage_out[slot] = make_uint2(gi, (uint32_t)d[k]);
+                            a.stage_out[slot] = make_uint2(gi, (uint32_t)d[i]);
                             atomicOr(&a.bm_out[gi >> 5], 1u << (gi & 31u));
                         }
                     }
-                    const uint32_t mv = __ballot_sync(0xffffffffu, vb[k]);
+                    const uint32_t mv = __ballot_sync(0xffffffffu, vb[i]);
                     if (mv) {
                         uint32_t leader = __ffs(mv) - 1, base = 0;
                         if (lane == leader) base = atomicAdd(&par->n_vb, __popc(mv));
                         base = __shfl_sync(0xffffffffu, base, leader);
-                        if (vb[k]) {
+                        if (vb[i]) {
                             const uint32_t slot = base + __popc(mv & lanemask_lt());
-                            a.stage_vb[slot] = make_uint2(gi, __float_as_uint(cur.v[k]));
+                            a.stage_vb[slot] = make_uint2(gi, __float_as_uint(cur.v[i]));
                             atomicOr(&a.bm_vb[gi >> 5], 1u << (gi & 31u));
                         }
                     }
@@ -570,24 +621,48 @@ __global__ void __launch_bounds__(TX / 4 * TY) k_pq(const __grid_constant__ Batc
             }
         }
 #pragma unroll
-        for (int k = 0; k < 4; k++) L2prev[k] = L2[k];
+        for (int i = 0; i < NP; i++) L2prev[i] = L2[i];
+    };
+
+    const uint32_t zstart = (MODE != 1 && z0 > 0) ? z0 - 1 : z0;
+    // a warp whose first column is past the row end has no point in any row
+    // (MODE 3 keeps every warp for the block barriers of its loop)
+    const uint32_t zlast = (MODE != 3 && xw >= vx) ? zstart : z1;
+#pragma unroll
+    for (int i = 0; i < NP; i++) hnxt.v[i] = 0.0f;
+    hnxt.l = 0.0f;
+    hnxt.hl = false;
+    if (zstart < zlast) fetch(zstart, nxt, hnxt);
+    for (uint32_t z = zstart; z < zlast; z++) {
+        cur = nxt;
+        hcur = hnxt;
+        if (z + 1 < zlast) fetch(z + 1, nxt, hnxt);
+        if (MODE != 3 && xw + 128u * SEG <= row_limit(((uint64_t)z * a.vy + y) * vx))
+            row(z, std::true_type{});
+        else
+            row(z, std::false_type{});
     }
 
     // flush the histogram window (and take the block's symbol range from it)
     // and the squared-error partial
     __syncthreads();
-    for (uint32_t i = tid; i < kHistWin; i += NT) {
-        const uint32_t c = shist[i];
-        if (c) {
-            const uint32_t sym = wlo + i;
-            atomicAdd(&a.hist[sym], c);
-            if (sym) {
-                glo = min(glo, sym);
-                ghi = max(ghi, sym);
+    for (uint32_t i = tid; i < kHistWin / 4; i += NT) {
+        const uint4 c4 = reinterpret_cast<const uint4*>(shist)[i];
+        if ((c4.x | c4.y | c4.z | c4.w) == 0u) continue;
+        const uint32_t cs[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (cs[k]) {
+                const uint32_t sym = wlo + 4u * i + k;
+                atomicAdd(&a.hist[sym], cs[k]);
+                if (sym) {
+                    glo = min(glo, sym);
+                    ghi = max(ghi, sym);
+                }
             }
         }
     }
-    double tot = block_sum_double(ff_to_double(acc), ssum);
+    double tot = block_sum_double(ff2_to_double(acc), ssum);
     if (tid == 0) a.sse_part[b] = tot;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1014,20 +1089,21 @@ __global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ Batch<
     } while (0)
 
 // Launches one k_pq variant over the fields of a batch that use it.
-template <int MODE, int TX, int TY>
+template <int MODE, int TX, int TY, int SEG>
 static void launch_pq_t(Batch<PQArgs>& b, uint32_t blocks, bool vec, cudaStream_t st) {
-    const dim3 blk(TX / 4, TY);
-    if (vec) k_pq<MODE, TX, TY, true><<<blocks, blk, 0, st>>>(b);
-    else k_pq<MODE, TX, TY, false><<<blocks, blk, 0, st>>>(b);
+    const dim3 blk(TX / (4 * SEG), TY);
+    if (vec) k_pq<MODE, TX, TY, true, SEG><<<blocks, blk, 0, st>>>(b);
+    else k_pq<MODE, TX, TY, false, SEG><<<blocks, blk, 0, st>>>(b);
 }
 
 static void launch_pq_variant(int mode, int tx, Batch<PQArgs>& b, uint32_t blocks, bool vec,
                               cudaStream_t st) {
-    if (mode == 1) launch_pq_t<1, 512, 1>(b, blocks, vec, st);
-    else if (mode == 3) launch_pq_t<3, 128, 8>(b, blocks, vec, st);
-    else if (tx == 128) launch_pq_t<2, 128, 1>(b, blocks, vec, st);
-    else if (tx == 256) launch_pq_t<2, 256, 1>(b, blocks, vec, st);
-    else launch_pq_t<2, 512, 1>(b, blocks, vec, st);
+    if (mode == 1) launch_pq_t<1, 1024, 1, 2>(b, blocks, vec, st);
+    else if (mode == 3) launch_pq_t<3, 128, 8, 1>(b, blocks, vec, st);
+    else if (tx == 128) launch_pq_t<2, 128, 1, 1>(b, blocks, vec, st);
+    else if (tx == 256) launch_pq_t<2, 256, 1, 1>(b, blocks, vec, st);
+    else if (tx == 512) launch_pq_t<2, 512, 1, 1>(b, blocks, vec, st);
+    else launch_pq_t<2, 1024, 1, 2>(b, blocks, vec, st);
 }
 
 // Small grid-stride kernels (emit, finalize) use this many blocks per field.

@@ -184,7 +184,7 @@ extern "C" int fpsnr_autotune(int ndim, const uint64_t* dims, double target_psnr
     const bool has_tx = cur.pq_tile_x != 0, has_band = cur.band_rows != 0;
     for (int param = 0; param < 3 && rc == FPSNR_OK; param++) {
         std::vector<int> vals;
-        if (param == 0 && has_tx) vals = {128, 256, 512};
+        if (param == 0 && has_tx) vals = {128, 256, 512, 1024};
         if (param == 1 && has_band) vals = {16, 32, 64};
         if (param == 2) vals = {128, 512};
         for (int v : vals) {

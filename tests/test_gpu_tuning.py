@@ -33,7 +33,7 @@ def test_tiles_keep_bytes(env, shape, psnr):
     blob0, rec0, _ = _run(env, base, xt)
     ob, _ = oracle.compress(x, psnr)
     assert blob0 == ob
-    for key, vals in (("pq_tile_x", (128, 256, 512)), ("band_rows", (16, 32, 64)),
+    for key, vals in (("pq_tile_x", (128, 256, 512, 1024)), ("band_rows", (16, 32, 64)),
                       ("dec_threads", (128, 512))):
         for v in vals:
             plan = fpsnr.Plan(shape, psnr)
