@@ -232,7 +232,7 @@ int fpsnr_psnr_static(const float* d_x, const float* d_xr, uint64_t n, double* h
  *   pq_tile_x    2D predictor tile width: 128, 256, 512 or 1024 points (0: by row length)
  *   band_rows    2D decompression band height: 16, 32 or 64 rows (0: 32); only
  *                for 2D fields with rows of at most 8192 points
- *   dec_threads  decoder block size: 128 or 512 (0: chosen per launch)
+ *   dec_threads  decoder block size: 128, 256 or 512 (0: chosen per launch)
  *   ms, bytes    filled by fpsnr_autotune: best compress + decompress time of the
  *                sample (milliseconds) and its compressed size at `chunk` */
 typedef struct {

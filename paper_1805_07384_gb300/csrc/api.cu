@@ -54,7 +54,7 @@ void carve(fpsnr_plan_s* p, uint8_t* base, size_t* total) {
     w.hbuf1 = c.take<unsigned long long>(p->nsym);
     w.hbuf2 = c.take<unsigned long long>(p->nsym);
     w.hpar = c.take<uint32_t>(2ull * p->nsym);
-    w.dlut = c.take<uint32_t>((1u << fp::kLutBits) + fp::kL2Cap);
+    w.dlut = c.take<uint32_t>(1u << fp::kLutBits);
     w.dsyms = c.take<uint16_t>(fp::kMaxSym);
     w.lb_flags = c.take<uint32_t>(std::max<uint64_t>(p->lb_tiles_total, 1));
     w.lb_vals = c.take<uint32_t>(2 * std::max<uint64_t>(p->lb_tiles_total, 1) * p->lb_width);
@@ -474,7 +474,7 @@ int fpsnr_plan_set_tuning(fpsnr_plan_t p, const fpsnr_tuning* t) {
     if (tx != 0 && p->ld != 2) return FPSNR_EINVAL;
     if (tr != 0 && (tr != 16 && tr != 32 && tr != 64)) return FPSNR_EINVAL;
     if (tr != 0 && !p->band.on) return FPSNR_EINVAL;
-    if (dt != 0 && dt != 128 && dt != 512) return FPSNR_EINVAL;
+    if (dt != 0 && dt != 128 && dt != 256 && dt != 512) return FPSNR_EINVAL;
     if (p->ld == 2 && p->n > 0) {
         const int keep = p->pq.tx;
         if (!pq_geometry(p, tx) || p->pq.nblocks > p->pq_blocks_cap) {

@@ -26,9 +26,8 @@ constexpr int kMaxLmax = 27;
 constexpr int kFineBins = 4096;  // fine histogram of the bound refinement (psnr_mode 1)
 constexpr uint32_t kZrSeg = 1024;          // lossless container: bytes per segment
 constexpr uint32_t kZrMagic = 0x315A5046u;  // bytes "FPZ1"
-constexpr int kLutBits = 12;  // decode look-up table width (first level)
-constexpr int kL2Sub = 6;     // second level: up to this many bits past the first level
-constexpr int kL2Cap = 4096;  // second-level entries (shared memory of the decoder)
+constexpr int kLutBits = 12;        // decode look-up table width
+constexpr uint32_t kLutLen = 0x20u;  // table entry flag: length only, symbol by canonical index
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 // Per-call device record.  Written by kernels, read by later kernels.
@@ -55,7 +54,6 @@ struct DevParams {
     uint64_t off_cb, off_ct, off_st, off_ou, off_vb, total;
     // decompression: header fields of the blob being decoded
     uint32_t d_radius, d_chunk, d_lmax, d_nsym, d_nchunks, d_words, d_nout, d_nvb;
-    uint32_t d_l2n;  // second-level table entries in use
     uint32_t d_count[32], d_first_code[32], d_first_index[32];
 };
 
@@ -80,7 +78,7 @@ struct Workspace {
     unsigned long long* hbuf2;  // [nsym] sort ping-pong
     uint32_t* hpar;             // [2*nsym] parent of every node
     // decoding tables
-    uint32_t* dlut;  // [(1 << kLutBits) + kL2Cap] first-level table, then second-level tables
+    uint32_t* dlut;  // [1 << kLutBits] decode table
     uint16_t* dsyms; // [kMaxSym]
     // inverse-Lorenzo look-back state
     uint32_t* lb_flags;  // [n_lb_tiles]

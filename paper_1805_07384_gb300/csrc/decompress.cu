@@ -69,9 +69,6 @@ __global__ void __launch_bounds__(1024) k_dsetup(const __grid_constant__ Batch<D
     __shared__ int s_ok;
     __shared__ uint32_t s_cnt[32];
     __shared__ unsigned long long s_kraft;
-    __shared__ unsigned long long s_ls[32], s_lj[32];  // canonical range of every length
-    __shared__ uint32_t s_pb[1u << kLutBits];           // per prefix: base << 4 | sub
-    __shared__ uint32_t s_sh[33], s_l2n;
     const uint32_t tid = threadIdx.x;
     // the scans' tile counters start every call at zero (see k_scan_contig)
     if (tid < 8) lb_ctr[tid] = 0;
@@ -173,108 +170,45 @@ __global__ void __launch_bounds__(1024) k_dsetup(const __grid_constant__ Batch<D
     }
     __syncthreads();
     if (par->flags & kFlagError) return;
-    // every first-level entry v (the next kLutBits bits) finds its code length as
-    // the first length whose canonical range ends above v (ranges are contiguous
-    // and ascending); prefixes of longer codes get 0 here and a second-level
-    // pointer below
-    const uint32_t lm = min(lmax, (uint32_t)kLutBits);
+    // Table over the next kLutBits bits.  Canonical code ranges tile the
+    // left-justified code space in order of length, so prefix v (a) holds one
+    // whole code of length l <= kLutBits: entry (sym << 8) | l; (b) lies inside
+    // the range of a single length l > kLutBits: entry kLutLen | l (the decoder
+    // finds the symbol from its canonical index); or (c) straddles the ranges of
+    // several lengths or has no code: entry 0 (the decoder searches the range
+    // ends).  Case (c) holds for at most one prefix per length boundary.
     for (uint32_t v = tid; v < (1u << kLutBits); v += blockDim.x) {
         const unsigned long long w = (unsigned long long)v << (32 - kLutBits);
         uint32_t e = 0;
-        for (uint32_t l = 1; l <= lm; l++) {
+        for (uint32_t l = 1; l <= lmax; l++) {
             const unsigned long long lje =
                 (unsigned long long)(par->d_first_code[l] + par->d_count[l]) << (32 - l);
             if (w < lje) {
-                const uint32_t code = v >> (kLutBits - l);
-                const uint32_t k = code - par->d_first_code[l];
-                if (k < par->d_count[l]) e = ((uint32_t)syms[par->d_first_index[l] + k] << 8) | l;
+                if (l <= (uint32_t)kLutBits) {
+                    const uint32_t code = v >> (kLutBits - l);
+                    const uint32_t k = code - par->d_first_code[l];
+                    if (k < par->d_count[l]) e = ((uint32_t)syms[par->d_first_index[l] + k] << 8) | l;
+                } else if (w + (1ull << (32 - kLutBits)) <= lje) {
+                    e = kLutLen | l;
+                }
                 break;
             }
         }
         lut[v] = e;
     }
-    // Second level.  Codes longer than kLutBits start with a prefix in [F, 2^kLutBits);
-    // prefix p gets a table over the next sub_p = min(longest code under p - kLutBits,
-    // kL2Sub) bits, tables laid out in prefix order while they fit kL2Cap entries.
-    // First-level pointer entry: (base << 12) | (sub << 8), length field 0.
-    // Second-level entry: (sym << 8) | length, or 0 for a code longer than the table.
-    if (tid < 32) {
-        const uint32_t l = tid;
-        const bool ok = l >= 1 && l <= lmax;
-        s_ls[l] = ok ? (unsigned long long)par->d_first_code[l] << (32 - l) : 0ull;
-        s_lj[l] = ok ? (unsigned long long)(par->d_first_code[l] + par->d_count[l]) << (32 - l) : 0ull;
-    }
-    if (tid == 0) s_l2n = 0;
-    __syncthreads();
-    if (lmax > (uint32_t)kLutBits) {
-        constexpr uint32_t P = 1u << kLutBits;
-        const uint32_t F = min(par->d_first_code[kLutBits] + par->d_count[kLutBits], P);
-        // 4 consecutive prefixes per thread so the scan runs in prefix order
-        uint32_t sub[4], sz[4], tot = 0;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const uint32_t p = F + 4u * tid + k;
-            uint32_t m = 0;
-            if (p < P) {
-                const unsigned long long lo_p = (unsigned long long)p << (32 - kLutBits);
-                const unsigned long long hi_p = (unsigned long long)(p + 1) << (32 - kLutBits);
-                for (uint32_t l = kLutBits + 1; l <= lmax; l++)
-                    if (s_lj[l] > s_ls[l] && s_ls[l] < hi_p && s_lj[l] > lo_p) m = l;
-            }
-            sub[k] = m ? min(m - (uint32_t)kLutBits, (uint32_t)kL2Sub) : 0u;
-            sz[k] = sub[k] ? 1u << sub[k] : 0u;
-            tot += sz[k];
-        }
-        uint32_t all;
-        uint32_t base = block_excl_scan(tot, s_sh, &all);
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const uint32_t p = F + 4u * tid + k;
-            if (p < P) {
-                const bool keep = sz[k] && base + sz[k] <= (uint32_t)kL2Cap;
-                s_pb[p] = (base << 4) | (keep ? sub[k] : 0u);
-                if (keep) {
-                    lut[p] = (base << 12) | (sub[k] << 8);
-                    atomicMax(&s_l2n, base + sz[k]);
-                }
-            }
-            base += sz[k];
-        }
-        __syncthreads();
-        const uint32_t n2 = s_l2n;
-        for (uint32_t i = tid; i < n2; i += blockDim.x) {
-            // the table holding entry i: the last prefix whose base is <= i
-            uint32_t lo = F, hi = P - 1;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi + 1) >> 1;
-                if ((s_pb[mid] >> 4) <= i) lo = mid;
-                else hi = mid - 1;
-            }
-            const uint32_t p = lo, sb = s_pb[p] & 15u, j = i - (s_pb[p] >> 4);
-            const uint32_t w = (p << (32 - kLutBits)) | (j << (32 - kLutBits - sb));
-            uint32_t e = 0;
-            for (uint32_t l = kLutBits + 1; l <= kLutBits + sb; l++) {
-                if ((unsigned long long)w < s_lj[l]) {
-                    const uint32_t k = (w >> (32 - l)) - par->d_first_code[l];
-                    if (k < par->d_count[l]) e = ((uint32_t)syms[par->d_first_index[l] + k] << 8) | l;
-                    break;
-                }
-            }
-            lut[P + i] = e;
-        }
-    }
-    if (tid == 0) par->d_l2n = s_l2n;
 }
 
 // One thread decodes one chunk of `chunk` symbols.  The bit window is 64 bits
 // held as two 32-bit halves (hi holds the next bits, left-justified); a stream
 // word is appended whenever 32 or fewer valid bits remain.  Every symbol is one
-// first-level table read (kLutBits bits), plus a second-level read for codes
-// up to kLutBits + kL2Sub bits, plus a funnel shift; longer codes are located
-// by comparing the left-justified window with the end of each length's
-// canonical range.  A chunk that consumes more bits than it owns, or meets a
-// prefix no code has, is corrupt.
-constexpr int kDecRing = 2;  // stream quads in flight per thread (power of two)
+// table read over the next kLutBits bits and a funnel shift: the entry gives
+// the code length, and the symbol itself for codes of up to kLutBits bits;
+// longer codes take their symbol from the canonical index, off the dependency
+// chain of the next code's position.  Prefixes shared by several lengths are
+// resolved by comparing the window with the end of each length's canonical
+// range.  A chunk that consumes more bits than it owns, or meets a prefix no
+// code has, is corrupt.
+constexpr int kDecRing = 4;  // stream quads in flight per thread (power of two)
 
 // Asynchronous 16-byte copy global -> shared memory through L2 (both 16-byte
 // aligned), one commit group per copy, and waits on the thread's own groups.
@@ -287,12 +221,10 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// dynamic shared memory of a THREADS-wide decode block: two table levels, then
-// the stream rings.  Small launches (few chunks) take 128-thread blocks to reach
-// more SMs; large ones 512-thread blocks, which share one copy of the tables
-// among more chunks.
+// dynamic shared memory of a THREADS-wide decode block: the table, then the
+// stream rings.
 constexpr uint32_t dec_smem(int threads) {
-    return ((1u << kLutBits) + kL2Cap + 4u * kDecRing * (uint32_t)threads) * 4u;
+    return ((1u << kLutBits) + 4u * kDecRing * (uint32_t)threads) * 4u;
 }
 
 struct DecArgs {
@@ -307,7 +239,7 @@ struct DecArgs {
 };
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 1536 / THREADS) k_decode(const __grid_constant__ Batch<DecArgs> B) {
+__global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_decode(const __grid_constant__ Batch<DecArgs> B) {
     const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
     const DecArgs& A = B.a[fld];
     const uint32_t bid = blockIdx.x - B.off[fld];
@@ -317,7 +249,7 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) k_decode(const __grid
     const uint64_t n = A.n;
     const uint32_t chunk = A.chunk;
     const uint64_t nchunks = A.nchunks;
-    extern __shared__ __align__(16) uint32_t slut[];  // first level, then second level
+    extern __shared__ __align__(16) uint32_t slut[];  // decode table, then the stream rings
     __shared__ uint32_t s_base[32];  // first index - first code of every length (mod 2^32)
     __shared__ unsigned long long s_lje[33];
     __shared__ __align__(8) unsigned long long s_mbar;
@@ -339,10 +271,8 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) k_decode(const __grid
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t lut_bytes = (1u << kLutBits) * 4u;
-        const uint32_t l2_bytes = ((min(par->d_l2n, (uint32_t)kL2Cap) + 3u) & ~3u) * 4u;
-        mbar_arrive_expect_tx(&s_mbar, lut_bytes + l2_bytes);
+        mbar_arrive_expect_tx(&s_mbar, lut_bytes);
         bulk_g2s(slut, lut_g, lut_bytes, &s_mbar);
-        if (l2_bytes) bulk_g2s(slut + (1u << kLutBits), lut_g + (1u << kLutBits), l2_bytes, &s_mbar);
     }
     if (!mbar_wait_bounded(&s_mbar, 0)) {
         // never expected; record it, let the copy land, then leave
@@ -370,7 +300,7 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) k_decode(const __grid
     // so a refill never waits on a later quad).  Words past the chunk belong to
     // the next chunk (or are zero past the section) and are never consumed by a
     // well-formed stream.
-    uint32_t* ring = slut + (1u << kLutBits) + kL2Cap + 4u * threadIdx.x;
+    uint32_t* ring = slut + (1u << kLutBits) + 4u * threadIdx.x;
     const uint32_t qend = (words + 3u) >> 2;  // quads in the 16-byte padded section
     uint32_t qk = w0 >> 2, ci = w0 & 3u;
     auto issue = [&](uint32_t qi) {
@@ -397,33 +327,30 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) k_decode(const __grid
                 cp_async_wait<kDecRing - 1>();
             }
         }
-        uint32_t e = slut[hi >> (32 - kLutBits)];
-        uint32_t l = e & 0xffu;
-        if (l == 0u) {
-            // second level over the next sub bits, when the prefix has a table
-            const uint32_t sub = (e >> 8) & 15u;
-            if (sub) e = slut[(1u << kLutBits) + (e >> 12) + ((hi << kLutBits) >> (32 - sub))];
-            l = e & 0xffu;
-            if (l == 0u) {
-                // longer still: binary search for the first length whose canonical
-                // range ends above the window (a fixed number of steps for every lane)
-                uint32_t a = kLutBits + 1 + sub, b = lmax;
-                const bool none = (unsigned long long)hi >= s_lje[lmax];  // no code has this prefix
+        const uint32_t e = slut[hi >> (32 - kLutBits)];
+        uint32_t l = e & 31u;
+        uint32_t sym = e >> 8;
+        if (e & kLutLen) {
+            // the symbol is not on the dependency chain of the next code's position
+            sym = __ldg(&syms[(s_base[l] + (hi >> (32 - l))) & 0xffffu]);
+        } else if (l == 0u) {
+            // a prefix shared by several lengths (or by no code): the first length
+            // whose canonical range ends above the window, by a fixed number of
+            // bisection steps over kLutBits + 1 .. lmax
+            uint32_t a = kLutBits + 1, b = lmax;
+            const bool none = (unsigned long long)hi >= s_lje[lmax];  // no code has this prefix
 #pragma unroll
-                for (int it = 0; it < 5; it++) {
-                    if (a < b) {
-                        const uint32_t m = (a + b) >> 1;
-                        if ((unsigned long long)hi < s_lje[m]) b = m;
-                        else a = m + 1;
-                    }
+            for (int it = 0; it < 5; it++) {
+                if (a < b) {
+                    const uint32_t m = (a + b) >> 1;
+                    if ((unsigned long long)hi < s_lje[m]) b = m;
+                    else a = m + 1;
                 }
-                l = a;
-                // the symbol is not on the dependency chain of the next code's position
-                e = none ? 0u : (uint32_t)__ldg(&syms[(s_base[l] + (hi >> (32 - l))) & 0xffffu]) << 8;
-                bad |= none;
             }
+            l = a;
+            sym = none ? 0u : (uint32_t)__ldg(&syms[(s_base[l] + (hi >> (32 - l))) & 0xffffu]);
+            bad |= none;
         }
-        const uint32_t sym = e >> 8;
         hi = __funnelshift_l(lo, hi, l);
         lo <<= l;
         nb -= l;
@@ -1012,20 +939,21 @@ static void launch_band(const Batch<BandArgs>& b, const uint32_t* nb, const uint
     else launch_band_t<4, VEC>(b, nb, ncol, prof, st);
 }
 
+template <int T>
+static bool decode_attrs() {
+    return cudaFuncSetAttribute(k_decode<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dec_smem(T)) == cudaSuccess &&
+           cudaFuncSetAttribute(k_decode<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
+               cudaSuccess;
+}
+
 int decode_prepare(const fpsnr_plan_s*) {
     static int done = 0;
     if (!done) {
         // the decoder reads its stream through cp.async into shared memory, not
-        // L1: take the largest shared-memory carveout so three 512-thread blocks fit
-        if (cudaFuncSetAttribute(k_decode<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dec_smem(128)) != cudaSuccess ||
-            cudaFuncSetAttribute(k_decode<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dec_smem(512)) != cudaSuccess ||
-            cudaFuncSetAttribute(k_decode<128>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 100) != cudaSuccess ||
-            cudaFuncSetAttribute(k_decode<512>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 100) != cudaSuccess)
-            return FPSNR_ECUDA;
+        // L1: take the largest shared-memory carveout so that 1536 threads' rings
+        // and their blocks' tables fit
+        if (!decode_attrs<128>() || !decode_attrs<256>() || !decode_attrs<512>()) return FPSNR_ECUDA;
         done = 1;
     }
     return FPSNR_OK;
@@ -1078,10 +1006,10 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
     }
     // decode every field into its plan's symbol buffer
     {
-        uint64_t chunks = 0;
-        for (int f = 0; f < count; f++) chunks += P[f]->n ? P[f]->nchunks : 0;
-        const int T = P[0]->dec_threads ? P[0]->dec_threads
-                                         : (chunks <= 256ull * (uint64_t)P[0]->sm_count ? 128 : 512);
+        // 128-thread blocks spread every field's chunks over all SMs: a field with
+        // long codes (slow chunks) then shares no SM's issue slots with itself more
+        // than the others do
+        const int T = P[0]->dec_threads ? P[0]->dec_threads : 128;
         Batch<DecArgs> b;
         b.count = 0;
         for (int f = 0; f < count; f++) {
@@ -1096,6 +1024,7 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
             const uint32_t tot = batch_offsets(b, blocks);
             StageScope sc(prof, kStDecode, st);
             if (T == 128) k_decode<128><<<tot, 128, dec_smem(128), st>>>(b);
+            else if (T == 256) k_decode<256><<<tot, 256, dec_smem(256), st>>>(b);
             else k_decode<512><<<tot, 512, dec_smem(512), st>>>(b);
             if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
         }

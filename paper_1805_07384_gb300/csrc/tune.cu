@@ -186,7 +186,7 @@ extern "C" int fpsnr_autotune(int ndim, const uint64_t* dims, double target_psnr
         std::vector<int> vals;
         if (param == 0 && has_tx) vals = {128, 256, 512, 1024};
         if (param == 1 && has_band) vals = {16, 32, 64};
-        if (param == 2) vals = {128, 512};
+        if (param == 2) vals = {128, 256, 512};
         for (int v : vals) {
             fpsnr_tuning t = cur;
             if (param == 0) t.pq_tile_x = v;

@@ -34,7 +34,7 @@ def test_tiles_keep_bytes(env, shape, psnr):
     ob, _ = oracle.compress(x, psnr)
     assert blob0 == ob
     for key, vals in (("pq_tile_x", (128, 256, 512, 1024)), ("band_rows", (16, 32, 64)),
-                      ("dec_threads", (128, 512))):
+                      ("dec_threads", (128, 256, 512))):
         for v in vals:
             plan = fpsnr.Plan(shape, psnr)
             plan.set_tuning({key: v})
@@ -55,7 +55,7 @@ def test_set_tuning_rejects(env):
     p3 = fpsnr.Plan((8, 16, 32), 60.0)
     p2wide = fpsnr.Plan((4, 9000), 60.0)
     for plan, t in ((p2, {"chunk": 512}), (p2, {"pq_tile_x": 64}), (p2, {"band_rows": 8}),
-                    (p2, {"dec_threads": 256}), (p3, {"pq_tile_x": 256}), (p3, {"band_rows": 32}),
+                    (p2, {"dec_threads": 384}), (p3, {"pq_tile_x": 256}), (p3, {"band_rows": 32}),
                     (p2wide, {"band_rows": 16})):
         before = plan.get_tuning()
         with pytest.raises(fpsnr.FpsnrError) as e:
