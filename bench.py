@@ -331,7 +331,7 @@ _UNITS = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 
 # benchmark stages by kernel-name prefix, with the source file that holds them
 _STAGE_KERNELS = [("range_plan", ("k_range_plan",), "compress.cu"),
                   ("predict_quantize", ("k_pq",), "compress.cu"),
-                  ("encode", ("k_enc_bits", "k_enc_scan", "k_enc_pack"), "compress.cu"),
+                  ("encode", ("k_enc_pack", "k_enc_scan", "k_enc_copy"), "compress.cu"),
                   ("decode", ("k_decode",), "decompress.cu"),
                   ("band_sum", ("k_band_sum",), "decompress.cu"),
                   ("scan_final_dequant", ("k_band_scan",), "decompress.cu")]
@@ -382,8 +382,8 @@ def write_traffic(path):
                      "over the launches of the capture; bench.py reports it as roofline.traffic only "
                      "while the kernel's source file still has the recorded SHA-1.",
            "_command": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-                       "--clock-control none -k regex:\"k_pq|k_decode|k_band_scan|k_band_sum|k_enc_bits|"
-                       "k_enc_pack|k_enc_scan|k_range_plan\" --csv --log-file traffic.csv python bench.py "
+                       "--clock-control none -k regex:\"k_pq|k_decode|k_band_scan|k_band_sum|k_enc_pack|"
+                       "k_enc_copy|k_enc_scan|k_range_plan\" --csv --log-file traffic.csv python bench.py "
                        "--steps 2 --warmup 3 --no-cpu-baseline --no-e2e --no-roofline; "
                        "python bench.py --write-traffic traffic.csv"}
     for stage, prefixes, src in _STAGE_KERNELS:

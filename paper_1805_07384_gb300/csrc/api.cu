@@ -60,6 +60,7 @@ void carve(fpsnr_plan_s* p, uint8_t* base, size_t* total) {
     w.lb_vals = c.take<uint32_t>(2 * std::max<uint64_t>(p->lb_tiles_total, 1) * p->lb_width);
     w.lb_ctr = c.take<uint32_t>(8);
     w.enc_tiles = c.take<uint32_t>(std::max<uint64_t>(p->enc_tiles, 1));
+    w.enc_scratch = c.take<uint32_t>(std::max<uint64_t>(p->nchunks * p->enc_slot_words, 1));
     w.bsum = c.take<uint32_t>(p->band.on ? (uint64_t)p->band_cap * p->band.nx : 1);
     w.fine_hist = c.take<uint32_t>(fp::kFineBins);
     w.zr_scratch = c.take<uint8_t>(p->lossless ? p->zr_scratch_cap : 16);
@@ -306,6 +307,7 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
     p->nwords = cdiv(n, 32);
     p->nbmblk = cdiv(p->nwords, 1024);
     p->enc_tiles = cdiv(p->nchunks, 8);
+    p->enc_slot_words = (uint32_t)cdiv((uint64_t)p->chunk * (uint64_t)p->lmax, 32);
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
         delete p;

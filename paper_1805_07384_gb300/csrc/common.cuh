@@ -85,6 +85,7 @@ struct Workspace {
     uint32_t* lb_vals;   // [2][n_lb_tiles * lb_width] aggregate, inclusive
     uint32_t* lb_ctr;    // [8] dynamic tile counters (pairs: counter, done)
     uint32_t* enc_tiles; // [enc_tiles] words per encoder tile, then their exclusive prefix
+    uint32_t* enc_scratch;  // [nchunks * enc_slot_words] packed chunks before placement
     uint32_t* bsum;      // [nbands * nx] 2D band column sums (band geometry only)
     uint32_t* fine_hist; // [kFineBins] bound refinement histogram (kept zero between calls)
     uint8_t* zr_scratch; // lossless plans: container (compress) / expanded blob (decompress)
@@ -170,6 +171,7 @@ struct fpsnr_plan_s {
     fp::BandGeom band;
     uint64_t lb_tiles_total, lb_width;
     uint64_t enc_tiles;
+    uint32_t enc_slot_words;  // scratch words per chunk (chunk * lmax bits)
     void* slab;
     size_t slab_bytes;
     fp::Workspace w;

@@ -81,11 +81,20 @@ __global__ void __launch_bounds__(512) k_range_plan(const __grid_constant__ Batc
     if (VEC) {
         const float4* x4 = reinterpret_cast<const float4*>(x);
         const uint64_t n4 = n >> 2;
-        for (uint64_t i = gtid; i < n4; i += gsz) {
-            float4 v = __ldcs(x4 + i);
-            nf |= !isfinite(v.x) | !isfinite(v.y) | !isfinite(v.z) | !isfinite(v.w);
-            lo = fminf(lo, fminf(fminf(v.x, v.y), fminf(v.z, v.w)));
-            hi = fmaxf(hi, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+        // four independent 16-byte loads in flight per thread
+        for (uint64_t i0 = gtid; i0 < n4; i0 += 4 * gsz) {
+            float4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint64_t i = i0 + k * gsz;
+                v[k] = i < n4 ? __ldcs(x4 + i) : v[0];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                nf |= !isfinite(v[k].x) | !isfinite(v[k].y) | !isfinite(v[k].z) | !isfinite(v[k].w);
+                lo = fminf(lo, fminf(fminf(v[k].x, v[k].y), fminf(v[k].z, v[k].w)));
+                hi = fmaxf(hi, fmaxf(fmaxf(v[k].x, v[k].y), fmaxf(v[k].z, v[k].w)));
+            }
         }
         for (uint64_t i = (n4 << 2) + gtid; i < n; i += gsz) {
             float v = x[i];
@@ -713,7 +722,7 @@ __global__ void __launch_bounds__(1024) k_rank_popc(const __grid_constant__ Batc
 }
 
 // ---------------------------------------------------------------------------
-// encoder: bits per chunk, offsets, packing -- one fused pass
+// encoder: packing into per-chunk slots, offsets, placement
 // ---------------------------------------------------------------------------
 
 static __device__ __forceinline__ uint64_t pad16(uint64_t b) { return (b + 15u) & ~(uint64_t)15u; }
@@ -730,60 +739,111 @@ struct EncArgs {
     uint32_t chunk;
     uint64_t nchunks;
     uint32_t ntiles;
+    uint32_t slot_words;    // scratch words per chunk: enough for chunk * lmax bits
+    uint32_t* scratch;      // [nchunks * slot_words] every chunk packed from its slot's start
     uint32_t* chunk_words;  // [nchunks] words of every chunk
     uint32_t* tile_sum;     // [ntiles] words of every tile, then their exclusive prefix
 };
 
-// Coded bits of symbols [beg, end) summed over the warp (8 per lane per step).
-__device__ __forceinline__ uint32_t warp_chunk_bits(const uint16_t* __restrict__ codes,
-                                                    const uint32_t* __restrict__ enc, uint64_t beg,
-                                                    uint64_t end, uint32_t lane) {
-    uint32_t bits = 0;
-    for (uint64_t i = beg + 8u * lane; i < end; i += 256u) {
-        if (i + 8 <= end) {
-            const uint4 v = *reinterpret_cast<const uint4*>(codes + i);
-            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                bits += __ldg(enc + (wv[k] & 0xffffu)) & 31u;
-                bits += __ldg(enc + (wv[k] >> 16)) & 31u;
-            }
-        } else {
-            for (uint64_t j = i; j < end; j++) bits += __ldg(enc + codes[j]) & 31u;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
-    return bits;
-}
-
 // Encoder, three launches with no inter-block waiting:
-//   k_enc_bits  one warp per chunk: its words; a block (tile of kEncWarps
-//               chunks) also writes the tile's total
+//   k_enc_pack  one warp per chunk: MSB-first packing into the chunk's own
+//               scratch slot (chunks start on word boundaries, so a chunk's
+//               words do not depend on where it lands): pieces of 256 symbols
+//               (8 per lane) are OR-ed into a per-warp shared-memory word
+//               buffer, full words go out coalesced and the partial last word
+//               carries into the next piece.  The chunk's word count and its
+//               tile's (kEncWarps chunks) total are recorded.
 //   k_enc_scan  one block per field: exclusive prefix of the tile totals, the
 //               section layout and the capacity check
-//   k_enc_pack  one block per tile: chunk word offsets (tile prefix + in-tile
-//               prefix), chunk table entries, MSB-first packing: pieces of 256
-//               symbols (8 per lane) are OR-ed into a per-warp shared-memory
-//               word buffer, full words go out coalesced and the partial last
-//               word carries into the next piece.  Every write is checked
-//               against the output capacity.
-__global__ void __launch_bounds__(kEncWarps * 32) k_enc_bits(const __grid_constant__ Batch<EncArgs> B) {
+//   k_enc_copy  one warp per chunk: word offset (tile prefix + in-tile prefix),
+//               chunk table entry, and the chunk's words copied from its slot
+//               into the stream.  Every write is checked against the output
+//               capacity.
+// The codes are read and looked up once; the packed stream (a fraction of
+// their bytes) is written twice and read once.
+__global__ void __launch_bounds__(kEncWarps * 32) k_enc_pack(const __grid_constant__ Batch<EncArgs> B) {
     const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
     const EncArgs& a = B.a[fld];
     const uint32_t t = blockIdx.x - B.off[fld];
     if (a.par->flags & (kFlagConstant | kFlagError)) return;
+    __shared__ uint32_t sbuf[kEncWarps][kPieceWords];
     __shared__ uint32_t s_words[kEncWarps];
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     const uint64_t c = (uint64_t)t * kEncWarps + wib;
-    const uint64_t beg = c * a.chunk;
-    const uint64_t end = min(beg + a.chunk, a.n);
-    const uint32_t bits = (c < a.nchunks) ? warp_chunk_bits(a.codes, a.enc, beg, end, lane) : 0u;
-    const uint32_t words = (bits + 31u) >> 5;
-    if (lane == 0) {
-        s_words[wib] = words;
-        if (c < a.nchunks) a.chunk_words[c] = words;
+    uint32_t wpos = 0;  // words of the chunk written so far
+    if (c < a.nchunks) {
+        const uint64_t beg = c * a.chunk;
+        const uint64_t end = min(beg + a.chunk, a.n);
+        uint32_t* dst = a.scratch + c * a.slot_words;
+        uint32_t* buf = sbuf[wib];
+        uint32_t carry = 0;  // partial word (bits from previous pieces)
+        uint32_t cbits = 0;  // valid bits in carry (< 32)
+        for (uint64_t pb = beg; pb < end; pb += 256u) {
+            uint32_t cw[8], cl[8];
+            uint32_t mybits = 0;
+            const uint64_t i = pb + 8u * lane;
+            if (i + 8 <= end) {
+                const uint4 v = *reinterpret_cast<const uint4*>(a.codes + i);
+                const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t e0 = __ldg(a.enc + (wv[k] & 0xffffu));
+                    const uint32_t e1 = __ldg(a.enc + (wv[k] >> 16));
+                    cw[2 * k] = e0 >> 5; cl[2 * k] = e0 & 31u;
+                    cw[2 * k + 1] = e1 >> 5; cl[2 * k + 1] = e1 & 31u;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const uint32_t e = (i + k < end) ? __ldg(a.enc + a.codes[i + k]) : 0u;
+                    cw[k] = e >> 5; cl[k] = e & 31u;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) mybits += cl[k];
+            uint32_t incl = mybits;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (uint32_t)o) incl += y;
+            }
+            const uint32_t piece_bits = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t nw = (cbits + piece_bits + 31u) >> 5;
+            for (uint32_t k = lane; k < nw; k += 32) buf[k] = 0u;
+            __syncwarp();
+            if (lane == 0) buf[0] = carry;
+            __syncwarp();
+            uint32_t bp = cbits + incl - mybits;  // bit position in buf
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const uint32_t l = cl[k];
+                if (l) {
+                    const uint32_t w = bp >> 5, o = bp & 31u;
+                    if (o + l <= 32u) {
+                        atomicOr(&buf[w], cw[k] << (32u - o - l));
+                    } else {
+                        atomicOr(&buf[w], cw[k] >> (o + l - 32u));
+                        atomicOr(&buf[w + 1], cw[k] << (64u - o - l));
+                    }
+                    bp += l;
+                }
+            }
+            __syncwarp();
+            const uint32_t tot = cbits + piece_bits;
+            const uint32_t full = tot >> 5;
+            for (uint32_t k = lane; k < full; k += 32) dst[wpos + k] = buf[k];
+            carry = (tot & 31u) ? buf[full] : 0u;
+            cbits = tot & 31u;
+            wpos += full;
+            __syncwarp();
+        }
+        if (cbits) {
+            if (lane == 0) dst[wpos] = carry;
+            wpos++;
+        }
+        if (lane == 0) a.chunk_words[c] = wpos;
     }
+    if (lane == 0) s_words[wib] = wpos;
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t sum = 0;
@@ -830,13 +890,12 @@ __global__ void __launch_bounds__(1024) k_enc_scan(const __grid_constant__ Batch
     }
 }
 
-__global__ void __launch_bounds__(kEncWarps * 32) k_enc_pack(const __grid_constant__ Batch<EncArgs> B) {
+__global__ void __launch_bounds__(kEncWarps * 32) k_enc_copy(const __grid_constant__ Batch<EncArgs> B) {
     const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
     const EncArgs& a = B.a[fld];
     const uint32_t t = blockIdx.x - B.off[fld];
     DevParams* par = a.par;
     if (par->flags & (kFlagConstant | kFlagError)) return;
-    __shared__ uint32_t sbuf[kEncWarps][kPieceWords];
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     const uint64_t c = (uint64_t)t * kEncWarps + wib;
     if (c >= a.nchunks) return;
@@ -851,72 +910,9 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_enc_pack(const __grid_consta
     if (lane == 0 && off_ct + 4ull * (c + 1) <= cap)
         reinterpret_cast<uint32_t*>(a.out + off_ct)[c] = wpos;
     if (off_st + 4ull * ((uint64_t)wpos + nwc) > cap) return;
-    const uint64_t beg = c * a.chunk;
-    const uint64_t end = min(beg + a.chunk, a.n);
-    uint32_t* stream = reinterpret_cast<uint32_t*>(a.out + off_st);
-    uint32_t* buf = sbuf[wib];
-    uint32_t carry = 0;  // partial word (bits from previous pieces)
-    uint32_t cbits = 0;  // valid bits in carry (< 32)
-    for (uint64_t pb = beg; pb < end; pb += 256u) {
-        uint32_t cw[8], cl[8];
-        uint32_t mybits = 0;
-        const uint64_t i = pb + 8u * lane;
-        if (i + 8 <= end) {
-            const uint4 v = *reinterpret_cast<const uint4*>(a.codes + i);
-            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t e0 = __ldg(a.enc + (wv[k] & 0xffffu));
-                const uint32_t e1 = __ldg(a.enc + (wv[k] >> 16));
-                cw[2 * k] = e0 >> 5; cl[2 * k] = e0 & 31u;
-                cw[2 * k + 1] = e1 >> 5; cl[2 * k + 1] = e1 & 31u;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const uint32_t e = (i + k < end) ? __ldg(a.enc + a.codes[i + k]) : 0u;
-                cw[k] = e >> 5; cl[k] = e & 31u;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 8; k++) mybits += cl[k];
-        uint32_t incl = mybits;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= (uint32_t)o) incl += y;
-        }
-        const uint32_t piece_bits = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t nw = (cbits + piece_bits + 31u) >> 5;
-        for (uint32_t k = lane; k < nw; k += 32) buf[k] = 0u;
-        __syncwarp();
-        if (lane == 0) buf[0] = carry;
-        __syncwarp();
-        uint32_t bp = cbits + incl - mybits;  // bit position in buf
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            const uint32_t l = cl[k];
-            if (l) {
-                const uint32_t w = bp >> 5, o = bp & 31u;
-                if (o + l <= 32u) {
-                    atomicOr(&buf[w], cw[k] << (32u - o - l));
-                } else {
-                    atomicOr(&buf[w], cw[k] >> (o + l - 32u));
-                    atomicOr(&buf[w + 1], cw[k] << (64u - o - l));
-                }
-                bp += l;
-            }
-        }
-        __syncwarp();
-        const uint32_t tot = cbits + piece_bits;
-        const uint32_t full = tot >> 5;
-        for (uint32_t k = lane; k < full; k += 32) stream[wpos + k] = buf[k];
-        carry = (tot & 31u) ? buf[full] : 0u;
-        cbits = tot & 31u;
-        wpos += full;
-        __syncwarp();
-    }
-    if (cbits && lane == 0) stream[wpos] = carry;
+    uint32_t* stream = reinterpret_cast<uint32_t*>(a.out + off_st) + wpos;
+    const uint32_t* __restrict__ src = a.scratch + c * a.slot_words;
+    for (uint32_t k = lane; k < nwc; k += 32) stream[k] = __ldcs(src + k);
 }
 
 // Outliers and verbatims in ascending index: rank = number of set bitmap bits
@@ -1254,6 +1250,8 @@ int launch_compress_batch(fpsnr_plan_s* const* P, const float* const* d_in, void
             e.chunk = (uint32_t)p->chunk;
             e.nchunks = p->nchunks;
             e.ntiles = (uint32_t)((p->nchunks + kEncWarps - 1) / kEncWarps);
+            e.slot_words = p->enc_slot_words;
+            e.scratch = w.enc_scratch;
             e.chunk_words = w.chunk_off;
             e.tile_sum = w.enc_tiles;
             b.a[f] = e;
@@ -1262,13 +1260,13 @@ int launch_compress_batch(fpsnr_plan_s* const* P, const float* const* d_in, void
         const uint32_t tot = batch_offsets(b, blocks);
         if (tot) {
             StageScope sc(prof, kStEncode, st);
-            k_enc_bits<<<tot, kEncWarps * 32, 0, st>>>(b);
+            k_enc_pack<<<tot, kEncWarps * 32, 0, st>>>(b);
             FP_LAUNCH_CHECK();
             for (int f = 0; f <= count; f++) b.off[f] = (uint32_t)f;
             k_enc_scan<<<count, 1024, 0, st>>>(b);
             FP_LAUNCH_CHECK();
             batch_offsets(b, blocks);
-            k_enc_pack<<<tot, kEncWarps * 32, 0, st>>>(b);
+            k_enc_copy<<<tot, kEncWarps * 32, 0, st>>>(b);
             FP_LAUNCH_CHECK();
         }
     }

@@ -767,6 +767,36 @@ __device__ __forceinline__ void band_row_residuals(const BandArgs& a, uint32_t r
     }
 }
 
+// Raw symbols of row r for columns [c0, c0 + 8G) as G 16-byte loads (VEC rows:
+// nx a multiple of 8); groups past the row end read nothing.
+template <int G>
+__device__ __forceinline__ void band_row_load(const BandArgs& a, uint32_t r, uint32_t c0, uint4 (&q)[G]) {
+    const uint64_t base = (uint64_t)r * a.nx;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        const uint32_t cg = c0 + 8u * g;
+        q[g] = cg < a.nx ? *reinterpret_cast<const uint4*>(a.syms + base + cg) : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// Residuals of row r from the raw symbols of band_row_load.
+template <int G>
+__device__ __forceinline__ void band_row_convert(const BandArgs& a, uint32_t r, uint32_t c0,
+                                                 const uint4 (&q)[G], uint32_t R,
+                                                 const uint2* __restrict__ ol, uint32_t no,
+                                                 uint32_t (&d)[8 * G]) {
+    const uint64_t base = (uint64_t)r * a.nx;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        const uint32_t cg = c0 + 8u * g;
+        const uint32_t v[8] = {q[g].x & 0xffffu, q[g].x >> 16, q[g].y & 0xffffu, q[g].y >> 16,
+                               q[g].z & 0xffffu, q[g].z >> 16, q[g].w & 0xffffu, q[g].w >> 16};
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            d[8 * g + k] = cg < a.nx ? residual_of(v[k], R, (uint32_t)(base + cg + k), ol, no, a.par) : 0u;
+    }
+}
+
 // one block per band: column sums of the band's residuals
 template <int G, bool VEC>
 __global__ void __launch_bounds__(256) k_band_sum(const __grid_constant__ Batch<BandArgs> B) {
@@ -862,11 +892,21 @@ __global__ void __launch_bounds__(256) k_band_scan(const __grid_constant__ Batch
         band_row_prefix<G>(col, sh);
     }
     const uint32_t r0 = band * a.tr, r1 = min(r0 + a.tr, a.rows);
+    const bool live = !cst && c0 < a.nx;
+    // VEC: the next row's symbols are loaded before this row's block scan
+    uint4 qn[G];
+    if (VEC && live && r0 < r1) band_row_load<G>(a, r0, c0, qn);
     for (uint32_t r = r0; r < r1; r++) {
         uint32_t d[8 * G];
-        if (cst || c0 >= a.nx) {
+        if (!live) {
 #pragma unroll
             for (int k = 0; k < 8 * G; k++) d[k] = 0u;
+        } else if (VEC) {
+            uint4 q[G];
+#pragma unroll
+            for (int g = 0; g < G; g++) q[g] = qn[g];
+            if (r + 1 < r1) band_row_load<G>(a, r + 1, c0, qn);
+            band_row_convert<G>(a, r, c0, q, R, ol, no, d);
         } else {
             band_row_residuals<G, VEC>(a, r, c0, R, ol, no, d);
         }
