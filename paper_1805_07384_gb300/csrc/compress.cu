@@ -813,20 +813,27 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_enc_pack(const __grid_consta
             __syncwarp();
             if (lane == 0) buf[0] = carry;
             __syncwarp();
-            uint32_t bp = cbits + incl - mybits;  // bit position in buf
+            // the lane's bits start at bit bp of buf: they are assembled in a
+            // 64-bit register (left-aligned, after bp % 32 bits of the word
+            // that belong to earlier lanes) and OR-ed in a word at a time
+            {
+                const uint32_t bp = cbits + incl - mybits;  // bit position in buf
+                uint32_t w = bp >> 5, nbit = bp & 31u;
+                unsigned long long acc = 0ull;
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const uint32_t l = cl[k];
-                if (l) {
-                    const uint32_t w = bp >> 5, o = bp & 31u;
-                    if (o + l <= 32u) {
-                        atomicOr(&buf[w], cw[k] << (32u - o - l));
-                    } else {
-                        atomicOr(&buf[w], cw[k] >> (o + l - 32u));
-                        atomicOr(&buf[w + 1], cw[k] << (64u - o - l));
+                for (int k = 0; k < 8; k++) {
+                    const uint32_t l = cl[k];
+                    // cw == 0 when l == 0, so the masked shift is harmless then
+                    acc |= (unsigned long long)cw[k] << ((64u - nbit - l) & 63u);
+                    nbit += l;
+                    if (nbit >= 32u) {
+                        atomicOr(&buf[w], (uint32_t)(acc >> 32));
+                        acc <<= 32;
+                        nbit -= 32u;
+                        w++;
                     }
-                    bp += l;
                 }
+                if (nbit > (bp & 31u) || (nbit && w > (bp >> 5))) atomicOr(&buf[w], (uint32_t)(acc >> 32));
             }
             __syncwarp();
             const uint32_t tot = cbits + piece_bits;
