@@ -81,8 +81,14 @@ __device__ void radix_pass(const unsigned long long* in, unsigned long long* out
     const uint32_t b0 = min(n, w * S), b1 = min(n, b0 + S);
     for (uint32_t d = lane; d < 256; d += 32) whist[w * 256 + d] = 0;
     __syncwarp();
-    for (uint32_t i = b0 + lane; i < b1; i += 32)
-        atomicAdd(&whist[w * 256 + (uint32_t)((in[i] >> shift) & mask)], 1u);
+    for (uint32_t i0 = b0 + lane; i0 < b1; i0 += 128) {
+        unsigned long long kk[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) kk[u] = i0 + 32u * u < b1 ? in[i0 + 32u * u] : 0ull;
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (i0 + 32u * u < b1) atomicAdd(&whist[w * 256 + (uint32_t)((kk[u] >> shift) & mask)], 1u);
+    }
     __syncthreads();
     uint32_t v[8], sum = 0;
 #pragma unroll
@@ -100,21 +106,38 @@ __device__ void radix_pass(const unsigned long long* in, unsigned long long* out
         ex += v[k];
     }
     __syncthreads();
-    for (uint32_t base = b0; base < b1; base += 32) {
-        const uint32_t i = base + lane;
-        const bool valid = i < b1;
-        const unsigned long long key = valid ? in[i] : 0ull;
-        const uint32_t d = valid ? (uint32_t)((key >> shift) & mask) : 0xffffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lanemask_lt());
-        uint32_t pos = 0;
-        if (valid) pos = whist[w * 256 + d] + rank;
-        __syncwarp();
-        if (valid) {
-            out[pos] = key;
-            if ((uint32_t)(__ffs(peers) - 1) == lane) whist[w * 256 + d] += __popc(peers);
+    for (uint32_t b4 = b0; b4 < b1; b4 += 128) {
+        // the keys of four groups of 32 are loaded before the first is placed
+        unsigned long long kk[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t i = b4 + 32u * u + lane;
+            kk[u] = i < b1 ? in[i] : 0ull;
         }
-        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t i = b4 + 32u * u + lane;
+            const bool valid = i < b1;
+            const unsigned long long key = kk[u];
+            const uint32_t d = valid ? (uint32_t)((key >> shift) & mask) : 0xffffu;
+            // lanes holding the same digit: one ballot per digit bit
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                const bool bit = (d >> b) & 1u;
+                const uint32_t bb = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bb : ~bb;
+            }
+            const uint32_t rank = __popc(peers & lanemask_lt());
+            uint32_t pos = 0;
+            if (valid) pos = whist[w * 256 + d] + rank;
+            __syncwarp();
+            if (valid) {
+                out[pos] = key;
+                if ((uint32_t)(__ffs(peers) - 1) == lane) whist[w * 256 + d] += __popc(peers);
+            }
+            __syncwarp();
+        }
     }
     __syncthreads();
 }
@@ -136,6 +159,38 @@ __device__ __forceinline__ uint32_t warp_first_false(uint32_t lo, uint32_t hi, P
     const uint32_t idx = lo + lane;
     const bool t = idx < hi && pred(idx);
     return lo + __popc(__ballot_sync(0xffffffffu, t));
+}
+
+// Two independent warp_first_false searches advanced in lockstep, so that the
+// probes of both are in flight together.
+template <class P1, class P2>
+__device__ __forceinline__ void warp_first_false2(uint32_t lo1, uint32_t hi1, P1 pred1, uint32_t lo2,
+                                                  uint32_t hi2, P2 pred2, uint32_t& r1, uint32_t& r2) {
+    const uint32_t lane = threadIdx.x & 31u;
+    while (hi1 - lo1 > 32 || hi2 - lo2 > 32) {
+        const bool a1 = hi1 - lo1 > 32, a2 = hi2 - lo2 > 32;  // warp-uniform
+        const uint32_t step1 = (hi1 - lo1 + 31) / 32, step2 = (hi2 - lo2 + 31) / 32;
+        const uint32_t q1 = lo1 + (lane + 1) * step1 - 1, q2 = lo2 + (lane + 1) * step2 - 1;
+        const bool t1 = a1 && q1 < hi1 && pred1(q1);
+        const bool t2 = a2 && q2 < hi2 && pred2(q2);
+        const uint32_t k1 = __popc(__ballot_sync(0xffffffffu, t1));
+        const uint32_t k2 = __popc(__ballot_sync(0xffffffffu, t2));
+        if (a1) {
+            const uint32_t nlo = lo1 + k1 * step1;
+            hi1 = min(hi1, nlo + step1);
+            lo1 = nlo;
+        }
+        if (a2) {
+            const uint32_t nlo = lo2 + k2 * step2;
+            hi2 = min(hi2, nlo + step2);
+            lo2 = nlo;
+        }
+    }
+    const uint32_t i1 = lo1 + lane, i2 = lo2 + lane;
+    const bool t1 = i1 < hi1 && pred1(i1);
+    const bool t2 = i2 < hi2 && pred2(i2);
+    r1 = lo1 + __popc(__ballot_sync(0xffffffffu, t1));
+    r2 = lo2 + __popc(__ballot_sync(0xffffffffu, t2));
 }
 
 __global__ void __launch_bounds__(1024, 1) k_codebook(const __grid_constant__ Batch<CBArgs> B) {
@@ -188,12 +243,22 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(const __grid_constant__ Ba
     if (tid == 0 && c0 > 0) a.list[0] = (unsigned long long)c0 << 16;
     const uint32_t lo = par->sym_lo, hi = min(par->sym_hi, a.nsym - 1);
     if (lo <= hi) {
+        // 4 consecutive bins per thread per pass (coalesced); the next pass's
+        // bins are loaded before this pass's scan
+        auto load4 = [&](uint32_t s0, uint32_t (&c)[4]) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) c[k] = (s0 + k <= hi) ? a.hist[s0 + k] : 0u;
+        };
+        uint32_t cn[4];
+        load4(lo + 4 * tid, cn);
         for (uint32_t base = lo; base <= hi; base += 4 * blockDim.x) {
             const uint32_t s0 = base + 4 * tid;
             uint32_t c[4], cnt = 0;
 #pragma unroll
+            for (int k = 0; k < 4; k++) c[k] = cn[k];
+            if (base + 4 * blockDim.x <= hi) load4(s0 + 4 * blockDim.x, cn);
+#pragma unroll
             for (int k = 0; k < 4; k++) {
-                c[k] = (s0 + k <= hi) ? a.hist[s0 + k] : 0u;
                 cnt += c[k] > 0;
                 maxc = max(maxc, c[k]);
             }
@@ -263,10 +328,11 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(const __grid_constant__ Ba
                         }
                     }
                     const uint32_t w1 = w[0] + w[1];
-                    const uint32_t kl =
-                        warp_first_false(lh, n, [&](uint32_t x) { return key_w(leaves[x]) <= w1; }) - lh;
-                    const uint32_t ki =
-                        warp_first_false(ih, it, [&](uint32_t x) { return iq[x] <= w1; }) - ih;
+                    uint32_t el, ei;
+                    warp_first_false2(
+                        lh, n, [&](uint32_t x) { return key_w(leaves[x]) <= w1; }, ih, it,
+                        [&](uint32_t x) { return iq[x] <= w1; }, el, ei);
+                    const uint32_t kl = el - lh, ki = ei - ih;
                     const uint32_t m = (kl + ki) >> 1;
                     // leaves among the first 2m nodes (merge path, leaf first on ties)
                     const uint32_t d = 2 * m;
@@ -330,8 +396,14 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(const __grid_constant__ Ba
                 __syncthreads();
             }
             uint32_t mx = 0;
-            for (uint32_t i = tid; i < n; i += blockDim.x)
-                mx = max(mx, (uint32_t)depth8[a.parent[i] - n] + 1);
+            for (uint32_t i0 = tid; i0 < n; i0 += 4 * blockDim.x) {
+                uint32_t pp[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) pp[u] = i0 + u * blockDim.x < n ? a.parent[i0 + u * blockDim.x] : 0u;
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (i0 + u * blockDim.x < n) mx = max(mx, (uint32_t)depth8[pp[u] - n] + 1);
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             if (tid == 0) s_max = 0;
@@ -339,8 +411,18 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(const __grid_constant__ Ba
             if ((tid & 31) == 0) atomicMax(&s_max, mx);
             __syncthreads();
             if (s_max <= (uint32_t)a.lmax) {
-                for (uint32_t i = tid; i < n; i += blockDim.x)
-                    a.len_sym[(uint32_t)(leaves[i] & 0xffffu)] = (uint8_t)(depth8[a.parent[i] - n] + 1);
+                for (uint32_t i0 = tid; i0 < n; i0 += 4 * blockDim.x) {
+                    uint32_t pp[4], ss[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const uint32_t i = i0 + u * blockDim.x;
+                        pp[u] = i < n ? a.parent[i] : 0u;
+                        ss[u] = i < n ? (uint32_t)(leaves[i] & 0xffffu) : 0u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if (i0 + u * blockDim.x < n) a.len_sym[ss[u]] = (uint8_t)(depth8[pp[u] - n] + 1);
+                }
                 break;
             }
             // too long: halve every count (in the symbol-ordered list) and rebuild
@@ -356,16 +438,32 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(const __grid_constant__ Ba
     __syncthreads();
 
     // ---- canonical order: stable sort of the symbol-ordered list by length ----
-    for (uint32_t i = tid; i < n; i += blockDim.x) {
-        const uint32_t s = (uint32_t)(a.list[i] & 0xffffu);
-        a.buf2[i] = ((unsigned long long)a.len_sym[s] << 16) | s;
+    for (uint32_t i0 = tid; i0 < n; i0 += 4 * blockDim.x) {
+        uint32_t ss[4], ll[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t i = i0 + u * blockDim.x;
+            ss[u] = i < n ? (uint32_t)(a.list[i] & 0xffffu) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) ll[u] = i0 + u * blockDim.x < n ? a.len_sym[ss[u]] : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (i0 + u * blockDim.x < n) a.buf2[i0 + u * blockDim.x] = ((unsigned long long)ll[u] << 16) | ss[u];
     }
     if (tid < 32) s_cnt[tid] = 0;
     __syncthreads();
     if (n <= kRankMax) rank_sort(a.buf2, a.buf1, n, kbuf);
     else radix_pass(a.buf2, a.buf1, n, 16, 31u, whist, sh);
     const unsigned long long* canon = a.buf1;
-    for (uint32_t i = tid; i < n; i += blockDim.x) atomicAdd(&s_cnt[(uint32_t)(canon[i] >> 16)], 1u);
+    for (uint32_t i0 = tid; i0 < n; i0 += 4 * blockDim.x) {
+        unsigned long long kk[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) kk[u] = i0 + u * blockDim.x < n ? canon[i0 + u * blockDim.x] : 0ull;
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (i0 + u * blockDim.x < n) atomicAdd(&s_cnt[(uint32_t)(kk[u] >> 16)], 1u);
+    }
     __syncthreads();
     if (tid == 0) {
         uint32_t code = 0, idx = 0;
@@ -381,11 +479,20 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(const __grid_constant__ Ba
     __syncthreads();
     const bool write_cb = kHeaderBytes + 4ull * n <= par->cap;
     uint32_t* cb = reinterpret_cast<uint32_t*>(a.out + kHeaderBytes);
-    for (uint32_t i = tid; i < n; i += blockDim.x) {
-        const uint32_t e = (uint32_t)canon[i];
-        const uint32_t l = e >> 16, s = e & 0xffffu;
-        a.enc[s] = ((s_fc[l] + (i - s_fi[l])) << 5) | l;
-        if (write_cb) cb[i] = e;
+    for (uint32_t i0 = tid; i0 < n; i0 += 4 * blockDim.x) {
+        uint32_t ee[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) ee[u] = i0 + u * blockDim.x < n ? (uint32_t)canon[i0 + u * blockDim.x] : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t i = i0 + u * blockDim.x;
+            if (i < n) {
+                const uint32_t e = ee[u];
+                const uint32_t l = e >> 16, s = e & 0xffffu;
+                a.enc[s] = ((s_fc[l] + (i - s_fi[l])) << 5) | l;
+                if (write_cb) cb[i] = e;
+            }
+        }
     }
 }
 
