@@ -9,9 +9,10 @@
 //                  staging + exact squared-error partials (Eq. 4)
 //   k_rank_popc    order-preserving compaction ranks for outliers/verbatims
 //   (k_codebook    Huffman code, huffman.cu)
-//   k_chunk_bits   coded bits per chunk
-//   k_scan_chunks  chunk word offsets and section layout
-//   k_pack         warp-cooperative MSB-first bit packing (SZ step 2, Sec. II-A)
+//   k_enc_pack     warp-cooperative MSB-first bit packing of every chunk into
+//                  its own scratch slot (SZ step 2, Sec. II-A)
+//   k_enc_scan     chunk word offsets and section layout
+//   k_enc_copy     chunk words placed in the stream, chunk table
 //   k_emit         outliers and verbatims written in index order
 //   k_finalize     header, size, statistics
 #include <float.h>
@@ -601,30 +602,36 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * TY,
             // outliers and verbatims are rare: one vote per row decides whether any
             // lane of the warp needs the order-preserving staging below
             if (__any_sync(0xffffffffu, rare)) {
+                // one slot reservation per list for the whole warp row: outlier
+                // count in the low half, verbatim count in the high half
+                uint32_t mine = 0;
+#pragma unroll
+                for (int i = 0; i < NP; i++) mine += (ol[i] ? 1u : 0u) + (vb[i] ? 0x10000u : 0u);
+                uint32_t incl = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= (uint32_t)o) incl += y;
+                }
+                const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+                uint32_t bo = 0, bv = 0;
+                if (lane == 0) {
+                    if (tot & 0xffffu) bo = atomicAdd(&par->n_out, tot & 0xffffu);
+                    if (tot >> 16) bv = atomicAdd(&par->n_vb, tot >> 16);
+                }
+                const uint32_t ex = incl - mine;
+                uint32_t so = __shfl_sync(0xffffffffu, bo, 0) + (ex & 0xffffu);
+                uint32_t sv = __shfl_sync(0xffffffffu, bv, 0) + (ex >> 16);
 #pragma unroll
                 for (int i = 0; i < NP; i++) {
                     const uint32_t gi = (uint32_t)rowbase + xb + 128u * (i / 4) + (i % 4);
-                    const uint32_t mo = __ballot_sync(0xffffffffu, ol[i]);
-                    if (mo) {
-                        uint32_t leader = __ffs(mo) - 1, base = 0;
-                        if (lane == leader) base = atomicAdd(&par->n_out, __popc(mo));
-                        base = __shfl_sync(0xffffffffu, base, leader);
-                        if (ol[i]) {
-                            const uint32_t slot = base + __popc(mo & lanemask_lt());
-                            a.stage_out[slot] = make_uint2(gi, (uint32_t)d[i]);
-                            atomicOr(&a.bm_out[gi >> 5], 1u << (gi & 31u));
-                        }
+                    if (ol[i]) {
+                        a.stage_out[so++] = make_uint2(gi, (uint32_t)d[i]);
+                        atomicOr(&a.bm_out[gi >> 5], 1u << (gi & 31u));
                     }
-                    const uint32_t mv = __ballot_sync(0xffffffffu, vb[i]);
-                    if (mv) {
-                        uint32_t leader = __ffs(mv) - 1, base = 0;
-                        if (lane == leader) base = atomicAdd(&par->n_vb, __popc(mv));
-                        base = __shfl_sync(0xffffffffu, base, leader);
-                        if (vb[i]) {
-                            const uint32_t slot = base + __popc(mv & lanemask_lt());
-                            a.stage_vb[slot] = make_uint2(gi, __float_as_uint(cur.v[i]));
-                            atomicOr(&a.bm_vb[gi >> 5], 1u << (gi & 31u));
-                        }
+                    if (vb[i]) {
+                        a.stage_vb[sv++] = make_uint2(gi, __float_as_uint(cur.v[i]));
+                        atomicOr(&a.bm_vb[gi >> 5], 1u << (gi & 31u));
                     }
                 }
             }
@@ -1109,10 +1116,12 @@ static void launch_pq_variant(int mode, int tx, Batch<PQArgs>& b, uint32_t block
     else launch_pq_t<2, 1024, 1, 2>(b, blocks, vec, st);
 }
 
-// Small grid-stride kernels (emit, finalize) use this many blocks per field.
+// Small grid-stride kernels (emit, finalize) use this many blocks per field:
+// about four per SM over the batch (the outlier / verbatim lists can hold a
+// tenth of the points at 120 dB).
 static uint32_t small_blocks(const fpsnr_plan_s* p, int count) {
-    const uint32_t g = (uint32_t)std::max(1, p->sm_count / std::max(1, count));
-    return std::min<uint32_t>(g, 64);
+    const uint32_t g = (uint32_t)std::max(1, 4 * p->sm_count / std::max(1, count));
+    return std::min<uint32_t>(g, 256);
 }
 
 int launch_compress_batch(fpsnr_plan_s* const* P, const float* const* d_in, void* const* d_out,

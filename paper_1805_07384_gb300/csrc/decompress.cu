@@ -20,9 +20,13 @@
 //                     between row segments; the last pass dequantizes
 //   k_patch         verbatim points restored
 //
-// Symbol 0 marks an outlier: every pass that turns symbols into residuals
-// finds its residual in the outlier list (sorted by point index) by binary
-// search.  The prefix sums run in modular uint32 arithmetic: intermediate
+// Symbol 0 marks an outlier.  After decoding, k_out_scatter checks the outlier
+// list against the symbols (strictly increasing indices, each at a symbol 0,
+// as many entries as symbols 0) and writes every outlier's residual at its
+// index in the caller's output buffer, which holds nothing else until the
+// last pass writes the floats; every pass that turns symbols into residuals
+// then reads an outlier's residual with one load, before the same thread
+// writes that point.  The prefix sums run in modular uint32 arithmetic: intermediate
 // partial sums may leave the int32 range, but every final lattice value is in
 // [0, 2^31), so the modular result is exact.
 #include <algorithm>
@@ -72,6 +76,7 @@ __global__ void __launch_bounds__(1024) k_dsetup(const __grid_constant__ Batch<D
     const uint32_t tid = threadIdx.x;
     // the scans' tile counters start every call at zero (see k_scan_contig)
     if (tid < 8) lb_ctr[tid] = 0;
+    if (tid == 0) par->d_zero = 0u;
     if (tid == 0) {
         const uint32_t e = (par->dec_epoch + 1) & 0x3fffffffu;
         par->dec_epoch = e ? e : 1u;
@@ -358,14 +363,23 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_decode(const __grid
     };
     uint16_t* __restrict__ dst = A.out + beg;
     const uint32_t cnt8 = cnt & ~7u;
+    uint32_t zeros2 = 0u;  // symbols 0, two 16-bit counters (at most 128 each per half-word)
     for (uint32_t i = 0; i < cnt8; i += 8) {
         uint32_t s[8];
 #pragma unroll
         for (int k = 0; k < 8; k++) s[k] = one();
-        *reinterpret_cast<uint4*>(dst + i) =
-            make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16), s[6] | (s[7] << 16));
+        const uint4 w = make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16),
+                                   s[6] | (s[7] << 16));
+        *reinterpret_cast<uint4*>(dst + i) = w;
+        zeros2 += __vseteq2(w.x, 0u) + __vseteq2(w.y, 0u) + __vseteq2(w.z, 0u) + __vseteq2(w.w, 0u);
     }
-    for (uint32_t i = cnt8; i < cnt; i++) dst[i] = (uint16_t)one();
+    uint32_t zeros = (zeros2 & 0xffffu) + (zeros2 >> 16);
+    for (uint32_t i = cnt8; i < cnt; i++) {
+        const uint32_t s = one();
+        dst[i] = (uint16_t)s;
+        zeros += s == 0u;
+    }
+    if (zeros) atomicAdd(&par->d_zero, zeros);
     // copies still in flight land before the block's shared memory is released
     cp_async_wait<0>();
     // bits consumed = appended - still valid; the chunk owns (w1 - w0) words
@@ -374,21 +388,10 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_decode(const __grid
 }
 
 // Residual of point `idx` from its symbol: code - R, or for symbol 0 (an
-// outlier) the residual stored for idx in the outlier list, which is sorted by
-// point index.  A missing entry means the blob is corrupt.
+// outlier) the residual k_out_scatter placed at idx.
 __device__ __forceinline__ uint32_t residual_of(uint32_t code, uint32_t R, uint32_t idx,
-                                                const uint2* __restrict__ ol, uint32_t no,
-                                                DevParams* par) {
-    if (code) return code - R;
-    uint32_t lo = 0u, hi = no;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(&ol[mid].x) < idx) lo = mid + 1u;
-        else hi = mid;
-    }
-    if (lo < no && __ldg(&ol[lo].x) == idx) return __ldg(&ol[lo].y);
-    set_error(par, FPSNR_ECORRUPT);
-    return 0u;
+                                                const uint32_t* __restrict__ od) {
+    return code ? code - R : od[idx];
 }
 
 // Loads IPT consecutive 16-bit values (IPT a multiple of 4; p 8-byte aligned,
@@ -432,6 +435,37 @@ __global__ void __launch_bounds__(256) k_patch(const __grid_constant__ Batch<Sma
         const uint2 e = vl[i];
         if (e.x >= A.n) { set_error(par, FPSNR_ECORRUPT); return; }
         out[e.x] = __uint_as_float(e.y);
+    }
+}
+
+struct ScatterArgs {
+    DevParams* par;
+    const uint8_t* blob;
+    const uint16_t* syms;  // decoded symbols
+    uint32_t* od;          // the caller's output buffer: outlier residuals at their indices
+    uint64_t n;
+    uint32_t G;            // blocks per field
+};
+
+// Outlier residuals placed at their point indices, after checking the list
+// against the decoded symbols; any mismatch means the blob is corrupt.
+__global__ void __launch_bounds__(256) k_out_scatter(const __grid_constant__ Batch<ScatterArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const ScatterArgs& A = B.a[fld];
+    const uint32_t bid = blockIdx.x - B.off[fld];
+    DevParams* par = A.par;
+    if (par->flags & (kFlagError | kFlagConstant)) return;
+    const uint32_t no = par->d_nout;
+    if (bid == 0 && threadIdx.x == 0 && par->d_zero != no) set_error(par, FPSNR_ECORRUPT);
+    const uint2* __restrict__ ol = reinterpret_cast<const uint2*>(A.blob + par->off_ou);
+    for (uint32_t i = bid * blockDim.x + threadIdx.x; i < no; i += A.G * blockDim.x) {
+        const uint2 e = ol[i];
+        const bool ok = e.x < A.n && (i + 1 == no || e.x < ol[i + 1].x) && A.syms[e.x] == 0;
+        if (!ok) {
+            set_error(par, FPSNR_ECORRUPT);
+            return;
+        }
+        A.od[e.x] = e.y;
     }
 }
 
@@ -493,18 +527,17 @@ __global__ void __launch_bounds__(256) k_scan_contig(const __grid_constant__ Bat
 #pragma unroll
             for (int k = 0; k < IPT; k++) v[k] = 0u;
         } else {
-            const uint32_t R = par->d_radius, no = par->d_nout;
-            const uint2* __restrict__ ol = reinterpret_cast<const uint2*>(a.blob + par->off_ou);
+            const uint32_t R = par->d_radius;
+            const uint32_t* od = a.data;  // outlier residuals, read before this thread writes
             if (VEC && c0 + IPT <= W) {
                 load_syms<IPT>(a.syms + rbase + c0, v);
 #pragma unroll
-                for (int k = 0; k < IPT; k++)
-                    v[k] = residual_of(v[k], R, (uint32_t)(rbase + c0 + k), ol, no, par);
+                for (int k = 0; k < IPT; k++) v[k] = residual_of(v[k], R, (uint32_t)(rbase + c0 + k), od);
             } else {
 #pragma unroll
                 for (int k = 0; k < IPT; k++)
                     v[k] = (c0 + k < W) ? residual_of(a.syms[rbase + c0 + k], R,
-                                                      (uint32_t)(rbase + c0 + k), ol, no, par)
+                                                      (uint32_t)(rbase + c0 + k), od)
                                         : 0u;
             }
         }
@@ -738,8 +771,8 @@ struct BandArgs {
 // Residuals of columns c0 .. c0 + 8G - 1 of row r (zero past the row end).
 template <int G, bool VEC>
 __device__ __forceinline__ void band_row_residuals(const BandArgs& a, uint32_t r, uint32_t c0,
-                                                   uint32_t R, const uint2* __restrict__ ol,
-                                                   uint32_t no, uint32_t (&d)[8 * G]) {
+                                                   uint32_t R, const uint32_t* __restrict__ od,
+                                                   uint32_t (&d)[8 * G]) {
     const uint64_t base = (uint64_t)r * a.nx;
     if (VEC) {
 #pragma unroll
@@ -750,7 +783,7 @@ __device__ __forceinline__ void band_row_residuals(const BandArgs& a, uint32_t r
                 load_syms<8>(a.syms + base + cg, v);
 #pragma unroll
                 for (int k = 0; k < 8; k++)
-                    v[k] = residual_of(v[k], R, (uint32_t)(base + cg + k), ol, no, a.par);
+                    v[k] = residual_of(v[k], R, (uint32_t)(base + cg + k), od);
             } else {
 #pragma unroll
                 for (int k = 0; k < 8; k++) v[k] = 0u;
@@ -762,7 +795,7 @@ __device__ __forceinline__ void band_row_residuals(const BandArgs& a, uint32_t r
 #pragma unroll
         for (int k = 0; k < 8 * G; k++)
             d[k] = (c0 + k < a.nx) ? residual_of(a.syms[base + c0 + k], R,
-                                                 (uint32_t)(base + c0 + k), ol, no, a.par)
+                                                 (uint32_t)(base + c0 + k), od)
                                    : 0u;
     }
 }
@@ -783,7 +816,7 @@ __device__ __forceinline__ void band_row_load(const BandArgs& a, uint32_t r, uin
 template <int G>
 __device__ __forceinline__ void band_row_convert(const BandArgs& a, uint32_t r, uint32_t c0,
                                                  const uint4 (&q)[G], uint32_t R,
-                                                 const uint2* __restrict__ ol, uint32_t no,
+                                                 const uint32_t* __restrict__ od,
                                                  uint32_t (&d)[8 * G]) {
     const uint64_t base = (uint64_t)r * a.nx;
 #pragma unroll
@@ -793,7 +826,7 @@ __device__ __forceinline__ void band_row_convert(const BandArgs& a, uint32_t r, 
                                q[g].z & 0xffffu, q[g].z >> 16, q[g].w & 0xffffu, q[g].w >> 16};
 #pragma unroll
         for (int k = 0; k < 8; k++)
-            d[8 * g + k] = cg < a.nx ? residual_of(v[k], R, (uint32_t)(base + cg + k), ol, no, a.par) : 0u;
+            d[8 * g + k] = cg < a.nx ? residual_of(v[k], R, (uint32_t)(base + cg + k), od) : 0u;
     }
 }
 
@@ -812,12 +845,12 @@ __global__ void __launch_bounds__(256) k_band_sum(const __grid_constant__ Batch<
 #pragma unroll
     for (int k = 0; k < 8 * G; k++) acc[k] = 0u;
     if (!(flags & kFlagConstant)) {
-        const uint32_t R = par->d_radius, no = par->d_nout;
-        const uint2* __restrict__ ol = reinterpret_cast<const uint2*>(a.blob + par->off_ou);
+        const uint32_t R = par->d_radius;
+        const uint32_t* __restrict__ od = reinterpret_cast<const uint32_t*>(a.out);
         const uint32_t r0 = band * a.tr, r1 = min(r0 + a.tr, a.rows);
         for (uint32_t r = r0; r < r1; r++) {
             uint32_t d[8 * G];
-            band_row_residuals<G, VEC>(a, r, c0, R, ol, no, d);
+            band_row_residuals<G, VEC>(a, r, c0, R, od, d);
 #pragma unroll
             for (int k = 0; k < 8 * G; k++) acc[k] += d[k];
         }
@@ -881,8 +914,9 @@ __global__ void __launch_bounds__(256) k_band_scan(const __grid_constant__ Batch
     const bool cst = (flags & kFlagConstant) != 0;
     const uint32_t c0 = threadIdx.x * 8u * G;
     const float s = par->s, xmin = par->xmin;
-    const uint32_t R = par->d_radius, no = par->d_nout;
-    const uint2* __restrict__ ol = reinterpret_cast<const uint2*>(a.blob + par->off_ou);
+    const uint32_t R = par->d_radius;
+    // outlier residuals, each read before this thread writes the point's float
+    const uint32_t* od = reinterpret_cast<const uint32_t*>(a.out);
     // S(r0 - 1, .) = prefix along x of the carry row
     uint32_t col[8 * G];
     {
@@ -906,9 +940,9 @@ __global__ void __launch_bounds__(256) k_band_scan(const __grid_constant__ Batch
 #pragma unroll
             for (int g = 0; g < G; g++) q[g] = qn[g];
             if (r + 1 < r1) band_row_load<G>(a, r + 1, c0, qn);
-            band_row_convert<G>(a, r, c0, q, R, ol, no, d);
+            band_row_convert<G>(a, r, c0, q, R, od, d);
         } else {
-            band_row_residuals<G, VEC>(a, r, c0, R, ol, no, d);
+            band_row_residuals<G, VEC>(a, r, c0, R, od, d);
         }
         band_row_prefix<G>(d, sh);
         float f[8 * G];
@@ -999,9 +1033,11 @@ int decode_prepare(const fpsnr_plan_s*) {
     return FPSNR_OK;
 }
 
+// Grid-stride kernels over the outlier / verbatim lists (which can hold a
+// tenth of the points at 120 dB): about four blocks per SM over the batch.
 static uint32_t small_blocks_d(const fpsnr_plan_s* p, int count) {
-    const int g = std::max(1, p->sm_count / std::max(1, count));
-    return (uint32_t)std::min(g, 64);
+    const int g = std::max(1, 4 * p->sm_count / std::max(1, count));
+    return (uint32_t)std::min(g, 256);
 }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -1066,6 +1102,22 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
             if (T == 128) k_decode<128><<<tot, 128, dec_smem(128), st>>>(b);
             else if (T == 256) k_decode<256><<<tot, 256, dec_smem(256), st>>>(b);
             else k_decode<512><<<tot, 512, dec_smem(512), st>>>(b);
+            if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
+            // outlier residuals into the output buffers (checked against the symbols)
+            Batch<ScatterArgs> sa;
+            sa.count = 0;
+            uint32_t sblocks[kMaxBatch];
+            for (int f = 0; f < count; f++) {
+                const fpsnr_plan_s* p = P[f];
+                if (p->n == 0) continue;
+                const uint32_t g = small_blocks_d(p, count);
+                sblocks[sa.count] = g;
+                sa.a[sa.count] = ScatterArgs{p->w.par, reinterpret_cast<const uint8_t*>(d_blob[f]),
+                                             p->w.codes, reinterpret_cast<uint32_t*>(d_out[f]), p->n, g};
+                sa.count++;
+            }
+            const uint32_t stot = batch_offsets(sa, sblocks);
+            if (stot) k_out_scatter<<<stot, 256, 0, st>>>(sa);
             if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
         }
     }
