@@ -54,7 +54,7 @@ struct DevParams {
     uint64_t off_cb, off_ct, off_st, off_ou, off_vb, total;
     // decompression: header fields of the blob being decoded
     uint32_t d_radius, d_chunk, d_lmax, d_nsym, d_nchunks, d_words, d_nout, d_nvb;
-    uint32_t d_zero;  // decoded symbols equal to 0 (outliers), counted by the decoder
+    uint32_t d_zero;  // symbols 0 (outliers) met by the first residual pass
     uint32_t d_count[32], d_first_code[32], d_first_index[32];
 };
 

@@ -21,12 +21,13 @@
 //   k_patch         verbatim points restored
 //
 // Symbol 0 marks an outlier.  After decoding, k_out_scatter checks the outlier
-// list against the symbols (strictly increasing indices, each at a symbol 0,
-// as many entries as symbols 0) and writes every outlier's residual at its
-// index in the caller's output buffer, which holds nothing else until the
-// last pass writes the floats; every pass that turns symbols into residuals
-// then reads an outlier's residual with one load, before the same thread
-// writes that point.  The prefix sums run in modular uint32 arithmetic: intermediate
+// list against the symbols (strictly increasing indices, each at a symbol 0)
+// and writes every outlier's residual at its index in the caller's output
+// buffer, which holds nothing else until the last pass writes the floats;
+// every pass that turns symbols into residuals then reads an outlier's
+// residual with one load, before the same thread writes that point.  The
+// first such pass counts the symbols 0 and k_patch checks that there are as
+// many as outliers.  The prefix sums run in modular uint32 arithmetic: intermediate
 // partial sums may leave the int32 range, but every final lattice value is in
 // [0, 2^31), so the modular result is exact.
 #include <algorithm>
@@ -363,23 +364,14 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_decode(const __grid
     };
     uint16_t* __restrict__ dst = A.out + beg;
     const uint32_t cnt8 = cnt & ~7u;
-    uint32_t zeros2 = 0u;  // symbols 0, two 16-bit counters (at most 128 each per half-word)
     for (uint32_t i = 0; i < cnt8; i += 8) {
         uint32_t s[8];
 #pragma unroll
         for (int k = 0; k < 8; k++) s[k] = one();
-        const uint4 w = make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16),
-                                   s[6] | (s[7] << 16));
-        *reinterpret_cast<uint4*>(dst + i) = w;
-        zeros2 += __vseteq2(w.x, 0u) + __vseteq2(w.y, 0u) + __vseteq2(w.z, 0u) + __vseteq2(w.w, 0u);
+        *reinterpret_cast<uint4*>(dst + i) =
+            make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16), s[6] | (s[7] << 16));
     }
-    uint32_t zeros = (zeros2 & 0xffffu) + (zeros2 >> 16);
-    for (uint32_t i = cnt8; i < cnt; i++) {
-        const uint32_t s = one();
-        dst[i] = (uint16_t)s;
-        zeros += s == 0u;
-    }
-    if (zeros) atomicAdd(&par->d_zero, zeros);
+    for (uint32_t i = cnt8; i < cnt; i++) dst[i] = (uint16_t)one();
     // copies still in flight land before the block's shared memory is released
     cp_async_wait<0>();
     // bits consumed = appended - still valid; the chunk owns (w1 - w0) words
@@ -428,6 +420,8 @@ __global__ void __launch_bounds__(256) k_patch(const __grid_constant__ Batch<Sma
     const uint32_t bid = blockIdx.x - B.off[fld];
     DevParams* par = A.par;
     if (par->flags & kFlagError) return;
+    // every symbol 0 had an outlier entry: as many of them as entries
+    if (bid == 0 && threadIdx.x == 0 && par->d_zero != par->d_nout) set_error(par, FPSNR_ECORRUPT);
     const uint32_t nv = par->d_nvb;
     const uint2* vl = reinterpret_cast<const uint2*>(A.blob + par->off_vb);
     float* out = reinterpret_cast<float*>(A.out);
@@ -456,7 +450,6 @@ __global__ void __launch_bounds__(256) k_out_scatter(const __grid_constant__ Bat
     DevParams* par = A.par;
     if (par->flags & (kFlagError | kFlagConstant)) return;
     const uint32_t no = par->d_nout;
-    if (bid == 0 && threadIdx.x == 0 && par->d_zero != no) set_error(par, FPSNR_ECORRUPT);
     const uint2* __restrict__ ol = reinterpret_cast<const uint2*>(A.blob + par->off_ou);
     for (uint32_t i = bid * blockDim.x + threadIdx.x; i < no; i += A.G * blockDim.x) {
         const uint2 e = ol[i];
@@ -529,17 +522,23 @@ __global__ void __launch_bounds__(256) k_scan_contig(const __grid_constant__ Bat
         } else {
             const uint32_t R = par->d_radius;
             const uint32_t* od = a.data;  // outlier residuals, read before this thread writes
+            uint32_t nzero = 0;           // symbols 0, checked against the list by k_patch
             if (VEC && c0 + IPT <= W) {
                 load_syms<IPT>(a.syms + rbase + c0, v);
 #pragma unroll
-                for (int k = 0; k < IPT; k++) v[k] = residual_of(v[k], R, (uint32_t)(rbase + c0 + k), od);
+                for (int k = 0; k < IPT; k++) {
+                    nzero += v[k] == 0u;
+                    v[k] = residual_of(v[k], R, (uint32_t)(rbase + c0 + k), od);
+                }
             } else {
 #pragma unroll
-                for (int k = 0; k < IPT; k++)
-                    v[k] = (c0 + k < W) ? residual_of(a.syms[rbase + c0 + k], R,
-                                                      (uint32_t)(rbase + c0 + k), od)
-                                        : 0u;
+                for (int k = 0; k < IPT; k++) {
+                    const uint32_t sym = (c0 + k < W) ? a.syms[rbase + c0 + k] : 1u;
+                    nzero += sym == 0u;
+                    v[k] = (c0 + k < W) ? residual_of(sym, R, (uint32_t)(rbase + c0 + k), od) : 0u;
+                }
             }
+            if (nzero) atomicAdd(&par->d_zero, nzero);
         }
     } else if (VEC && c0 + IPT <= W) {
 #pragma unroll
@@ -772,7 +771,7 @@ struct BandArgs {
 template <int G, bool VEC>
 __device__ __forceinline__ void band_row_residuals(const BandArgs& a, uint32_t r, uint32_t c0,
                                                    uint32_t R, const uint32_t* __restrict__ od,
-                                                   uint32_t (&d)[8 * G]) {
+                                                   uint32_t (&d)[8 * G], uint32_t& nzero) {
     const uint64_t base = (uint64_t)r * a.nx;
     if (VEC) {
 #pragma unroll
@@ -782,8 +781,10 @@ __device__ __forceinline__ void band_row_residuals(const BandArgs& a, uint32_t r
             if (cg < a.nx) {
                 load_syms<8>(a.syms + base + cg, v);
 #pragma unroll
-                for (int k = 0; k < 8; k++)
+                for (int k = 0; k < 8; k++) {
+                    nzero += v[k] == 0u;
                     v[k] = residual_of(v[k], R, (uint32_t)(base + cg + k), od);
+                }
             } else {
 #pragma unroll
                 for (int k = 0; k < 8; k++) v[k] = 0u;
@@ -793,10 +794,11 @@ __device__ __forceinline__ void band_row_residuals(const BandArgs& a, uint32_t r
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < 8 * G; k++)
-            d[k] = (c0 + k < a.nx) ? residual_of(a.syms[base + c0 + k], R,
-                                                 (uint32_t)(base + c0 + k), od)
-                                   : 0u;
+        for (int k = 0; k < 8 * G; k++) {
+            const uint32_t sym = (c0 + k < a.nx) ? a.syms[base + c0 + k] : 1u;
+            nzero += sym == 0u;
+            d[k] = (c0 + k < a.nx) ? residual_of(sym, R, (uint32_t)(base + c0 + k), od) : 0u;
+        }
     }
 }
 
@@ -848,12 +850,14 @@ __global__ void __launch_bounds__(256) k_band_sum(const __grid_constant__ Batch<
         const uint32_t R = par->d_radius;
         const uint32_t* __restrict__ od = reinterpret_cast<const uint32_t*>(a.out);
         const uint32_t r0 = band * a.tr, r1 = min(r0 + a.tr, a.rows);
+        uint32_t nzero = 0;  // symbols 0 (outliers), checked against the list by k_patch
         for (uint32_t r = r0; r < r1; r++) {
             uint32_t d[8 * G];
-            band_row_residuals<G, VEC>(a, r, c0, R, od, d);
+            band_row_residuals<G, VEC>(a, r, c0, R, od, d, nzero);
 #pragma unroll
             for (int k = 0; k < 8 * G; k++) acc[k] += d[k];
         }
+        if (nzero) atomicAdd(&par->d_zero, nzero);
     }
     uint32_t* dst = a.bsum + (uint64_t)band * a.nx;
 #pragma unroll
@@ -942,7 +946,8 @@ __global__ void __launch_bounds__(256) k_band_scan(const __grid_constant__ Batch
             if (r + 1 < r1) band_row_load<G>(a, r + 1, c0, qn);
             band_row_convert<G>(a, r, c0, q, R, od, d);
         } else {
-            band_row_residuals<G, VEC>(a, r, c0, R, od, d);
+            uint32_t unused = 0;  // counted by k_band_sum
+            band_row_residuals<G, VEC>(a, r, c0, R, od, d, unused);
         }
         band_row_prefix<G>(d, sh);
         float f[8 * G];

@@ -294,6 +294,43 @@ def test_corrupt_blobs(env):
     assert status_of(good, nbytes) == 0
 
 
+def test_corrupt_outlier_list(env):
+    """The outlier list is checked against the decoded symbols: an index past
+    the field, two entries out of order, or an entry moved off its symbol 0
+    (leaving a symbol 0 without an entry) are all reported as corrupt."""
+    torch, fpsnr, oracle = env
+    x = field_for((90, 120), 7)
+    plan, xt, out, nbytes, st, blob = run_gpu(env, x, 80.0, radius=16)
+    h = oracle.parse_blob(blob)
+    no = h["n_outlier"]
+    assert no >= 3
+    pad = lambda v: (v + 15) & ~15
+    o_ou = 128 + pad(4 * h["n_sym"]) + pad(4 * h["n_chunks"]) + pad(4 * h["stream_words"])
+    good = out[:nbytes].clone()
+    idx = h["out_idx"].astype(np.int64)
+
+    def status_with(entries):
+        b = good.clone()
+        words = b[o_ou:o_ou + 8 * no].view(torch.int32).view(-1, 2)
+        for i, v in entries:
+            words[i, 0] = int(v)
+        _, status = plan.decompress(b, nbytes)
+        torch.cuda.synchronize()
+        return int(status.item())
+
+    assert status_with([]) == 0
+    assert status_with([(1, x.size + 5)]) == fpsnr.FPSNR_ECORRUPT              # past the field
+    assert status_with([(0, idx[1]), (1, idx[0])]) == fpsnr.FPSNR_ECORRUPT     # out of order
+    # an entry moved to the next point when that point is not an outlier
+    moved = [i for i in range(no) if (i + 1 == no or idx[i] + 1 < idx[i + 1])]
+    assert moved
+    i = moved[0]
+    assert status_with([(i, idx[i] + 1)]) == fpsnr.FPSNR_ECORRUPT
+    _, status = plan.decompress(good, nbytes)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+
+
 # ---------------------------------------------------------------------------
 # workload shapes
 # ---------------------------------------------------------------------------
