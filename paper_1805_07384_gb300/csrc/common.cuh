@@ -184,7 +184,8 @@ struct fpsnr_plan_s {
     fp::Profiler prof;
 };
 
-// Brackets one kernel launch with the plan's profiler.
+// Brackets the kernel launches of one stage with the plan's profiler; the
+// scope counts one launch, more() the stage's further launches.
 struct StageScope {
     fp::Profiler& pr;
     int stage;
@@ -193,6 +194,7 @@ struct StageScope {
     StageScope(fp::Profiler& p, int s, cudaStream_t stream) : pr(p), stage(s), st(stream) {
         pr.begin(stage, st, &a);
     }
+    void more(int k) { pr.launches[stage] += (uint64_t)k; }
     ~StageScope() { pr.end(stage, st, a); }
 };
 

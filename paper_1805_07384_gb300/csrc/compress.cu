@@ -1180,6 +1180,7 @@ int launch_compress_batch(fpsnr_plan_s* const* P, const float* const* d_in, void
             StageScope sc(prof, kStRefine, st);
             k_fine_hist<<<tf, 512, 0, st>>>(bf);
             k_eb_refine<<<tr, kRefineThreads, 0, st>>>(br);
+            sc.more(1);
         }
     }
     FP_LAUNCH_CHECK();
@@ -1284,6 +1285,7 @@ int launch_compress_batch(fpsnr_plan_s* const* P, const float* const* d_in, void
             batch_offsets(b, blocks);
             k_enc_copy<<<tot, kEncWarps * 32, 0, st>>>(b);
             FP_LAUNCH_CHECK();
+            sc.more(2);
         }
     }
 

@@ -1122,7 +1122,10 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
                 sa.count++;
             }
             const uint32_t stot = batch_offsets(sa, sblocks);
-            if (stot) k_out_scatter<<<stot, 256, 0, st>>>(sa);
+            if (stot) {
+                k_out_scatter<<<stot, 256, 0, st>>>(sa);
+                sc.more(1);
+            }
             if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
         }
     }
@@ -1239,6 +1242,7 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
         for (int f = 0; f < count; f++) sb.off[f] = (uint32_t)f;
         sb.off[count] = (uint32_t)count;
         k_status<<<count, 32, 0, st>>>(sb);
+        prof.launches[kStPatch]++;  // counted with the verbatim patch
     }
     return cudaGetLastError() == cudaSuccess ? FPSNR_OK : FPSNR_ECUDA;
 }

@@ -309,6 +309,7 @@ int launch_zr_wrap(fpsnr_plan_s* const* P, void* const* d_out, uint64_t* d_out_b
     k_zr_layout<<<b1.count, 1024, 0, st>>>(b1);
     k_zr_write<<<tot, 256, 0, st>>>(b);
     k_zr_copy<<<tot, 256, 0, st>>>(b);
+    sc.more(3);
     return cudaGetLastError() == cudaSuccess ? FPSNR_OK : FPSNR_ECUDA;
 }
 

@@ -109,3 +109,27 @@ def test_batch_rejects_repeated_plan(env):
     rc = fpsnr.fpsnr_compress_batch([pl.handle, pl.handle], [x.data_ptr()] * 2,
                                     [out.data_ptr()] * 2, [out.numel()] * 2)
     assert rc == fpsnr.FPSNR_EINVAL
+
+
+def test_profiler_counts_every_launch(env):
+    """The launch count the benchmark reports is the number of library kernels:
+    a batch of 2D fields (band path) takes range, predictor, ranks, codebook,
+    the encoder's three kernels, emit and finalize to compress (9), and
+    decode setup, decode, outlier scatter, band sum, carry and scan, patch and
+    status to decompress (8)."""
+    torch, fpsnr, _ = env
+    xs = [torch.from_numpy(synth.single_2d(256, s)).cuda() for s in (1, 2)]
+    plans = [fpsnr.Plan(tuple(x.shape), p) for x, p in zip(xs, (60.0, 100.0))]
+    outs, nb, st = fpsnr.compress_batch(plans, xs)
+    fpsnr.decompress_batch(plans, outs)
+    torch.cuda.synchronize()
+    fpsnr.fpsnr_plan_profile(plans[0].handle, True)
+    fpsnr.fpsnr_plan_profile_read(plans[0].handle)
+    fpsnr.compress_batch(plans, xs, outs=outs)
+    comp = sum(v[1] for v in fpsnr.fpsnr_plan_profile_read(plans[0].handle).values())
+    recs, status = fpsnr.decompress_batch(plans, outs)
+    dec = sum(v[1] for v in fpsnr.fpsnr_plan_profile_read(plans[0].handle).values())
+    torch.cuda.synchronize()
+    fpsnr.fpsnr_plan_profile(plans[0].handle, False)
+    assert all(int(s) == 0 for s in status.cpu())
+    assert (comp, dec) == (9, 8)
