@@ -674,7 +674,10 @@ def main():
     # batch mode: the fields split into `nsub` sub-batches, one per stream, so
     # that one sub-batch's latency-bound stages overlap another's bandwidth work
     nsub = max(1, min(a.sub_batches, F, S))
-    groups = [list(range(g, F, nsub)) for g in range(nsub)]
+    # fields dealt round-robin in order of decreasing target (the dearest
+    # first), so that every sub-batch gets a share of the expensive ones
+    dealt = sorted(range(F), key=lambda i: (-psnrs[i], i))
+    groups = [sorted(dealt[g::nsub]) for g in range(nsub)]
     nb_all = [torch.zeros(len(g), dtype=torch.int64, device=dev) for g in groups]
     st_all = [torch.zeros((len(g), fpsnr.STATS_BYTES), dtype=torch.uint8, device=dev) for g in groups]
     dst_all = [torch.zeros(len(g), dtype=torch.int32, device=dev) for g in groups]

@@ -1026,15 +1026,13 @@ static bool decode_attrs() {
                cudaSuccess;
 }
 
+// Called at every plan creation: the attributes are per device (and cheap to
+// set), so no process-wide flag skips them.
 int decode_prepare(const fpsnr_plan_s*) {
-    static int done = 0;
-    if (!done) {
-        // the decoder reads its stream through cp.async into shared memory, not
-        // L1: take the largest shared-memory carveout so that 1536 threads' rings
-        // and their blocks' tables fit
-        if (!decode_attrs<128>() || !decode_attrs<256>() || !decode_attrs<512>()) return FPSNR_ECUDA;
-        done = 1;
-    }
+    // the decoder reads its stream through cp.async into shared memory, not
+    // L1: take the largest shared-memory carveout so that the rings of its
+    // resident threads and their blocks' tables fit
+    if (!decode_attrs<128>() || !decode_attrs<256>() || !decode_attrs<512>()) return FPSNR_ECUDA;
     return FPSNR_OK;
 }
 
