@@ -903,14 +903,18 @@ def main():
         dom = max(bw_stages.items(), key=lambda kv: kv[1][0]) if bw_stages else None
         if dom:
             name, (t, n, byts) = dom
+            # one stage call per batched call: a sub-batch per call in batch mode,
+            # a field per call in streams mode (a stage can launch several kernels)
+            n = a.steps * (len(groups) if a.mode == "batch" else F)
             achieved = byts / (t / 1e3) / 1e9
             traffic = measured_traffic(name)
             roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                     "traffic": traffic, "peak_source": "measured" if peaks else "fallback",
                     "bytes_per_launch": byts // n, "launch_ms": round(t / n, 5),
-                    "timing": f"CUDA events around each launch over a second timed pass of "
-                              f"{a.steps} steps on one stream ({a.mode} mode)",
+                    "timing": f"CUDA events around each stage call over a second timed pass of "
+                              f"{a.steps} steps on one stream ({a.mode} mode); a launch here is "
+                              f"one stage call over one batched call",
                     "step_ms_one_stream": round(ms1, 4)}
 
     # end to end through host buffers

@@ -381,13 +381,14 @@ void fpsnr_server_destroy(fpsnr_server_t s);
 const uint16_t* fpsnr_plan_codes(fpsnr_plan_t plan);
 
 /* Stage profiler.  The library's kernels are grouped into FPSNR_NSTAGES
- * stages (fpsnr_stage_name gives each name).  Launches per stage are always
- * counted on the host.  With fpsnr_plan_profile(plan, 1) every launch is also
- * bracketed by CUDA events on its stream; fpsnr_plan_profile_read
- * synchronizes those events, adds each stage's total milliseconds and launch
- * count since the last read into ms[i] and launches[i] (arrays of nstages
- * entries, either may be NULL), and resets the counters.  Recording adds one
- * event pair per launch; it does not change what the kernels compute.
+ * stages (fpsnr_stage_name gives each name).  Kernel launches per stage are
+ * always counted on the host (a stage call can launch several kernels).  With
+ * fpsnr_plan_profile(plan, 1) every stage call is also bracketed by CUDA
+ * events on its stream; fpsnr_plan_profile_read synchronizes those events,
+ * adds each stage's total milliseconds and kernel launch count since the last
+ * read into ms[i] and launches[i] (arrays of nstages entries, either may be
+ * NULL), and resets the counters.  Recording adds one event pair per stage
+ * call; it does not change what the kernels compute.
  * Returns FPSNR_OK, FPSNR_EINVAL or FPSNR_ECUDA. */
 #define FPSNR_NSTAGES 18
 int fpsnr_plan_profile(fpsnr_plan_t plan, int enable);
