@@ -74,3 +74,48 @@ def test_cosmology_full_size(env):
     n = int(nb[1].item())
     assert n == len(ob) and outs[1][:n].cpu().numpy().tobytes() == ob
     assert stats[1]["sse"] == pytest.approx(ost["sse"], rel=1e-12, abs=0)
+
+
+def test_climate_batch_in_bench_configuration(env):
+    """The benchmark's workload in its launch configuration: 24 fields of
+    1800x3600 at the mixed targets, dealt into 3 sub-batches by decreasing
+    target, each compressed and decompressed by one batched call on its own
+    stream, the three streams concurrent.  Every field meets its bound and
+    reports the standalone PSNR; three sampled fields (a 120 dB one, a 40 dB
+    one and the one with a constant rectangle) match the oracle byte for byte
+    and float for float."""
+    torch, fpsnr, oracle = env
+    F = 24
+    fields, meta = synth.climate_batch(F)
+    psnrs = [synth.mixed_psnr(i) for i in range(F)]
+    dealt = sorted(range(F), key=lambda i: (-psnrs[i], i))
+    groups = [sorted(dealt[g::3]) for g in range(3)]
+    xs = [torch.from_numpy(f).cuda() for f in fields]
+    plans = [fpsnr.Plan(tuple(x.shape), p) for x, p in zip(xs, psnrs)]
+    streams = [torch.cuda.Stream() for _ in groups]
+    res = {}
+    torch.cuda.synchronize()
+    for s, idx in zip(streams, groups):
+        with torch.cuda.stream(s):
+            gp = [plans[i] for i in idx]
+            outs, nb, st = fpsnr.compress_batch(gp, [xs[i] for i in idx], stream=s)
+            recs, status = fpsnr.decompress_batch(gp, outs, stream=s)
+            res[tuple(idx)] = (outs, nb, st, recs, status)
+    torch.cuda.synchronize()
+    got = {}
+    for idx, (outs, nb, st, recs, status) in res.items():
+        for k, i in enumerate(idx):
+            s = fpsnr.parse_stats(st[k])
+            assert s["status"] == 0 and int(status[k].item()) == 0, i
+            _properties(env, xs[i], recs[k], s)
+            got[i] = (outs[k][:int(nb[k].item())], recs[k], s)
+    const = [i for i, m in enumerate(meta) if m["const_rect"]][0]
+    sample = sorted({next(i for i in range(F) if psnrs[i] == 120.0),
+                     next(i for i in range(F) if psnrs[i] == 40.0), const})
+    for i in sample:
+        ob, ost = oracle.compress(fields[i], psnrs[i])
+        blob, rec, s = got[i]
+        assert blob.numel() == len(ob) and blob.cpu().numpy().tobytes() == ob, i
+        oxr = oracle.decompress(ob, fields[i].shape)
+        assert np.array_equal(rec.cpu().numpy().view(np.uint32), oxr.view(np.uint32)), i
+        assert s["sse"] == pytest.approx(ost["sse"], rel=1e-12, abs=0), i
