@@ -47,7 +47,7 @@ struct DevParams {
     // replays correctly)
     uint32_t dec_epoch;
     float kinv;               // (float)(kFineBins / vr): fine-histogram bin scale
-    // lossless container: wrap decision and sizes; unwrap verdict and raw length
+    // lossless container: wrap decision and sizes; unwrap outcome and raw length
     uint32_t zr_use, zr_bad;
     uint64_t zr_total, zr_dstart, zr_raw;
     uint64_t cap;             // output capacity of this call

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) k_zr_copy(const __grid_constant__ Batch<Z
 }
 
 // Unwrap into the plan's scratch.  A plain blob (no container magic) is
-// copied; a container is expanded segment by segment.  The verdict goes to
+// copied; a container is expanded segment by segment.  The outcome goes to
 // par->zr_bad (the header check that follows must not clear it) and the raw
 // length to par->zr_raw.
 __global__ void __launch_bounds__(256) k_zr_expand(const __grid_constant__ Batch<ZrArgs> B) {
