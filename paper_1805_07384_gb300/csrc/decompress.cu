@@ -206,7 +206,9 @@ __global__ void __launch_bounds__(1024) k_dsetup(const __grid_constant__ Batch<D
 
 // One thread decodes one chunk of `chunk` symbols.  The bit window is 64 bits
 // held as two 32-bit halves (hi holds the next bits, left-justified); a stream
-// word is appended whenever 32 or fewer valid bits remain.  Every symbol is one
+// word is appended whenever 32 or fewer valid bits remain (checked before
+// every code, or before every second code when no code is longer than 16
+// bits: a refill leaves at least 32 valid bits).  Every symbol is one
 // table read over the next kLutBits bits and a funnel shift: the entry gives
 // the code length, and the symbol itself for codes of up to kLutBits bits;
 // longer codes take their symbol from the canonical index, off the dependency
@@ -257,6 +259,7 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_decode(const __grid
     const uint64_t nchunks = A.nchunks;
     extern __shared__ __align__(16) uint32_t slut[];  // decode table, then the stream rings
     __shared__ uint32_t s_base[32];  // first index - first code of every length (mod 2^32)
+    __shared__ uint32_t s_short;     // every code has at most 16 bits
     __shared__ unsigned long long s_lje[33];
     __shared__ __align__(8) unsigned long long s_mbar;
     // constant fields have no stream: their residuals are all zero
@@ -269,6 +272,8 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_decode(const __grid
         s_base[l] = par->d_first_index[l] - par->d_first_code[l];
         // end of length l's codes, left-justified in 32 bits (2^32 once the code is complete)
         s_lje[l] = l ? (unsigned long long)(par->d_first_code[l] + par->d_count[l]) << (32 - l) : 0ull;
+        const uint32_t used = __ballot_sync(0xffffffffu, l && par->d_count[l] > 0u);
+        if (l == 0) s_short = (used >> 17) == 0u;  // no code longer than 16 bits
     }
     if (threadIdx.x == 0) {
         s_lje[32] = ~0ull;
@@ -317,7 +322,9 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_decode(const __grid
     for (uint32_t r = 0; r < (uint32_t)kDecRing; r++) issue(qk + r);
     cp_async_wait<kDecRing - 1>();
     bool bad = false;
-    auto one = [&]() -> uint32_t {
+    // two codes of at most 16 bits each fit the >= 32 valid bits a refill leaves
+    const bool short_codes = s_short != 0u;
+    auto refill = [&]() {
         if (nb <= 32u) {
             const uint32_t wd = ring[(qk & (kDecRing - 1)) * (4u * THREADS) + ci];
             hi |= __funnelshift_rc(wd, 0u, nb);       // wd >> nb (0 when nb == 32)
@@ -333,6 +340,8 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_decode(const __grid
                 cp_async_wait<kDecRing - 1>();
             }
         }
+    };
+    auto dec = [&]() -> uint32_t {
         const uint32_t e = slut[hi >> (32 - kLutBits)];
         uint32_t l = e & 31u;
         uint32_t sym = e >> 8;
@@ -367,11 +376,17 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_decode(const __grid
     for (uint32_t i = 0; i < cnt8; i += 8) {
         uint32_t s[8];
 #pragma unroll
-        for (int k = 0; k < 8; k++) s[k] = one();
+        for (int k = 0; k < 8; k++) {
+            if (!short_codes || (k & 1) == 0) refill();  // warp-uniform condition
+            s[k] = dec();
+        }
         *reinterpret_cast<uint4*>(dst + i) =
             make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16), s[6] | (s[7] << 16));
     }
-    for (uint32_t i = cnt8; i < cnt; i++) dst[i] = (uint16_t)one();
+    for (uint32_t i = cnt8; i < cnt; i++) {
+        refill();
+        dst[i] = (uint16_t)dec();
+    }
     // copies still in flight land before the block's shared memory is released
     cp_async_wait<0>();
     // bits consumed = appended - still valid; the chunk owns (w1 - w0) words
