@@ -216,10 +216,19 @@ def oracle_field(args):
     return time.perf_counter() - t0, len(blob), st["psnr_actual"]
 
 
+def _worker_ready(_):
+    import oracle  # noqa: F401  (loads the oracle library in the worker)
+    return os.getpid()
+
+
 def cpu_pool(workers: int):
+    """Spawned worker pool, returned once every worker has started and loaded
+    the oracle, so that no worker start-up overlaps a timed region."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
-    return ctx.Pool(workers)
+    pool = ctx.Pool(workers)
+    pool.map(_worker_ready, range(4 * workers), chunksize=1)
+    return pool
 
 
 def run_oracle_sample(pool, fields_np, psnrs, chunk):
