@@ -290,7 +290,9 @@ def workload_config(a, streams):
                      f"2D Lorenzo, R=32768, chunk {a.chunk}",
          "fields": a.fields, "shape": [a.ny, a.nx], "radius": 32768, "chunk": a.chunk,
          "lorenzo_dims": 2,
-         "l2": f"inputs {a.fields * a.ny * a.nx * 4 / 1e6:.0f} MB > 129 MB L2, no flush"}
+         "l2": (f"inputs {a.fields * a.ny * a.nx * 4 / 1e6:.0f} MB > 129 MB L2, no flush"
+                if a.fields * a.ny * a.nx * 4 > 129e6 else
+                f"inputs {a.fields * a.ny * a.nx * 4 / 1e6:.1f} MB fit the 129 MB L2 (small case)")}
     if streams is not None:
         c["mode"] = getattr(a, "mode", "batch")
         if c["mode"] == "streams":
