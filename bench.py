@@ -341,13 +341,20 @@ def measured_traffic(stage):
     e = json.load(open(tf)).get(stage)
     if not e:
         return None
-    src = os.path.join(ROOT, e["source"])
-    if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != e["source_sha1"]:
-        return None
+    want = dict(e.get("sources", {}))
+    want[e["source"]] = e["source_sha1"]
+    for rel, sha in want.items():
+        src = os.path.join(ROOT, rel)
+        if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != sha:
+            return None
     return e["dram_bytes_per_launch"]
 
 
 # ncu --csv logs -> per-launch figures (profiles/ summaries and traffic.json)
+
+# files every kernel's binary depends on besides its own source
+_TRAFFIC_DEPS = (os.path.join("paper_1805_07384_gb300", "csrc", "common.cuh"),
+                 os.path.join("paper_1805_07384_gb300", "build.py"))
 _UNITS = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9,
           "ns": 1e-3, "nsecond": 1e-3, "us": 1, "usecond": 1, "ms": 1e3, "msecond": 1e3}
 # benchmark stages by kernel-name prefix, with the source file that holds them
@@ -393,7 +400,9 @@ def launch_table(path):
 
 def write_traffic(path):
     """profiles/traffic.json: DRAM bytes per launch of every stage, with the
-    SHA-1 of the source file the counters were taken from."""
+    SHA-1 of the source file the counters were taken from and of the files
+    every kernel build also depends on (the shared device header and the
+    build script that holds the compiler flags)."""
     import hashlib
     launches = {}
     for lid, k, m, v in _ncu_rows(path):
@@ -423,11 +432,14 @@ def write_traffic(path):
             continue
         n = first[0]
         rel = os.path.join("paper_1805_07384_gb300", "csrc", src)
+        deps = {d: hashlib.sha1(open(os.path.join(ROOT, d), "rb").read()).hexdigest()
+                for d in _TRAFFIC_DEPS if os.path.exists(os.path.join(ROOT, d))}
         out[stage] = {"kernels": sorted(kernels), "launches": n,
                       "dram_bytes_per_launch": int(round((rd + wr) / n)),
                       "dram_read": int(round(rd / n)), "dram_write": int(round(wr / n)),
                       "source": rel,
-                      "source_sha1": hashlib.sha1(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()}
+                      "source_sha1": hashlib.sha1(open(os.path.join(ROOT, rel), "rb").read()).hexdigest(),
+                      "sources": deps}
     dst = os.path.join(ROOT, "profiles", "traffic.json")
     with open(dst, "w") as f:
         json.dump(out, f, indent=1)

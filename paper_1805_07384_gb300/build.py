@@ -21,7 +21,13 @@ LIB = os.path.join(PKG, "libfpsnr.so")
 SOURCES = ["api.cu", "compress.cu", "huffman.cu", "decompress.cu", "psnr.cu", "psnr_static.cu",
            "tune.cu", "serve.cu", "lossless.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# -fmad=false: a plain float multiply followed by an add is not contracted into
+# an fma, as in the oracle's -ffp-contract=off build.  (It does not cover the
+# packed f32x2 intrinsics: a __fmul2_rn result that feeds a __fadd2_rn directly
+# was measured to round as one fma even with this flag, so the kernels never
+# chain those two where the product's rounding matters.)
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I",
+              CSRC]
 
 
 def nvcc() -> str:
@@ -34,6 +40,7 @@ def nvcc() -> str:
 def _deps():
     hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     hdrs.append(os.path.join(INCLUDE, "fpsnr.h"))
+    hdrs.append(os.path.abspath(__file__))  # the flags above
     return hdrs
 
 

@@ -365,6 +365,9 @@ __device__ __forceinline__ void ff2_add_sq_diff(FF2& acc, float2 a, float2 nb, f
     float2 np = __fmul2_rn(dh, ndh);
     float2 e = __ffma2_rn(dh, dh, np);
     e = __ffma2_rn(__fadd2_rn(dh, dh), dl, e);
+    // np reaches the adds below only through these selects: a __fmul2_rn result
+    // that feeds a __fadd2_rn directly was measured to be fused into one fma,
+    // which would fold e into err and count it twice
     np.x = keep0 ? np.x : 0.0f;
     np.y = keep1 ? np.y : 0.0f;
     e.x = keep0 ? e.x : 0.0f;

@@ -69,6 +69,8 @@ def test_write_traffic(tmp_path, monkeypatch):
     src = tmp_path / "paper_1805_07384_gb300" / "csrc"
     src.mkdir(parents=True)
     (src / "compress.cu").write_text("kernel source\n")
+    (src / "common.cuh").write_text("shared header\n")
+    (src.parent / "build.py").write_text("flags\n")
     bench.write_traffic(_log(tmp_path, rows))
     t = json.load(open(out / "traffic.json"))
     pq = t["predict_quantize"]
@@ -81,6 +83,14 @@ def test_write_traffic(tmp_path, monkeypatch):
     assert pq["source_sha1"] == hashlib.sha1(b"kernel source\n").hexdigest()
     assert "decode" not in t
     # the SHA-1 check: traffic is reported only while the source is unchanged
+    assert bench.measured_traffic("predict_quantize") == 201_000_000
+    # ... and while the shared header and the compiler flags are unchanged
+    (src.parent / "build.py").write_text("other flags\n")
+    assert bench.measured_traffic("predict_quantize") is None
+    (src.parent / "build.py").write_text("flags\n")
+    (src / "common.cuh").write_text("changed header\n")
+    assert bench.measured_traffic("predict_quantize") is None
+    (src / "common.cuh").write_text("shared header\n")
     assert bench.measured_traffic("predict_quantize") == 201_000_000
     (src / "compress.cu").write_text("changed\n")
     assert bench.measured_traffic("predict_quantize") is None
