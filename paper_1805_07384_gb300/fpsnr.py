@@ -219,10 +219,17 @@ def _ptr_array(vals):
     return (C.c_void_p * len(vals))(*[int(v) if v else None for v in vals])
 
 
+def _same_length(n, **lists):
+    for name, v in lists.items():
+        if len(v) != n:
+            raise ValueError(f"{name} has {len(v)} entries for {n} plans")
+
+
 def fpsnr_compress_batch(plans, d_in, d_out, out_cap, d_out_bytes: int = 0, d_stats: int = 0,
                          stream: int = 0) -> int:
     """Lists of plan handles, input/output device pointers and capacities."""
     n = len(plans)
+    _same_length(n, d_in=d_in, d_out=d_out, out_cap=out_cap)
     caps = (C.c_uint64 * n)(*[int(c) for c in out_cap])
     return load().fpsnr_compress_batch(_ptr_array(plans), _ptr_array(d_in), _ptr_array(d_out),
                                        caps, d_out_bytes or None, d_stats or None, n,
@@ -232,6 +239,7 @@ def fpsnr_compress_batch(plans, d_in, d_out, out_cap, d_out_bytes: int = 0, d_st
 def fpsnr_decompress_batch(plans, d_blob, blob_bytes, d_out, d_status: int = 0,
                            stream: int = 0) -> int:
     n = len(plans)
+    _same_length(n, d_blob=d_blob, blob_bytes=blob_bytes, d_out=d_out)
     nb = (C.c_uint64 * n)(*[int(b) for b in blob_bytes])
     return load().fpsnr_decompress_batch(_ptr_array(plans), _ptr_array(d_blob), nb,
                                          _ptr_array(d_out), d_status or None, n, stream or None)
@@ -290,6 +298,24 @@ def fpsnr_stage_name(stage: int) -> str:
 # torch convenience wrapper
 # ---------------------------------------------------------------------------
 
+def _check(t, name, dtype, numel=None, min_numel=None, device=None):
+    """Argument checks of the torch wrappers, before anything is enqueued (the
+    C side sees bare pointers and sizes and cannot check a tensor's type,
+    layout or device)."""
+    if not getattr(t, "is_cuda", False):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{name} has {t.numel()} elements, needs at least {min_numel}")
+
+
 def _stream_handle(stream) -> int:
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -327,7 +353,7 @@ def autotune(sample, target_psnr_db: float, max_size_increase: float = 0.01, rad
     """Chunk size and launch shapes for fields shaped like `sample` (a float32
     CUDA tensor, numpy C-order shape) at this target; see fpsnr_autotune."""
     import torch
-    assert sample.dtype == torch.float32 and sample.is_cuda and sample.is_contiguous()
+    _check(sample, "sample", torch.float32)
     o = fpsnr_default_opts()
     o.radius, o.chunk, o.lmax, o.lorenzo_dims = radius, chunk, lmax, lorenzo_dims
     shape = tuple(sample.shape)
@@ -373,11 +399,13 @@ class Plan:
         Returns (out, nbytes, stats) device tensors: nbytes is int64[1] holding
         the blob size, stats is uint8[STATS_BYTES] (see parse_stats)."""
         import torch
-        assert x.dtype == torch.float32 and x.is_cuda and x.is_contiguous()
-        assert x.numel() == self.n
+        _check(x, "x", torch.float32, numel=self.n)
         out = self.alloc_out() if out is None else out
         nbytes = torch.zeros(1, dtype=torch.int64, device=x.device) if nbytes is None else nbytes
         stats = torch.zeros(STATS_BYTES, dtype=torch.uint8, device=x.device) if stats is None else stats
+        _check(out, "out", torch.uint8, device=x.device)
+        _check(nbytes, "nbytes", torch.int64, min_numel=1, device=x.device)
+        _check(stats, "stats", torch.uint8, min_numel=STATS_BYTES, device=x.device)
         rc = fpsnr_compress(self.handle, x.data_ptr(), out.data_ptr(), out.numel(),
                             nbytes.data_ptr(), stats.data_ptr(), _stream_handle(stream))
         if rc:
@@ -388,8 +416,13 @@ class Plan:
         """Enqueue decompression; returns (float32 tensor of the plan's shape,
         int32[1] device status)."""
         import torch
+        _check(blob, "blob", torch.uint8)
+        if not 0 <= int(blob_bytes) <= blob.numel():
+            raise ValueError(f"blob_bytes {int(blob_bytes)} outside the blob's {blob.numel()} bytes")
         out = torch.empty(self.shape, dtype=torch.float32, device=blob.device) if out is None else out
         status = torch.zeros(1, dtype=torch.int32, device=blob.device) if status is None else status
+        _check(out, "out", torch.float32, numel=self.n, device=blob.device)
+        _check(status, "status", torch.int32, min_numel=1, device=blob.device)
         rc = fpsnr_decompress(self.handle, blob.data_ptr(), int(blob_bytes), out.data_ptr(), self.n,
                               status.data_ptr(), _stream_handle(stream))
         if rc:
@@ -439,11 +472,21 @@ def compress_batch(plans, xs, outs=None, nbytes=None, stats=None, stream=None):
     """Compress fields xs[i] with plans[i] in one batched call.  Returns (outs,
     nbytes int64[count], stats uint8[count, STATS_BYTES]) device tensors."""
     import torch
+    n = len(plans)
+    _same_length(n, xs=xs)
+    if n == 0:
+        raise ValueError("empty batch")
     dev = xs[0].device
     outs = [p.alloc_out() for p in plans] if outs is None else outs
-    nbytes = torch.zeros(len(plans), dtype=torch.int64, device=dev) if nbytes is None else nbytes
-    stats = (torch.zeros((len(plans), STATS_BYTES), dtype=torch.uint8, device=dev)
+    nbytes = torch.zeros(n, dtype=torch.int64, device=dev) if nbytes is None else nbytes
+    stats = (torch.zeros((n, STATS_BYTES), dtype=torch.uint8, device=dev)
              if stats is None else stats)
+    _same_length(n, outs=outs)
+    for i, (p, x, o) in enumerate(zip(plans, xs, outs)):
+        _check(x, f"xs[{i}]", torch.float32, numel=p.n, device=dev)
+        _check(o, f"outs[{i}]", torch.uint8, device=dev)
+    _check(nbytes, "nbytes", torch.int64, min_numel=n, device=dev)
+    _check(stats, "stats", torch.uint8, min_numel=n * STATS_BYTES, device=dev)
     rc = fpsnr_compress_batch([p.handle for p in plans], [x.data_ptr() for x in xs],
                               [o.data_ptr() for o in outs], [o.numel() for o in outs],
                               nbytes.data_ptr(), stats.data_ptr(), _stream_handle(stream))
@@ -456,11 +499,22 @@ def decompress_batch(plans, blobs, blob_bytes=None, outs=None, status=None, stre
     """Decompress blobs[i] with plans[i] in one batched call.  blob_bytes
     defaults to each buffer's size.  Returns (outs, status int32[count])."""
     import torch
+    n = len(plans)
+    _same_length(n, blobs=blobs)
+    if n == 0:
+        raise ValueError("empty batch")
     dev = blobs[0].device
     outs = ([torch.empty(p.shape, dtype=torch.float32, device=dev) for p in plans]
             if outs is None else outs)
-    status = torch.zeros(len(plans), dtype=torch.int32, device=dev) if status is None else status
-    blob_bytes = [b.numel() for b in blobs] if blob_bytes is None else blob_bytes
+    status = torch.zeros(n, dtype=torch.int32, device=dev) if status is None else status
+    blob_bytes = [b.numel() for b in blobs] if blob_bytes is None else [int(v) for v in blob_bytes]
+    _same_length(n, outs=outs, blob_bytes=blob_bytes)
+    for i, (p, b, nb, o) in enumerate(zip(plans, blobs, blob_bytes, outs)):
+        _check(b, f"blobs[{i}]", torch.uint8, device=dev)
+        if not 0 <= nb <= b.numel():
+            raise ValueError(f"blob_bytes[{i}] = {nb} outside the blob's {b.numel()} bytes")
+        _check(o, f"outs[{i}]", torch.float32, numel=p.n, device=dev)
+    _check(status, "status", torch.int32, min_numel=n, device=dev)
     rc = fpsnr_decompress_batch([p.handle for p in plans], [b.data_ptr() for b in blobs],
                                 blob_bytes, [o.data_ptr() for o in outs], status.data_ptr(),
                                 _stream_handle(stream))
@@ -471,7 +525,9 @@ def decompress_batch(plans, blobs, blob_bytes=None, outs=None, status=None, stre
 
 def psnr(x, xr, stream=None):
     """(PSNR dB, MSE, vr) of reconstruction xr against x (CUDA float32 tensors)."""
-    assert x.numel() == xr.numel()
+    import torch
+    _check(x, "x", torch.float32)
+    _check(xr, "xr", torch.float32, numel=x.numel(), device=x.device)
     return fpsnr_psnr(x.data_ptr(), xr.data_ptr(), x.numel(), _stream_handle(stream))
 
 
@@ -522,6 +578,9 @@ class Server:
     def submit_compress(self, x, psnr: float, out, arrival_us: float = 0.0, radius: int = 32768,
                         chunk: int = 256, lmax: int = 27, lorenzo_dims: int = 0) -> int:
         """Queue compression of x (float32 CUDA tensor) into out (uint8 CUDA tensor)."""
+        import torch
+        _check(x, "x", torch.float32)
+        _check(out, "out", torch.uint8, device=x.device)
         return self._submit(FPSNR_REQ_COMPRESS, x.shape, x.data_ptr(), 0, out.data_ptr(),
                             out.numel(), psnr, arrival_us, (x, out), radius, chunk, lmax,
                             lorenzo_dims)
@@ -531,6 +590,11 @@ class Server:
                           lorenzo_dims: int = 0) -> int:
         """Queue decompression of blob (uint8 CUDA tensor) into out (float32
         CUDA tensor of the field's shape)."""
+        import torch
+        _check(blob, "blob", torch.uint8)
+        if not 0 <= int(nbytes) <= blob.numel():
+            raise ValueError(f"nbytes {int(nbytes)} outside the blob's {blob.numel()} bytes")
+        _check(out, "out", torch.float32, device=blob.device)
         return self._submit(FPSNR_REQ_DECOMPRESS, out.shape, blob.data_ptr(), nbytes,
                             out.data_ptr(), 4 * out.numel(), 60.0, arrival_us, (blob, out),
                             radius, chunk, lmax, lorenzo_dims)

@@ -133,3 +133,39 @@ def test_profiler_counts_every_launch(env):
     fpsnr.fpsnr_plan_profile(plans[0].handle, False)
     assert all(int(s) == 0 for s in status.cpu())
     assert (comp, dec) == (9, 8)
+
+
+def test_wrappers_reject_bad_tensors(env):
+    """Wrong dtype, layout, size or capacity raises in Python before anything
+    is enqueued; the plan is still usable afterwards."""
+    torch, fpsnr, _ = env
+    p = fpsnr.Plan((33, 47), 60.0)
+    x = torch.rand(33, 47, device="cuda")
+    with pytest.raises(TypeError, match="must be torch.float32"):
+        p.compress(x.double())
+    with pytest.raises(ValueError, match="contiguous"):
+        p.compress(torch.rand(47, 33, device="cuda").t())
+    with pytest.raises(ValueError, match="elements"):
+        p.compress(torch.rand(10, device="cuda"))
+    with pytest.raises(TypeError, match="out must be torch.uint8"):
+        p.compress(x, out=torch.empty(p.max_bytes, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError, match="stats has"):
+        p.compress(x, stats=torch.zeros(4, dtype=torch.uint8, device="cuda"))
+    out, nb, st = p.compress(x)
+    torch.cuda.synchronize()
+    n = int(nb.item())
+    with pytest.raises(ValueError, match="outside the blob"):
+        p.decompress(out, out.numel() + 1)
+    with pytest.raises(TypeError, match="out must be torch.float32"):
+        p.decompress(out, n, out=torch.empty(33 * 47, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError, match="xs has 1 entries for 2 plans"):
+        fpsnr.compress_batch([p, p], [x])
+    with pytest.raises(ValueError, match=r"blob_bytes\[0\]"):
+        fpsnr.decompress_batch([p], [out], blob_bytes=[out.numel() + 16])
+    with pytest.raises(ValueError, match="elements"):
+        fpsnr.psnr(x, torch.rand(5, device="cuda"))
+    xr, status = p.decompress(out, n)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert (xr - x).abs().max().item() <= fpsnr.parse_stats(st)["eb_abs"]
+    p.close()

@@ -67,3 +67,31 @@ def test_null_handles(lib):
     assert lib.fpsnr_compress(None, 0, 0, 0) == lib.FPSNR_EINVAL
     assert lib.fpsnr_decompress(None, 0, 0, 0, 0) == lib.FPSNR_EINVAL
     lib.fpsnr_plan_destroy(None)
+
+
+def test_wrappers_check_arguments_before_enqueueing(lib):
+    """The Python layer rejects mismatched lists and tensors that are not
+    contiguous CUDA tensors of the right type before anything reaches the C
+    side (which sees bare pointers and cannot check them)."""
+    import types
+
+    import torch
+
+    # low-level batch wrappers: one entry per plan in every list
+    with pytest.raises(ValueError, match="d_in has 1 entries for 2 plans"):
+        lib.fpsnr_compress_batch([1, 2], [8], [16, 24], [4, 4])
+    with pytest.raises(ValueError, match="blob_bytes has 3 entries"):
+        lib.fpsnr_decompress_batch([1, 2], [8, 8], [4, 4, 4], [16, 24])
+    # torch wrappers
+    x = torch.zeros(6, dtype=torch.float32)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        lib.psnr(x, x)
+    fake = [types.SimpleNamespace(n=6, handle=None, shape=(6,)) for _ in range(2)]
+    with pytest.raises(ValueError, match="xs has 1 entries for 2 plans"):
+        lib.compress_batch(fake, [x])
+    with pytest.raises(ValueError, match="empty batch"):
+        lib.compress_batch([], [])
+    with pytest.raises(TypeError, match=r"xs\[0\] must be a CUDA tensor"):
+        lib.compress_batch(fake, [x, x], outs=[x, x], nbytes=x, stats=x)
+    with pytest.raises(ValueError, match="blobs has 1 entries"):
+        lib.decompress_batch(fake, [x])
