@@ -344,12 +344,15 @@ typedef struct {
  * batches              launches (each one batched compress or decompress call)
  * p50_us, p99_us, max_us   latency (done - arrival) over completed requests
  * plans, plan_bytes    plans cached now and the device memory they hold
- * bytes_in             original field bytes of completed requests */
+ * bytes_in             original field bytes of completed requests
+ * plans_created        plans allocated since creation (a request that waits
+ *                      for room allocates nothing until its plan fits) */
 typedef struct {
     uint64_t completed, failed, batches;
     double p50_us, p99_us, max_us;
     uint64_t plans, plan_bytes;
     uint64_t bytes_in;
+    uint64_t plans_created;
 } fpsnr_server_stats;
 
 /* Creates a server on the current device (its worker thread starts at once).

@@ -8,6 +8,7 @@
 #include <new>
 
 #include "common.cuh"
+#include "plan.cuh"
 
 namespace {
 
@@ -269,6 +270,22 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
                const fpsnr_opts* opts) {
     if (!out) return FPSNR_EINVAL;
     *out = nullptr;
+    fpsnr_plan_s* p = nullptr;
+    int rc = fp::plan_layout(&p, ndim, dims, target_psnr_db, opts);
+    if (rc != FPSNR_OK) return rc;
+    rc = fp::plan_allocate(p);
+    if (rc != FPSNR_OK) return rc;
+    *out = p;
+    return FPSNR_OK;
+}
+
+}  // extern "C"
+
+namespace fp {
+
+int plan_layout(fpsnr_plan_s** out, int ndim, const uint64_t* dims, double target_psnr_db,
+                const fpsnr_opts* opts) {
+    *out = nullptr;
     if (ndim < 1 || ndim > 3 || !dims || !psnr_ok(target_psnr_db)) return FPSNR_EINVAL;
     fpsnr_opts o;
     fpsnr_default_opts(&o);
@@ -369,6 +386,13 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
     }
     size_t bytes = 0;
     carve(p, nullptr, &bytes);
+    p->slab_bytes = bytes;
+    *out = p;
+    return FPSNR_OK;
+}
+
+int plan_allocate(fpsnr_plan_s* p) {
+    size_t bytes = p->slab_bytes;
     void* slab = nullptr;
     if (cudaMalloc(&slab, bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -376,7 +400,6 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
         return FPSNR_ENOMEM;
     }
     p->slab = slab;
-    p->slab_bytes = bytes;
     carve(p, reinterpret_cast<uint8_t*>(slab), &bytes);
     const fp::Workspace& w = p->w;
     bool ok = cudaMemset(w.par, 0, sizeof(fp::DevParams)) == cudaSuccess &&
@@ -393,9 +416,12 @@ int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_
         return FPSNR_ECUDA;
     }
     p->cb_smem = fp::codebook_smem_bytes();
-    *out = p;
     return FPSNR_OK;
 }
+
+}  // namespace fp
+
+extern "C" {
 
 int fpsnr_plan_set_psnr(fpsnr_plan_t p, double target_psnr_db) {
     if (!p || !psnr_ok(target_psnr_db)) return FPSNR_EINVAL;

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "plan.cuh"
 
 namespace {
 
@@ -92,6 +93,7 @@ struct fpsnr_server_s {
     std::deque<Req> pending;  // ordered by arrival
     std::list<CachedPlan> plans;
     size_t plan_bytes = 0;
+    uint64_t plans_created = 0;
     uint64_t use_clock = 0;
     std::vector<Slot> slots;
     std::vector<cudaStream_t> streams;
@@ -128,7 +130,9 @@ void fpsnr_server_s::finish(const Req& q, const fpsnr_result& res) {
 // A plan for the request's key: an idle cached one, else a new one inside the
 // budget (evicting idle plans of any key, least recently used first).  Returns
 // nullptr with *err = 0 when the request must wait for a busy plan, or with
-// *err set when it can never be served.
+// *err set when it can never be served.  A new plan is sized on the host
+// first: while the request has to wait, nothing is allocated or evicted
+// (both synchronise the device).
 CachedPlan* fpsnr_server_s::acquire(const Req& q, int* err) {
     *err = 0;
     for (auto& c : plans)
@@ -137,32 +141,45 @@ CachedPlan* fpsnr_server_s::acquire(const Req& q, int* err) {
             c.last_use = ++use_clock;
             return &c;
         }
-    fpsnr_plan_t p = nullptr;
-    int rc = fpsnr_plan(&p, q.r.ndim, q.r.dims, q.r.kind == FPSNR_REQ_COMPRESS ? q.r.target_psnr_db : 60.0,
-                        &q.r.opts);
+    fpsnr_plan_s* p = nullptr;
+    int rc = fp::plan_layout(&p, q.r.ndim, q.r.dims,
+                             q.r.kind == FPSNR_REQ_COMPRESS ? q.r.target_psnr_db : 60.0, &q.r.opts);
     if (rc) {
         *err = rc;
         return nullptr;
     }
     const size_t need = p->slab_bytes;
     if (need > o.hbm_budget) {
-        fpsnr_plan_destroy(p);
+        delete p;
         *err = FPSNR_ENOMEM;
+        return nullptr;
+    }
+    size_t idle = 0;
+    for (auto& c : plans)
+        if (!c.busy) idle += c.bytes;
+    if (plan_bytes - idle + need > o.hbm_budget) {
+        // it cannot fit until a batch finishes: wait
+        delete p;
         return nullptr;
     }
     while (plan_bytes + need > o.hbm_budget) {
         auto victim = plans.end();
         for (auto it = plans.begin(); it != plans.end(); ++it)
             if (!it->busy && (victim == plans.end() || it->last_use < victim->last_use)) victim = it;
-        if (victim == plans.end()) {
-            // everything cached is busy: wait for a batch to finish
-            fpsnr_plan_destroy(p);
+        if (victim == plans.end()) {  // not reached: the idle plans cover the shortfall
+            delete p;
             return nullptr;
         }
         plan_bytes -= victim->bytes;
         fpsnr_plan_destroy(victim->p);
         plans.erase(victim);
     }
+    rc = fp::plan_allocate(p);
+    if (rc) {
+        *err = rc;
+        return nullptr;
+    }
+    plans_created++;
     plans.push_back(CachedPlan{p, q.key, need, true, ++use_clock});
     plan_bytes += need;
     return &plans.back();
@@ -479,6 +496,7 @@ int fpsnr_server_get_stats(fpsnr_server_t s, fpsnr_server_stats* st) {
     st->batches = s->batches;
     st->plans = s->plans.size();
     st->plan_bytes = s->plan_bytes;
+    st->plans_created = s->plans_created;
     st->bytes_in = s->bytes_in;
     if (!s->lat.empty()) {
         std::vector<double> v = s->lat;

@@ -95,7 +95,8 @@ class fpsnr_result(C.Structure):
 class fpsnr_server_stats(C.Structure):
     _fields_ = [("completed", C.c_uint64), ("failed", C.c_uint64), ("batches", C.c_uint64),
                 ("p50_us", C.c_double), ("p99_us", C.c_double), ("max_us", C.c_double),
-                ("plans", C.c_uint64), ("plan_bytes", C.c_uint64), ("bytes_in", C.c_uint64)]
+                ("plans", C.c_uint64), ("plan_bytes", C.c_uint64), ("bytes_in", C.c_uint64),
+                ("plans_created", C.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -97,11 +97,13 @@ def test_server_budget(env):
     assert all(r["status"] == 0 for r in res)
     st = srv.stats()
     assert st["plans"] == 1 and st["plan_bytes"] <= int(slab * 1.5)
+    # the requests that waited for the busy plan allocated nothing meanwhile
+    assert st["plans_created"] == 1
     # a different shape evicts the idle plan
     y = torch.from_numpy(field_for((400, 900), 6)).cuda()
     o2 = torch.empty(fpsnr.Plan((400, 900), 80.0).max_bytes, dtype=torch.uint8, device="cuda")
     assert srv.wait(srv.submit_compress(y, 80.0, o2))["status"] == 0
-    assert srv.stats()["plans"] == 1
+    assert srv.stats()["plans"] == 1 and srv.stats()["plans_created"] == 2
     srv.close()
     # no room for the plan at all
     srv = fpsnr.Server(hbm_budget=int(slab // 2), max_batch=4, streams=1)
