@@ -128,8 +128,10 @@ int fpsnr_default_opts(fpsnr_opts* opts);
 /* Create a plan for fields of one shape on the current CUDA device.
  *   ndim 1..3; dims[ndim], x fastest, each >= 0 (a zero extent gives an empty
  *   field); target_psnr_db in (0, FPSNR_MAX_PSNR]; opts NULL = defaults.
- * The plan owns all device scratch (about 20 bytes per point) and is not
+ * The plan owns all device scratch (about 20 bytes per point, one cudaMalloc;
+ * creating a plan synchronises the device once, destroying it too) and is not
  * thread-safe: one call at a time per plan (calls on one stream serialize).
+ * Arguments are checked before any device call.
  * Returns FPSNR_OK, FPSNR_EINVAL, FPSNR_ENOMEM or FPSNR_ECUDA. */
 int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_psnr_db,
                const fpsnr_opts* opts);
