@@ -41,13 +41,24 @@ FLAG_CONSTANT, FLAG_LATTICE_OFF = 1, 2
 HEADER_BYTES = 128
 
 
+# gcc flags of the oracle library: no FMA contraction, IEEE arithmetic
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC", "-shared"]
+
+# A test may point this variable at another build of fpsnr_oracle.c (the
+# mutation test loads copies with one deliberate mistake each, to show that
+# the pins catch it); unset, the library is built and loaded from here.
+LIB_ENV = "FPSNR_ORACLE_LIB"
+
+
+def compile_library(src: str, out: str) -> None:
+    subprocess.run(["gcc", *CFLAGS, "-o", out, src, "-lm"], check=True)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle shared library in place (gcc, no FMA contraction)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC",
-               "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        compile_library(_SRC, tmp)
         os.replace(tmp, _SO)
     return _SO
 
@@ -75,7 +86,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            _lib = C.CDLL(build())
+            _lib = C.CDLL(os.environ.get(LIB_ENV) or build())
             L = _lib
             P = C.c_void_p
             L.or_eb_rel_from_psnr.restype = C.c_double

@@ -356,6 +356,39 @@ def test_pred_mse_matches_lattice_sse(oracle):
             assert pred == pytest.approx(st["mse"], rel=0.02), (psnr, pred, st["mse"])
 
 
+def test_pred_mse_brute_force_within_fine_bins(oracle):
+    """Eq. 3 with the PDF constant inside every fine bin, against brute force:
+    with a lattice step of 8 fine bins no fine bin straddles a quantization
+    boundary, so the predicted MSE must equal the mean of (x - L)^2 over
+    points spread uniformly inside the occupied fine bins, L the lattice point
+    nearest each (midpoint rule, 4000 points per bin).  A single bin next to
+    a lattice point gives w^2 / 3: w^2 / 4 from its centre's offset and
+    w^2 / 12 from the spread inside it."""
+    K = oracle.FINE_BINS
+    vr = 1.0
+    w = vr / K
+    eb = 4.0 * w  # lattice step 2 eb = 8 fine bins, lattice points at multiples of 8 w
+    h = np.zeros(K, np.uint32)
+    occupied = {3: 5, 4: 2, 7: 1, 100: 3, 2047: 4, 4095: 1}
+    for j, c in occupied.items():
+        h[j] = c
+    n = int(h.sum())
+    m = 4000
+    brute = 0.0
+    for j, c in occupied.items():
+        xs = (j + (np.arange(m) + 0.5) / m) * w
+        lat = 8.0 * w * np.round(xs / (8.0 * w))
+        assert np.all(lat == lat[0])  # one quantization bin per fine bin
+        brute += c * float(np.mean((xs - lat) ** 2))
+    brute /= n
+    assert oracle.pred_mse(h, n, vr, eb) == pytest.approx(brute, rel=1e-6)
+    h1 = np.zeros(K, np.uint32)
+    h1[0] = 1  # the bin [0, w]: nearest lattice point 0
+    xs = (np.arange(m) + 0.5) / m * w
+    assert float(np.mean(xs ** 2)) == pytest.approx(w * w / 3.0, rel=1e-6)
+    assert oracle.pred_mse(h1, 1, vr, eb) == pytest.approx(float(np.mean(xs ** 2)), rel=1e-6)
+
+
 def test_refine_eb_reduces_to_eq8_on_flat_pdf(oracle):
     """Uniform data is Eq. 6's setting (error uniform in every bin): the refined
     eb stays at Eq. 8's to within a few per cent; above ~59 dB (a bin narrower
