@@ -87,8 +87,29 @@ MUTANTS = [
     ("refine_bisection_reversed",
      "if (or_pred_mse(h, n, vr, mid) <= mse_target) lo = mid;\n        else hi = mid;",
      "if (or_pred_mse(h, n, vr, mid) <= mse_target) hi = mid;\n        else lo = mid;"),
+    ("refine_bracket_narrowed", "double lo = eb0 * 0.25, hi = eb0 * 64.0;",
+     "double lo = eb0 * 0.25, hi = eb0 * 4.0;"),
+    ("refine_gate_at_4_fine_bins", "p.eb_abs * (double)OR_FINE_BINS >= 8.0 * p.vr",
+     "p.eb_abs * (double)OR_FINE_BINS >= 2.0 * p.vr"),
+    ("fine_hist_rounds", "int b = (int)u; /* truncation toward zero; u >= 0 */",
+     "int b = (int)(u + 0.5f);"),
+    # range, degenerate fields, plan
+    ("nonfinite_not_rejected", "if (!isfinite(v)) return OR_ENONFINITE;", "(void)0;"),
+    ("min_tracks_max", "if (i == 0 || v < lo) lo = v;", "if (i == 0 || v > lo) lo = v;"),
+    ("constant_field_not_detected", "if (n == 0 || p->vr == 0.0) {", "if (n == 0) {"),
+    ("eb_not_scaled_by_vr", "scalars_for_eb(eb_rel * p->vr, p);", "scalars_for_eb(eb_rel, p);"),
+    ("eq7_range_term_halved", "return 20.0 * log10(vr / eb_abs) + 10.0 * log10(3.0);",
+     "return 10.0 * log10(vr / eb_abs) + 10.0 * log10(3.0);"),
+    # lists, single-symbol code, prefix sums over planes
+    ("outlier_residual_negated", "out_delta[no] = (int32_t)d; }", "out_delta[no] = (int32_t)-d; }"),
+    ("verbatim_bits_flipped", "vb_bits[nv] = b; }", "vb_bits[nv] = b ^ 1u; }"),
+    ("single_symbol_length_2", "if (w[s] > 0) len[s] = 1;", "if (w[s] > 0) len[s] = 2;"),
+    ("inverse_lorenzo_skips_second_plane", "for (uint64_t z = 1; z < nz; z++)",
+     "for (uint64_t z = 2; z < nz; z++)"),
     # zero-run container
     ("zero_run_length_off_by_one", "uint64_t v = k - 1;", "uint64_t v = k;"),
+    ("zero_run_codes_equal_size_segments", "rawflag[sg] = c >= len;", "rawflag[sg] = c > len;"),
+    ("container_kept_when_larger", "if (total >= raw_bytes) {", "if (total > raw_bytes + 64) {"),
 ]
 
 
