@@ -95,3 +95,31 @@ def test_wrappers_check_arguments_before_enqueueing(lib):
         lib.compress_batch(fake, [x, x], outs=[x, x], nbytes=x, stats=x)
     with pytest.raises(ValueError, match="blobs has 1 entries"):
         lib.decompress_batch(fake, [x])
+
+
+def test_ctypes_layouts_match_the_header(lib, tmp_path):
+    """Every struct the binding mirrors has the size and field offsets that a
+    C compiler gives the declaration in include/fpsnr.h."""
+    import ctypes
+    import subprocess
+
+    structs = [lib.fpsnr_opts, lib.fpsnr_stats, lib.fpsnr_tuning, lib.fpsnr_server_opts,
+               lib.fpsnr_request, lib.fpsnr_result, lib.fpsnr_server_stats]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "fpsnr.h"', "int main(void) {"]
+    want = []
+    for s in structs:
+        name = s.__name__
+        lines.append(f'printf("%zu\\n", sizeof({name}));')
+        want.append(ctypes.sizeof(s))
+        for f, _ in s._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({name}, {f}));')
+            want.append(getattr(s, f).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got == want
