@@ -238,6 +238,22 @@ def run_oracle_sample(pool, fields_np, psnrs, chunk):
     return wall, res
 
 
+def cpu_baseline_summary(total_bytes, wall, workers, field_bytes, res):
+    """The cpu_baseline object: whole-batch GB/s over the wall time of the pool
+    run, and the single-core GB/s of each field (every worker runs one field
+    on one core, res[i][0] its seconds)."""
+    one_core = [b / r[0] / 1e9 for b, r in zip(field_bytes, res) if r[0] > 0]
+    out = {"value": round(total_bytes / wall / 1e9, 4), "unit": "GB/s", "cores": workers,
+           "kind": "oracle",
+           "sample": f"all {len(res)} fields of one step (compress + decompress), one field per "
+                     f"worker process, {wall:.1f} s wall"}
+    if one_core:
+        out["one_core_gbs_per_field"] = {"median": round(statistics.median(one_core), 4),
+                                         "min": round(min(one_core), 4),
+                                         "max": round(max(one_core), 4)}
+    return out
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle on the host cores
 # ---------------------------------------------------------------------------
@@ -259,17 +275,19 @@ def run_reference(a):
             run_oracle_sample(pool, fields[:workers], psnrs[:workers], a.chunk)
         times = []
         for _ in range(a.steps):
-            wall, _ = run_oracle_sample(pool, fields, psnrs, a.chunk)
+            wall, res = run_oracle_sample(pool, fields, psnrs, a.chunk)
             times.append(wall)
     ms = 1e3 * sum(times) / len(times)
     value = nbytes / (ms / 1e3) / 1e9
+    cpu = cpu_baseline_summary(nbytes, ms / 1e3, workers, [4 * f.size for f in fields], res)
+    cpu["value"] = value
+    cpu["sample"] = f"all {a.fields} fields per step, one field per worker process"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(a, streams=None),
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": workers, "kind": "oracle",
-                         "sample": f"all {a.fields} fields per step, one field per worker process"},
+        "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -966,12 +984,10 @@ def main():
         fields_np = [f.cpu().numpy() for f in fields]
         wall, res = run_oracle_sample(pool, fields_np, psnrs, a.chunk)
         pool.close()
-        cpu = {"value": round(total_bytes / wall / 1e9, 4), "unit": "GB/s",
-               "cores": pool_workers, "kind": "oracle",
-               "sample": f"all {F} fields of one step (compress + decompress), one field per "
-                         f"worker process, {wall:.1f} s wall"}
+        cpu = cpu_baseline_summary(total_bytes, wall, pool_workers, [4 * f.size for f in fields_np], res)
         for (t, nbyt, p_or), pf in zip(res, per_field):
             pf["oracle_psnr"] = round(p_or, 6)
+            pf["oracle_s"] = round(t, 3)
 
     if rank == 0:
         line = {

@@ -94,3 +94,13 @@ def test_write_traffic(tmp_path, monkeypatch):
     assert bench.measured_traffic("predict_quantize") == 201_000_000
     (src / "compress.cu").write_text("changed\n")
     assert bench.measured_traffic("predict_quantize") is None
+
+
+def test_cpu_baseline_summary():
+    """Whole-batch GB/s over the pool's wall time, plus each field's one-core
+    GB/s from its worker's own time."""
+    res = [(2.0, 10, 80.0), (1.0, 10, 60.0), (4.0, 10, 40.0)]
+    c = bench.cpu_baseline_summary(3_000_000_000, 5.0, 3, [1e9, 1e9, 1e9], res)
+    assert c["value"] == 0.6 and c["cores"] == 3 and c["kind"] == "oracle"
+    assert c["one_core_gbs_per_field"] == {"median": 0.5, "min": 0.25, "max": 1.0}
+    assert "3 fields" in c["sample"]
