@@ -1,11 +1,20 @@
 #!/usr/bin/env python
 """Throughput of fixed-PSNR compression + decompression on GB300.
 
-Workload (one step): the climate-like batch of 24 float32 fields of
-1800 x 3600 points (622 MB, larger than the 129 MB L2), each compressed at a
-target PSNR from the sweep {40, 60, 80, 100, 120} dB (field i gets
-sweep[i mod 5]) with the 2D Lorenzo predictor and R = 32768, then
-decompressed.  metric = original bytes / (compress + decompress time).
+One step compresses every field of a batch at its target PSNR and decompresses
+it again; metric = original bytes / (compress + decompress time).  Workloads
+(--workload, seeded synthetic stand-ins shaped like the paper's data sets,
+Table 1):
+
+  c3 (default)  6 NYX-like 3D fields of 512^3 points (3.2 GB): two lognormal
+                densities, three velocity components, one temperature; field i
+                at {40, 60, 80}[i mod 3] dB; 3D Lorenzo
+  c2            13 hurricane-like 3D fields of 100 x 500 x 500 points (1.3 GB);
+                field i at 30 + 10 (i mod 10) dB; 3D Lorenzo
+  c1            24 climate-like 2D fields of 1800 x 3600 points (622 MB); field
+                i at {40, 60, 80, 100, 120}[i mod 5] dB; 2D Lorenzo
+  c0            one 512 x 512 2D field at 80 dB (1 MiB: fits L2, which is
+                flushed between timed steps)
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on the
 host cores instead (the reference arm of this method: the paper ships no GPU
@@ -45,9 +54,17 @@ def parse():
     ap.add_argument("--mode", choices=["batch", "streams"], default="batch",
                     help="batch: one batched compress + decompress call per step; "
                          "streams: one plain call per field, fields spread over --streams")
-    ap.add_argument("--fields", type=int, default=24)
-    ap.add_argument("--ny", type=int, default=1800)
-    ap.add_argument("--nx", type=int, default=3600)
+    ap.add_argument("--workload", choices=WORKLOADS, default="c3",
+                    help="c3: 6 NYX-like 512^3 fields (default); c2: 13 hurricane-like "
+                         "100x500x500 fields; c1: 24 climate-like 1800x3600 fields; c0: one "
+                         "512x512 field")
+    ap.add_argument("--fields", type=int, default=0, help="0 = the workload's field count")
+    ap.add_argument("--ny", type=int, default=1800, help="c1: rows")
+    ap.add_argument("--nx", type=int, default=3600, help="c1: columns")
+    ap.add_argument("--n3", type=int, default=512, help="c3: points per axis")
+    ap.add_argument("--cpu-steps", type=int, default=3,
+                    help="CPU baseline: oracle steps (rounds of one task per worker); the "
+                         "median is reported")
     ap.add_argument("--chunk", type=int, default=256)
     ap.add_argument("--autotune", action="store_true",
                     help="pick chunk size and tile shapes per target PSNR with fpsnr_autotune "
@@ -77,7 +94,69 @@ def parse():
     ap.add_argument("--launch-table", metavar="CSV",
                     help="print the per-kernel launch table of an ncu --csv log of "
                          "gpu__time_duration.sum (no GPU work)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    a.fields = a.fields or DEFAULT_FIELDS[a.workload]
+    if a.workload == "c3" and a.fields > 6:
+        ap.error("c3 has six fields")
+    return a
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+WORKLOADS = ("c0", "c1", "c2", "c3")
+DEFAULT_FIELDS = {"c0": 1, "c1": 24, "c2": 13, "c3": 6}
+COSMO_TARGETS = (40.0, 60.0, 80.0)
+HURRICANE_SHAPE = (100, 500, 500)
+
+
+def field_shape(a):
+    """numpy (C-order) shape of every field of the workload."""
+    return {"c0": (512, 512), "c1": (a.ny, a.nx), "c2": HURRICANE_SHAPE,
+            "c3": (a.n3, a.n3, a.n3)}[a.workload]
+
+
+def targets(a, count):
+    """Target PSNR of every field, or one value for all (--psnr)."""
+    from paper_1805_07384_gb300 import synth
+    if a.psnr > 0:
+        return [a.psnr] * count
+    if a.workload == "c0":
+        return [80.0] * count
+    if a.workload == "c1":
+        return [synth.mixed_psnr(i) for i in range(count)]
+    if a.workload == "c2":
+        return [synth.psnr_sweep_3d(i) for i in range(count)]
+    return [COSMO_TARGETS[i % 3] for i in range(count)]
+
+
+def make_fields(a, seed, device):
+    """The workload's float32 fields as torch tensors on `device`, drawn there
+    (c1-c3) or on the host (c0, numpy); generation is never timed."""
+    import torch
+    from paper_1805_07384_gb300 import synth
+    if a.workload == "c0":
+        return [torch.from_numpy(synth.single_2d(512, seed=seed - 1)).to(device)
+                for _ in range(a.fields)]
+    if a.workload == "c1":
+        return synth.climate_batch(a.fields, a.ny, a.nx, seed=seed, device=device)[0]
+    if a.workload == "c2":
+        return synth.hurricane_batch(a.fields, *HURRICANE_SHAPE, seed=seed, device=device)[0]
+    fields, _ = synth.cosmology_fields(a.n3, seed=seed + 2, device=device)
+    return [f.contiguous() for f in fields[:a.fields]]
+
+
+def cpu_tasks(a, shape):
+    """CPU-baseline tasks: (field index, first plane, end plane) of one oracle
+    compress + decompress each.  Whole fields, except for c3, whose 512^3
+    fields are cut into z-slabs of 64 planes so that every host core takes a
+    share of every step (a slab is compressed as a field of its own)."""
+    if a.workload == "c3":
+        slab = 64
+        return [(f, z0, min(z0 + slab, shape[0])) for z0 in range(0, shape[0], slab)
+                for f in range(a.fields)]
+    return [(f, 0, shape[0]) for f in range(a.fields)]
 
 
 # ---------------------------------------------------------------------------
@@ -206,14 +285,19 @@ class ClockSampler:
                 "samples": len(self.smi_rows), "source": "nvidia-smi, 200 ms"}
 
 
-def oracle_field(args):
-    """One oracle compress + decompress (worker process)."""
-    x, psnr, chunk = args
+def oracle_task(args):
+    """One oracle compress + decompress of planes [z0, z1) of a field held in
+    the host field file (worker process).  Returns (seconds, blob bytes, PSNR)."""
+    path, offset, shape, z0, z1, psnr, chunk = args
+    import numpy as np
     import oracle
+    x = np.memmap(path, dtype=np.float32, mode="r", offset=offset, shape=shape)[z0:z1]
     t0 = time.perf_counter()
     blob, st = oracle.compress(x, psnr, chunk=chunk)
     oracle.decompress(blob, x.shape)
-    return time.perf_counter() - t0, len(blob), st["psnr_actual"]
+    dt = time.perf_counter() - t0
+    del x
+    return dt, len(blob), st["psnr_actual"]
 
 
 def _worker_ready(_):
@@ -231,26 +315,88 @@ def cpu_pool(workers: int):
     return pool
 
 
-def run_oracle_sample(pool, fields_np, psnrs, chunk):
-    t0 = time.perf_counter()
-    res = pool.map(oracle_field, [(f, p, chunk) for f, p in zip(fields_np, psnrs)])
-    wall = time.perf_counter() - t0
-    return wall, res
+class HostFields:
+    """The workload's fields written once into one file (in /dev/shm when it
+    has room, else the temporary directory), so that an oracle task carries
+    only a path and an offset (no field crosses a pipe inside a timed
+    region) and the workers read the pages from memory."""
+
+    def __init__(self, arrays):
+        import tempfile
+        import numpy as np
+        self.shapes = [tuple(x.shape) for x in arrays]
+        self.offsets, off = [], 0
+        for x in arrays:
+            self.offsets.append(off)
+            off += (4 * x.size + 4095) & ~4095
+        d = "/dev/shm"
+        try:
+            st = os.statvfs(d)
+            if st.f_bavail * st.f_frsize < off + (1 << 30):
+                d = tempfile.gettempdir()
+        except OSError:
+            d = tempfile.gettempdir()
+        fd, self.path = tempfile.mkstemp(prefix="fpsnr_fields_", suffix=".f32", dir=d)
+        os.close(fd)
+        m = np.memmap(self.path, dtype=np.uint8, mode="w+", shape=(max(off, 4096),))
+        for x, o in zip(arrays, self.offsets):
+            m[o:o + 4 * x.size] = np.ascontiguousarray(x, dtype=np.float32).reshape(-1).view(np.uint8)
+        m.flush()
+        del m
+
+    def args(self, task, psnrs, chunk):
+        f, z0, z1 = task
+        return (self.path, self.offsets[f], self.shapes[f], z0, z1, psnrs[f], chunk)
+
+    def task_bytes(self, task):
+        f, z0, z1 = task
+        plane = 4 * math.prod(self.shapes[f][1:])
+        return plane * (z1 - z0)
+
+    def close(self):
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
 
 
-def cpu_baseline_summary(total_bytes, wall, workers, field_bytes, res):
-    """The cpu_baseline object: whole-batch GB/s over the wall time of the pool
-    run, and the single-core GB/s of each field (every worker runs one field
-    on one core, res[i][0] its seconds)."""
-    one_core = [b / r[0] / 1e9 for b, r in zip(field_bytes, res) if r[0] > 0]
-    out = {"value": round(total_bytes / wall / 1e9, 4), "unit": "GB/s", "cores": workers,
+def run_cpu_steps(pool, hf, tasks, psnrs, chunk, workers, steps, first=0):
+    """`steps` oracle steps; step k runs the next round of `workers` tasks
+    (cycling through the task list) on the pool.  Returns [(wall s, bytes,
+    [(task, task bytes, result)])]."""
+    out = []
+    k = first
+    per = min(workers, len(tasks))
+    for _ in range(steps):
+        batch = [tasks[(k + j) % len(tasks)] for j in range(per)]
+        k += per
+        t0 = time.perf_counter()
+        res = pool.map(oracle_task, [hf.args(t, psnrs, chunk) for t in batch], chunksize=1)
+        wall = time.perf_counter() - t0
+        tb = [hf.task_bytes(t) for t in batch]
+        out.append((wall, sum(tb), list(zip(batch, tb, res))))
+    return out
+
+
+def cpu_baseline_summary(a, runs, workers, ntasks):
+    """The cpu_baseline object: the median over the steps of a round's bytes
+    over its wall time, and the single-core GB/s of every task (each worker
+    runs one task on one core)."""
+    rates = [b / w / 1e9 for w, b, _ in runs]
+    one_core = [b / r[0] / 1e9 for _, _, tr in runs for _, b, r in tr if r[0] > 0]
+    per = len(runs[0][2]) if runs else 0
+    unit = "64-plane z-slab" if a.workload == "c3" else "field"
+    out = {"value": round(statistics.median(rates), 4), "unit": "GB/s", "cores": workers,
            "kind": "oracle",
-           "sample": f"all {len(res)} fields of one step (compress + decompress), one field per "
-                     f"worker process, {wall:.1f} s wall"}
+           "sample": f"{len(runs)} steps, each {per} oracle compress + decompress tasks (one "
+                     f"{unit} per worker process, cycling through the workload's {ntasks} "
+                     f"{unit}s); value = median over the steps of the round's original bytes "
+                     f"over its wall time ({', '.join(f'{w:.3g}' for w, _, _ in runs)} s)",
+           "steps_gbs": [round(v, 4) for v in rates]}
     if one_core:
-        out["one_core_gbs_per_field"] = {"median": round(statistics.median(one_core), 4),
-                                         "min": round(min(one_core), 4),
-                                         "max": round(max(one_core), 4)}
+        out["one_core_gbs_per_task"] = {"median": round(statistics.median(one_core), 4),
+                                        "min": round(min(one_core), 4),
+                                        "max": round(max(one_core), 4)}
     return out
 
 
@@ -258,30 +404,47 @@ def cpu_baseline_summary(total_bytes, wall, workers, field_bytes, res):
 # reference arm: the CPU oracle on the host cores
 # ---------------------------------------------------------------------------
 
+def host_fields(a, seed):
+    """The workload's fields as numpy float32 arrays: drawn with torch on the
+    GPU when there is one (the same inputs the GPU arm compresses), else on
+    the host."""
+    import torch
+    dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
+    xs = make_fields(a, seed, dev)
+    out = [x.cpu().numpy() for x in xs]
+    del xs
+    if dev.type == "cuda":
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from paper_1805_07384_gb300 import synth
     import oracle
     oracle.build()
-    fields, meta = synth.climate_batch(a.fields, a.ny, a.nx)
-    psnrs = targets(a, a.fields)
     workers = a.cpu_workers or os.cpu_count() or 1
-    workers = max(1, min(workers, a.fields))
-    nbytes = sum(4 * f.size for f in fields)
-    with cpu_pool(workers) as pool:
-        for _ in range(a.warmup):
-            run_oracle_sample(pool, fields[:workers], psnrs[:workers], a.chunk)
-        times = []
-        for _ in range(a.steps):
-            wall, res = run_oracle_sample(pool, fields, psnrs, a.chunk)
-            times.append(wall)
-    ms = 1e3 * sum(times) / len(times)
-    value = nbytes / (ms / 1e3) / 1e9
-    cpu = cpu_baseline_summary(nbytes, ms / 1e3, workers, [4 * f.size for f in fields], res)
-    cpu["value"] = value
-    cpu["sample"] = f"all {a.fields} fields per step, one field per worker process"
+    shape = field_shape(a)
+    tasks = cpu_tasks(a, shape)
+    workers = max(1, min(workers, len(tasks)))
+    pool = cpu_pool(workers)  # spawned before the first GPU call
+    hf = HostFields(host_fields(a, rank_seed(0)))
+    psnrs = targets(a, a.fields)
+    try:
+        run_cpu_steps(pool, hf, tasks, psnrs, a.chunk, workers, a.warmup)
+        runs = run_cpu_steps(pool, hf, tasks, psnrs, a.chunk, workers, a.steps,
+                             first=a.warmup * workers)
+    finally:
+        pool.close()
+        hf.close()
+    wall = sum(w for w, _, _ in runs)
+    nbytes = sum(b for _, b, _ in runs)
+    value = nbytes / wall / 1e9
+    ms = 1e3 * wall / len(runs)
+    cpu = cpu_baseline_summary(a, runs, workers, len(tasks))
+    cpu["value"] = round(value, 4)
+    cpu["sample"] = cpu["sample"].replace("median over the steps of", "total over the steps of")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -293,24 +456,33 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
-def targets(a, count):
-    """Target PSNR of every field: the mixed sweep, or one value for all (--psnr)."""
-    from paper_1805_07384_gb300 import synth
-    return [a.psnr if a.psnr > 0 else synth.mixed_psnr(i) for i in range(count)]
+WORKLOAD_TEXT = {
+    "c0": "one 2D float32 GRF field 512x512 (P(k)~k^-3, rescaled to [-1,1], seed 0), 2D Lorenzo",
+    "c1": "{F} climate-like 2D float32 GRF fields {ny}x{nx} (alpha~U[2,4], affine offsets "
+          "1e-3..1e5, 1 field with a constant rectangle), 2D Lorenzo",
+    "c2": "{F} hurricane-like 3D float32 fields 100x500x500 (anisotropic GRFs, correlation length "
+          "4x longer horizontally; field 0 with a vortex mean; 2 fields with 0.1% spikes at "
+          "50 std), 3D Lorenzo",
+    "c3": "{F} NYX-like 3D float32 fields {n}^3 (2 lognormal densities exp(2G), G a GRF with "
+          "P(k)~k^-2; 3 velocity GRFs P(k)~k^-3; 1 temperature exp(G)), 3D Lorenzo",
+}
+TARGET_TEXT = {"c0": "target PSNR 80 dB",
+               "c1": "target PSNR field i -> {40,60,80,100,120}[i mod 5] dB",
+               "c2": "target PSNR field i -> 30 + 10 (i mod 10) dB",
+               "c3": "target PSNR field i -> {40,60,80}[i mod 3] dB"}
 
 
 def workload_config(a, streams):
-    c = {"workload": f"{a.fields} climate-like 2D float32 GRF fields {a.ny}x{a.nx} "
-                     f"(alpha~U[2,4], affine offsets 1e-3..1e5, 1 field with a constant "
-                     f"rectangle), "
-                     + (f"target PSNR {a.psnr:g} dB for every field, " if a.psnr > 0 else
-                        "target PSNR field i -> {40,60,80,100,120}[i mod 5] dB, ") +
-                     f"2D Lorenzo, R=32768, chunk {a.chunk}",
-         "fields": a.fields, "shape": [a.ny, a.nx], "radius": 32768, "chunk": a.chunk,
-         "lorenzo_dims": 2,
-         "l2": (f"inputs {a.fields * a.ny * a.nx * 4 / 1e6:.0f} MB > 129 MB L2, no flush"
-                if a.fields * a.ny * a.nx * 4 > 129e6 else
-                f"inputs {a.fields * a.ny * a.nx * 4 / 1e6:.1f} MB fit the 129 MB L2 (small case)")}
+    shape = field_shape(a)
+    total = a.fields * 4 * math.prod(shape)
+    text = WORKLOAD_TEXT[a.workload].format(F=a.fields, ny=a.ny, nx=a.nx, n=a.n3)
+    tgt = f"target PSNR {a.psnr:g} dB for every field" if a.psnr > 0 else TARGET_TEXT[a.workload]
+    c = {"workload": f"{a.workload}: {text}, {tgt}, R=32768, chunk {a.chunk}",
+         "name": a.workload, "fields": a.fields, "shape": list(shape), "radius": 32768,
+         "chunk": a.chunk, "lorenzo_dims": len(shape),
+         "l2": (f"inputs {total / 1e6:.0f} MB > 129 MB L2, no flush" if total > L2_FLUSH_BELOW else
+                f"inputs {total / 1e6:.1f} MB fit the 129 MB L2: a 512 MB buffer is written "
+                f"between timed steps (outside the events) to flush it")}
     if streams is not None:
         c["mode"] = getattr(a, "mode", "batch")
         if c["mode"] == "streams":
@@ -319,6 +491,10 @@ def workload_config(a, streams):
             c["sub_batches"] = max(1, min(a.sub_batches, a.fields, streams))
         c["launch"] = "eager" if getattr(a, "no_graph", False) else "one CUDA graph per step"
     return c
+
+
+# inputs at most this large are timed step by step with an L2 flush in between
+L2_FLUSH_BELOW = 256 * 10**6
 
 
 # ---------------------------------------------------------------------------
@@ -465,12 +641,20 @@ def write_traffic(path):
     print(dst)
 
 
-# algorithmic bytes per launch of each stage (N points, B compressed bytes of one field)
-def stage_bytes(stage, N, B):
+# algorithmic bytes per launch of each stage (N points, B compressed bytes of one
+# field; ndim of the predictor)
+def stage_bytes(stage, N, B, ndim=2):
     # 2D fields: decode writes 16-bit symbols; the band pass reads them and the
-    # final band scan reads them again and writes the floats
-    return {"range_plan": 4 * N, "predict_quantize": 6 * N, "encode": 2 * N + B,
-            "decode": B + 2 * N, "band_sum": 2 * N, "scan_final_dequant": 6 * N}.get(stage)
+    # final band scan reads them again and writes the floats.  3D fields: the
+    # x pass reads the symbols and writes int32 lattice sums, the y pass reads
+    # and writes them, the z pass reads them and writes the floats.
+    table = {"range_plan": 4 * N, "predict_quantize": 6 * N, "encode": 2 * N + B,
+             "decode": B + 2 * N}
+    if ndim == 2:
+        table.update({"band_sum": 2 * N, "scan_final_dequant": 6 * N})
+    else:
+        table.update({"scan_x": 6 * N, "scan_y": 8 * N, "scan_final_dequant": 8 * N})
+    return table.get(stage)
 
 
 # ---------------------------------------------------------------------------
@@ -670,11 +854,15 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    # CPU baseline pool first (spawn), rank 0 only
+    shape = field_shape(a)
+    N = math.prod(shape)
+    ndim = len(shape)
+    # CPU baseline pool first (spawn, before the first GPU call), rank 0 only
     pool = None
+    tasks = cpu_tasks(a, shape)
     if rank == 0 and not a.no_cpu_baseline:
         workers = a.cpu_workers or os.cpu_count() or 1
-        workers = max(1, min(workers, a.fields))
+        workers = max(1, min(workers, len(tasks)))
         import oracle
         oracle.build()
         pool = cpu_pool(workers)
@@ -682,12 +870,11 @@ def main():
 
     from paper_1805_07384_gb300 import build as fbuild
     fbuild.build()
-    from paper_1805_07384_gb300 import fpsnr, synth
+    from paper_1805_07384_gb300 import fpsnr
 
     F, S = a.fields, max(1, a.streams)
-    fields, meta = synth.climate_batch(F, a.ny, a.nx, seed=rank_seed(rank), device=dev)
+    fields = make_fields(a, rank_seed(rank), dev)
     psnrs = targets(a, F)
-    N = a.ny * a.nx
     tuning = None
     if a.autotune:
         tuning = {}
@@ -697,16 +884,16 @@ def main():
         plans = []
         for i in range(F):
             t = tuning[psnrs[i]]
-            p = fpsnr.Plan((a.ny, a.nx), psnrs[i], chunk=t["chunk"])
+            p = fpsnr.Plan(shape, psnrs[i], chunk=t["chunk"])
             # the decoder's block size is left to each batched launch
             p.set_tuning({"pq_tile_x": t["pq_tile_x"], "band_rows": t["band_rows"]})
             plans.append(p)
     else:
-        plans = [fpsnr.Plan((a.ny, a.nx), psnrs[i], chunk=a.chunk) for i in range(F)]
+        plans = [fpsnr.Plan(shape, psnrs[i], chunk=a.chunk) for i in range(F)]
     outs = [p.alloc_out() for p in plans]
     nbs = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(F)]
     sts = [torch.zeros(fpsnr.STATS_BYTES, dtype=torch.uint8, device=dev) for _ in range(F)]
-    recs = [torch.empty((a.ny, a.nx), dtype=torch.float32, device=dev) for _ in range(F)]
+    recs = [torch.empty(shape, dtype=torch.float32, device=dev) for _ in range(F)]
     dsts = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in range(F)]
     streams = [torch.cuda.Stream(device=dev) for _ in range(S)]
     main_s = torch.cuda.current_stream(dev)
@@ -841,17 +1028,34 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # inputs that fit L2 are timed step by step, with a 512 MB write between
+    # the steps (outside the events) that evicts them
+    flush = (torch.empty(512 * 2**20, dtype=torch.uint8, device=dev)
+             if 4 * N * F <= L2_FLUSH_BELOW else None)
+
     def timed(k, nstreams, graph=False, **kw):
         barrier()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
         wall0 = time.perf_counter()
-        t0.record(main_s)
-        for _ in range(k):
-            run_step(nstreams, graph, **kw)
-        t1.record(main_s)
-        barrier()
-        ms = max_over_ranks(t0.elapsed_time(t1) / k, world, dist, dev)
+        if flush is None:
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(main_s)
+            for _ in range(k):
+                run_step(nstreams, graph, **kw)
+            t1.record(main_s)
+            barrier()
+            total = t0.elapsed_time(t1)
+        else:
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(k)]
+            for e0, e1 in ev:
+                flush.zero_()
+                e0.record(main_s)
+                run_step(nstreams, graph, **kw)
+                e1.record(main_s)
+            barrier()
+            total = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+        ms = max_over_ranks(total / k, world, dist, dev)
         return ms, (time.perf_counter() - wall0)
 
     use_graph = not a.no_graph
@@ -929,17 +1133,23 @@ def main():
             fpsnr.fpsnr_plan_profile(p.handle, False)
         for name, e in agg.items():
             # algorithmic bytes of the stage for every field, every timed step
-            sb = [stage_bytes(name, N, comp_bytes[i]) for i in range(F)]
+            sb = [stage_bytes(name, N, comp_bytes[i], ndim) for i in range(F)]
             e[2] = a.steps * sum(sb) if e[1] and all(v is not None for v in sb) else 0
         step_ms = ms1
-        stage_table = {k: {"ms_per_step": round(v[0] / a.steps, 4), "launches_per_step": v[1] // a.steps,
-                           "share": round(v[0] / a.steps / step_ms, 4),
-                           "gbs": round(v[2] / (v[0] / 1e3) / 1e9, 1) if v[0] > 0 and v[2] else None}
-                       for k, v in agg.items() if v[1]}
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
         peak = peaks["hbm_gbs"] if peaks else 6800.0
-        bw_stages = {k: v for k, v in agg.items() if stage_bytes(k, N, 1) is not None and v[0] > 0}
+        stage_table = {}
+        for k, v in agg.items():
+            if not v[1]:
+                continue
+            gbs = v[2] / (v[0] / 1e3) / 1e9 if v[0] > 0 and v[2] else None
+            stage_table[k] = {"ms_per_step": round(v[0] / a.steps, 4),
+                              "launches_per_step": v[1] // a.steps,
+                              "share": round(v[0] / a.steps / step_ms, 4),
+                              "gbs": round(gbs, 1) if gbs else None,
+                              "frac_of_hbm": round(gbs / peak, 4) if gbs else None}
+        bw_stages = {k: v for k, v in agg.items() if stage_bytes(k, N, 1, ndim) is not None and v[0] > 0}
         dom = max(bw_stages.items(), key=lambda kv: kv[1][0]) if bw_stages else None
         if dom:
             name, (t, n, byts) = dom
@@ -961,7 +1171,7 @@ def main():
     e2e = None
     if not a.no_e2e:
         h2d = [f.cpu().pin_memory() for f in fields]
-        d2h = ([torch.empty((a.ny, a.nx), dtype=torch.float32).pin_memory() for _ in range(F)],
+        d2h = ([torch.empty(shape, dtype=torch.float32).pin_memory() for _ in range(F)],
                [torch.empty((len(g), fpsnr.STATS_BYTES), dtype=torch.uint8).pin_memory()
                 for g in egroups]
                if a.mode == "batch" else
@@ -981,13 +1191,19 @@ def main():
 
     cpu = None
     if pool is not None:
-        fields_np = [f.cpu().numpy() for f in fields]
-        wall, res = run_oracle_sample(pool, fields_np, psnrs, a.chunk)
-        pool.close()
-        cpu = cpu_baseline_summary(total_bytes, wall, pool_workers, [4 * f.size for f in fields_np], res)
-        for (t, nbyt, p_or), pf in zip(res, per_field):
-            pf["oracle_psnr"] = round(p_or, 6)
-            pf["oracle_s"] = round(t, 3)
+        hf = HostFields([f.cpu().numpy() for f in fields])
+        try:
+            runs = run_cpu_steps(pool, hf, tasks, psnrs, a.chunk, pool_workers, max(1, a.cpu_steps))
+        finally:
+            pool.close()
+            hf.close()
+        cpu = cpu_baseline_summary(a, runs, pool_workers, len(tasks))
+        if a.workload != "c3":
+            # whole fields: the oracle's PSNR and seconds beside the GPU's
+            for _, _, tr in runs:
+                for (f, _, _), _, (t, nbyt, p_or) in tr:
+                    per_field[f]["oracle_psnr"] = round(p_or, 6)
+                    per_field[f]["oracle_s"] = round(t, 3)
 
     if rank == 0:
         line = {

@@ -165,11 +165,17 @@ def mixed_psnr(i: int, sweep=PSNR_SWEEP_2D) -> float:
     return float(sweep[i % len(sweep)])
 
 
-def hurricane_batch(count: int = 13, nz: int = 100, ny: int = 500, nx: int = 500, seed: int = 2):
+def hurricane_batch(count: int = 13, nz: int = 100, ny: int = 500, nx: int = 500, seed: int = 2,
+                    device=None):
     """Hurricane-like batch: anisotropic GRFs (horizontal correlation length 4x
     the vertical one; z is the slowest, vertical axis), field 0 plus a smooth
     vortex-shaped mean, two fields with 0.1% of points spiked to 50x the std.
-    Returns (fields, meta); target PSNRs are 30..120 dB step 10 (psnr_i)."""
+    Returns (fields, meta); target PSNRs are 30..120 dB step 10 (psnr_i).
+    With `device` the fields are drawn with torch there and returned as
+    float32 torch tensors on that device (same recipe, different random
+    stream)."""
+    if device is not None:
+        return _hurricane_batch_torch(count, nz, ny, nx, seed, device)
     rng = np.random.default_rng(seed)
     spike_ids = set(rng.choice(np.arange(1, count), size=min(2, count - 1), replace=False).tolist()) \
         if count > 1 else set()
@@ -190,6 +196,35 @@ def hurricane_batch(count: int = 13, nz: int = 100, ny: int = 500, nx: int = 500
             spikes = int(m.sum())
         fields.append(g.astype(np.float32))
         meta.append(dict(seed=fseed, vortex=(i == 0), spikes=spikes, psnr=30.0 + 10.0 * (i % 10)))
+    return fields, meta
+
+
+def _hurricane_batch_torch(count, nz, ny, nx, seed, device):
+    import torch
+    rng = np.random.default_rng(seed)
+    spike_ids = set(rng.choice(np.arange(1, count), size=min(2, count - 1), replace=False).tolist()) \
+        if count > 1 else set()
+    fields, meta = [], []
+    for i in range(count):
+        fseed = int(rng.integers(0, 2**31 - 1))
+        g = grf_torch((nz, ny, nx), 3.0, fseed, device, stretch=(4.0, 1.0, 1.0))
+        if i == 0:
+            zz = torch.linspace(0, 1, nz, device=device, dtype=torch.float64).reshape(nz, 1, 1)
+            yy = torch.linspace(-1, 1, ny, device=device, dtype=torch.float64).reshape(1, ny, 1)
+            xx = torch.linspace(-1, 1, nx, device=device, dtype=torch.float64).reshape(1, 1, nx)
+            r = torch.sqrt(xx * xx + yy * yy) / 0.3
+            g = g + 5.0 * r * torch.exp(1.0 - r) * (1.0 - 0.5 * zz)
+        spikes = 0
+        if i in spike_ids:
+            sd = float(g.std())
+            gen = torch.Generator(device=device)
+            gen.manual_seed(fseed + 1)
+            m = torch.rand(g.shape, generator=gen, device=device, dtype=torch.float64) < 1e-3
+            g = torch.where(m, g + 50.0 * sd, g)
+            spikes = int(m.sum().item())
+        fields.append(g.to(torch.float32).contiguous())
+        meta.append(dict(seed=fseed, vortex=(i == 0), spikes=spikes, psnr=30.0 + 10.0 * (i % 10)))
+        del g
     return fields, meta
 
 

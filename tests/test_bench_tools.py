@@ -1,5 +1,6 @@
-"""bench.py's host-side helpers: the per-field targets (--psnr), the launch
-table and the DRAM traffic file built from ncu --csv logs (no GPU)."""
+"""bench.py's host-side helpers: the workloads and their targets, the CPU
+baseline's tasks, field file and summary, the launch table and the DRAM
+traffic file built from ncu --csv logs (no GPU)."""
 import json
 import os
 import sys
@@ -27,17 +28,83 @@ def _log(tmp_path, rows):
     return str(p)
 
 
-def test_targets():
+def _args(*argv):
     old = sys.argv
     try:
-        sys.argv = ["bench.py"]
-        assert bench.targets(bench.parse(), 7) == [40.0, 60.0, 80.0, 100.0, 120.0, 40.0, 60.0]
-        sys.argv = ["bench.py", "--psnr", "90"]
-        a = bench.parse()
-        assert bench.targets(a, 3) == [90.0, 90.0, 90.0]
-        assert "target PSNR 90 dB for every field" in bench.workload_config(a, None)["workload"]
+        sys.argv = ["bench.py", *argv]
+        return bench.parse()
     finally:
         sys.argv = old
+
+
+def test_targets_per_workload():
+    a = _args()
+    assert a.workload == "c3" and a.fields == 6
+    assert bench.targets(a, 6) == [40.0, 60.0, 80.0, 40.0, 60.0, 80.0]
+    assert bench.field_shape(a) == (512, 512, 512)
+    a = _args("--workload", "c1")
+    assert a.fields == 24
+    assert bench.targets(a, 7) == [40.0, 60.0, 80.0, 100.0, 120.0, 40.0, 60.0]
+    a = _args("--workload", "c2")
+    assert a.fields == 13 and bench.field_shape(a) == (100, 500, 500)
+    assert bench.targets(a, 13)[:11] == [30.0 + 10 * k for k in range(10)] + [30.0]
+    a = _args("--workload", "c0")
+    assert a.fields == 1 and bench.targets(a, 1) == [80.0]
+    assert "fit the 129 MB L2" in bench.workload_config(a, None)["l2"]
+    a = _args("--workload", "c1", "--psnr", "90")
+    assert bench.targets(a, 3) == [90.0, 90.0, 90.0]
+    assert "target PSNR 90 dB for every field" in bench.workload_config(a, None)["workload"]
+    for wl in bench.WORKLOADS:
+        c = bench.workload_config(_args("--workload", wl), 3)
+        assert c["name"] == wl and c["workload"].startswith(wl + ":")
+    with pytest.raises(SystemExit):
+        _args("--workload", "c3", "--fields", "7")
+
+
+def test_cpu_tasks():
+    """c3 is cut into 64-plane z-slabs covering every plane of every field;
+    the other workloads take whole fields."""
+    a = _args()
+    t = bench.cpu_tasks(a, (512, 512, 512))
+    assert len(t) == 48 and len(set(t)) == 48
+    for f in range(6):
+        planes = sorted((z0, z1) for g, z0, z1 in t if g == f)
+        assert planes[0][0] == 0 and planes[-1][1] == 512
+        assert all(p[1] == q[0] for p, q in zip(planes, planes[1:]))
+    a = _args("--workload", "c2")
+    assert bench.cpu_tasks(a, (100, 500, 500)) == [(f, 0, 100) for f in range(13)]
+
+
+def test_host_fields_and_oracle_task():
+    """The shared field file holds every field at its offset; a task runs the
+    oracle on its planes and reports the oracle's own PSNR."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(0)
+    xs = [rng.standard_normal((6, 5, 7)).astype(np.float32), rng.standard_normal((3, 9)).astype(np.float32)]
+    hf = bench.HostFields(xs)
+    try:
+        args = hf.args((0, 2, 5), [60.0, 80.0], 256)
+        v = np.memmap(args[0], dtype=np.float32, mode="r", offset=args[1], shape=args[2])
+        assert np.array_equal(v, xs[0])
+        assert hf.task_bytes((0, 2, 5)) == 4 * 3 * 5 * 7
+        dt, nb, p = bench.oracle_task(args)
+        blob, st = oracle.compress(xs[0][2:5], 60.0)
+        assert nb == len(blob) and p == st["psnr_actual"] and dt > 0
+        args = hf.args((1, 0, 3), [60.0, 80.0], 256)
+        v = np.memmap(args[0], dtype=np.float32, mode="r", offset=args[1], shape=args[2])
+        assert np.array_equal(v, xs[1])
+    finally:
+        hf.close()
+    assert not os.path.exists(args[0])
+
+
+def test_stage_bytes():
+    assert bench.stage_bytes("predict_quantize", 10, 3) == 60
+    assert bench.stage_bytes("scan_final_dequant", 10, 3, 2) == 60
+    assert bench.stage_bytes("scan_final_dequant", 10, 3, 3) == 80
+    assert bench.stage_bytes("band_sum", 10, 3, 3) is None
+    assert bench.stage_bytes("decode", 10, 3, 3) == 23
 
 
 def test_launch_table(tmp_path):
@@ -97,10 +164,14 @@ def test_write_traffic(tmp_path, monkeypatch):
 
 
 def test_cpu_baseline_summary():
-    """Whole-batch GB/s over the pool's wall time, plus each field's one-core
+    """Median over the steps of each round's GB/s, plus each task's one-core
     GB/s from its worker's own time."""
-    res = [(2.0, 10, 80.0), (1.0, 10, 60.0), (4.0, 10, 40.0)]
-    c = bench.cpu_baseline_summary(3_000_000_000, 5.0, 3, [1e9, 1e9, 1e9], res)
-    assert c["value"] == 0.6 and c["cores"] == 3 and c["kind"] == "oracle"
-    assert c["one_core_gbs_per_field"] == {"median": 0.5, "min": 0.25, "max": 1.0}
-    assert "3 fields" in c["sample"]
+    a = _args("--workload", "c1")
+    runs = [(2.0, 2 * 10**9, [((0, 0, 1), 10**9, (2.0, 10, 80.0)), ((1, 0, 1), 10**9, (1.0, 10, 60.0))]),
+            (1.0, 2 * 10**9, [((2, 0, 1), 10**9, (4.0, 10, 40.0)), ((3, 0, 1), 10**9, (0.5, 10, 40.0))]),
+            (4.0, 2 * 10**9, [((0, 0, 1), 10**9, (1.0, 10, 80.0)), ((1, 0, 1), 10**9, (1.0, 10, 60.0))])]
+    c = bench.cpu_baseline_summary(a, runs, 2, 24)
+    assert c["value"] == 1.0 and c["cores"] == 2 and c["kind"] == "oracle"
+    assert c["steps_gbs"] == [1.0, 2.0, 0.5]
+    assert c["one_core_gbs_per_task"] == {"median": 1.0, "min": 0.25, "max": 2.0}
+    assert "3 steps" in c["sample"] and "24 fields" in c["sample"]
