@@ -13,6 +13,8 @@ Lossy Compression for Scientific Data"):
 * ``lattice`` -- prediction + uniform quantization (Sec. II-A, Sec. III, Sec. IV)
 * ``huffman_lengths`` / ``canonical_codes`` -- SZ's Huffman stage (Sec. II-A)
 * ``compress`` / ``decompress`` -- the whole pipeline and its inverse (Sec. III, Eq. 1)
+* ``fine_hist`` / ``pred_mse`` / ``refine_eb`` -- the optional bound refinement on the
+  field's empirical PDF (Eq. 3); ``sum_exact`` -- the exactly rounded sum of its terms
 * ``psnr`` -- Eq. 4-5 (sign of Eq. 5 read as 20 log10 vr - 10 log10 MSE)
 * ``classic_sz`` -- comparison path predicting from reconstructed values (Sec. III)
 
@@ -111,7 +113,9 @@ def lib():
             L.or_fine_hist.restype = None
             L.or_fine_hist.argtypes = [P, C.c_uint64, C.c_float, C.c_double, P]
             L.or_pred_mse.restype = C.c_double
-            L.or_pred_mse.argtypes = [P, C.c_uint64, C.c_double, C.c_double]
+            L.or_pred_mse.argtypes = [P, C.c_uint64, C.c_double]
+            L.or_sum_exact.restype = C.c_double
+            L.or_sum_exact.argtypes = [P, P, C.c_uint32]
             L.or_refine_eb.restype = C.c_double
             L.or_refine_eb.argtypes = [P, C.c_uint64, C.c_double, C.c_double, C.c_double]
             L.or_decompress.argtypes = [P, C.c_uint64, P, C.c_uint64]
@@ -331,14 +335,25 @@ def fine_hist(x: np.ndarray, xmin: float, vr: float) -> np.ndarray:
     return h
 
 
-def pred_mse(h: np.ndarray, n: int, vr: float, eb: float) -> float:
+def pred_mse(h: np.ndarray, n: int, r: float) -> float:
+    """Eq. 3's predicted MSE over vr^2 for the relative bound r = eb / vr."""
     h = np.ascontiguousarray(h, dtype=np.uint32)
-    return lib().or_pred_mse(_ptr(h), int(n), float(vr), float(eb))
+    return lib().or_pred_mse(_ptr(h), int(n), float(r))
 
 
-def refine_eb(h: np.ndarray, n: int, vr: float, eb0: float, mse_target: float) -> float:
+def sum_exact(h, t) -> float:
+    """sum(h[i] * t[i]) for uint32 counts and finite non-negative float32
+    terms, computed exactly and rounded once to the nearest double."""
     h = np.ascontiguousarray(h, dtype=np.uint32)
-    return lib().or_refine_eb(_ptr(h), int(n), float(vr), float(eb0), float(mse_target))
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    assert h.size == t.size
+    return lib().or_sum_exact(_ptr(h), _ptr(t), h.size)
+
+
+def refine_eb(h: np.ndarray, n: int, vr: float, eb0: float, mse_rel: float) -> float:
+    """Largest eb in [eb0/4, 64 eb0] with pred_mse(h, n, eb / vr) <= mse_rel."""
+    h = np.ascontiguousarray(h, dtype=np.uint32)
+    return lib().or_refine_eb(_ptr(h), int(n), float(vr), float(eb0), float(mse_rel))
 
 
 def _zcall(fn, data: bytes) -> bytes:

@@ -36,7 +36,9 @@
  *                          over each quantization bin, then the largest eb
  *                          whose predicted MSE meets the target (Sec. V notes
  *                          the constant-PDF estimate degrades as bins widen;
- *                          Sec. VI leaves low targets to future work)
+ *                          Sec. VI leaves low targets to future work); the
+ *                          sum of Eq. 3's terms is exact, rounded once
+ *                          (or_sum_exact)
  *   or_zrle_wrap / or_zrle_unwrap ... optional lossless layer over the finished
  *                          blob, standing in for SZ's lossless step 3 (Sec. II-A,
  *                          "optional"; the paper names GZIP): zero-byte runs
@@ -155,7 +157,6 @@ void or_plan_scalars(double eb_rel, float xmin, float xmax, uint64_t n, or_scala
 /* ------------------------------------------------------------------------ */
 
 #define OR_FINE_BINS 4096   /* bins of the fine histogram over [xmin, xmax] */
-#define OR_SUM_GROUPS 1024  /* the predicted MSE sums 4 bins per group, then pairs of groups */
 #define OR_BISECT_STEPS 16
 
 /* Fine histogram of the field: bin = trunc((x - xmin) * kinv) in float32,
@@ -172,44 +173,91 @@ void or_fine_hist(const float* x, uint64_t n, float xmin, double vr, uint32_t* h
     }
 }
 
-/* Eq. 3 with the PDF taken constant over each fine bin of width w = vr / K
- * rather than over each quantization bin: with midpoint reconstruction on the
- * lattice of step 2eb anchored at xmin, a fine bin centred at c (relative to
- * xmin) contributes h (e^2 + w^2 / 12), e = c - 2eb round(c / 2eb).  Per-bin
- * terms in float32; their sum in FP64, 4 bins per group in order, then the
- * OR_SUM_GROUPS group sums added pairwise (group i += group i + s for s =
- * 512, 256, ..., 1).  Returns the predicted MSE. */
-double or_pred_mse(const uint32_t* h, uint64_t n, double vr, double eb) {
-    const double w = vr / (double)OR_FINE_BINS;
-    const float df = (float)(2.0 * eb);
-    const float w212 = (float)(w * w / 12.0);
-    double part[OR_SUM_GROUPS];
-    for (int t = 0; t < OR_SUM_GROUPS; t++) {
-        double acc = 0.0;
-        for (int k = 0; k < OR_FINE_BINS / OR_SUM_GROUPS; k++) {
-            int j = t * (OR_FINE_BINS / OR_SUM_GROUPS) + k;
-            float c = (float)(((double)j + 0.5) * w);
-            float q = rintf(c / df);
-            float e = c - q * df;
-            float term = e * e + w212;
-            acc = acc + (double)h[j] * (double)term;
+/* Exact sum of k products h[i] * t[i] (h counts, t finite non-negative
+ * floats), rounded once to the nearest double (ties to even).  Every float is
+ * an integer multiple of 2^-149, and h * t < 2^32 * 2^128, so the products
+ * are added without rounding as integers in units of 2^OR_SUM_LSB, in
+ * OR_SUM_LIMBS 32-bit limbs (enough for 4096 terms with room to spare), and
+ * the total is rounded to 53 bits at the end.  The order of the terms does
+ * not matter: integer addition is exact. */
+#define OR_SUM_LIMBS 12
+#define OR_SUM_LSB (-172) /* 2^-149 = 2^23 * 2^-172, the smallest float's mantissa times 2^-172 */
+double or_sum_exact(const uint32_t* h, const float* t, uint32_t k) {
+    uint32_t acc[OR_SUM_LIMBS];
+    memset(acc, 0, sizeof(acc));
+    for (uint32_t i = 0; i < k; i++) {
+        if (h[i] == 0 || t[i] == 0.0f) continue;
+        int e;
+        const float m = frexpf(t[i], &e); /* t = m 2^e, m in [0.5, 1) */
+        const uint64_t mant = (uint64_t)ldexpf(m, 24); /* t = mant 2^(e - 24), mant < 2^24 */
+        uint64_t prod = (uint64_t)h[i] * mant; /* < 2^56 */
+        int shift = e - 24 - OR_SUM_LSB; /* bit position of prod's lowest bit, >= 0 */
+        int limb = shift / 32, bit = shift % 32;
+        /* add prod << bit into limbs limb, limb + 1, ... with carries */
+        uint64_t carry = 0;
+        uint64_t piece[3] = {(prod << bit) & 0xffffffffull, (prod >> (32 - bit)) & 0xffffffffull,
+                             bit ? (prod >> (64 - bit)) : 0};
+        if (bit == 0) piece[1] = (prod >> 32) & 0xffffffffull;
+        for (int j = limb; j < OR_SUM_LIMBS; j++) {
+            uint64_t v = (uint64_t)acc[j] + carry + (j - limb < 3 ? piece[j - limb] : 0);
+            acc[j] = (uint32_t)v;
+            carry = v >> 32;
+            if (j - limb >= 2 && carry == 0) break;
         }
-        part[t] = acc;
     }
-    for (int s2 = OR_SUM_GROUPS / 2; s2 >= 1; s2 >>= 1)
-        for (int i = 0; i < s2; i++) part[i] = part[i] + part[i + s2];
-    return part[0] / (double)n;
+    /* highest set bit */
+    int top = -1;
+    for (int j = OR_SUM_LIMBS - 1; j >= 0 && top < 0; j--)
+        for (int b = 31; b >= 0; b--)
+            if ((acc[j] >> b) & 1u) { top = 32 * j + b; break; }
+    if (top < 0) return 0.0;
+#define BIT(p) ((int)((acc[(p) / 32] >> ((p) % 32)) & 1u))
+    /* the 53 bits from the top down, then the round bit and the sticky bits */
+    const int low = top - 52 > 0 ? top - 52 : 0;
+    uint64_t mant = 0;
+    for (int p = top; p >= low; p--) mant = (mant << 1) | (uint64_t)BIT(p);
+    if (low > 0) {
+        const int round = BIT(low - 1);
+        int sticky = 0;
+        for (int p = low - 2; p >= 0 && !sticky; p--) sticky = BIT(p);
+        if (round && (sticky || (mant & 1u))) mant++; /* 2^53 is still exact */
+    }
+#undef BIT
+    return ldexp((double)mant, low + OR_SUM_LSB);
 }
 
-/* Largest eb in [eb0 / 4, 64 eb0] whose predicted MSE does not exceed
- * mse_target, by OR_BISECT_STEPS bisections on the geometric midpoint. */
-double or_refine_eb(const uint32_t* h, uint64_t n, double vr, double eb0, double mse_target) {
+/* Eq. 3 with the PDF taken constant over each fine bin rather than over each
+ * quantization bin, in units of the value range (Eq. 3 is scale invariant, and
+ * in these units every term is a moderate float whatever the field's range):
+ * with midpoint reconstruction on the lattice of step 2r (r = eb / vr)
+ * anchored at xmin, the fine bin j, of width w = 1/K and centre
+ * c = (j + 1/2) w, contributes h_j (e^2 + w^2 / 12), e = c - 2r round(c / 2r).
+ * Per-bin terms in float32; their sum exact, rounded once (or_sum_exact).
+ * Returns the predicted MSE over vr^2. */
+double or_pred_mse(const uint32_t* h, uint64_t n, double r) {
+    const double w = 1.0 / (double)OR_FINE_BINS;
+    const float df = (float)(2.0 * r);
+    const float w212 = (float)(w * w / 12.0);
+    float term[OR_FINE_BINS];
+    for (int j = 0; j < OR_FINE_BINS; j++) {
+        float c = (float)(((double)j + 0.5) * w);
+        float q = rintf(c / df);
+        float e = c - q * df;
+        term[j] = e * e + w212;
+    }
+    return or_sum_exact(h, term, OR_FINE_BINS) / (double)n;
+}
+
+/* Largest eb in [eb0 / 4, 64 eb0] whose predicted MSE over vr^2 does not
+ * exceed mse_rel = 10^(-PSNR/10), by OR_BISECT_STEPS bisections on the
+ * geometric midpoint. */
+double or_refine_eb(const uint32_t* h, uint64_t n, double vr, double eb0, double mse_rel) {
     double lo = eb0 * 0.25, hi = eb0 * 64.0;
-    if (or_pred_mse(h, n, vr, lo) > mse_target) return lo;
-    if (or_pred_mse(h, n, vr, hi) <= mse_target) return hi;
+    if (or_pred_mse(h, n, lo / vr) > mse_rel) return lo;
+    if (or_pred_mse(h, n, hi / vr) <= mse_rel) return hi;
     for (int it = 0; it < OR_BISECT_STEPS; it++) {
         double mid = sqrt(lo * hi);
-        if (or_pred_mse(h, n, vr, mid) <= mse_target) lo = mid;
+        if (or_pred_mse(h, n, mid / vr) <= mse_rel) lo = mid;
         else hi = mid;
     }
     return lo;
@@ -712,8 +760,8 @@ int or_compress_mode(const float* x, int ndim, const uint64_t* dims_in, int lore
         uint32_t* fh = (uint32_t*)malloc(OR_FINE_BINS * sizeof(uint32_t));
         if (!fh) return st->status = OR_ENOMEM;
         or_fine_hist(x, n, xmin, p.vr, fh);
-        const double mse_target = p.vr * p.vr * pow(10.0, -target_psnr / 10.0);
-        const double eb = or_refine_eb(fh, n, p.vr, p.eb_abs, mse_target);
+        const double mse_rel = pow(10.0, -target_psnr / 10.0);
+        const double eb = or_refine_eb(fh, n, p.vr, p.eb_abs, mse_rel);
         free(fh);
         p.flags = 0;
         p.eb_rel = eb / p.vr;

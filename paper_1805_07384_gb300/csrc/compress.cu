@@ -201,12 +201,14 @@ __global__ void __launch_bounds__(512) k_range_plan(const __grid_constant__ Batc
 // Eq. 8 takes the quantization error as uniform over every bin (Eq. 6).  With
 // psnr_mode 1 the bound is refined on a kFineBins-bin histogram of the field:
 // every fine bin contributes h (e^2 + w^2/12), e the lattice error of its
-// centre, and a fixed bisection finds the largest eb whose predicted MSE meets
-// the target.  Only when Eq. 8's bin spans at least 16 fine bins.  The order of
-// every operation is fixed (float per-bin terms, FP64 sums over 1024 groups of
-// 4 bins, a pairwise tree), and explicit round-to-nearest intrinsics keep the
-// compiler from fusing any of them, so the result is the same bit for bit
-// wherever it is computed.
+// centre, w its width, and a fixed bisection finds the largest eb whose
+// predicted MSE meets the target.  Only when Eq. 8's bin spans at least 16
+// fine bins.  Eq. 3 is scale invariant, so it is evaluated in units of the
+// value range (w = 1/K, bin centres (j + 1/2)/K, lattice step 2 eb/vr, target
+// 10^(-PSNR/10)): every float term is then a moderate number whatever the
+// field's range.  Per-bin terms are computed in float with explicit
+// round-to-nearest intrinsics; their weighted sum is exact and rounded once,
+// so the result does not depend on how the sum is split among threads.
 
 __device__ __forceinline__ bool refine_applies(const DevParams* par) {
     return par->flags == 0 && __dmul_rn(par->eb_abs, (double)kFineBins) >= __dmul_rn(8.0, par->vr);
@@ -265,15 +267,73 @@ struct RefineArgs {
 constexpr int kRefineThreads = 1024;
 constexpr int kBisectSteps = 16;
 
+// Unsigned 128-bit integer as two 64-bit halves.
+struct U128 {
+    uint64_t lo, hi;
+};
+
+__device__ __forceinline__ U128 u128_add(U128 a, U128 b) {
+    U128 r;
+    r.lo = a.lo + b.lo;
+    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
+    return r;
+}
+
+// p << s for p < 2^56 and 0 <= s < 72.
+__device__ __forceinline__ U128 u128_shl(uint64_t p, uint32_t s) {
+    U128 r;
+    if (s == 0) {
+        r.lo = p;
+        r.hi = 0;
+    } else if (s < 64) {
+        r.lo = p << s;
+        r.hi = p >> (64 - s);
+    } else {
+        r.lo = 0;
+        r.hi = p << (s - 64);
+    }
+    return r;
+}
+
+// Nearest double (ties to even) to v * 2^e (v < 2^127, result within the
+// normal range).
+__device__ double u128_to_double_rn(U128 v, int e) {
+    if (v.hi == 0 && v.lo < (1ull << 53)) return __dmul_rn((double)v.lo, ldexp(1.0, e));
+    const int top = v.hi ? 127 - __clzll((long long)v.hi) : 63 - __clzll((long long)v.lo);
+    const int sh = top - 52;  // >= 1: bits below sh are rounded off
+    uint64_t mant;
+    if (sh < 64) mant = (v.lo >> sh) | (sh ? (v.hi << (64 - sh)) : 0ull);
+    else mant = v.hi >> (sh - 64);
+    const int rb = sh - 1;  // round bit position
+    const uint32_t round = (uint32_t)((rb < 64 ? (v.lo >> rb) : (v.hi >> (rb - 64))) & 1ull);
+    bool sticky;
+    if (rb == 0) sticky = false;
+    else if (rb < 64) sticky = (v.lo & ((1ull << rb) - 1ull)) != 0ull;
+    else if (rb == 64) sticky = v.lo != 0ull;
+    else sticky = v.lo != 0ull || (v.hi & ((1ull << (rb - 64)) - 1ull)) != 0ull;
+    if (round && (sticky || (mant & 1ull))) mant++;  // 2^53 is exact
+    return __dmul_rn((double)mant, ldexp(1.0, sh + e));
+}
+
 // One block per field: the bisection of Eq. 3's predicted MSE, then the plan
 // scalars for the refined bound.  Clears the fine histogram for the next call.
+//
+// The weighted sum of the terms is exact.  Every term is at least w212 =
+// fl(w^2/12) (a float e^2 >= 0 plus w212, rounded), so all terms are integer
+// multiples of u = 2^E0, the unit in the last place of w212.  A term is below
+// (111 + 1/K)^2 (|e| <= max(c, step / 2) and the step 2 eb / vr <= 128 sqrt(3)),
+// about 2^42 w212, so term / u < 2^66 and, with sum(h) = n < 2^32, the total
+// is an integer below 2^98 in units of u: each thread adds its products as
+// 128-bit integers, the block adds those, and the total is rounded to a
+// double once.
 __global__ void __launch_bounds__(kRefineThreads) k_eb_refine(const __grid_constant__ Batch<RefineArgs> B) {
     const RefineArgs& A = B.a[blockIdx.x];
     DevParams* par = A.par;
     if (!refine_applies(par)) return;
     static_assert(kFineBins == 4 * kRefineThreads, "4 fine bins per thread");
-    __shared__ double part[kRefineThreads];
-    const uint32_t t = threadIdx.x;
+    __shared__ uint64_t part_lo[kRefineThreads / 32], part_hi[kRefineThreads / 32];
+    __shared__ double s_pred;
+    const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
     uint32_t h[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -281,32 +341,53 @@ __global__ void __launch_bounds__(kRefineThreads) k_eb_refine(const __grid_const
         A.fh[4 * t + k] = 0u;
     }
     const double vr = par->vr, eb0 = par->eb_abs;
-    const double w = __ddiv_rn(vr, (double)kFineBins);
+    const double w = 1.0 / (double)kFineBins;
     const float w212 = __double2float_rn(__ddiv_rn(__dmul_rn(w, w), 12.0));
+    // exponent field of w212 (a normal float): terms are multiples of 2^E0
+    const int bw = (int)((__float_as_uint(w212) >> 23) & 0xffu);
+    const int E0 = (bw > 0 ? bw : 1) - 150;
     float c[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) c[k] = __double2float_rn(__dmul_rn(__dadd_rn((double)(4 * t + k), 0.5), w));
     const double nd = (double)A.n;
     auto pred = [&](double eb) -> double {
-        const float df = __double2float_rn(__dmul_rn(2.0, eb));
-        double acc = 0.0;
+        const float df = __double2float_rn(__dmul_rn(2.0, __ddiv_rn(eb, vr)));
+        U128 acc = {0ull, 0ull};
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const float q = rintf(__fdiv_rn(c[k], df));
             const float e = __fsub_rn(c[k], __fmul_rn(q, df));
             const float term = __fadd_rn(__fmul_rn(e, e), w212);
-            acc = __dadd_rn(acc, __dmul_rn((double)h[k], (double)term));
+            const uint32_t bits = __float_as_uint(term);
+            const int bt = (int)((bits >> 23) & 0xffu);
+            const uint64_t mant = (uint64_t)((bits & 0x7fffffu) | (bt ? 0x800000u : 0u));
+            // term = mant 2^(max(bt, 1) - 150); the shift stays below 66 (see above)
+            const int s = (bt > 0 ? bt : 1) - 150 - E0;
+            const uint32_t sh = (uint32_t)min(max(s, 0), 71);
+            acc = u128_add(acc, u128_shl((uint64_t)h[k] * mant, sh));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            U128 other;
+            other.lo = __shfl_xor_sync(0xffffffffu, acc.lo, o);
+            other.hi = __shfl_xor_sync(0xffffffffu, acc.hi, o);
+            acc = u128_add(acc, other);
         }
         __syncthreads();  // the previous evaluation's result has been read
-        part[t] = acc;
-        __syncthreads();
-        for (uint32_t s2 = kRefineThreads / 2; s2 >= 1; s2 >>= 1) {
-            if (t < s2) part[t] = __dadd_rn(part[t], part[t + s2]);
-            __syncthreads();
+        if (lane == 0) {
+            part_lo[warp] = acc.lo;
+            part_hi[warp] = acc.hi;
         }
-        return __ddiv_rn(part[0], nd);
+        __syncthreads();
+        if (t == 0) {
+            U128 tot = {0ull, 0ull};
+            for (int i = 0; i < kRefineThreads / 32; i++) tot = u128_add(tot, U128{part_lo[i], part_hi[i]});
+            s_pred = __ddiv_rn(u128_to_double_rn(tot, E0), nd);
+        }
+        __syncthreads();
+        return s_pred;
     };
-    const double target = __dmul_rn(__dmul_rn(vr, vr), A.mse_rel);
+    const double target = A.mse_rel;
     double lo = __dmul_rn(eb0, 0.25), hi = __dmul_rn(eb0, 64.0), eb;
     if (pred(lo) > target) {
         eb = lo;

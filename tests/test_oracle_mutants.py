@@ -82,11 +82,24 @@ MUTANTS = [
     ("inverse_lorenzo_skips_second_row", "for (uint64_t y = 1; y < ny; y++)",
      "for (uint64_t y = 2; y < ny; y++)"),
     # histogram-refined bound (Eq. 3)
-    ("pred_mse_drops_bin_variance", "float term = e * e + w212;", "float term = e * e;"),
+    ("pred_mse_drops_bin_variance", "term[j] = e * e + w212;", "term[j] = e * e;"),
     ("pred_mse_floors", "float q = rintf(c / df);", "float q = floorf(c / df);"),
     ("refine_bisection_reversed",
-     "if (or_pred_mse(h, n, vr, mid) <= mse_target) lo = mid;\n        else hi = mid;",
-     "if (or_pred_mse(h, n, vr, mid) <= mse_target) hi = mid;\n        else lo = mid;"),
+     "if (or_pred_mse(h, n, mid / vr) <= mse_rel) lo = mid;\n        else hi = mid;",
+     "if (or_pred_mse(h, n, mid / vr) <= mse_rel) hi = mid;\n        else lo = mid;"),
+    # the exact sum of Eq. 3's terms: another grouping or rounding of it
+    ("pred_mse_sequential_double_sum", "return or_sum_exact(h, term, OR_FINE_BINS) / (double)n;",
+     "double s = 0.0;\n    for (int j = 0; j < OR_FINE_BINS; j++) s += (double)h[j] * (double)term[j];\n"
+     "    return s / (double)n;"),
+    ("pred_mse_blocked_pairwise_sum", "return or_sum_exact(h, term, OR_FINE_BINS) / (double)n;",
+     "double part[1024];\n    for (int g = 0; g < 1024; g++) {\n        double a = 0.0;\n"
+     "        for (int k = 0; k < 4; k++) a += (double)h[4 * g + k] * (double)term[4 * g + k];\n"
+     "        part[g] = a;\n    }\n    for (int s2 = 512; s2 >= 1; s2 >>= 1)\n"
+     "        for (int i = 0; i < s2; i++) part[i] += part[i + s2];\n    return part[0] / (double)n;"),
+    ("exact_sum_truncates", "if (round && (sticky || (mant & 1u))) mant++;", "(void)round;"),
+    ("exact_sum_ties_away", "if (round && (sticky || (mant & 1u))) mant++;", "if (round) mant++;"),
+    ("exact_sum_drops_sticky", "for (int p = low - 2; p >= 0 && !sticky; p--) sticky = BIT(p);",
+     "(void)0;"),
     ("refine_bracket_narrowed", "double lo = eb0 * 0.25, hi = eb0 * 64.0;",
      "double lo = eb0 * 0.25, hi = eb0 * 4.0;"),
     ("refine_gate_at_4_fine_bins", "p.eb_abs * (double)OR_FINE_BINS >= 8.0 * p.vr",

@@ -352,8 +352,8 @@ def test_pred_mse_matches_lattice_sse(oracle):
             blob, st = oracle.compress(x, psnr)
             h = oracle.fine_hist(x, st["xmin"], st["vr"])
             assert int(h.sum()) == x.size
-            pred = oracle.pred_mse(h, x.size, st["vr"], st["eb_abs"])
-            assert pred == pytest.approx(st["mse"], rel=0.02), (psnr, pred, st["mse"])
+            pred = oracle.pred_mse(h, x.size, st["eb_abs"] / st["vr"])
+            assert pred == pytest.approx(st["mse"] / st["vr"] ** 2, rel=0.02), (psnr, pred, st["mse"])
 
 
 def test_pred_mse_brute_force_within_fine_bins(oracle):
@@ -381,12 +381,122 @@ def test_pred_mse_brute_force_within_fine_bins(oracle):
         assert np.all(lat == lat[0])  # one quantization bin per fine bin
         brute += c * float(np.mean((xs - lat) ** 2))
     brute /= n
-    assert oracle.pred_mse(h, n, vr, eb) == pytest.approx(brute, rel=1e-6)
+    assert oracle.pred_mse(h, n, eb / vr) == pytest.approx(brute / vr ** 2, rel=1e-6)
     h1 = np.zeros(K, np.uint32)
     h1[0] = 1  # the bin [0, w]: nearest lattice point 0
     xs = (np.arange(m) + 0.5) / m * w
     assert float(np.mean(xs ** 2)) == pytest.approx(w * w / 3.0, rel=1e-6)
-    assert oracle.pred_mse(h1, 1, vr, eb) == pytest.approx(float(np.mean(xs ** 2)), rel=1e-6)
+    assert oracle.pred_mse(h1, 1, eb / vr) == pytest.approx(float(np.mean(xs ** 2)), rel=1e-6)
+
+
+def _exact(h, t):
+    """sum(h * t) as an exact rational, rounded once to the nearest double
+    (Python's int / int division is correctly rounded)."""
+    from fractions import Fraction
+    s = sum(Fraction(int(a)) * Fraction(float(b)) for a, b in zip(h, t))
+    return s.numerator / s.denominator if s else 0.0
+
+
+def test_sum_exact_against_rationals(oracle):
+    """The sum of Eq. 3's terms is the exact sum rounded once: against exact
+    rational arithmetic on inputs where any other order or grouping of
+    double additions rounds differently."""
+    f32 = np.float32
+    # (a) 4095 terms of half an ulp of the first: added one by one in double
+    # every addition is a tie that rounds back down; exactly they add
+    # 4095 * 2^7 = 2047.5 ulps, which rounds (ties to even) to 2048 ulps
+    h = np.ones(4096, np.uint32)
+    t = np.full(4096, 128.0, f32)
+    t[0] = f32(2.0 ** 60)
+    assert oracle.sum_exact(h, t) == 2.0 ** 60 + 2.0 ** 19
+    naive = 0.0
+    for a, b in zip(h, t):
+        naive += float(a) * float(b)
+    assert naive == 2.0 ** 60
+    # (b) ties at the 53rd bit: 2^53 + 1 rounds to even (down), 2^53 + 3 up
+    assert oracle.sum_exact(np.array([1, 1], np.uint32), np.array([2.0 ** 53, 1.0], f32)) == 2.0 ** 53
+    assert oracle.sum_exact(np.array([1, 3], np.uint32), np.array([2.0 ** 53, 1.0], f32)) == 2.0 ** 53 + 4
+    # ... and anything past the tie rounds up (the sticky bits count)
+    assert oracle.sum_exact(np.array([1, 1, 1], np.uint32),
+                            np.array([2.0 ** 53, 1.0, 2.0 ** -20], f32)) == 2.0 ** 53 + 2
+    # (c) the extremes: the smallest subnormal, the largest count and float
+    hmax = np.uint32(2 ** 32 - 1)
+    assert oracle.sum_exact(np.array([1], np.uint32), np.array([2.0 ** -149], f32)) == 2.0 ** -149
+    big = float(np.finfo(np.float32).max)
+    assert oracle.sum_exact(np.array([hmax, hmax], np.uint32), np.array([big, big], f32)) == \
+        _exact([hmax, hmax], [big, big])
+    assert oracle.sum_exact(np.zeros(3, np.uint32), np.ones(3, f32)) == 0.0
+    # (d) random counts and terms over 80 binades: equal to the rational sum
+    # every time, while a plain double loop misses it in some cases
+    rng = np.random.default_rng(11)
+    misses = 0
+    for trial in range(40):
+        k = 4096
+        h = rng.integers(0, 2 ** 32, k, dtype=np.uint64).astype(np.uint32)
+        h[rng.uniform(size=k) < 0.2] = 0
+        t = (rng.uniform(0.5, 1.0, k) * np.exp2(rng.integers(-40, 40, k))).astype(f32)
+        want = _exact(h, t)
+        assert oracle.sum_exact(h, t) == want, trial
+        plain = 0.0
+        for a, b in zip(h.tolist(), t.tolist()):
+            plain += a * b
+        misses += plain != want
+    assert misses > 0
+
+
+def test_pred_mse_sums_exactly(oracle):
+    """pred_mse adds its per-bin terms exactly and rounds once: each term is
+    what pred_mse gives for one point in that bin alone (n = 1), and the whole
+    prediction must equal the correctly rounded rational sum of count x term,
+    then divided by n.  Counts and bounds are chosen so that a blocked or
+    sequential double sum misses it."""
+    K = oracle.FINE_BINS
+    rng = np.random.default_rng(12)
+    misses = 0
+    for r in (0.0123, 0.07, 0.3, 2.5):
+        unit = np.zeros(K, np.uint32)
+        terms = np.zeros(K, np.float32)
+        for j in range(K):
+            unit[j] = 1
+            terms[j] = np.float32(oracle.pred_mse(unit, 1, r))
+            unit[j] = 0
+        for trial in range(3):
+            # heavy-tailed counts (1 to 2^31, 30% empty bins): products over
+            # many binades, where the rounding of partial sums shows
+            h = np.floor(np.exp2(rng.uniform(0, 31, K))).astype(np.uint64).astype(np.uint32)
+            h[rng.uniform(size=K) < 0.3] = 0
+            n = int(h.sum())
+            want = _exact(h, terms) / n
+            assert oracle.pred_mse(h, n, r) == want, (r, trial)
+            # a sum of 4-bin groups combined pairwise misses it in some cases
+            part = [sum(float(h[4 * g + k]) * float(terms[4 * g + k]) for k in range(4))
+                    for g in range(K // 4)]
+            while len(part) > 1:
+                half = len(part) // 2
+                part = [part[i] + part[i + half] for i in range(half)]
+            misses += part[0] / n != want
+    assert misses > 0
+
+
+def test_refinement_is_scale_invariant(oracle):
+    """Eq. 3 does not depend on the units of the field: scaling a field by a
+    power of two scales the refined eb by exactly that power and leaves the
+    symbols unchanged, from ranges of about 2^-80 to 2^100 (where a float
+    e^2 in the field's own units would overflow or lose its precision)."""
+    rng = np.random.default_rng(14)
+    x = np.exp(1.5 * rng.standard_normal((60, 700))).astype(np.float32)
+    for psnr in (30.0, 45.0):
+        b0, st0 = oracle.compress(x, psnr, psnr_mode=1)
+        assert st0["eb_abs"] != oracle.compress(x, psnr)[1]["eb_abs"]  # the refinement acted
+        for k in (-90, -20, 20, 90):
+            xs = (x.astype(np.float64) * 2.0 ** k).astype(np.float32)
+            b1, st1 = oracle.compress(xs, psnr, psnr_mode=1)
+            assert st1["eb_abs"] == st0["eb_abs"] * 2.0 ** k, (psnr, k)
+            assert st1["eb_rel"] == st0["eb_rel"]
+            p0 = oracle.parse_blob(b0)
+            p1 = oracle.parse_blob(b1)
+            assert np.array_equal(p1["stream"], p0["stream"]), (psnr, k)
+            assert np.array_equal(p1["codebook"], p0["codebook"]), (psnr, k)
 
 
 def test_refine_eb_reduces_to_eq8_on_flat_pdf(oracle):
@@ -416,14 +526,14 @@ def test_refine_eb_bracket(oracle):
     h = oracle.fine_hist(x, lo, vr)
     for psnr in (30.0, 40.0, 50.0):
         eb0 = oracle.eb_rel_from_psnr(psnr) * vr
-        tgt = vr * vr * 10.0 ** (-psnr / 10.0)
+        tgt = 10.0 ** (-psnr / 10.0)  # the target MSE over vr^2
         eb = oracle.refine_eb(h, x.size, vr, eb0, tgt)
         assert eb0 * 0.25 <= eb <= eb0 * 64.0
-        assert oracle.pred_mse(h, x.size, vr, eb) <= tgt
+        assert oracle.pred_mse(h, x.size, eb / vr) <= tgt
         if eb < eb0 * 64.0:
-            assert oracle.pred_mse(h, x.size, vr, eb * 1.01) > tgt
+            assert oracle.pred_mse(h, x.size, eb * 1.01 / vr) > tgt
         else:
-            assert float(np.mean((x.astype(np.float64) - lo) ** 2)) < tgt
+            assert float(np.mean((x.astype(np.float64) - lo) ** 2)) / vr ** 2 < tgt
 
 
 def test_refined_eb_meets_skewed_targets(oracle):
