@@ -644,16 +644,16 @@ def write_traffic(path):
 # algorithmic bytes per launch of each stage (N points, B compressed bytes of one
 # field; ndim of the predictor)
 def stage_bytes(stage, N, B, ndim=2):
-    # 2D fields: decode writes 16-bit symbols; the band pass reads them and the
-    # final band scan reads them again and writes the floats.  3D fields: the
-    # x pass reads the symbols and writes int32 lattice sums, the y pass reads
-    # and writes them, the z pass reads them and writes the floats.
+    # decode writes 16-bit symbols; the tile (3D) or band (2D) sums read them,
+    # and the final scan reads them again and writes the floats (the sums and
+    # their prefixes, N / 16 to N / 4 bytes, are not counted).  3D rows wider
+    # than a tile covers take look-back scans instead: the x pass reads the
+    # symbols and writes int32 lattice sums, the y pass reads and writes them,
+    # the z pass reads them and writes the floats.
     table = {"range_plan": 4 * N, "predict_quantize": 6 * N, "encode": 2 * N + B,
-             "decode": B + 2 * N}
-    if ndim == 2:
-        table.update({"band_sum": 2 * N, "scan_final_dequant": 6 * N})
-    else:
-        table.update({"scan_x": 6 * N, "scan_y": 8 * N, "scan_final_dequant": 8 * N})
+             "decode": B + 2 * N, "band_sum": 2 * N, "scan_final_dequant": 6 * N}
+    if ndim == 3:
+        table.update({"scan_x": 6 * N, "scan_y": 8 * N})
     return table.get(stage)
 
 

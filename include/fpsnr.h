@@ -83,6 +83,10 @@ typedef struct {
                          predicted MSE meets the target, by 16 geometric
                          bisections; only when Eq. 8's bin 2 eb8 spans at least
                          16 fine bins (targets below about 59 dB), else eb8.
+                         Eq. 3 is evaluated in units of the value range (bin
+                         centres (j + 1/2)/4096, target 10^(-PSNR/10)), each
+                         term in float and their weighted sum exactly, rounded
+                         once to FP64.
                          Costs one more pass over the input.  The blob records
                          the eb used; decompression is unchanged. */
     int lossless;     /* 0: none (0).  1: optional lossless layer (the paper's
@@ -125,7 +129,11 @@ typedef struct {
 /* Fill *opts with the defaults.  Returns FPSNR_OK, or FPSNR_EINVAL if NULL. */
 int fpsnr_default_opts(fpsnr_opts* opts);
 
-/* Create a plan for fields of one shape on the current CUDA device.
+/* Create a plan for fields of one shape on the current CUDA device.  The
+ * plan evaluates Eq. 8 (Sec. IV) on the host in FP64: eb_rel =
+ * sqrt(3) 10^(-PSNR/20), the bound relative to the value range that makes the
+ * uniform quantizer's MSE (Eq. 6-7) meet the target; eb_abs = eb_rel * vr is
+ * formed on the device once the range is known.
  *   ndim 1..3; dims[ndim], x fastest, each >= 0 (a zero extent gives an empty
  *   field); target_psnr_db in (0, FPSNR_MAX_PSNR]; opts NULL = defaults.
  * The plan owns all device scratch (about 20 bytes per point, one cudaMalloc;
@@ -136,8 +144,8 @@ int fpsnr_default_opts(fpsnr_opts* opts);
 int fpsnr_plan(fpsnr_plan_t* out, int ndim, const uint64_t* dims, double target_psnr_db,
                const fpsnr_opts* opts);
 
-/* Change the plan's target PSNR (Eq. 8 is re-evaluated on the host; no
- * allocation).  Returns FPSNR_OK or FPSNR_EINVAL. */
+/* Change the plan's target PSNR (Eq. 8, Sec. IV, is re-evaluated on the host;
+ * no allocation).  Returns FPSNR_OK or FPSNR_EINVAL. */
 int fpsnr_plan_set_psnr(fpsnr_plan_t plan, double target_psnr_db);
 
 /* eb_rel of the plan's current target (Eq. 8), computed on the host in FP64. */
@@ -149,7 +157,14 @@ uint64_t fpsnr_plan_points(fpsnr_plan_t plan);
 /* Upper bound on the compressed size of any field of the plan's shape. */
 uint64_t fpsnr_max_compressed_bytes(fpsnr_plan_t plan);
 
-/* Compress d_in (n float32 points of the plan's shape) into d_out.
+/* Compress d_in (n float32 points of the plan's shape) into d_out: the value
+ * range vr (Sec. IV, under Eq. 5), eb_abs = eb_rel * vr (Sec. IV, after Eq. 7),
+ * prediction by the Lorenzo predictor and uniform quantization with bins of
+ * width 2 eb_abs (Sec. II-A steps 1-2, Sec. IV), Huffman coding of the
+ * quantization codes (Sec. II-A step 2), and the reconstruction error the
+ * decompressor will reproduce, summed into the achieved PSNR (Eq. 4-5; Sec.
+ * III shows the error of the data equals the error of the prediction
+ * residuals, Eq. 1, so it is known at compression time).
  *   d_in: 4-byte aligned; d_out: 16-byte aligned, out_cap bytes.
  *   d_out_bytes (device, may be NULL): receives the blob size, 0 on error.
  *   d_stats (device, may be NULL): receives fpsnr_stats.
@@ -159,7 +174,12 @@ uint64_t fpsnr_max_compressed_bytes(fpsnr_plan_t plan);
 int fpsnr_compress(fpsnr_plan_t plan, const float* d_in, void* d_out, uint64_t out_cap,
                    uint64_t* d_out_bytes, fpsnr_stats* d_stats, void* stream);
 
-/* Decompress a blob produced for a field of the plan's shape.
+/* Decompress a blob produced for a field of the plan's shape (Sec. III: the
+ * quantization codes are decoded, the prediction residuals rebuilt, and the
+ * data recovered from them by inverting the Lorenzo predictor, Eq. 1; the
+ * midpoint of each bin is the reconstructed value, Sec. IV).  A caller that
+ * holds only the blob gets a fitting plan from fpsnr_blob_info and
+ * fpsnr_plan_from_blob.
  *   d_blob: 16-byte aligned, blob_bytes long; d_out: n_out floats, 16-byte
  *   aligned, n_out == fpsnr_plan_points(plan).  d_out is also used as int32
  *   scratch while decoding.  d_status (device, may be NULL) receives
@@ -168,7 +188,42 @@ int fpsnr_compress(fpsnr_plan_t plan, const float* d_in, void* d_out, uint64_t o
 int fpsnr_decompress(fpsnr_plan_t plan, const void* d_blob, uint64_t blob_bytes, float* d_out,
                      uint64_t n_out, int* d_status, void* stream);
 
-/* Batched compression: `count` fields, each with its own plan (shape, target
+/* Header of a compressed blob, as fpsnr_blob_info reads it (the byte format
+ * above; for the lossless container, the header of the blob inside it). */
+typedef struct {
+    int ndim;             /* 1..3 */
+    int lorenzo_dims;     /* predictor dimension the blob was made with */
+    uint64_t dims[3];     /* x fastest; unused = 1 */
+    uint64_t points;      /* dims[0] * dims[1] * dims[2] */
+    double target_psnr;   /* dB, as planned */
+    double eb_rel, eb_abs, vr;
+    float xmin, xmax;
+    uint32_t flags;       /* 1 constant field, 2 lattice off */
+    int radius, chunk, lmax;
+    int lossless;         /* 1: the bytes are the "FPZ1" container */
+    uint64_t raw_bytes;   /* size of the plain blob (inside the container, if any) */
+    uint64_t n_outlier, n_verbatim;
+} fpsnr_blob_header;
+
+/* Reads the header of a blob (device or host memory, blob_bytes long), so
+ * that a caller holding only the bytes can plan their decompression (the
+ * workflow of Sec. IV ends with the compressed data alone; the decompressor
+ * must recover everything else from it).  For the lossless container it
+ * expands the first segment on the host.  Copies at most a few KiB to the
+ * host on `stream` and synchronizes it; allocates nothing.
+ * Returns FPSNR_OK, FPSNR_EINVAL (null pointer), FPSNR_ECORRUPT (not a blob
+ * of this library, or a header no plan can take) or FPSNR_ECUDA. */
+int fpsnr_blob_info(const void* blob, uint64_t blob_bytes, fpsnr_blob_header* info, void* stream);
+
+/* Creates a plan that decompresses blobs with this header: the blob's shape,
+ * predictor dimension, radius, chunk size, code-length limit and target, and
+ * opts.lossless set when the blob is a container.  As fpsnr_plan otherwise
+ * (allocates the plan's workspace, synchronizes the device once).
+ * Returns FPSNR_OK, FPSNR_EINVAL, FPSNR_ENOMEM or FPSNR_ECUDA. */
+int fpsnr_plan_from_blob(fpsnr_plan_t* out, const fpsnr_blob_header* info);
+
+/* Batched compression (Sec. II-A, III, IV per field, as fpsnr_compress):
+ * `count` fields, each with its own plan (shape, target
  * PSNR, options), compressed by one kernel launch per stage, so that stages
  * bound by latency (Huffman construction, look-back chains, small kernels)
  * overlap across fields.  plans, d_in, d_out, out_cap: host arrays of `count`
@@ -182,14 +237,15 @@ int fpsnr_compress_batch(const fpsnr_plan_t* plans, const float* const* d_in, vo
                          const uint64_t* out_cap, uint64_t* d_out_bytes, fpsnr_stats* d_stats,
                          int count, void* stream);
 
-/* Batched decompression, the counterpart of fpsnr_compress_batch: host arrays
+/* Batched decompression (Sec. III, Eq. 1, per field as fpsnr_decompress), the
+ * counterpart of fpsnr_compress_batch: host arrays
  * plans, d_blob, blob_bytes, d_out of `count` entries; d_status: device array
  * of `count` ints (may be NULL).  Asynchronous, no allocation. */
 int fpsnr_decompress_batch(const fpsnr_plan_t* plans, const void* const* d_blob,
                            const uint64_t* blob_bytes, float* const* d_out, int* d_status,
                            int count, void* stream);
 
-/* Distortion of a reconstruction (Eq. 4-5): vr = max - min of d_x (FP64),
+/* Distortion of a reconstruction (Eq. 4-5, Sec. IV): vr = max - min of d_x (FP64),
  * MSE = sum((x - xr)^2) / n with exact squares accumulated to FP64,
  * PSNR = 20 log10 vr - 10 log10 MSE (+inf when MSE == 0), log10 on the host.
  *   d_x, d_xr: n float32 points each, 4-byte aligned.
@@ -200,8 +256,8 @@ int fpsnr_decompress_batch(const fpsnr_plan_t* plans, const void* const* d_blob,
 int fpsnr_psnr(const float* d_x, const float* d_xr, uint64_t n, double* h_psnr_db,
                double* h_mse, double* h_vr, void* stream);
 
-/* PSNR of a reconstruction without allocating device memory.  There is no
- * counterpart in the paper: this entry point exists for callers that cannot
+/* PSNR of a reconstruction (Eq. 4-5) without allocating device memory.  There
+ * is no counterpart in the paper: this entry point exists for callers that cannot
  * allocate device memory while they run, such as code inside a device memory
  * allocator's or memory pool's own callback (allocating there would re-enter
  * the allocator), processes held to a fixed memory budget reserved up front,
@@ -212,10 +268,16 @@ int fpsnr_psnr(const float* d_x, const float* d_xr, uint64_t n, double* h_psnr_d
  * GPU that loads the library holds until the process exits.
  *   n <= FPSNR_PSNR_STATIC_MAX_POINTS (2^28 points, 1 GiB of float32); a
  *   larger n returns FPSNR_EINVAL without touching the device.
- *   Results agree with fpsnr_psnr to rounding of the final FP64 sum (the
- *   partial sums are combined over a different number of blocks).
+ *   The two entry points split the points among threads and blocks
+ *   differently (512 x 256 points per block here, a grid capped at four
+ *   blocks per SM there), so their float-float partial sums round
+ *   differently: the MSE agrees to about 1e-12 relative, the PSNR to about
+ *   1e-11 dB.
  * The first call on each device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All calls
+ * device current and keeps it for the process; make that first call before
+ * any stream capture.  A cudaDeviceReset of that device (which unloads the
+ * library's module, and with it the array) leaves the kept address stale:
+ * after a reset this entry point must not be called again.  All calls
  * share the one array, which keeps the last call's contents; each call clears
  * the part that must start at zero.  Calls that overlap on the GPU (from two
  * host threads, or on two streams of one device) race on the array: the
@@ -253,6 +315,18 @@ typedef struct {
  * in flight. */
 int fpsnr_plan_set_tuning(fpsnr_plan_t plan, const fpsnr_tuning* t);
 int fpsnr_plan_get_tuning(fpsnr_plan_t plan, fpsnr_tuning* t);
+
+/* Failure handling.  Every wait of one thread block on another (the
+ * decoupled look-back of the scans that invert the predictor for 1D fields and
+ * for rows wider than one tile, and the decoder's wait for its table copy)
+ * polls at most `spins` times (0: the default, 2^22; each poll sleeps about
+ * 32 ns), then records FPSNR_ETIMEOUT in the device status and returns, so
+ * that a wait that cannot end leaves an error, not a hung GPU.  test_unmet = 1
+ * makes the look-back waits expect a flag that no block ever sets, so that
+ * every such wait runs out: for tests of this path (the output is then
+ * meaningless and the status FPSNR_ETIMEOUT); 0 for normal use.  Not while a
+ * call on the plan is in flight.  Returns FPSNR_OK or FPSNR_EINVAL. */
+int fpsnr_plan_set_wait_limit(fpsnr_plan_t plan, uint32_t spins, int test_unmet);
 
 /* Autotuner: picks the chunk size and launch shapes for fields of this shape,
  * target and options by timing compress + decompress of `d_sample` (a device

@@ -63,6 +63,10 @@ void carve(fpsnr_plan_s* p, uint8_t* base, size_t* total) {
     w.enc_tiles = c.take<uint32_t>(std::max<uint64_t>(p->enc_tiles, 1));
     w.enc_scratch = c.take<uint32_t>(std::max<uint64_t>(p->nchunks * p->enc_slot_words, 1));
     w.bsum = c.take<uint32_t>(p->band.on ? (uint64_t)p->band_cap * p->band.nx : 1);
+    const fp::VolGeom& v = p->vol;
+    w.vcb = c.take<uint32_t>(v.on ? (uint64_t)v.nz * v.nbands * v.nx : 1);
+    w.vds = c.take<uint32_t>(v.on ? (uint64_t)v.nslabs * v.ny * v.nx : 1);
+    w.vts = c.take<uint32_t>(v.on ? (uint64_t)v.nslabs * v.nbands * v.nx : 1);
     w.fine_hist = c.take<uint32_t>(fp::kFineBins);
     w.zr_scratch = c.take<uint8_t>(p->lossless ? p->zr_scratch_cap : 16);
     w.zr_seg = c.take<uint32_t>(p->lossless ? p->zr_seg_cap : 1);
@@ -316,6 +320,8 @@ int plan_layout(fpsnr_plan_s** out, int ndim, const uint64_t* dims, double targe
     p->mse_rel = pow(10.0, -target_psnr_db / 10.0);
     p->psnr_mode = o.psnr_mode;
     p->lossless = o.lossless;
+    p->spin_limit = fp::kSpinLimit;
+    p->wait_skew = 0;
     p->radius = o.radius;
     p->chunk = o.chunk;
     p->lmax = o.lmax;
@@ -348,6 +354,7 @@ int plan_layout(fpsnr_plan_s** out, int ndim, const uint64_t* dims, double targe
     // inverse-Lorenzo passes
     p->n_passes = 0;
     p->band = fp::BandGeom{};
+    p->vol = fp::VolGeom{};
     if (n > 0) {
         if (ld == 1) {
             p->pass[p->n_passes++] = contig_pass(1, n, true);
@@ -365,6 +372,19 @@ int plan_layout(fpsnr_plan_s** out, int ndim, const uint64_t* dims, double targe
             const uint64_t nx = d[0], rows = n / nx;
             p->pass[p->n_passes++] = contig_pass(rows, nx, false);
             p->pass[p->n_passes++] = strided_pass(1, rows, nx, true);
+        } else if (d[0] <= fp::kVolMaxNx) {
+            fp::VolGeom& v = p->vol;
+            v.on = true;
+            v.nx = (uint32_t)d[0];
+            v.ny = (uint32_t)d[1];
+            v.nz = (uint32_t)(n / (d[0] * d[1]));
+            v.cpl = v.nx <= 128 ? 4 : (v.nx <= 256 ? 8 : 16);
+            v.wpr = v.nx <= 512 ? 1 : (v.nx <= 1024 ? 2 : 4);
+            v.ty = 16u / (uint32_t)v.wpr;
+            v.tz = fp::kVolSlab;
+            v.nbands = (uint32_t)cdiv(v.ny, v.ty);
+            v.nslabs = (uint32_t)cdiv(v.nz, v.tz);
+            v.vec = (v.nx % 4u) == 0;
         } else {
             p->pass[p->n_passes++] = contig_pass(d[2] * d[1], d[0], false);
             p->pass[p->n_passes++] = strided_pass(d[2], d[1], d[0], false);
@@ -515,6 +535,13 @@ int fpsnr_plan_set_tuning(fpsnr_plan_t p, const fpsnr_tuning* t) {
     return FPSNR_OK;
 }
 
+int fpsnr_plan_set_wait_limit(fpsnr_plan_t p, uint32_t spins, int test_unmet) {
+    if (!p || (test_unmet != 0 && test_unmet != 1)) return FPSNR_EINVAL;
+    p->spin_limit = spins ? spins : fp::kSpinLimit;
+    p->wait_skew = (uint32_t)test_unmet;
+    return FPSNR_OK;
+}
+
 int fpsnr_plan_get_tuning(fpsnr_plan_t p, fpsnr_tuning* t) {
     if (!p || !t) return FPSNR_EINVAL;
     memset(t, 0, sizeof(*t));
@@ -523,6 +550,155 @@ int fpsnr_plan_get_tuning(fpsnr_plan_t p, fpsnr_tuning* t) {
     t->band_rows = p->band.on ? (int)p->band.tr : 0;
     t->dec_threads = p->dec_threads;
     return FPSNR_OK;
+}
+
+// ---- reading a blob's header (host) ----
+
+static uint32_t rd_u32(const uint8_t* b) {
+    return (uint32_t)b[0] | ((uint32_t)b[1] << 8) | ((uint32_t)b[2] << 16) | ((uint32_t)b[3] << 24);
+}
+static uint64_t rd_u64(const uint8_t* b) { return (uint64_t)rd_u32(b) | ((uint64_t)rd_u32(b + 4) << 32); }
+static double rd_f64(const uint8_t* b) {
+    double v;
+    memcpy(&v, b, 8);
+    return v;
+}
+static float rd_f32(const uint8_t* b) {
+    float v;
+    memcpy(&v, b, 4);
+    return v;
+}
+
+// Copies `bytes` bytes at offset `off` of the caller's blob (device or host
+// memory) to the host and waits for them.
+static int blob_read(const void* blob, uint64_t off, void* dst, uint64_t bytes, cudaStream_t st) {
+    if (cudaMemcpyAsync(dst, static_cast<const uint8_t*>(blob) + off, bytes, cudaMemcpyDefault, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return FPSNR_ECUDA;
+    }
+    return FPSNR_OK;
+}
+
+// Header fields of a plain blob (kHeaderBytes bytes); FPSNR_ECORRUPT unless
+// they describe a field this library can plan.
+static int parse_header(const uint8_t* h, fpsnr_blob_header* info) {
+    if (rd_u32(h) != fp::kMagic || rd_u32(h + 4) != fp::kVersion) return FPSNR_ECORRUPT;
+    info->ndim = (int)rd_u32(h + 8);
+    info->lorenzo_dims = (int)rd_u32(h + 12);
+    uint64_t n = 1;
+    for (int i = 0; i < 3; i++) info->dims[i] = rd_u64(h + 16 + 8 * i);
+    if (info->ndim < 1 || info->ndim > 3 || info->lorenzo_dims < 1 || info->lorenzo_dims > info->ndim)
+        return FPSNR_ECORRUPT;
+    for (int i = 0; i < 3; i++) {
+        if (i >= info->ndim && info->dims[i] != 1) return FPSNR_ECORRUPT;
+        if (info->dims[i] > 0xFFFFFFFFull) return FPSNR_ECORRUPT;
+        n *= info->dims[i];
+        if (n > 0xFFFFFFFFull) return FPSNR_ECORRUPT;
+    }
+    info->target_psnr = rd_f64(h + 40);
+    info->eb_rel = rd_f64(h + 48);
+    info->eb_abs = rd_f64(h + 56);
+    info->vr = rd_f64(h + 64);
+    info->xmin = rd_f32(h + 72);
+    info->xmax = rd_f32(h + 76);
+    info->flags = rd_u32(h + 92);
+    info->radius = (int)rd_u32(h + 96);
+    info->chunk = (int)rd_u32(h + 100);
+    info->lmax = (int)rd_u32(h + 104);
+    info->n_outlier = rd_u32(h + 120);
+    info->n_verbatim = rd_u32(h + 124);
+    info->points = n;
+    auto pad = [](uint64_t b) { return (b + 15u) & ~(uint64_t)15u; };
+    info->raw_bytes = fp::kHeaderBytes;
+    if (!(info->flags & fp::kFlagConstant))
+        info->raw_bytes += pad(4ull * rd_u32(h + 108)) + pad(4ull * rd_u32(h + 112)) +
+                           pad(4ull * rd_u32(h + 116)) + pad(8ull * rd_u32(h + 120)) +
+                           pad(8ull * rd_u32(h + 124));
+    if ((info->flags & ~3u) != 0 || !psnr_ok(info->target_psnr) || info->radius < 1 ||
+        info->radius > fp::kMaxRadius || info->chunk < 32 || info->chunk > 65536 ||
+        (info->chunk % 32) != 0 || info->lmax < 1 || info->lmax > fp::kMaxLmax ||
+        (1ull << info->lmax) < 2ull * (uint64_t)info->radius)
+        return FPSNR_ECORRUPT;
+    return FPSNR_OK;
+}
+
+int fpsnr_blob_info(const void* blob, uint64_t blob_bytes, fpsnr_blob_header* info, void* stream) {
+    if (!blob || !info) return FPSNR_EINVAL;
+    memset(info, 0, sizeof(*info));
+    if (blob_bytes < 32) return FPSNR_ECORRUPT;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t head[fp::kHeaderBytes];
+    const uint64_t first = std::min<uint64_t>(blob_bytes, fp::kHeaderBytes);
+    int rc = blob_read(blob, 0, head, first, st);
+    if (rc) return rc;
+    if (rd_u32(head) != fp::kZrMagic) {
+        if (blob_bytes < fp::kHeaderBytes) return FPSNR_ECORRUPT;
+        rc = parse_header(head, info);
+        if (rc) return rc;
+        return info->raw_bytes <= blob_bytes ? FPSNR_OK : FPSNR_ECORRUPT;
+    }
+    // lossless container: expand its first segment, which holds the header
+    const uint64_t raw = rd_u64(head + 8);
+    const uint64_t nseg = rd_u32(head + 20);
+    const uint64_t dstart = 32 + ((4 * (nseg + 1) + 15) & ~(uint64_t)15);
+    if (rd_u32(head + 4) != 1u || rd_u32(head + 16) != fp::kZrSeg || raw < fp::kHeaderBytes ||
+        nseg != (raw + fp::kZrSeg - 1) / fp::kZrSeg || dstart > blob_bytes)
+        return FPSNR_ECORRUPT;
+    uint8_t offs[8];
+    if ((rc = blob_read(blob, 32, offs, 8, st))) return rc;
+    const uint32_t e0 = rd_u32(offs), e1 = rd_u32(offs + 4);
+    const uint64_t lo = e0 & 0x7FFFFFFFu, hi = e1 & 0x7FFFFFFFu;
+    const uint32_t len = (uint32_t)std::min<uint64_t>(fp::kZrSeg, raw);
+    if (lo > hi || hi - lo > fp::kZrSeg || dstart + hi > blob_bytes) return FPSNR_ECORRUPT;
+    uint8_t code[fp::kZrSeg], seg[fp::kZrSeg];
+    if (hi > lo && (rc = blob_read(blob, dstart + lo, code, hi - lo, st))) return rc;
+    const uint64_t clen = hi - lo;
+    if (e0 & 0x80000000u) {
+        if (clen != len) return FPSNR_ECORRUPT;
+        memcpy(seg, code, len);
+    } else {
+        // a nonzero byte stands for itself; 0x00 and LEB128 k - 1 for k zeros
+        uint64_t i = 0;
+        uint32_t w = 0;
+        while (i < clen) {
+            const uint8_t v = code[i++];
+            if (v) {
+                if (w >= len) return FPSNR_ECORRUPT;
+                seg[w++] = v;
+                continue;
+            }
+            uint32_t k = 0;
+            for (int sh = 0;; sh += 7) {
+                if (i >= clen || sh > 28) return FPSNR_ECORRUPT;
+                const uint8_t t = code[i++];
+                k |= (uint32_t)(t & 127u) << sh;
+                if (!(t & 128u)) break;
+            }
+            if ((uint64_t)w + k + 1 > len) return FPSNR_ECORRUPT;
+            memset(seg + w, 0, k + 1);
+            w += k + 1;
+        }
+        if (w != len) return FPSNR_ECORRUPT;
+    }
+    rc = parse_header(seg, info);
+    if (rc) return rc;
+    info->lossless = 1;
+    return info->raw_bytes == raw ? FPSNR_OK : FPSNR_ECORRUPT;
+}
+
+int fpsnr_plan_from_blob(fpsnr_plan_t* out, const fpsnr_blob_header* info) {
+    if (!out || !info) return FPSNR_EINVAL;
+    *out = nullptr;
+    fpsnr_opts o;
+    fpsnr_default_opts(&o);
+    o.radius = info->radius;
+    o.chunk = info->chunk;
+    o.lmax = info->lmax;
+    o.lorenzo_dims = info->lorenzo_dims;
+    o.lossless = info->lossless ? 1 : 0;
+    return fpsnr_plan(out, info->ndim, info->dims, info->target_psnr, &o);
 }
 
 const uint16_t* fpsnr_plan_codes(fpsnr_plan_t p) { return p ? p->w.codes : nullptr; }

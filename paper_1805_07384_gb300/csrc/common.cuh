@@ -88,6 +88,9 @@ struct Workspace {
     uint32_t* enc_tiles; // [enc_tiles] words per encoder tile, then their exclusive prefix
     uint32_t* enc_scratch;  // [nchunks * enc_slot_words] packed chunks before placement
     uint32_t* bsum;      // [nbands * nx] 2D band column sums (band geometry only)
+    uint32_t* vcb;       // 3D tiles: [nz][nbands][nx] band column sums of every plane
+    uint32_t* vds;       // 3D tiles: [nslabs][ny][nx] slab sums of every row
+    uint32_t* vts;       // 3D tiles: [nslabs][nbands][nx] column sums of every tile
     uint32_t* fine_hist; // [kFineBins] bound refinement histogram (kept zero between calls)
     uint8_t* zr_scratch; // lossless plans: container (compress) / expanded blob (decompress)
     uint32_t* zr_seg;    // lossless plans: per-segment lengths, then offsets
@@ -112,6 +115,20 @@ struct BandGeom {
     uint32_t nx, rows, tr, nbands;
     int g;     // 8 * g columns per thread
     bool vec;  // nx % 8 == 0: symbol rows and output rows start on 16-byte boundaries
+};
+
+// 3D inverse Lorenzo by tiles of tz planes x ty rows x the whole row, used
+// when a row fits one block (nx <= kVolMaxNx): reduce, carry, scan.  A block
+// has 16 warps; a row takes wpr of them (cpl columns per lane), so a tile has
+// ty = 16 / wpr rows.
+constexpr uint32_t kVolMaxNx = 2048;  // 4 warps x 32 lanes x 16 columns
+constexpr uint32_t kVolSlab = 32;     // planes per slab
+struct VolGeom {
+    bool on;
+    uint32_t nx, ny, nz, ty, tz, nbands, nslabs;
+    int cpl;   // columns per lane: 4 (nx <= 128), 8 (<= 256), 16
+    int wpr;   // warps per row: 1 (nx <= 512), 2 (<= 1024), 4 (<= 2048)
+    bool vec;  // nx % 4 == 0: rows of floats start on 16-byte boundaries
 };
 
 struct ScanPass {
@@ -170,6 +187,7 @@ struct fpsnr_plan_s {
     int n_passes;
     fp::ScanPass pass[3];
     fp::BandGeom band;
+    fp::VolGeom vol;
     uint64_t lb_tiles_total, lb_width;
     uint64_t enc_tiles;
     uint32_t enc_slot_words;  // scratch words per chunk (chunk * lmax bits)
@@ -179,6 +197,8 @@ struct fpsnr_plan_s {
     int sm_count;
     int cb_smem;               // dynamic shared memory of the codebook kernel
     int dec_threads;           // decoder block size: 0 chosen per launch, or 128 / 512
+    uint32_t spin_limit;       // polls before an inter-block wait gives up (FPSNR_ETIMEOUT)
+    uint32_t wait_skew;        // test switch: look-back waits expect an epoch no block publishes
     uint32_t pq_blocks_cap;    // predictor blocks the workspace holds partials for (any tile width)
     uint32_t band_cap;         // band sums the workspace holds (band height 16)
     fp::Profiler prof;
@@ -436,9 +456,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* mbar, uint32_t
     return ok != 0;
 }
 
-// Bounded wait for phase `phase` of an mbarrier; false after the limit.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* mbar, uint32_t phase) {
-    for (uint32_t it = 0; it < kSpinLimit; it++)
+// Bounded wait for phase `phase` of an mbarrier; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* mbar, uint32_t phase,
+                                                  uint32_t limit = kSpinLimit) {
+    for (uint32_t it = 0; it < limit; it++)
         if (mbar_try_wait(mbar, phase)) return true;
     return false;
 }
@@ -456,13 +477,14 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
 // Decoupled look-back over tiles [first, t): one warp inspects 32 predecessors
 // per round trip.  Each tile publishes flags[tile] = epoch << 2 | state with
 // state 1 (its own aggregate in agg[tile]) or 2 (inclusive prefix in inc[tile]).
-// Waits (bounded) until every inspected predecessor has published, adds the
-// aggregates of those nearer than the nearest inclusive prefix plus that
-// prefix, and stops there.  Returns the exclusive prefix of tile t in every
-// lane; on a timeout sets FPSNR_ETIMEOUT and returns what it has.
+// Waits (at most `limit` polls per round trip) until every inspected
+// predecessor has published under `epoch`, adds the aggregates of those nearer
+// than the nearest inclusive prefix plus that prefix, and stops there.
+// Returns the exclusive prefix of tile t in every lane; on a timeout sets
+// FPSNR_ETIMEOUT and returns what it has.
 __device__ __forceinline__ uint32_t warp_lookback(const uint32_t* flags, const uint32_t* agg,
                                                   const uint32_t* inc, uint32_t t, uint32_t first,
-                                                  uint32_t epoch, DevParams* par) {
+                                                  uint32_t epoch, uint32_t limit, DevParams* par) {
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t carry = 0;
     int64_t hi = (int64_t)t - 1;
@@ -476,7 +498,7 @@ __device__ __forceinline__ uint32_t warp_lookback(const uint32_t* flags, const u
                 if ((f >> 2) == epoch && (f & 3u)) st = f & 3u;
             }
             if (__all_sync(0xffffffffu, !valid || st != 0)) break;
-            if (it >= kSpinLimit) {
+            if (it >= limit) {
                 if (lane == 0) set_error(par, FPSNR_ETIMEOUT);
                 return __shfl_sync(0xffffffffu, carry, 0);
             }

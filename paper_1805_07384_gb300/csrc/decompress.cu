@@ -237,6 +237,7 @@ constexpr uint32_t dec_smem(int threads) {
 
 struct DecArgs {
     DevParams* par;
+    uint32_t spin_limit;  // polls of the table copy's mbarrier before giving up
     const uint8_t* blob;
     const uint32_t* lut_g;
     const uint16_t* syms;
@@ -285,8 +286,8 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_decode(const __grid
         mbar_arrive_expect_tx(&s_mbar, lut_bytes);
         bulk_g2s(slut, lut_g, lut_bytes, &s_mbar);
     }
-    if (!mbar_wait_bounded(&s_mbar, 0)) {
-        // never expected; record it, let the copy land, then leave
+    if (!mbar_wait_bounded(&s_mbar, 0, A.spin_limit)) {
+        // never expected; record it, let the copy land (bounded), then leave
         set_error(par, FPSNR_ETIMEOUT);
         mbar_wait_bounded(&s_mbar, 0);
         return;
@@ -502,6 +503,8 @@ struct ScanArgs {
     uint32_t* agg;          // [tiles * width]
     uint32_t* inc;          // [tiles * width]
     uint32_t* ctr;          // [2]: tile counter, done counter
+    uint32_t spin_limit;    // polls per look-back round trip before giving up
+    uint32_t skew;          // 0; a test sets 1: predecessors are awaited under an epoch never published
 };
 
 __device__ __forceinline__ void tile_done(uint32_t* ctr, uint32_t tiles) {
@@ -579,7 +582,8 @@ __global__ void __launch_bounds__(256) k_scan_contig(const __grid_constant__ Bat
                 st_release(a.flags + id, (epoch << 2) | (t == 0 ? kStP : kStA));
             }
             if (t > 0) {
-                carry = warp_lookback(a.flags, a.agg, a.inc, id, id - t, epoch, par);
+                carry = warp_lookback(a.flags, a.agg, a.inc, id, id - t, epoch + a.skew,
+                                      a.spin_limit, par);
                 if (tid == 0) {
                     a.inc[id] = carry + agg;
                     __threadfence();
@@ -692,10 +696,10 @@ __global__ void __launch_bounds__(256) k_scan_strided(const __grid_constant__ Ba
                 for (uint32_t it = 0;; it++) {
                     if (valid && st == 0) {
                         const uint32_t f = ld_acquire(a.flags + pt);
-                        if ((f >> 2) == epoch && (f & 3u)) st = f & 3u;
+                        if ((f >> 2) == epoch + a.skew && (f & 3u)) st = f & 3u;
                     }
                     if (__all_sync(0xffffffffu, !valid || st != 0)) break;
-                    if (it >= kSpinLimit) { timeout = true; break; }
+                    if (it >= a.spin_limit) { timeout = true; break; }
                     __nanosleep(32);
                 }
                 const uint32_t pmask = __ballot_sync(0xffffffffu, valid && st == kStP);
@@ -987,6 +991,400 @@ __global__ void __launch_bounds__(256) k_band_scan(const __grid_constant__ Batch
 }
 
 // ---------------------------------------------------------------------------
+// 3D inverse Lorenzo over tiles of planes x rows: reduce, carry, scan
+// ---------------------------------------------------------------------------
+//
+// q is the 3D inclusive prefix sum of the residuals.  The field is cut into
+// tiles of tz planes (a slab s) by ty rows (a band b) by the whole row.  For a
+// point (z, y, x) of tile (s, b), with z0 and y0 the tile's first plane and
+// row, the column sum
+//   A(z, y, x) = sum of the residuals at (z', y', x) with z' <= z and y' <= y
+// splits into four parts:
+//   K[s][b][x]                                z' < z0,  y' < y0
+//   sum over y0 <= y' <= y of E[s][y'][x]     z' < z0,  y0 <= y' <= y
+//   sum over z0 <= z' <= z of F[z'][b][x]     z0 <= z' <= z,  y' < y0
+//   the tile's own residuals                  z0 <= z' <= z,  y0 <= y' <= y
+// and q(z, y, x) is the prefix of A(z, y, .) along x.  E (per row, over the
+// earlier slabs), F (per plane, over the earlier bands) and K (per tile, over
+// both) are exclusive prefixes of the slab sums of every row, the band column
+// sums of every plane and the column sums of every tile, which one reading of
+// the residuals gives.  Three launches with no waiting between blocks:
+//   k_vol_sum    one block per tile: the three kinds of sums
+//   k_vol_carry  their exclusive prefixes, in place
+//   k_vol_scan   one block per tile, plane by plane: the column prefix along
+//                y (plus F) by one thread per column, then A of every row in
+//                the registers of the warp that owns the row, its prefix along
+//                x by warp shuffles, and x' = fmaf((float)q, s, xmin) on the
+//                write
+// Both tile kernels stage each plane's rows of the tile (one contiguous range
+// of symbols) in shared memory with a bulk copy two planes ahead.  The
+// symbols are read twice and the floats written once.  All sums are modular
+// uint32 (every final q is in [0, 2^31)).
+
+struct VolArgs {
+    DevParams* par;
+    const uint16_t* syms;  // [nz][ny][nx] decoded symbols (the buffer holds 8 more)
+    float* out;            // [nz][ny][nx]; outlier residuals (u32) at their indices until written
+    uint32_t* cb;          // [nz][nbands][nx] band column sums of every plane -> F
+    uint32_t* ds;          // [nslabs][ny][nx] slab sums of every row -> E
+    uint32_t* ts;          // [nslabs][nbands][nx] column sums of every tile -> K
+    uint32_t nx, ny, nz, tz, nbands, nslabs;
+    uint32_t nF, nE;       // k_vol_carry: blocks of its first two roles
+    uint32_t spin_limit;   // polls of a plane's copy before giving up
+};
+
+constexpr uint32_t kVolSymBytes = 16384 + 32;  // one plane of a tile: 8192 symbols + alignment
+
+// Shared-memory staging of a tile's planes: two buffers of symbols at `base`
+// (kVolSymBytes apart), each filled by one bulk copy completing on its own
+// mbarrier.  Thread 0 counts the copies it issues to each buffer; every
+// thread counts the ones it has waited for.
+struct VolStage {
+    uint8_t* base;
+    unsigned long long* mbar;  // [2]
+    uint32_t issued0, issued1;
+    uint32_t waited0, waited1;
+    __device__ __forceinline__ const uint16_t* buf(int which) const {
+        return reinterpret_cast<const uint16_t*>(base + (which ? kVolSymBytes : 0u));
+    }
+};
+
+// Byte range of plane z's rows [y0, y1) of the tile, widened to 16-byte
+// boundaries (the symbol buffer holds 16 bytes past the field's end).
+__device__ __forceinline__ void vol_plane_range(const VolArgs& a, uint32_t z, uint32_t y0, uint32_t y1,
+                                                uint64_t* from, uint32_t* bytes, uint32_t* skew) {
+    const uint64_t b0 = 2ull * ((uint64_t)z * a.ny + y0) * a.nx;
+    const uint64_t b1 = 2ull * ((uint64_t)z * a.ny + y1) * a.nx;
+    const uint64_t lo = b0 & ~15ull, hi = (b1 + 15ull) & ~15ull;
+    *from = lo;
+    *bytes = (uint32_t)(hi - lo);
+    *skew = (uint32_t)((b0 - lo) >> 1);  // symbols before the tile's first one
+}
+
+// Thread 0: start the copy of plane z into buffer `which`.
+__device__ __forceinline__ void vol_issue(const VolArgs& a, VolStage& st, int which, uint32_t z,
+                                          uint32_t y0, uint32_t y1) {
+    uint64_t from;
+    uint32_t bytes, skew;
+    vol_plane_range(a, z, y0, y1, &from, &bytes, &skew);
+    // earlier generic reads of the buffer are ordered before the copy's writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    unsigned long long* mb = st.mbar + which;
+    mbar_arrive_expect_tx(mb, bytes);
+    bulk_g2s(st.base + (which ? kVolSymBytes : 0u), reinterpret_cast<const uint8_t*>(a.syms) + from, bytes, mb);
+    if (which) st.issued1++;
+    else st.issued0++;
+}
+
+// Every thread: wait (at most `limit` polls) for the next copy into buffer
+// `which`; false if it did not land in time (it then stays counted as
+// outstanding, for vol_drain).
+__device__ __forceinline__ bool vol_wait(VolStage& st, int which, uint32_t limit) {
+    const uint32_t k = which ? st.waited1 : st.waited0;
+    if (!mbar_wait_bounded(st.mbar + which, k & 1u, limit)) return false;
+    if (which) st.waited1++;
+    else st.waited0++;
+    return true;
+}
+
+// After a timeout: thread 0 waits (bounded) for every copy still in flight,
+// so that none lands after the block has left.
+__device__ __forceinline__ void vol_drain(const VolStage& st) {
+    if (threadIdx.x != 0) return;
+    for (uint32_t k = st.waited0; k < st.issued0; k++) mbar_wait_bounded(st.mbar, k & 1u);
+    for (uint32_t k = st.waited1; k < st.issued1; k++) mbar_wait_bounded(st.mbar + 1, k & 1u);
+}
+
+// Residual of symbol `sym` at point idx: symbol - R, or the outlier residual
+// k_out_scatter placed at idx for a symbol 0.
+__device__ __forceinline__ uint32_t vol_residual(uint32_t sym, uint32_t R, uint64_t idx,
+                                                 const uint32_t* __restrict__ od, uint32_t& nzero) {
+    if (sym) return sym - R;
+    nzero++;
+    return od[idx];
+}
+
+template <int CPL, int WPR>
+__global__ void __launch_bounds__(512) k_vol_sum(const __grid_constant__ Batch<VolArgs> B) {
+    constexpr uint32_t TY = 16 / WPR;
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const VolArgs& a = B.a[fld];
+    const uint32_t t = blockIdx.x - B.off[fld];
+    DevParams* par = a.par;
+    const uint32_t flags = par->flags;
+    if (flags & kFlagError) return;  // uniform over the block
+    extern __shared__ __align__(16) uint8_t vsm[];
+    __shared__ __align__(8) unsigned long long s_mbar[2];
+    const uint32_t s = t / a.nbands, b = t % a.nbands;
+    const uint32_t z0 = s * a.tz, z1 = min(z0 + a.tz, a.nz);
+    const uint32_t y0 = b * TY, y1 = min(y0 + TY, a.ny), nrows = y1 - y0;
+    const bool cst = (flags & kFlagConstant) != 0;
+    VolStage st{vsm, s_mbar, 0u, 0u, 0u, 0u};
+    if (threadIdx.x == 0) {
+        mbar_init(&s_mbar[0], 1);
+        mbar_init(&s_mbar[1], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !cst) {
+        vol_issue(a, st, 0, z0, y0, y1);
+        if (z0 + 1 < z1) vol_issue(a, st, 1, z0 + 1, y0, y1);
+    }
+    const uint32_t R = par->d_radius;
+    const uint32_t* __restrict__ od = reinterpret_cast<const uint32_t*>(a.out);
+    uint32_t dacc[WPR][TY], tacc[WPR];
+#pragma unroll
+    for (int q = 0; q < WPR; q++) {
+        tacc[q] = 0u;
+#pragma unroll
+        for (uint32_t r = 0; r < TY; r++) dacc[q][r] = 0u;
+    }
+    uint32_t nzero = 0;  // symbols 0 (outliers), checked against the list by k_patch
+    for (uint32_t z = z0; z < z1; z++) {
+        const int which = (int)((z - z0) & 1u);
+        const bool late = !cst && !vol_wait(st, which, a.spin_limit);
+        uint64_t from;
+        uint32_t bytes, skew;
+        vol_plane_range(a, z, y0, y1, &from, &bytes, &skew);
+        const uint16_t* sb = st.buf(which) + skew;
+#pragma unroll
+        for (int q = 0; q < WPR; q++) {
+            const uint32_t j = threadIdx.x + 512u * q;
+            if (j >= a.nx) continue;
+            uint32_t cs = 0u;
+#pragma unroll
+            for (uint32_t r = 0; r < TY; r++) {
+                if (r < nrows && !cst) {
+                    const uint32_t sym = sb[r * a.nx + j];
+                    const uint32_t d =
+                        vol_residual(sym, R, ((uint64_t)z * a.ny + y0 + r) * a.nx + j, od, nzero);
+                    cs += d;
+                    dacc[q][r] += d;
+                }
+            }
+            a.cb[((uint64_t)z * a.nbands + b) * a.nx + j] = cs;
+            tacc[q] += cs;
+        }
+        if (__syncthreads_or(late)) {  // every thread is done with the buffer
+            if (threadIdx.x == 0) set_error(par, FPSNR_ETIMEOUT);
+            vol_drain(st);
+            return;
+        }
+        if (threadIdx.x == 0 && !cst && z + 2 < z1) vol_issue(a, st, which, z + 2, y0, y1);
+    }
+    if (nzero) atomicAdd(&par->d_zero, nzero);
+#pragma unroll
+    for (int q = 0; q < WPR; q++) {
+        const uint32_t j = threadIdx.x + 512u * q;
+        if (j >= a.nx) continue;
+#pragma unroll
+        for (uint32_t r = 0; r < TY; r++)
+            if (r < nrows) a.ds[((uint64_t)s * a.ny + y0 + r) * a.nx + j] = dacc[q][r];
+        a.ts[((uint64_t)s * a.nbands + b) * a.nx + j] = tacc[q];
+    }
+}
+
+// count values at p, p + stride, ... replaced by their exclusive prefix
+__device__ __forceinline__ void excl_prefix_strided(uint32_t* p, uint32_t count, uint64_t stride) {
+    uint32_t acc = 0u, i = 0;
+    for (; i + 8 <= count; i += 8) {
+        uint32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = p[(uint64_t)(i + k) * stride];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            p[(uint64_t)(i + k) * stride] = acc;
+            acc += v[k];
+        }
+    }
+    for (; i < count; i++) {
+        const uint32_t v = p[(uint64_t)i * stride];
+        p[(uint64_t)i * stride] = acc;
+        acc += v;
+    }
+}
+
+// Three roles by block: F (one thread per plane and column: over the bands),
+// E (one thread per row and column: over the slabs), K (32 columns per block:
+// over the slabs, then, after a block barrier, over the bands).
+__global__ void __launch_bounds__(256) k_vol_carry(const __grid_constant__ Batch<VolArgs> B) {
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const VolArgs& a = B.a[fld];
+    const uint32_t t = blockIdx.x - B.off[fld];
+    if (a.par->flags & kFlagError) return;  // uniform over the block
+    if (t < a.nF) {
+        const uint64_t i = (uint64_t)t * 256u + threadIdx.x;  // z * nx + x
+        if (i >= (uint64_t)a.nz * a.nx) return;
+        const uint64_t z = i / a.nx, x = i % a.nx;
+        excl_prefix_strided(a.cb + z * a.nbands * a.nx + x, a.nbands, a.nx);
+    } else if (t < a.nF + a.nE) {
+        const uint64_t i = (uint64_t)(t - a.nF) * 256u + threadIdx.x;  // y * nx + x
+        if (i >= (uint64_t)a.ny * a.nx) return;
+        excl_prefix_strided(a.ds + i, a.nslabs, (uint64_t)a.ny * a.nx);
+    } else {
+        const uint32_t x = (t - a.nF - a.nE) * 32u + (threadIdx.x & 31u), r = threadIdx.x >> 5;
+        if (x < a.nx)
+            for (uint32_t b = r; b < a.nbands; b += 8)
+                excl_prefix_strided(a.ts + (uint64_t)b * a.nx + x, a.nslabs, (uint64_t)a.nbands * a.nx);
+        __syncthreads();  // every thread of the block reaches it
+        if (x < a.nx)
+            for (uint32_t s = r; s < a.nslabs; s += 8)
+                excl_prefix_strided(a.ts + (uint64_t)s * a.nbands * a.nx + x, a.nbands, a.nx);
+    }
+}
+
+// Word of column j in a row of the column-prefix buffer: groups of 4 words
+// (one 128-bit read of a lane) are permuted within each run of 8 groups, so
+// that both the column threads' writes and the lanes' 128-bit reads of a row
+// are free of bank conflicts.
+__device__ __forceinline__ uint32_t vol_swz(uint32_t j) {
+    const uint32_t c = j >> 2;
+    return ((c ^ ((c >> 3) & 7u)) << 2) | (j & 3u);
+}
+
+template <int CPL, int WPR, bool FV>
+__global__ void __launch_bounds__(512, 2) k_vol_scan(const __grid_constant__ Batch<VolArgs> B) {
+    constexpr uint32_t TY = 16 / WPR;
+    constexpr uint32_t RS = 32u * CPL * WPR;  // words per row of the column-prefix buffer
+    const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
+    const VolArgs& a = B.a[fld];
+    const uint32_t t = blockIdx.x - B.off[fld];
+    DevParams* par = a.par;
+    const uint32_t flags = par->flags;
+    if (flags & kFlagError) return;  // uniform over the block
+    extern __shared__ __align__(16) uint8_t vsm[];
+    __shared__ __align__(8) unsigned long long s_mbar[2];
+    __shared__ uint32_t wt[2][16];  // WPR > 1: warp totals of a row's parts
+    uint32_t* D0 = reinterpret_cast<uint32_t*>(vsm + 2 * kVolSymBytes);
+    uint32_t* D1 = D0 + TY * RS;
+    const uint32_t s = t / a.nbands, b = t % a.nbands;
+    const uint32_t z0 = s * a.tz, z1 = min(z0 + a.tz, a.nz);
+    const uint32_t y0 = b * TY, y1 = min(y0 + TY, a.ny), nrows = y1 - y0;
+    const bool cst = (flags & kFlagConstant) != 0;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    VolStage st{vsm, s_mbar, 0u, 0u, 0u, 0u};
+    if (threadIdx.x == 0) {
+        mbar_init(&s_mbar[0], 1);
+        mbar_init(&s_mbar[1], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !cst) {
+        vol_issue(a, st, 0, z0, y0, y1);
+        if (z0 + 1 < z1) vol_issue(a, st, 1, z0 + 1, y0, y1);
+    }
+    const uint32_t R = par->d_radius;
+    const float sc = par->s, xmin = par->xmin;
+    // outlier residuals, each read by a column thread before the barrier that
+    // precedes the float write of its point
+    const uint32_t* __restrict__ od = reinterpret_cast<const uint32_t*>(a.out);
+
+    // A(z0 - 1, y, .) of the band's rows, by the column threads into D1
+#pragma unroll
+    for (int q = 0; q < WPR; q++) {
+        const uint32_t j = threadIdx.x + 512u * q;
+        if (j >= RS) continue;
+        uint32_t run = j < a.nx ? a.ts[((uint64_t)s * a.nbands + b) * a.nx + j] : 0u;
+#pragma unroll
+        for (uint32_t r = 0; r < TY; r++) {
+            if (j < a.nx && r < nrows) run += a.ds[((uint64_t)s * a.ny + y0 + r) * a.nx + j];
+            D1[r * RS + vol_swz(j)] = run;
+        }
+    }
+    __syncthreads();
+    const uint32_t row = warp / WPR;  // the row this warp owns in phase B
+    const uint32_t c0 = (warp % WPR) * 32u * CPL + lane * CPL;
+    uint32_t P[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; k += 4) {
+        const uint4 v = *reinterpret_cast<const uint4*>(D1 + row * RS + vol_swz(c0 + k));
+        P[k] = v.x; P[k + 1] = v.y; P[k + 2] = v.z; P[k + 3] = v.w;
+    }
+    // F of the next plane, loaded a plane ahead by the column threads
+    uint32_t fn[WPR];
+#pragma unroll
+    for (int q = 0; q < WPR; q++) {
+        const uint32_t j = threadIdx.x + 512u * q;
+        fn[q] = (j < a.nx && z0 < z1) ? a.cb[((uint64_t)z0 * a.nbands + b) * a.nx + j] : 0u;
+    }
+    for (uint32_t z = z0; z < z1; z++) {
+        const int which = (int)((z - z0) & 1u);
+        uint32_t* D = which ? D1 : D0;
+        const bool late = !cst && !vol_wait(st, which, a.spin_limit);
+        uint64_t from;
+        uint32_t bytes, skew;
+        vol_plane_range(a, z, y0, y1, &from, &bytes, &skew);
+        const uint16_t* sb = st.buf(which) + skew;
+        // phase A: per column, F plus the prefix over the band's rows
+#pragma unroll
+        for (int q = 0; q < WPR; q++) {
+            const uint32_t j = threadIdx.x + 512u * q;
+            if (j >= RS) continue;
+            uint32_t c = fn[q];
+            fn[q] = (j < a.nx && z + 1 < z1) ? a.cb[((uint64_t)(z + 1) * a.nbands + b) * a.nx + j] : 0u;
+#pragma unroll
+            for (uint32_t r = 0; r < TY; r++) {
+                if (j < a.nx && r < nrows && !cst) {
+                    uint32_t unused = 0;
+                    c += vol_residual(sb[r * a.nx + j], R, ((uint64_t)z * a.ny + y0 + r) * a.nx + j, od,
+                                      unused);
+                }
+                D[r * RS + vol_swz(j)] = j < a.nx ? c : 0u;
+            }
+        }
+        if (__syncthreads_or(late)) {
+            if (threadIdx.x == 0) set_error(par, FPSNR_ETIMEOUT);
+            vol_drain(st);
+            return;
+        }
+        if (threadIdx.x == 0 && !cst && z + 2 < z1) vol_issue(a, st, which, z + 2, y0, y1);
+        // phase B: the warp's row, A = A(z - 1) + this plane's column prefix,
+        // then its prefix along x
+        uint32_t v[CPL];
+#pragma unroll
+        for (int k = 0; k < CPL; k += 4) {
+            const uint4 cq = *reinterpret_cast<const uint4*>(D + row * RS + vol_swz(c0 + k));
+            P[k] += cq.x; P[k + 1] += cq.y; P[k + 2] += cq.z; P[k + 3] += cq.w;
+        }
+        v[0] = P[0];
+#pragma unroll
+        for (int k = 1; k < CPL; k++) v[k] = v[k - 1] + P[k];
+        const uint32_t tot = v[CPL - 1];
+        uint32_t incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        uint32_t ex = incl - tot;
+        if constexpr (WPR > 1) {
+            if (lane == 31u) wt[which][warp] = incl;
+            __syncthreads();
+            for (uint32_t p = 0; p < warp % WPR; p++) ex += wt[which][row * WPR + p];
+        }
+        if (row < nrows) {
+            const uint64_t rb = ((uint64_t)z * a.ny + y0 + row) * a.nx;
+            float f[CPL];
+#pragma unroll
+            for (int k = 0; k < CPL; k++) f[k] = __fmaf_rn(__int2float_rn((int32_t)(v[k] + ex)), sc, xmin);
+            float* o = a.out + rb + c0;
+            if (FV && c0 + CPL <= a.nx) {
+#pragma unroll
+                for (int k = 0; k < CPL; k += 4)
+                    *reinterpret_cast<float4*>(o + k) = make_float4(f[k], f[k + 1], f[k + 2], f[k + 3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < CPL; k++)
+                    if (c0 + k < a.nx) o[k] = f[k];
+            }
+        }
+    }
+}
+
+// dynamic shared memory of the tile kernels
+constexpr uint32_t vol_sum_smem() { return 2 * kVolSymBytes; }
+template <int CPL, int WPR>
+constexpr uint32_t vol_scan_smem() { return 2 * kVolSymBytes + 2 * (16 / WPR) * 32u * CPL * WPR * 4u; }
+
+// ---------------------------------------------------------------------------
 // host launcher
 // ---------------------------------------------------------------------------
 
@@ -1033,6 +1431,43 @@ static void launch_band(const Batch<BandArgs>& b, const uint32_t* nb, const uint
     else launch_band_t<4, VEC>(b, nb, ncol, prof, st);
 }
 
+template <int CPL, int WPR, bool FV>
+static void launch_vol_t(const Batch<VolArgs>& b, const uint32_t* ntile, const uint32_t* ncarry,
+                         fp::Profiler& prof, cudaStream_t st) {
+    Batch<VolArgs> bt = b;
+    const uint32_t tt = batch_offsets(bt, ntile);
+    {
+        StageScope sc(prof, kStBandSum, st);
+        k_vol_sum<CPL, WPR><<<tt, 512, vol_sum_smem(), st>>>(bt);
+    }
+    Batch<VolArgs> bc = b;
+    const uint32_t tc = batch_offsets(bc, ncarry);
+    {
+        StageScope sc(prof, kStBandCarry, st);
+        k_vol_carry<<<tc, 256, 0, st>>>(bc);
+    }
+    {
+        StageScope sc(prof, kStScanFinal, st);
+        k_vol_scan<CPL, WPR, FV><<<tt, 512, vol_scan_smem<CPL, WPR>(), st>>>(bt);
+    }
+}
+
+template <bool FV>
+static void launch_vol(const Batch<VolArgs>& b, const uint32_t* ntile, const uint32_t* ncarry, int cpl,
+                       int wpr, fp::Profiler& prof, cudaStream_t st) {
+    if (wpr == 4) launch_vol_t<16, 4, FV>(b, ntile, ncarry, prof, st);
+    else if (wpr == 2) launch_vol_t<16, 2, FV>(b, ntile, ncarry, prof, st);
+    else if (cpl == 16) launch_vol_t<16, 1, FV>(b, ntile, ncarry, prof, st);
+    else if (cpl == 8) launch_vol_t<8, 1, FV>(b, ntile, ncarry, prof, st);
+    else launch_vol_t<4, 1, FV>(b, ntile, ncarry, prof, st);
+}
+
+template <int CPL, int WPR, bool FV>
+static bool vol_attrs() {
+    return cudaFuncSetAttribute(k_vol_scan<CPL, WPR, FV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)vol_scan_smem<CPL, WPR>()) == cudaSuccess;
+}
+
 template <int T>
 static bool decode_attrs() {
     return cudaFuncSetAttribute(k_decode<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1048,6 +1483,12 @@ int decode_prepare(const fpsnr_plan_s*) {
     // L1: take the largest shared-memory carveout so that the rings of its
     // resident threads and their blocks' tables fit
     if (!decode_attrs<128>() || !decode_attrs<256>() || !decode_attrs<512>()) return FPSNR_ECUDA;
+    // the 3D tile scans stage symbols and column prefixes in shared memory
+    if (!vol_attrs<4, 1, false>() || !vol_attrs<4, 1, true>() || !vol_attrs<8, 1, false>() ||
+        !vol_attrs<8, 1, true>() || !vol_attrs<16, 1, false>() || !vol_attrs<16, 1, true>() ||
+        !vol_attrs<16, 2, false>() || !vol_attrs<16, 2, true>() || !vol_attrs<16, 4, false>() ||
+        !vol_attrs<16, 4, true>())
+        return FPSNR_ECUDA;
     return FPSNR_OK;
 }
 
@@ -1111,8 +1552,8 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
             if (p->n == 0) continue;
             const Workspace& w = p->w;
             blocks[b.count] = (uint32_t)((p->nchunks + T - 1) / T);
-            b.a[b.count++] = DecArgs{w.par, reinterpret_cast<const uint8_t*>(d_blob[f]), w.dlut,
-                                     w.dsyms, w.codes, p->n, (uint32_t)p->chunk, p->nchunks};
+            b.a[b.count++] = DecArgs{w.par, p->spin_limit, reinterpret_cast<const uint8_t*>(d_blob[f]),
+                                     w.dlut, w.dsyms, w.codes, p->n, (uint32_t)p->chunk, p->nchunks};
         }
         if (b.count) {
             const uint32_t tot = batch_offsets(b, blocks);
@@ -1170,6 +1611,48 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
             if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
         }
     }
+    // 3D fields whose rows fit one block: tiles of planes x rows, grouped by kernel variant
+    {
+        bool done[kMaxBatch] = {};
+        for (int f0 = 0; f0 < count; f0++) {
+            const fpsnr_plan_s* p0 = P[f0];
+            if (done[f0] || p0->n == 0 || !p0->vol.on) continue;
+            const bool vec0 = p0->vol.vec && aligned16(d_out[f0]);
+            Batch<VolArgs> b;
+            b.count = 0;
+            uint32_t ntile[kMaxBatch], ncarry[kMaxBatch];
+            for (int f = f0; f < count; f++) {
+                const fpsnr_plan_s* p = P[f];
+                if (done[f] || p->n == 0 || !p->vol.on) continue;
+                const bool vec = p->vol.vec && aligned16(d_out[f]);
+                if (p->vol.cpl != p0->vol.cpl || p->vol.wpr != p0->vol.wpr || vec != vec0) continue;
+                done[f] = true;
+                const VolGeom& g = p->vol;
+                VolArgs va;
+                va.par = p->w.par;
+                va.syms = p->w.codes;
+                va.out = d_out[f];
+                va.cb = p->w.vcb;
+                va.ds = p->w.vds;
+                va.ts = p->w.vts;
+                va.nx = g.nx;
+                va.ny = g.ny;
+                va.nz = g.nz;
+                va.tz = g.tz;
+                va.nbands = g.nbands;
+                va.nslabs = g.nslabs;
+                va.nF = (uint32_t)(((uint64_t)g.nz * g.nx + 255u) / 256u);
+                va.nE = (uint32_t)(((uint64_t)g.ny * g.nx + 255u) / 256u);
+                va.spin_limit = p->spin_limit;
+                ntile[b.count] = g.nslabs * g.nbands;
+                ncarry[b.count] = va.nF + va.nE + (g.nx + 31u) / 32u;
+                b.a[b.count++] = va;
+            }
+            if (vec0) launch_vol<true>(b, ntile, ncarry, p0->vol.cpl, p0->vol.wpr, prof, st);
+            else launch_vol<false>(b, ntile, ncarry, p0->vol.cpl, p0->vol.wpr, prof, st);
+            if (cudaGetLastError() != cudaSuccess) return FPSNR_ECUDA;
+        }
+    }
     // other shapes: inverse Lorenzo passes, grouped by pass index and kernel variant
     for (int i = 0; i < 3; i++) {
         bool done[kMaxBatch] = {};
@@ -1206,6 +1689,8 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
                 a.agg = w.lb_vals + sp.val_off * p->lb_width;
                 a.inc = w.lb_vals + (p->lb_tiles_total + sp.val_off) * p->lb_width;
                 a.ctr = w.lb_ctr + 2 * sp.ctr_slot;
+                a.spin_limit = p->spin_limit;
+                a.skew = p->wait_skew;
                 if (sp.kind == 0) {
                     a.tpr = (sp.L + 256u * sp.ipt - 1) / (256u * sp.ipt);
                     a.nbt = 1;

@@ -38,7 +38,8 @@ EXPORTS = ("fpsnr_default_opts", "fpsnr_plan", "fpsnr_plan_set_psnr", "fpsnr_pla
            "fpsnr_decompress_batch", "fpsnr_plan_set_tuning", "fpsnr_plan_get_tuning",
            "fpsnr_autotune", "fpsnr_server_create", "fpsnr_server_submit", "fpsnr_server_poll",
            "fpsnr_server_wait", "fpsnr_server_drain", "fpsnr_server_get_stats",
-           "fpsnr_server_now", "fpsnr_server_destroy", "fpsnr_server_take_any")
+           "fpsnr_server_now", "fpsnr_server_destroy", "fpsnr_server_take_any",
+           "fpsnr_blob_info", "fpsnr_plan_from_blob", "fpsnr_plan_set_wait_limit")
 FPSNR_EAGAIN = -8
 FPSNR_REQ_COMPRESS = 0
 FPSNR_REQ_DECOMPRESS = 1
@@ -102,6 +103,20 @@ class fpsnr_server_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class fpsnr_blob_header(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("lorenzo_dims", C.c_int), ("dims", C.c_uint64 * 3),
+                ("points", C.c_uint64), ("target_psnr", C.c_double), ("eb_rel", C.c_double),
+                ("eb_abs", C.c_double), ("vr", C.c_double), ("xmin", C.c_float),
+                ("xmax", C.c_float), ("flags", C.c_uint32), ("radius", C.c_int),
+                ("chunk", C.c_int), ("lmax", C.c_int), ("lossless", C.c_int),
+                ("raw_bytes", C.c_uint64), ("n_outlier", C.c_uint64), ("n_verbatim", C.c_uint64)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["dims"] = [int(v) for v in self.dims]
+        return d
+
+
 class fpsnr_tuning(C.Structure):
     _fields_ = [("chunk", C.c_int), ("pq_tile_x", C.c_int), ("band_rows", C.c_int),
                 ("dec_threads", C.c_int), ("ms", C.c_double), ("bytes", C.c_uint64)]
@@ -161,6 +176,9 @@ def load(path: str = LIB_PATH):
         L.fpsnr_plan_get_tuning.argtypes = [P, C.POINTER(fpsnr_tuning)]
         L.fpsnr_autotune.argtypes = [C.c_int, C.POINTER(U64), D, C.POINTER(fpsnr_opts), P, D,
                                      C.POINTER(fpsnr_tuning), P]
+        L.fpsnr_blob_info.argtypes = [P, U64, C.POINTER(fpsnr_blob_header), P]
+        L.fpsnr_plan_from_blob.argtypes = [C.POINTER(P), C.POINTER(fpsnr_blob_header)]
+        L.fpsnr_plan_set_wait_limit.argtypes = [P, C.c_uint32, C.c_int]
         _lib = L
         return L
 
@@ -263,6 +281,28 @@ def fpsnr_psnr_static(d_x: int, d_xr: int, n: int, stream: int = 0):
     if rc:
         raise FpsnrError(rc, "fpsnr_psnr_static")
     return p.value, m.value, v.value
+
+
+def fpsnr_blob_info(blob: int, blob_bytes: int, stream: int = 0) -> fpsnr_blob_header:
+    """Header of the blob at `blob` (device or host pointer); raises FpsnrError."""
+    h = fpsnr_blob_header()
+    rc = load().fpsnr_blob_info(blob, int(blob_bytes), C.byref(h), stream or None)
+    if rc:
+        raise FpsnrError(rc, "fpsnr_blob_info")
+    return h
+
+
+def fpsnr_plan_from_blob(header: fpsnr_blob_header):
+    """Plan handle (int) that decompresses blobs with this header; raises FpsnrError."""
+    p = C.c_void_p()
+    rc = load().fpsnr_plan_from_blob(C.byref(p), C.byref(header))
+    if rc:
+        raise FpsnrError(rc, "fpsnr_plan_from_blob")
+    return p.value
+
+
+def fpsnr_plan_set_wait_limit(plan, spins: int, test_unmet: int = 0) -> int:
+    return load().fpsnr_plan_set_wait_limit(plan, int(spins), int(test_unmet))
 
 
 def fpsnr_plan_codes(plan) -> int:
@@ -384,6 +424,30 @@ class Plan:
         self.target = float(target_psnr_db)
         self.max_bytes = fpsnr_max_compressed_bytes(self.handle)
         self.device = torch.device("cuda", torch.cuda.current_device())
+
+    @classmethod
+    def from_blob(cls, blob, blob_bytes: int, stream=None) -> "Plan":
+        """A plan for decompressing `blob` (uint8 CUDA tensor holding blob_bytes
+        bytes), built from the blob's own header (fpsnr_blob_info and
+        fpsnr_plan_from_blob): nothing else about the field is needed."""
+        import torch
+        _check(blob, "blob", torch.uint8)
+        if not 0 <= int(blob_bytes) <= blob.numel():
+            raise ValueError(f"blob_bytes {int(blob_bytes)} outside the blob's {blob.numel()} bytes")
+        h = fpsnr_blob_info(blob.data_ptr(), int(blob_bytes), _stream_handle(stream))
+        self = cls.__new__(cls)
+        self.header = h.as_dict()
+        self.shape = tuple(int(h.dims[i]) for i in reversed(range(h.ndim)))
+        self.n = int(h.points)
+        o = fpsnr_default_opts()
+        o.radius, o.chunk, o.lmax, o.lorenzo_dims = h.radius, h.chunk, h.lmax, h.lorenzo_dims
+        o.lossless = h.lossless
+        self.opts = o
+        self.handle = fpsnr_plan_from_blob(h)
+        self.target = float(h.target_psnr)
+        self.max_bytes = fpsnr_max_compressed_bytes(self.handle)
+        self.device = blob.device
+        return self
 
     def set_psnr(self, target_psnr_db: float) -> None:
         rc = fpsnr_plan_set_psnr(self.handle, target_psnr_db)

@@ -102,8 +102,9 @@ def test_host_fields_and_oracle_task():
 def test_stage_bytes():
     assert bench.stage_bytes("predict_quantize", 10, 3) == 60
     assert bench.stage_bytes("scan_final_dequant", 10, 3, 2) == 60
-    assert bench.stage_bytes("scan_final_dequant", 10, 3, 3) == 80
-    assert bench.stage_bytes("band_sum", 10, 3, 3) is None
+    assert bench.stage_bytes("scan_final_dequant", 10, 3, 3) == 60
+    assert bench.stage_bytes("band_sum", 10, 3, 3) == 20
+    assert bench.stage_bytes("scan_y", 10, 3, 3) == 80 and bench.stage_bytes("scan_y", 10, 3, 2) is None
     assert bench.stage_bytes("decode", 10, 3, 3) == 23
 
 

@@ -97,13 +97,17 @@ def _refine_fields():
     return [("density", dens[0]), ("temperature", dens[5]), ("velocity", dens[2]),
             ("climate", field_for((300, 700), 13)),
             ("lognormal1d", np.exp(1.5 * rng.standard_normal(100003)).astype(np.float32)),
-            ("uniform", rng.uniform(-2.0, 7.0, (64, 1000)).astype(np.float32))]
+            ("uniform", rng.uniform(-2.0, 7.0, (64, 1000)).astype(np.float32)),
+            # ranges near 2^50 and 2^-30: Eq. 3 is evaluated in units of vr
+            ("lognormal_x2^40", (np.exp(1.5 * rng.standard_normal((50, 600))) * 2.0 ** 40).astype(np.float32)),
+            ("lognormal_x2^-40", (np.exp(1.5 * rng.standard_normal((50, 600))) * 2.0 ** -40).astype(np.float32))]
 
 
 @pytest.mark.parametrize("psnr", [30.0, 40.0, 50.0, 80.0])
 def test_parity_refined_eb(env, psnr):
     """Bytes, floats and PSNR with the refined bound: the device must reach the
-    oracle's eb bit for bit (same histogram, same fixed-order sums)."""
+    oracle's eb bit for bit (same histogram, same float terms, both sums exact
+    and rounded once)."""
     for name, x in _refine_fields():
         _, st, ost = check_case(env, x, psnr, psnr_mode=1)
         assert st["eb_abs"] == ost["eb_abs"] and st["eb_rel"] == ost["eb_rel"], name
@@ -113,7 +117,7 @@ def test_refined_eb_batch_and_constant(env):
     """Refined and plain fields mixed in one batch; a constant field is left alone."""
     torch, fpsnr, oracle = env
     fields = [x for _, x in _refine_fields()] + [np.full((40, 50), 3.5, np.float32)]
-    modes = [1, 0, 1, 1, 0, 1, 1]
+    modes = [1, 0, 1, 1, 0, 1, 1, 0, 1][:len(fields) - 1] + [1]
     plans = [fpsnr.Plan(x.shape, 35.0, psnr_mode=m) for x, m in zip(fields, modes)]
     xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in fields]
     outs, nb, st = fpsnr.compress_batch(plans, xs)
@@ -136,6 +140,12 @@ SHAPES = [
     ((5, 9, 300), 2), ((4, 6, 33), 1),
     # 2D rows of 8*G columns per thread (G = 2, 4) and rows wider than one block
     ((40, 2056), 2), ((37, 5000), 2), ((11, 8200), 2), ((9, 9001), 2),
+    # 3D tiles of 32 planes x 16/G rows: several slabs and bands with partial
+    # last ones, 4G columns per thread (G = 1, 2, 4) as vectors or one by one,
+    # and rows wider than a tile covers (look-back scans)
+    ((70, 37, 64), 3), ((33, 17, 130), 3), ((65, 20, 500), 3), ((3, 300, 16), 3),
+    ((34, 19, 520), 3), ((5, 25, 1000), 3), ((6, 11, 530), 3), ((35, 9, 1030), 3), ((4, 13, 2048), 3),
+    ((3, 6, 1200), 3), ((2, 3, 2100), 3),
 ]
 
 

@@ -104,7 +104,7 @@ def test_ctypes_layouts_match_the_header(lib, tmp_path):
     import subprocess
 
     structs = [lib.fpsnr_opts, lib.fpsnr_stats, lib.fpsnr_tuning, lib.fpsnr_server_opts,
-               lib.fpsnr_request, lib.fpsnr_result, lib.fpsnr_server_stats]
+               lib.fpsnr_request, lib.fpsnr_result, lib.fpsnr_server_stats, lib.fpsnr_blob_header]
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "fpsnr.h"', "int main(void) {"]
     want = []
     for s in structs:
