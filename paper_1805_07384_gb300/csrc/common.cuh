@@ -342,25 +342,65 @@ struct FF {
     float hi, lo;
 };
 
-__device__ __forceinline__ void ff_add_sq_diff(FF& acc, float a, float b) {
-    // exact d = a - b as dh + dl
-    float nb = -b;
-    float dh = __fadd_rn(a, nb);
-    float bb = __fsub_rn(dh, a);
-    float dl = __fadd_rn(__fsub_rn(a, __fsub_rn(dh, bb)), __fsub_rn(nb, bb));
-    // d^2 = p + e (+ 2 dh dl + dl^2, both far below the float-float precision needed)
-    float p = __fmul_rn(dh, dh);
-    float e = __fmaf_rn(dh, dh, -p);
-    e = __fmaf_rn(__fadd_rn(dh, dh), dl, e);
-    // acc += p + e
-    float t = __fadd_rn(acc.hi, p);
-    float tb = __fsub_rn(t, acc.hi);
-    float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(t, tb)), __fsub_rn(p, tb));
-    acc.hi = t;
-    acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+__device__ __forceinline__ double ff_to_double(const FF& a) { return (double)a.hi + (double)a.lo; }
+
+// Sum of squared differences for any float range: the difference is split
+// exactly (TwoSum) in the inputs' own units, and its two parts are scaled by
+// 2^-e before the exact square is accumulated in float-float, e a unit kept
+// above every difference seen so far (|dh| < 2^(e+1)).  When a larger
+// difference arrives the unit rises and the float-float sum so far moves to an
+// FP64 spill (a rare branch), so squares neither overflow nor lose their low
+// parts to underflow.  Total = spill + float-float sum * 2^(2e).
+struct SqSum {
+    FF acc;
+    double spill;
+    int e;      // the unit's exponent
+    float sc;   // 2^-e
+    float lim;  // 2^(e + 1)
+};
+
+__device__ __forceinline__ void sq_init(SqSum& q) {
+    q.acc = FF{0.0f, 0.0f};
+    q.spill = 0.0;
+    q.e = -100;  // differences of floats are 0 or at least 2^-149
+    q.sc = __uint_as_float((uint32_t)(127 + 100) << 23);
+    q.lim = __uint_as_float((uint32_t)(127 - 99) << 23);
 }
 
-__device__ __forceinline__ double ff_to_double(const FF& a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double sq_unit2(int e) {
+    return __longlong_as_double((long long)(1023 + 2 * e) << 52);  // 2^(2e)
+}
+
+__device__ __forceinline__ void sq_add(SqSum& q, float a, float b) {
+    // exact a - b = dh + dl
+    const float nb = -b;
+    const float dh = __fadd_rn(a, nb);
+    const float bb = __fsub_rn(dh, a);
+    const float dl = __fadd_rn(__fsub_rn(a, __fsub_rn(dh, bb)), __fsub_rn(nb, bb));
+    if (!(fabsf(dh) < q.lim)) {
+        // raise the unit above |dh| (an infinite or NaN dh takes the top unit)
+        q.spill = __dadd_rn(q.spill, __dmul_rn(ff_to_double(q.acc), sq_unit2(q.e)));
+        q.acc = FF{0.0f, 0.0f};
+        const int bd = (int)((__float_as_uint(dh) >> 23) & 0xffu);
+        q.e = min(max(q.e, bd - 127 + 1), 126);
+        q.sc = __uint_as_float((uint32_t)(127 - q.e) << 23);
+        q.lim = q.e < 126 ? __uint_as_float((uint32_t)(127 + q.e + 1) << 23) : __int_as_float(0x7f800000);
+    }
+    const float h = __fmul_rn(dh, q.sc), l = __fmul_rn(dl, q.sc);
+    // (h + l)^2 = p + e with the 2 h l cross term (l^2 is below the precision kept)
+    const float p = __fmul_rn(h, h);
+    float er = __fmaf_rn(h, h, -p);
+    er = __fmaf_rn(__fadd_rn(h, h), l, er);
+    const float t = __fadd_rn(q.acc.hi, p);
+    const float tb = __fsub_rn(t, q.acc.hi);
+    const float err = __fadd_rn(__fsub_rn(q.acc.hi, __fsub_rn(t, tb)), __fsub_rn(p, tb));
+    q.acc.hi = t;
+    q.acc.lo = __fadd_rn(q.acc.lo, __fadd_rn(err, er));
+}
+
+__device__ __forceinline__ double sq_total(const SqSum& q) {
+    return __dadd_rn(q.spill, __dmul_rn(ff_to_double(q.acc), sq_unit2(q.e)));
+}
 
 // Two independent float-float accumulators in the packed f32x2 lanes.  The
 // subtractions are fma(x, -1, y): the product is exact, so each is the single

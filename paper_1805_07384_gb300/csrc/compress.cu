@@ -464,9 +464,26 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * TY,
     DevParams* par = a.par;
     const uint32_t flags = par->flags;
     if (flags & (kFlagConstant | kFlagError)) return;
-    const float xmin = par->xmin, inv = par->inv, s = par->s, thr = par->thr;
-    // -x' = fma(q, -s, -xmin) rounds to exactly the negated reconstruction
-    const float ns = -s, nxmin = -xmin;
+    const float xmin = par->xmin, inv = par->inv, s = par->s, thr0 = par->thr;
+    // The reconstruction test and the exact error sums run in units of 2^k,
+    // k the exponent of the bound when it lies outside [2^-40, 2^40] (else 0):
+    // a non-verbatim error is below the bound, so its square stays a normal
+    // float for any range.  Scaling by a power of two is exact, so the test's
+    // decisions are those of the unscaled arithmetic (|x| <= 2^24 vr keeps
+    // every scaled value below 2^54); the block's sum is scaled back in FP64.
+    int ke = 0;
+    {
+        const int bt = (int)((__float_as_uint(thr0) >> 23) & 0xffu);  // 0: subnormal
+        if (thr0 > 0.0f && (bt < 127 - 40 || bt >= 127 + 40)) ke = min(max(bt - 127, -126), 126);
+        // a nonzero xmin must stay a normal float once scaled (else the
+        // reconstruction's rounding could differ from the unscaled one)
+        const int bx = (int)((__float_as_uint(xmin) >> 23) & 0xffu);
+        if (xmin != 0.0f && bx - ke < 1) ke = 0;
+    }
+    const float ssc = __uint_as_float((uint32_t)(127 - ke) << 23);  // 2^-k
+    const float2 ssc2 = make_float2(ssc, ssc);
+    // -x' 2^-k = fma(q, -s 2^-k, -xmin 2^-k) rounds to exactly the scaled, negated reconstruction
+    const float ns = __fmul_rn(-s, ssc), nxmin = __fmul_rn(-xmin, ssc), thr = __fmul_rn(thr0, ssc);
     const bool off = (flags & kFlagLatticeOff) != 0;
     const int R = a.radius;
 
@@ -574,8 +591,9 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * TY,
 
     // One row.  FULL: every point of the warp lies inside the row (a uniform
     // branch per warp), so no point needs a bounds flag.
-    auto row = [&](uint32_t z, auto full_tag) {
+    auto row = [&](uint32_t z, auto full_tag, auto scaled_tag) {
         constexpr bool FULL = decltype(full_tag)::value;
+        constexpr bool SCALED = decltype(scaled_tag)::value;
         const uint64_t rowbase = ((uint64_t)z * a.vy + y) * vx;
         const uint32_t lim = row_limit(rowbase);
         bool in[NP];
@@ -669,7 +687,8 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * TY,
             bool rare = false;
 #pragma unroll
             for (int i = 0; i < NP; i += 2) {
-                const float2 xv = make_float2(cur.v[i], cur.v[i + 1]);
+                const float2 x2 = make_float2(cur.v[i], cur.v[i + 1]);
+                const float2 xv = SCALED ? __fmul2_rn(x2, ssc2) : x2;
                 const float2 nxr = make_float2(__fmaf_rn(__int2float_rn(q[i]), ns, nxmin),
                                                __fmaf_rn(__int2float_rn(q[i + 1]), ns, nxmin));
                 const float2 df = __fadd2_rn(xv, nxr);  // fl(x - x') per point
@@ -730,15 +749,20 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * TY,
     hnxt.l = 0.0f;
     hnxt.hl = false;
     if (zstart < zlast) fetch(zstart, nxt, hnxt);
-    for (uint32_t z = zstart; z < zlast; z++) {
-        cur = nxt;
-        hcur = hnxt;
-        if (z + 1 < zlast) fetch(z + 1, nxt, hnxt);
-        if (MODE != 3 && xw + 128u * SEG <= row_limit(((uint64_t)z * a.vy + y) * vx))
-            row(z, std::true_type{});
-        else
-            row(z, std::false_type{});
-    }
+    // one copy of the loop per scaling (uniform over the block)
+    auto rows = [&](auto scaled_tag) {
+        for (uint32_t z = zstart; z < zlast; z++) {
+            cur = nxt;
+            hcur = hnxt;
+            if (z + 1 < zlast) fetch(z + 1, nxt, hnxt);
+            if (MODE != 3 && xw + 128u * SEG <= row_limit(((uint64_t)z * a.vy + y) * vx))
+                row(z, std::true_type{}, scaled_tag);
+            else
+                row(z, std::false_type{}, scaled_tag);
+        }
+    };
+    if (ke != 0) rows(std::true_type{});
+    else rows(std::false_type{});
 
     // flush the histogram window (and take the block's symbol range from it)
     // and the squared-error partial
@@ -760,7 +784,7 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * TY,
         }
     }
     double tot = block_sum_double(ff2_to_double(acc), ssum);
-    if (tid == 0) a.sse_part[b] = tot;
+    if (tid == 0) a.sse_part[b] = __dmul_rn(tot, __longlong_as_double((long long)(1023 + 2 * ke) << 52));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         glo = min(glo, __shfl_xor_sync(0xffffffffu, glo, o));
@@ -985,29 +1009,48 @@ __global__ void __launch_bounds__(1024) k_enc_scan(const __grid_constant__ Batch
     }
 }
 
+// One block per tile: the word offsets of the tile's chunks (tile prefix plus
+// the prefix of their word counts, in shared memory), the chunk table, then
+// every word of the tile's chunks copied by its own thread (the words of a
+// tile are contiguous in the stream).
 __global__ void __launch_bounds__(kEncWarps * 32) k_enc_copy(const __grid_constant__ Batch<EncArgs> B) {
     const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
     const EncArgs& a = B.a[fld];
     const uint32_t t = blockIdx.x - B.off[fld];
     DevParams* par = a.par;
-    if (par->flags & (kFlagConstant | kFlagError)) return;
-    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-    const uint64_t c = (uint64_t)t * kEncWarps + wib;
-    if (c >= a.nchunks) return;
+    if (par->flags & (kFlagConstant | kFlagError)) return;  // uniform over the block
+    __shared__ uint32_t pre[kEncWarps + 1];
+    const uint64_t c0 = (uint64_t)t * kEncWarps;
+    const uint32_t nch = (uint32_t)min((uint64_t)kEncWarps, a.nchunks - c0);
     const uint64_t cap = par->cap;
     const uint64_t off_ct = par->off_ct;
     const uint64_t off_st = par->off_st;
-    // word offset of this chunk: tile prefix + words of the tile's earlier chunks
-    uint32_t wpos = a.tile_sum[t];
-    const uint64_t c0 = (uint64_t)t * kEncWarps;
-    for (uint64_t k = c0; k < c; k++) wpos += a.chunk_words[k];
-    const uint32_t nwc = a.chunk_words[c];
-    if (lane == 0 && off_ct + 4ull * (c + 1) <= cap)
-        reinterpret_cast<uint32_t*>(a.out + off_ct)[c] = wpos;
-    if (off_st + 4ull * ((uint64_t)wpos + nwc) > cap) return;
-    uint32_t* stream = reinterpret_cast<uint32_t*>(a.out + off_st) + wpos;
-    const uint32_t* __restrict__ src = a.scratch + c * a.slot_words;
-    for (uint32_t k = lane; k < nwc; k += 32) stream[k] = __ldcs(src + k);
+    const uint32_t tile_off = a.tile_sum[t];  // words of all earlier tiles
+    if (threadIdx.x < 32) {
+        const uint32_t lane = threadIdx.x;
+        const uint32_t w = lane < nch ? a.chunk_words[c0 + lane] : 0u;
+        uint32_t incl = w;
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {  // inclusive prefix over lanes 0..15
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        if (lane <= (uint32_t)kEncWarps) pre[lane] = incl - w;  // pre[nch..] = the tile's total
+        if (lane < nch && off_ct + 4ull * (c0 + lane + 1) <= cap)
+            reinterpret_cast<uint32_t*>(a.out + off_ct)[c0 + lane] = tile_off + incl - w;
+    }
+    __syncthreads();
+    const uint32_t total = pre[nch];
+    uint32_t* stream = reinterpret_cast<uint32_t*>(a.out + off_st) + tile_off;
+    // words that fit the output (the layout already flagged a short buffer)
+    const uint64_t room = off_st + 4ull * tile_off <= cap ? (cap - off_st - 4ull * tile_off) / 4ull : 0ull;
+    const uint32_t lim = (uint32_t)min((uint64_t)total, room);
+    for (uint32_t w = threadIdx.x; w < lim; w += blockDim.x) {
+        uint32_t k = 0;  // the chunk holding word w: the last k with pre[k] <= w
+#pragma unroll
+        for (int i = 1; i < kEncWarps; i++) k += ((uint32_t)i < nch && pre[i] <= w) ? 1u : 0u;
+        stream[w] = __ldcs(a.scratch + (c0 + k) * a.slot_words + (w - pre[k]));
+    }
 }
 
 // Outliers and verbatims in ascending index: rank = number of set bitmap bits

@@ -1095,15 +1095,6 @@ __device__ __forceinline__ void vol_drain(const VolStage& st) {
     for (uint32_t k = st.waited1; k < st.issued1; k++) mbar_wait_bounded(st.mbar + 1, k & 1u);
 }
 
-// Residual of symbol `sym` at point idx: symbol - R, or the outlier residual
-// k_out_scatter placed at idx for a symbol 0.
-__device__ __forceinline__ uint32_t vol_residual(uint32_t sym, uint32_t R, uint64_t idx,
-                                                 const uint32_t* __restrict__ od, uint32_t& nzero) {
-    if (sym) return sym - R;
-    nzero++;
-    return od[idx];
-}
-
 template <int CPL, int WPR>
 __global__ void __launch_bounds__(512) k_vol_sum(const __grid_constant__ Batch<VolArgs> B) {
     constexpr uint32_t TY = 16 / WPR;
@@ -1150,15 +1141,27 @@ __global__ void __launch_bounds__(512) k_vol_sum(const __grid_constant__ Batch<V
         for (int q = 0; q < WPR; q++) {
             const uint32_t j = threadIdx.x + 512u * q;
             if (j >= a.nx) continue;
-            uint32_t cs = 0u;
+            uint32_t cs = 0u, zeros = 0u;  // bit r: row r holds a symbol 0 (an outlier)
+            if (!cst) {
 #pragma unroll
-            for (uint32_t r = 0; r < TY; r++) {
-                if (r < nrows && !cst) {
-                    const uint32_t sym = sb[r * a.nx + j];
-                    const uint32_t d =
-                        vol_residual(sym, R, ((uint64_t)z * a.ny + y0 + r) * a.nx + j, od, nzero);
-                    cs += d;
-                    dacc[q][r] += d;
+                for (uint32_t r = 0; r < TY; r++) {
+                    if (r < nrows) {
+                        const uint32_t sym = sb[r * a.nx + j];
+                        zeros |= (sym == 0u ? 1u : 0u) << r;
+                        cs += sym - R;
+                        dacc[q][r] += sym - R;
+                    }
+                }
+                if (zeros) {  // rare: an outlier's residual replaces its symbol's -R
+                    nzero += __popc(zeros);
+#pragma unroll
+                    for (uint32_t r = 0; r < TY; r++) {
+                        if ((zeros >> r) & 1u) {
+                            const uint32_t fix = od[((uint64_t)z * a.ny + y0 + r) * a.nx + j] + R;
+                            cs += fix;
+                            dacc[q][r] += fix;
+                        }
+                    }
                 }
             }
             a.cb[((uint64_t)z * a.nbands + b) * a.nx + j] = cs;
@@ -1318,16 +1321,34 @@ __global__ void __launch_bounds__(512, 2) k_vol_scan(const __grid_constant__ Bat
         for (int q = 0; q < WPR; q++) {
             const uint32_t j = threadIdx.x + 512u * q;
             if (j >= RS) continue;
-            uint32_t c = fn[q];
+            const uint32_t f0 = fn[q];
             fn[q] = (j < a.nx && z + 1 < z1) ? a.cb[((uint64_t)(z + 1) * a.nbands + b) * a.nx + j] : 0u;
+            uint32_t* dcol = D + vol_swz(j);
+            if (j >= a.nx) {
+#pragma unroll
+                for (uint32_t r = 0; r < TY; r++) dcol[r * RS] = 0u;
+                continue;
+            }
+            uint32_t c = f0, zeros = 0u;  // bit r: row r holds a symbol 0 (an outlier)
 #pragma unroll
             for (uint32_t r = 0; r < TY; r++) {
-                if (j < a.nx && r < nrows && !cst) {
-                    uint32_t unused = 0;
-                    c += vol_residual(sb[r * a.nx + j], R, ((uint64_t)z * a.ny + y0 + r) * a.nx + j, od,
-                                      unused);
+                if (r < nrows && !cst) {
+                    const uint32_t sym = sb[r * a.nx + j];
+                    zeros |= (sym == 0u ? 1u : 0u) << r;
+                    c += sym - R;
                 }
-                D[r * RS + vol_swz(j)] = j < a.nx ? c : 0u;
+                dcol[r * RS] = c;
+            }
+            if (zeros) {  // rare: the column again, with the outliers' residuals
+                c = f0;
+#pragma unroll
+                for (uint32_t r = 0; r < TY; r++) {
+                    if (r < nrows) {
+                        const uint32_t sym = sb[r * a.nx + j];
+                        c += sym ? sym - R : od[((uint64_t)z * a.ny + y0 + r) * a.nx + j];
+                    }
+                    dcol[r * RS] = c;
+                }
             }
         }
         if (__syncthreads_or(late)) {

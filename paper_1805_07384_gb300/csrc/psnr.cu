@@ -3,7 +3,9 @@
 // PSNR = 20 log10 vr - 10 log10 MSE.
 //
 // One pass over both arrays: per point the difference is made exact with a
-// float32 TwoSum, its square exact with an FMA TwoProd, and both parts are
+// float32 TwoSum, scaled by a per-thread power-of-two unit that follows the
+// largest difference seen (so that squares stay normal floats for any range,
+// see SqSum), its square made exact with an FMA TwoProd, and both parts are
 // accumulated in float-float per thread; threads and blocks combine in FP64 in
 // a fixed order, so the result does not depend on scheduling.  The log10 is
 // taken on the host.
@@ -32,7 +34,8 @@ __global__ void __launch_bounds__(512) k_psnr(const float* __restrict__ x,
     const uint64_t gsz = (uint64_t)gridDim.x * blockDim.x;
     float lo = FLT_MAX, hi = -FLT_MAX;
     int nf = 0;
-    FF acc = {0.0f, 0.0f};
+    SqSum acc;
+    sq_init(acc);
     uint64_t tail = 0;
     if (VEC) {
         const float4* x4 = reinterpret_cast<const float4*>(x);
@@ -43,10 +46,10 @@ __global__ void __launch_bounds__(512) k_psnr(const float* __restrict__ x,
             nf |= !isfinite(a.x) | !isfinite(a.y) | !isfinite(a.z) | !isfinite(a.w);
             lo = fminf(lo, fminf(fminf(a.x, a.y), fminf(a.z, a.w)));
             hi = fmaxf(hi, fmaxf(fmaxf(a.x, a.y), fmaxf(a.z, a.w)));
-            ff_add_sq_diff(acc, a.x, b.x);
-            ff_add_sq_diff(acc, a.y, b.y);
-            ff_add_sq_diff(acc, a.z, b.z);
-            ff_add_sq_diff(acc, a.w, b.w);
+            sq_add(acc, a.x, b.x);
+            sq_add(acc, a.y, b.y);
+            sq_add(acc, a.z, b.z);
+            sq_add(acc, a.w, b.w);
         }
         tail = n4 << 2;
     }
@@ -55,7 +58,7 @@ __global__ void __launch_bounds__(512) k_psnr(const float* __restrict__ x,
         nf |= !isfinite(a);
         lo = fminf(lo, a);
         hi = fmaxf(hi, a);
-        ff_add_sq_diff(acc, a, b);
+        sq_add(acc, a, b);
     }
     __shared__ double sdbl[16];
     __shared__ float slo[16], shi[16];
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(512) k_psnr(const float* __restrict__ x,
         nf |= __shfl_xor_sync(0xffffffffu, nf, o);
     }
     if ((tid & 31) == 0) { slo[tid >> 5] = lo; shi[tid >> 5] = hi; snf[tid >> 5] = nf; }
-    const double bs = block_sum_double(ff_to_double(acc), sdbl);
+    const double bs = block_sum_double(sq_total(acc), sdbl);
     if (tid == 0) {
         for (uint32_t w = 1; w < (blockDim.x >> 5); w++) {
             lo = fminf(lo, slo[w]); hi = fmaxf(hi, shi[w]); nf |= snf[w];

@@ -98,9 +98,9 @@ def _refine_fields():
             ("climate", field_for((300, 700), 13)),
             ("lognormal1d", np.exp(1.5 * rng.standard_normal(100003)).astype(np.float32)),
             ("uniform", rng.uniform(-2.0, 7.0, (64, 1000)).astype(np.float32)),
-            # ranges near 2^50 and 2^-30: Eq. 3 is evaluated in units of vr
-            ("lognormal_x2^40", (np.exp(1.5 * rng.standard_normal((50, 600))) * 2.0 ** 40).astype(np.float32)),
-            ("lognormal_x2^-40", (np.exp(1.5 * rng.standard_normal((50, 600))) * 2.0 ** -40).astype(np.float32))]
+            # ranges near 2^100 and 2^-80: Eq. 3 is evaluated in units of vr
+            ("lognormal_x2^90", (np.exp(1.5 * rng.standard_normal((50, 600))) * 2.0 ** 90).astype(np.float32)),
+            ("lognormal_x2^-90", (np.exp(1.5 * rng.standard_normal((50, 600))) * 2.0 ** -90).astype(np.float32))]
 
 
 @pytest.mark.parametrize("psnr", [30.0, 40.0, 50.0, 80.0])
@@ -126,6 +126,30 @@ def test_refined_eb_batch_and_constant(env):
         ob, _ = oracle.compress(x, 35.0, psnr_mode=m)
         n = int(nb[i].item())
         assert outs[i][:n].cpu().numpy().tobytes() == ob, i
+
+
+# ---------------------------------------------------------------------------
+# value ranges far from 1: the error sums stay exact (squares in units of the
+# bound's exponent on compression, of the largest difference seen in the
+# standalone reduction)
+# ---------------------------------------------------------------------------
+
+def _extreme_fields():
+    rng = np.random.default_rng(17)
+    g = synth.rescale(synth.grf((70, 300), 3.0, 4), 0.0, 1.0)
+    ln = np.exp(1.5 * rng.standard_normal((60, 333)))
+    return [("lognormal_x2^90", (ln * 2.0 ** 90).astype(np.float32)),
+            ("lognormal_x2^-90", (ln * 2.0 ** -90).astype(np.float32)),
+            ("mixing_ratio_1e-9", (1e-9 + 1e-9 * g).astype(np.float32)),
+            ("offset_1e30", (1e30 * (1.0 + 1e-3 * g)).astype(np.float32)),
+            ("grf_x2^120", (g * 2.0 ** 120 - 2.0 ** 119).astype(np.float32))]
+
+
+@pytest.mark.parametrize("psnr", [40.0, 120.0, 170.0])
+def test_parity_extreme_ranges(env, psnr):
+    for name, x in _extreme_fields():
+        _, st, ost = check_case(env, x, psnr)
+        assert math.isfinite(st["sse"]), name
 
 
 # ---------------------------------------------------------------------------
