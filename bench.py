@@ -89,8 +89,12 @@ def parse():
                     help="one target PSNR (dB) for every field instead of the mixed sweep "
                          "(field i -> {40,60,80,100,120}[i mod 5])")
     ap.add_argument("--write-traffic", metavar="CSV",
-                    help="read an ncu --csv log of dram__bytes_{read,write}.sum and write "
-                         "profiles/traffic.json (no GPU work)")
+                    help="read an ncu --csv log of dram__bytes_{read,write}.sum and add it to "
+                         "profiles/traffic.json under --workload (no GPU work)")
+    ap.add_argument("--traffic-points", type=int, default=0,
+                    help="--write-traffic: points one captured launch covers")
+    ap.add_argument("--traffic-command", type=str, default="",
+                    help="--write-traffic: the command line of the capture, recorded with it")
     ap.add_argument("--launch-table", metavar="CSV",
                     help="print the per-kernel launch table of an ncu --csv log of "
                          "gpu__time_duration.sum (no GPU work)")
@@ -525,23 +529,23 @@ def rank_seed(rank: int) -> int:
 # our arm
 # ---------------------------------------------------------------------------
 
-def measured_traffic(stage):
-    """DRAM bytes per launch of `stage` from the committed ncu capture, or None
-    when the kernel's source file changed since the counters were taken."""
+def measured_traffic(workload, stage, points):
+    """DRAM bytes of one launch of `stage` over `points` points, from the
+    committed ncu capture of the same workload (bytes per point on a smaller
+    case, times the points), or None when the capture is missing or a file the
+    kernel's binary depends on changed since the counters were taken."""
     import hashlib
     tf = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(tf):
         return None
-    e = json.load(open(tf)).get(stage)
+    e = json.load(open(tf)).get(workload, {}).get(stage)
     if not e:
         return None
-    want = dict(e.get("sources", {}))
-    want[e["source"]] = e["source_sha1"]
-    for rel, sha in want.items():
+    for rel, sha in e["sources"].items():
         src = os.path.join(ROOT, rel)
         if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != sha:
             return None
-    return e["dram_bytes_per_launch"]
+    return int(round(e["dram_bytes_per_point"] * points))
 
 
 # ncu --csv logs -> per-launch figures (profiles/ summaries and traffic.json)
@@ -556,8 +560,8 @@ _STAGE_KERNELS = [("range_plan", ("k_range_plan",), "compress.cu"),
                   ("predict_quantize", ("k_pq",), "compress.cu"),
                   ("encode", ("k_enc_pack", "k_enc_scan", "k_enc_copy"), "compress.cu"),
                   ("decode", ("k_decode",), "decompress.cu"),
-                  ("band_sum", ("k_band_sum",), "decompress.cu"),
-                  ("scan_final_dequant", ("k_band_scan",), "decompress.cu")]
+                  ("band_sum", ("k_band_sum", "k_vol_sum"), "decompress.cu"),
+                  ("scan_final_dequant", ("k_band_scan", "k_vol_scan"), "decompress.cu")]
 
 
 def _ncu_rows(path):
@@ -592,51 +596,51 @@ def launch_table(path):
     return "\n".join(rows)
 
 
-def write_traffic(path):
-    """profiles/traffic.json: DRAM bytes per launch of every stage, with the
-    SHA-1 of the source file the counters were taken from and of the files
-    every kernel build also depends on (the shared device header and the
-    build script that holds the compiler flags)."""
+def write_traffic(path, workload, points, command):
+    """Adds to profiles/traffic.json, under `workload`, the DRAM bytes per
+    point of every benchmark stage found in an ncu --csv log of
+    dram__bytes_{read,write}.sum (each launch covering `points` points), with
+    the SHA-1 of the kernel's source file and of the files every kernel build
+    depends on (the shared device header and the build script with the
+    compiler flags).  A stage of several kernels needs all of them in the log
+    (or in logs added one after another: entries of a stage's other kernels
+    are kept)."""
     import hashlib
     launches = {}
     for lid, k, m, v in _ncu_rows(path):
         if m in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
             launches.setdefault((lid, k), {})[m] = v
-    out = {"_about": "DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each "
-                     "benchmark stage (one launch = one sub-batch of the benchmark's batch), averaged "
-                     "over the launches of the capture; bench.py reports it as roofline.traffic only "
-                     "while the kernel's source file still has the recorded SHA-1.",
-           "_command": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-                       "--clock-control none -k regex:\"k_pq|k_decode|k_band_scan|k_band_sum|k_enc_pack|"
-                       "k_enc_copy|k_enc_scan|k_range_plan\" --csv --log-file traffic.csv python bench.py "
-                       "--steps 2 --warmup 3 --no-cpu-baseline --no-e2e --no-roofline; "
-                       "python bench.py --write-traffic traffic.csv"}
+    dst = os.path.join(ROOT, "profiles", "traffic.json")
+    out = json.load(open(dst)) if os.path.exists(dst) else {}
+    out["_about"] = ("DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per point of each "
+                     "benchmark stage, per workload: the average over the captured launches of a "
+                     "small case of the workload (one kernel per capture, at most three launches), "
+                     "divided by the points one launch covers; bench.py reports it, times the points "
+                     "of its own launch, as roofline.traffic only while the recorded SHA-1s match.")
+    wl = out.setdefault(workload, {})
     for stage, prefixes, src in _STAGE_KERNELS:
-        rd = wr = 0.0
-        kernels = set()
-        first = [0]
+        per_kernel = {}
         for (lid, k), mv in launches.items():
             if k.startswith(prefixes):
-                rd += mv.get("dram__bytes_read.sum", 0.0)
-                wr += mv.get("dram__bytes_write.sum", 0.0)
-                kernels.add(k)
-                if k.startswith(prefixes[0]):
-                    first[0] += 1
-        if not first[0]:
+                e = per_kernel.setdefault(k, [0, 0.0, 0.0])
+                e[0] += 1
+                e[1] += mv.get("dram__bytes_read.sum", 0.0)
+                e[2] += mv.get("dram__bytes_write.sum", 0.0)
+        if not per_kernel:
             continue
-        n = first[0]
+        entry = wl.setdefault(stage, {"kernels": {}})
+        for k, (n, rd, wr) in per_kernel.items():
+            entry["kernels"][k] = {"launches": n, "read_per_point": rd / n / points,
+                                   "write_per_point": wr / n / points, "points_per_launch": points,
+                                   "command": command}
         rel = os.path.join("paper_1805_07384_gb300", "csrc", src)
         deps = {d: hashlib.sha1(open(os.path.join(ROOT, d), "rb").read()).hexdigest()
-                for d in _TRAFFIC_DEPS if os.path.exists(os.path.join(ROOT, d))}
-        out[stage] = {"kernels": sorted(kernels), "launches": n,
-                      "dram_bytes_per_launch": int(round((rd + wr) / n)),
-                      "dram_read": int(round(rd / n)), "dram_write": int(round(wr / n)),
-                      "source": rel,
-                      "source_sha1": hashlib.sha1(open(os.path.join(ROOT, rel), "rb").read()).hexdigest(),
-                      "sources": deps}
-    dst = os.path.join(ROOT, "profiles", "traffic.json")
+                for d in (rel,) + _TRAFFIC_DEPS if os.path.exists(os.path.join(ROOT, d))}
+        entry["sources"] = deps
+        entry["dram_bytes_per_point"] = round(sum(v["read_per_point"] + v["write_per_point"]
+                                                  for v in entry["kernels"].values()), 4)
     with open(dst, "w") as f:
-        json.dump(out, f, indent=1)
+        json.dump(out, f, indent=1, sort_keys=True)
         f.write("\n")
     print(dst)
 
@@ -831,7 +835,7 @@ def run_serve(a):
 def main():
     a = parse()
     if a.write_traffic:
-        write_traffic(a.write_traffic)
+        write_traffic(a.write_traffic, a.workload, a.traffic_points, a.traffic_command)
         return
     if a.launch_table:
         print(launch_table(a.launch_table))
@@ -1153,11 +1157,12 @@ def main():
         dom = max(bw_stages.items(), key=lambda kv: kv[1][0]) if bw_stages else None
         if dom:
             name, (t, n, byts) = dom
+            bytes_pts = a.steps * N * F  # points of every call of the stage in the timed pass
             # one stage call per batched call: a sub-batch per call in batch mode,
             # a field per call in streams mode (a stage can launch several kernels)
             n = a.steps * (len(groups) if a.mode == "batch" else F)
             achieved = byts / (t / 1e3) / 1e9
-            traffic = measured_traffic(name)
+            traffic = measured_traffic(a.workload, name, bytes_pts // n)
             roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                     "traffic": traffic, "peak_source": "measured" if peaks else "fallback",

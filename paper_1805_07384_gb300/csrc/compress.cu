@@ -443,7 +443,8 @@ __device__ __forceinline__ int32_t prequant(float x, float xmin, float inv, bool
 // MODE 1: flat 1D predictor over a (rows x vx) traversal, left neighbour of a
 //         row start is the previous row's last point, no upper-row term.
 // MODE 2: 2D predictor on (vz rows) x vx, TY must be 1 (vy == 1).
-// MODE 3: 3D predictor on vz x vy x vx with TY rows per tile.
+// MODE 3: 3D predictor on vz x vy x vx with TY rows per tile, plus a halo
+//         warp for the row above the tile.
 // A warp covers SEG consecutive segments of 128 columns of a tile row, 4
 // points per lane in each, so a thread handles 4 * SEG points of every row.
 // Register budget: the two-segment kernel keeps all of its state (124
@@ -451,11 +452,13 @@ __device__ __forceinline__ int32_t prequant(float x, float xmin, float inv, bool
 // one-segment kernels are held to 7 blocks of 128 threads per SM (2D) or
 // 4 blocks of 256 (3D).
 template <int MODE, int TX, int TY, bool VEC, int SEG>
-__global__ void __launch_bounds__(TX / (4 * SEG) * TY,
-                                  SEG == 2 ? 1 : (MODE == 3 ? 1024 : 896) / (TX / (4 * SEG) * TY))
+__global__ void __launch_bounds__(TX / (4 * SEG) * (TY + (MODE == 3 ? 1 : 0)),
+                                  SEG == 2 ? 1 : (MODE == 3 ? 3 : 896 / (TX / (4 * SEG) * TY)))
     k_pq(const __grid_constant__ Batch<PQArgs> B) {
     constexpr int TPR = TX / (4 * SEG);  // threads per tile row
-    constexpr int NT = TPR * TY;
+    // MODE 3 adds a halo warp (threadIdx.y == 0) that only forms the row
+    // differences of the row above the tile
+    constexpr int NT = TPR * (TY + (MODE == 3 ? 1 : 0));
     constexpr int NP = 4 * SEG;          // points per thread per row
     static_assert(TPR % 32 == 0, "whole warps per tile row");
     const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
@@ -508,9 +511,11 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * TY,
     const uint32_t cb = (threadIdx.x >> 5) * (128u * SEG) + 4u * lane;
     const uint32_t xb = x0 + cb;
     const uint32_t xw = xb - 4u * lane;  // the warp's first column
-    const uint32_t y = y0 + threadIdx.y;
+    // MODE 3: warp row threadIdx.y holds row y0 + threadIdx.y - 1 (row y0 - 1
+    // for the halo warp, which exists only when y0 > 0)
+    const uint32_t y = (MODE == 3) ? y0 + threadIdx.y - 1u : y0 + threadIdx.y;
     const uint32_t vx = a.vx;
-    const bool yin = (MODE == 3) ? (y < a.vy) : true;
+    const bool yin = (MODE == 3) ? (threadIdx.y == 0 ? y0 > 0 : y < a.vy) : true;
     // histogram window [wlo, wlo + kHistWin) around the zero residual; the
     // unsigned difference code - wlo wraps for codes below the window
     const uint32_t wlo = (uint32_t)(R - kHistWin / 2);
@@ -553,14 +558,9 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * TY,
             }
         }
     };
-    auto fetch = [&](uint32_t z, Row& r, Row& h) {
-        const uint64_t rowbase = ((uint64_t)z * a.vy + y) * vx;
+    auto fetch = [&](uint32_t z, Row& r) {
+        const uint64_t rowbase = ((uint64_t)z * a.vy + (yin ? y : 0u)) * vx;
         load_row(x + rowbase, rowbase, yin, row_limit(rowbase), r);
-        if (MODE == 3 && threadIdx.y == 0 && y0 > 0) {
-            // halo row y0 - 1 of plane z
-            const uint64_t hb = ((uint64_t)z * a.vy + (y0 - 1)) * vx;
-            load_row(x + hb, hb, true, vx, h);
-        }
     };
     // row differences of 4 * SEG lattice values whose left neighbour (of the
     // warp's first point) is ql0: segment j > 0 of lane 0 continues from lane
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * TY,
     FF2 acc = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
     uint32_t glo = 0xffffffffu, ghi = 0u;  // nonzero symbols counted outside the window
     int buf = 0;
-    Row cur, nxt, hcur, hnxt;
+    Row cur, nxt;
 
     // One row.  FULL: every point of the warp lies inside the row (a uniform
     // branch per warp), so no point needs a bounds flag.
@@ -608,26 +608,17 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * TY,
 
         int32_t L2[NP];
         if (MODE == 3) {
+            // every warp row's differences along x (zero for a missing halo
+            // row); the row above's come back after the barrier
 #pragma unroll
-            for (int i = 0; i < NP; i++) sL1[buf][threadIdx.y + 1][cb + 128u * (i / 4) + (i % 4)] = L1[i];
-            if (threadIdx.y == 0) {
-                int32_t h[NP], hd[NP];
-                int32_t hl = 0;
-#pragma unroll
-                for (int i = 0; i < NP; i++) h[i] = 0;
-                if (y0 > 0) {
-#pragma unroll
-                    for (int i = 0; i < NP; i++)
-                        h[i] = (xb + 128u * (i / 4) + (i % 4) < vx) ? prequant(hcur.v[i], xmin, inv, off) : 0;
-                    if (hcur.hl) hl = prequant(hcur.l, xmin, inv, off);
-                }
-                row_diff(h, hl, hd);
-#pragma unroll
-                for (int i = 0; i < NP; i++) sL1[buf][0][cb + 128u * (i / 4) + (i % 4)] = hd[i];
-            }
+            for (int i = 0; i < NP; i++) sL1[buf][threadIdx.y][cb + 128u * (i / 4) + (i % 4)] = L1[i];
             __syncthreads();
+            if (threadIdx.y == 0) {  // the halo warp is done with this plane
+                buf ^= 1;
+                return;
+            }
 #pragma unroll
-            for (int i = 0; i < NP; i++) L2[i] = L1[i] - sL1[buf][threadIdx.y][cb + 128u * (i / 4) + (i % 4)];
+            for (int i = 0; i < NP; i++) L2[i] = L1[i] - sL1[buf][threadIdx.y - 1][cb + 128u * (i / 4) + (i % 4)];
             buf ^= 1;
         } else {
 #pragma unroll
@@ -744,18 +735,14 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * TY,
     // a warp whose first column is past the row end has no point in any row
     // (MODE 3 keeps every warp for the block barriers of its loop)
     const uint32_t zlast = (MODE != 3 && xw >= vx) ? zstart : z1;
-#pragma unroll
-    for (int i = 0; i < NP; i++) hnxt.v[i] = 0.0f;
-    hnxt.l = 0.0f;
-    hnxt.hl = false;
-    if (zstart < zlast) fetch(zstart, nxt, hnxt);
+    if (zstart < zlast) fetch(zstart, nxt);
     // one copy of the loop per scaling (uniform over the block)
     auto rows = [&](auto scaled_tag) {
         for (uint32_t z = zstart; z < zlast; z++) {
             cur = nxt;
-            hcur = hnxt;
-            if (z + 1 < zlast) fetch(z + 1, nxt, hnxt);
-            if (MODE != 3 && xw + 128u * SEG <= row_limit(((uint64_t)z * a.vy + y) * vx))
+            if (z + 1 < zlast) fetch(z + 1, nxt);
+            // MODE 3: the halo warp of the first band has no row (yin false)
+            if ((MODE != 3 || yin) && xw + 128u * SEG <= row_limit(((uint64_t)z * a.vy + y) * vx))
                 row(z, std::true_type{}, scaled_tag);
             else
                 row(z, std::false_type{}, scaled_tag);
@@ -1225,7 +1212,7 @@ __global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ Batch<
 // Launches one k_pq variant over the fields of a batch that use it.
 template <int MODE, int TX, int TY, int SEG>
 static void launch_pq_t(Batch<PQArgs>& b, uint32_t blocks, bool vec, cudaStream_t st) {
-    const dim3 blk(TX / (4 * SEG), TY);
+    const dim3 blk(TX / (4 * SEG), TY + (MODE == 3 ? 1 : 0));  // MODE 3: plus the halo warp
     if (vec) k_pq<MODE, TX, TY, true, SEG><<<blocks, blk, 0, st>>>(b);
     else k_pq<MODE, TX, TY, false, SEG><<<blocks, blk, 0, st>>>(b);
 }

@@ -120,17 +120,13 @@ def test_launch_table(tmp_path):
 
 
 def test_write_traffic(tmp_path, monkeypatch):
+    """Bytes per point per workload and stage from separate one-kernel
+    captures; reported for a launch of any size while the sources match."""
     rows = []
     for lid in (1, 2):  # two launches of the predictor
-        k = "void fp::k_pq<2, 1024, 1, 1, 2>(fp::Batch<fp::PQArgs>)"
+        k = "void fp::k_pq<3, 128, 8, 1, 1>(fp::Batch<fp::PQArgs>)"
         rows += [_row(lid, k, "dram__bytes_read.sum", "Mbyte", "200"),
-                 _row(lid, k, "dram__bytes_write.sum", "byte", "1000000"),
-                 _row(lid, k, "gpu__time_duration.sum", "us", "150")]
-    for lid, k in ((3, "void fp::k_enc_pack(fp::Batch<fp::EncArgs>)"),
-                   (4, "void fp::k_enc_scan(fp::Batch<fp::EncArgs>)"),
-                   (5, "void fp::k_enc_copy(fp::Batch<fp::EncArgs>)")):
-        rows += [_row(lid, k, "dram__bytes_read.sum", "byte", "100"),
-                 _row(lid, k, "dram__bytes_write.sum", "byte", "10")]
+                 _row(lid, k, "dram__bytes_write.sum", "byte", "1000000")]
     out = tmp_path / "profiles"
     out.mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
@@ -139,29 +135,36 @@ def test_write_traffic(tmp_path, monkeypatch):
     (src / "compress.cu").write_text("kernel source\n")
     (src / "common.cuh").write_text("shared header\n")
     (src.parent / "build.py").write_text("flags\n")
-    bench.write_traffic(_log(tmp_path, rows))
+    bench.write_traffic(_log(tmp_path, rows), "c3", 10**8, "ncu ... k_pq")
+    # the encoder's kernels captured one at a time add up
+    enc = [_row(3, "void fp::k_enc_pack(fp::Batch<fp::EncArgs>)", "dram__bytes_read.sum", "byte", "100"),
+           _row(3, "void fp::k_enc_pack(fp::Batch<fp::EncArgs>)", "dram__bytes_write.sum", "byte", "10")]
+    bench.write_traffic(_log(tmp_path, enc), "c3", 10, "ncu ... k_enc_pack")
+    cp = [_row(4, "void fp::k_enc_copy(fp::Batch<fp::EncArgs>)", "dram__bytes_read.sum", "byte", "30"),
+          _row(4, "void fp::k_enc_copy(fp::Batch<fp::EncArgs>)", "dram__bytes_write.sum", "byte", "20")]
+    bench.write_traffic(_log(tmp_path, cp), "c3", 10, "ncu ... k_enc_copy")
     t = json.load(open(out / "traffic.json"))
-    pq = t["predict_quantize"]
-    assert pq["launches"] == 2 and pq["dram_read"] == 200_000_000 and pq["dram_write"] == 1_000_000
-    assert pq["dram_bytes_per_launch"] == 201_000_000
-    enc = t["encode"]
-    assert enc["launches"] == 1 and enc["dram_bytes_per_launch"] == 330
-    assert sorted(enc["kernels"]) == ["k_enc_copy", "k_enc_pack", "k_enc_scan"]
+    pq = t["c3"]["predict_quantize"]
+    assert pq["dram_bytes_per_point"] == pytest.approx(2.01)
+    assert pq["kernels"]["k_pq<3, 128, 8, 1, 1>"]["launches"] == 2
+    assert t["c3"]["encode"]["dram_bytes_per_point"] == pytest.approx(16.0)
+    assert sorted(t["c3"]["encode"]["kernels"]) == ["k_enc_copy", "k_enc_pack"]
     import hashlib
-    assert pq["source_sha1"] == hashlib.sha1(b"kernel source\n").hexdigest()
-    assert "decode" not in t
-    # the SHA-1 check: traffic is reported only while the source is unchanged
-    assert bench.measured_traffic("predict_quantize") == 201_000_000
-    # ... and while the shared header and the compiler flags are unchanged
+    assert pq["sources"]["paper_1805_07384_gb300/csrc/compress.cu"] == hashlib.sha1(b"kernel source\n").hexdigest()
+    assert "decode" not in t["c3"] and "c1" not in t
+    # scaled to the launch of the benchmark's own size
+    assert bench.measured_traffic("c3", "predict_quantize", 10**9) == 2_010_000_000
+    assert bench.measured_traffic("c1", "predict_quantize", 10**9) is None
+    # reported only while the source, the shared header and the flags are unchanged
     (src.parent / "build.py").write_text("other flags\n")
-    assert bench.measured_traffic("predict_quantize") is None
+    assert bench.measured_traffic("c3", "predict_quantize", 10**9) is None
     (src.parent / "build.py").write_text("flags\n")
     (src / "common.cuh").write_text("changed header\n")
-    assert bench.measured_traffic("predict_quantize") is None
+    assert bench.measured_traffic("c3", "predict_quantize", 10**9) is None
     (src / "common.cuh").write_text("shared header\n")
-    assert bench.measured_traffic("predict_quantize") == 201_000_000
+    assert bench.measured_traffic("c3", "predict_quantize", 10**9) == 2_010_000_000
     (src / "compress.cu").write_text("changed\n")
-    assert bench.measured_traffic("predict_quantize") is None
+    assert bench.measured_traffic("c3", "predict_quantize", 10**9) is None
 
 
 def test_cpu_baseline_summary():
