@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--tune-tol", type=float, default=0.01,
                     help="autotune: largest accepted compressed-size increase over the smallest")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve-run", action="store_true",
+                    help="leave out the short served run (2,000 requests at 5,000 req/s) of the line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true")
     ap.add_argument("--cpu-workers", type=int, default=0, help="0 = all host cores")
@@ -686,147 +688,217 @@ def serve_field(shape, seed, device):
     return g.to(torch.float32).contiguous()
 
 
-def run_serve(a):
+SERVE_LARGE_POOL = 8  # distinct seeded inputs of each large shape (>= 16 MB)
+
+
+class ServeSetup:
+    """Inputs, blobs and output buffers of a request stream.  Requests are
+    drawn first (Poisson arrivals, shape uniform over SERVE_SHAPES, target
+    U[30, 120] dB, compress or decompress at even odds); every request's input
+    is seeded by its own id for the small shapes, and is one of
+    SERVE_LARGE_POOL seeded fields for the large ones (1800x3600, 100x500x500,
+    256^3), to bound the memory held.  A decompression request gets the blob of
+    its input at the nearest 10 dB target, made beforehand."""
+
+    def __init__(self, dev, request_lists):
+        import numpy as np
+        import torch
+        from paper_1805_07384_gb300 import fpsnr
+        self.nbytes = {s: 4 * int(np.prod(s)) for s in SERVE_SHAPES}
+        self.large = {s: self.nbytes[s] >= (16 << 20) for s in SERVE_SHAPES}
+        self.fields, need_blob = {}, set()
+        for reqs in request_lists:
+            for (ta, s, psnr, kind, rid) in reqs:
+                key = (s, self.input_id(s, rid))
+                if key not in self.fields:
+                    self.fields[key] = serve_field(s, 7919 * SERVE_SHAPES.index(s) + key[1], dev)
+                if kind == 1:
+                    need_blob.add((key, self.bucket(psnr)))
+        self.blobs = {}
+        plans = {s: fpsnr.Plan(s, 60.0) for s in SERVE_SHAPES}
+        for (key, b) in sorted(need_blob):
+            p = plans[key[0]]
+            p.set_psnr(b)
+            out, nb, st = p.compress(self.fields[key])
+            torch.cuda.synchronize()
+            n = int(nb.item())
+            assert fpsnr.parse_stats(st)["status"] == 0
+            self.blobs[(key, b)] = (out[:n].clone(), n)
+            del out
+        for p in plans.values():
+            p.close()
+        # output buffers per shape (a compressed blob may take up to 4n + 1 MiB)
+        self.pool_n = {s: (64 if self.nbytes[s] <= (4 << 20) else (16 if self.nbytes[s] <= (64 << 20) else 8))
+                       for s in SERVE_SHAPES}
+        cap = {s: self.nbytes[s] + (1 << 20) for s in SERVE_SHAPES}
+        self.bufs = {s: [torch.empty(cap[s], dtype=torch.uint8, device=dev) for _ in range(self.pool_n[s])]
+                     for s in SERVE_SHAPES}
+
+    def input_id(self, s, rid):
+        return rid % SERVE_LARGE_POOL if self.large[s] else rid
+
+    @staticmethod
+    def bucket(psnr):
+        return min(SERVE_BUCKETS, key=lambda v: abs(v - psnr))
+
+    def describe(self):
+        return ("requests with Poisson arrivals; shape uniform over "
+                + ", ".join("x".join(map(str, s)) for s in SERVE_SHAPES)
+                + "; target PSNR U[30,120] dB; half compress, half decompress of a blob made "
+                  "beforehand at the nearest 10 dB target; every request's input seeded by its id "
+                  f"for the small shapes, one of {SERVE_LARGE_POOL} seeded fields for the shapes of "
+                  "16 MB and more; inputs resident on the device")
+
+
+def serve_requests(n, rate, seed):
+    """(arrival us, shape, target, kind 0 compress / 1 decompress, request id)."""
     import numpy as np
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1e6 / rate, size=n)
+    out = []
+    t = 0.0
+    for i in range(n):
+        t += gaps[i]
+        s = SERVE_SHAPES[int(rng.integers(len(SERVE_SHAPES)))]
+        psnr = float(rng.uniform(30.0, 120.0))
+        kind = int(rng.integers(2))
+        out.append((t, s, psnr, kind, i + 1000000 * seed))
+    return out
+
+
+def serve_session(srv, setup, reqs, rate):
+    """Submits the requests at their arrival times through the server and
+    returns latency percentiles and served GB/s."""
+    import torch
+    free = {s: list(range(setup.pool_n[s])) for s in SERVE_SHAPES}
+    owner, lat, done_t, failed = {}, [], [], 0
+    total_bytes = 0
+    st0 = srv.stats()
+
+    def collect(block):
+        nonlocal total_bytes, failed
+        while True:
+            item = srv.take_any()
+            if item is None:
+                if not block:
+                    return
+                time.sleep(20e-6)
+                continue
+            t, r = item
+            s, bi = owner.pop(t)
+            free[s].append(bi)
+            if r["status"]:
+                failed += 1
+            else:
+                lat.append(r["done_us"] - r["arrival_us"])
+                total_bytes += setup.nbytes[s]
+            done_t.append(r["done_us"])
+            return
+
+    t0 = srv.now() + 20000.0
+    for (ta, s, psnr, kind, rid) in reqs:
+        while not free[s]:
+            collect(True)
+        collect(False)
+        bi = free[s].pop()
+        buf = setup.bufs[s][bi]
+        key = (s, setup.input_id(s, rid))
+        if kind == 0:
+            t = srv.submit_compress(setup.fields[key], psnr, buf, arrival_us=t0 + ta)
+        else:
+            blob, n = setup.blobs[(key, setup.bucket(psnr))]
+            t = srv.submit_decompress(blob, n, buf[:setup.nbytes[s]].view(torch.float32).view(s),
+                                      arrival_us=t0 + ta)
+        owner[t] = (s, bi)
+    while owner:
+        collect(True)
+    st1 = srv.stats()
+    span = (max(done_t) - t0) / 1e6
+    lat_ms = sorted(v / 1e3 for v in lat)
+    q = lambda f: lat_ms[min(len(lat_ms) - 1, int(f * (len(lat_ms) - 1) + 0.5))]
+    nb = st1["batches"] - st0["batches"]
+    return {"rate_rps": rate, "requests": len(reqs), "failed": failed,
+            "p50_ms": round(q(0.5), 3), "p99_ms": round(q(0.99), 3),
+            "max_ms": round(lat_ms[-1], 3), "gbs": round(total_bytes / span / 1e9, 2),
+            "offered_gbs": round(sum(setup.nbytes[s] for _, s, _, _, _ in reqs) /
+                                 (reqs[-1][0] / 1e6) / 1e9, 2),
+            "batches": nb, "mean_batch": round(len(reqs) / max(nb, 1), 2)}
+
+
+SERVER_OPTS = {"hbm_budget": 40 << 30, "max_batch": 16, "streams": 4}
+
+
+def warm_server(srv, setup):
+    """One request of each kind per shape, so that every plan is cached."""
+    import torch
+    for s in SERVE_SHAPES:
+        key = next(k for k in setup.fields if k[0] == s)
+        srv.wait(srv.submit_compress(setup.fields[key], 60.0, setup.bufs[s][0]))
+        bk = next((k for k in setup.blobs if k[0][0] == s), None)
+        if bk is not None:
+            blob, n = setup.blobs[bk]
+            srv.wait(srv.submit_decompress(blob, n, setup.bufs[s][0][:setup.nbytes[s]].view(torch.float32).view(s)))
+
+
+def served_short(dev, rate=5000.0, n=2000):
+    """The short served run of the default benchmark line."""
+    from paper_1805_07384_gb300 import fpsnr
+    reqs = serve_requests(n, rate, seed=5)
+    setup = ServeSetup(dev, [reqs])
+    srv = fpsnr.Server(**SERVER_OPTS)
+    try:
+        warm_server(srv, setup)
+        r = serve_session(srv, setup, reqs, rate)
+    finally:
+        srv.close()
+    r["inputs"] = setup.describe()
+    r["latency"] = "completion observed by the server minus scheduled arrival"
+    return r
+
+
+def run_serve(a):
     import torch
     from paper_1805_07384_gb300 import build as fbuild
     fbuild.build()
     from paper_1805_07384_gb300 import fpsnr
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    K = 2  # pre-staged fields per shape
-    fields = {s: [serve_field(s, 100 * i + j, dev) for j in range(K)] for i, s in enumerate(SERVE_SHAPES)}
-    nbytes = {s: 4 * int(np.prod(s)) for s in SERVE_SHAPES}
-    # blobs for the decompression requests: every field at every target bucket
-    blobs = {}
-    for s in SERVE_SHAPES:
-        p = fpsnr.Plan(s, 60.0)
-        for j in range(K):
-            for b in SERVE_BUCKETS:
-                p.set_psnr(b)
-                out, nb, st = p.compress(fields[s][j])
-                torch.cuda.synchronize()
-                n = int(nb.item())
-                assert fpsnr.parse_stats(st)["status"] == 0
-                blobs[(s, j, b)] = (out[:n].clone(), n)
-        p.close()
-    # output buffers per shape (a compressed blob may take up to 4n + 1 MiB)
-    pool_n = {s: (64 if nbytes[s] <= (4 << 20) else (16 if nbytes[s] <= (64 << 20) else 8))
-              for s in SERVE_SHAPES}
-    cap = {s: nbytes[s] + (1 << 20) for s in SERVE_SHAPES}
-    bufs = {s: [torch.empty(cap[s], dtype=torch.uint8, device=dev) for _ in range(pool_n[s])]
-            for s in SERVE_SHAPES}
-
-    def requests(n, rate, seed):
-        rng = np.random.default_rng(seed)
-        gaps = rng.exponential(1e6 / rate, size=n)
-        out = []
-        t = 0.0
-        for i in range(n):
-            t += gaps[i]
-            s = SERVE_SHAPES[int(rng.integers(len(SERVE_SHAPES)))]
-            psnr = float(rng.uniform(30.0, 120.0))
-            kind = int(rng.integers(2))
-            out.append((t, s, psnr, kind, i % K))
-        return out
-
-    srv = fpsnr.Server(hbm_budget=40 << 30, max_batch=16, streams=4)
-    # warm the plan cache: one request of each kind per shape
-    for s in SERVE_SHAPES:
-        srv.wait(srv.submit_compress(fields[s][0], 60.0, bufs[s][0]))
-        blob, n = blobs[(s, 0, 60.0)]
-        srv.wait(srv.submit_decompress(blob, n, bufs[s][0][:nbytes[s]].view(torch.float32).view(s)))
-
-    runs = []
-    for rate in [float(r) for r in a.serve_rates.split(",")]:
-        reqs = requests(a.serve_requests, rate, seed=int(rate))
-        free = {s: list(range(pool_n[s])) for s in SERVE_SHAPES}
-        owner, lat, done_t, total_bytes, failed = {}, [], [], 0, 0
-        st0 = srv.stats()
-
-        def collect(block):
-            nonlocal total_bytes, failed
-            while True:
-                item = srv.take_any()
-                if item is None:
-                    if not block:
-                        return
-                    time.sleep(20e-6)
-                    continue
-                t, r = item
-                s, bi = owner.pop(t)
-                free[s].append(bi)
-                if r["status"]:
-                    failed += 1
-                else:
-                    lat.append(r["done_us"] - r["arrival_us"])
-                    total_bytes += nbytes[s]
-                done_t.append(r["done_us"])
-                return
-
-        t0 = srv.now() + 20000.0
-        for (ta, s, psnr, kind, j) in reqs:
-            while not free[s]:
-                collect(True)
-            collect(False)
-            bi = free[s].pop()
-            buf = bufs[s][bi]
-            if kind == 0:
-                t = srv.submit_compress(fields[s][j], psnr, buf, arrival_us=t0 + ta)
-            else:
-                b = min(SERVE_BUCKETS, key=lambda v: abs(v - psnr))
-                blob, n = blobs[(s, j, b)]
-                t = srv.submit_decompress(blob, n, buf[:nbytes[s]].view(torch.float32).view(s),
-                                          arrival_us=t0 + ta)
-            owner[t] = (s, bi)
-        while owner:
-            collect(True)
-        st1 = srv.stats()
-        span = (max(done_t) - t0) / 1e6
-        lat_ms = sorted(v / 1e3 for v in lat)
-        q = lambda f: lat_ms[min(len(lat_ms) - 1, int(f * (len(lat_ms) - 1) + 0.5))]
-        nb = st1["batches"] - st0["batches"]
-        runs.append({"rate_rps": rate, "requests": len(reqs), "failed": failed,
-                     "p50_ms": round(q(0.5), 3), "p99_ms": round(q(0.99), 3),
-                     "max_ms": round(lat_ms[-1], 3), "gbs": round(total_bytes / span / 1e9, 2),
-                     "offered_gbs": round(sum(nbytes[s] for _, s, _, _, _ in reqs) /
-                                          (reqs[-1][0] / 1e6) / 1e9, 2),
-                     "batches": nb, "mean_batch": round(len(reqs) / max(nb, 1), 2)})
+    rates = [float(r) for r in a.serve_rates.split(",")]
+    lists = [serve_requests(a.serve_requests, rate, seed=int(rate)) for rate in rates]
+    serial = serve_requests(a.serve_serial, rates[0], seed=1)
+    setup = ServeSetup(dev, lists + [serial])
+    srv = fpsnr.Server(**SERVER_OPTS)
+    warm_server(srv, setup)
+    runs = [serve_session(srv, setup, reqs, rate) for reqs, rate in zip(lists, rates)]
     pst = srv.stats()
     srv.close()
 
-    # serial plain calls on the first requests of the lowest rate's list
-    reqs = requests(a.serve_serial, float(a.serve_rates.split(",")[0]), seed=1)
+    # serial plain calls
     plans = {s: fpsnr.Plan(s, 60.0) for s in SERVE_SHAPES}
     torch.cuda.synchronize()
     w0 = time.perf_counter()
     tot = 0
-    for (ta, s, psnr, kind, j) in reqs:
+    for (ta, s, psnr, kind, rid) in serial:
         p = plans[s]
-        buf = bufs[s][0]
+        buf = setup.bufs[s][0]
+        key = (s, setup.input_id(s, rid))
         if kind == 0:
             p.set_psnr(psnr)
-            p.compress(fields[s][j], out=buf)
+            p.compress(setup.fields[key], out=buf)
         else:
-            b = min(SERVE_BUCKETS, key=lambda v: abs(v - psnr))
-            blob, n = blobs[(s, j, b)]
-            p.decompress(blob, n, out=buf[:nbytes[s]].view(torch.float32).view(s))
+            blob, n = setup.blobs[(key, setup.bucket(psnr))]
+            p.decompress(blob, n, out=buf[:setup.nbytes[s]].view(torch.float32).view(s))
         torch.cuda.synchronize()
-        tot += nbytes[s]
+        tot += setup.nbytes[s]
     serial_gbs = tot / (time.perf_counter() - w0) / 1e9
     for p in plans.values():
         p.close()
     line = {"metric": "served compress/decompress requests: p50/p99 latency and aggregate GB/s",
             "unit": "ms / GB/s", "n_gpus": 1, "data": "synthetic", "impl": "ours",
-            "config": {"workload": "requests with Poisson arrivals; shape uniform over "
-                                   + ", ".join("x".join(map(str, s)) for s in SERVE_SHAPES)
-                                   + "; target PSNR U[30,120] dB; half compress, half decompress "
-                                   "of a blob made beforehand at the nearest 10 dB target; inputs "
-                                   f"pre-staged on the device ({K} fields per shape)",
-                       "server": {"hbm_budget": 40 << 30, "max_batch": 16, "streams": 4},
+            "config": {"workload": setup.describe(), "server": SERVER_OPTS,
                        "latency": "completion observed by the server minus scheduled arrival"},
             "runs": runs,
-            "serial_plain": {"gbs": round(serial_gbs, 2), "requests": len(reqs),
+            "serial_plain": {"gbs": round(serial_gbs, 2), "requests": len(serial),
                              "note": "one plain call per request, synchronized after each"},
             "plans_cached": pst["plans"], "plan_bytes": pst["plan_bytes"]}
     print(json.dumps(line), flush=True)
@@ -1210,6 +1282,13 @@ def main():
                     per_field[f]["oracle_psnr"] = round(p_or, 6)
                     per_field[f]["oracle_s"] = round(t, 3)
 
+    served = None
+    if rank == 0 and not a.no_serve_run:
+        graphs.clear()
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+        served = served_short(dev)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
@@ -1221,7 +1300,7 @@ def main():
                                "tuning": {str(k): {kk: v[kk] for kk in ("chunk", "pq_tile_x", "band_rows")}
                                           for k, v in tuning.items()}} if tuning else {})),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk,
+            "gpu_launches": launches, "clocks": clk, "served": served,
             "hbm_frac_of_step": round(value / (6775.6 if roof is None else roof["peak"]), 4),
             "psnr": {"mean_abs_dev_db": round(sum(dev_abs) / len(dev_abs), 4) if dev_abs else None,
                      "meet_rate": round(sum(meets) / len(meets), 4) if meets else None},

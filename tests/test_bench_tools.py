@@ -179,3 +179,19 @@ def test_cpu_baseline_summary():
     assert c["steps_gbs"] == [1.0, 2.0, 0.5]
     assert c["one_core_gbs_per_task"] == {"median": 1.0, "min": 0.25, "max": 2.0}
     assert "3 steps" in c["sample"] and "24 fields" in c["sample"]
+
+
+def test_serve_requests():
+    """The served stream: Poisson arrivals at the stated rate, every shape and
+    both kinds, targets in [30, 120] dB, request ids unique per seed."""
+    reqs = bench.serve_requests(4000, 5000.0, seed=5)
+    assert len(reqs) == 4000 and len({r[4] for r in reqs}) == 4000
+    t = [r[0] for r in reqs]
+    assert all(b > a for a, b in zip(t, t[1:]))
+    rate = len(t) / (t[-1] / 1e6)
+    assert 4500 < rate < 5500
+    assert {r[1] for r in reqs} == set(bench.SERVE_SHAPES)
+    assert {r[3] for r in reqs} == {0, 1}
+    assert all(30.0 <= r[2] <= 120.0 for r in reqs)
+    assert bench.serve_requests(4000, 5000.0, seed=5) == reqs
+    assert bench.ServeSetup.bucket(44.9) == 40.0 and bench.ServeSetup.bucket(115.1) == 120.0
