@@ -28,6 +28,7 @@ constexpr uint32_t kZrSeg = 1024;          // lossless container: bytes per segm
 constexpr uint32_t kZrMagic = 0x315A5046u;  // bytes "FPZ1"
 constexpr int kLutBits = 12;        // decode look-up table width
 constexpr uint32_t kLutLen = 0x20u;  // table entry flag: length only, symbol by canonical index
+constexpr uint32_t kLutSlow = 0x40u; // table entry flag: not a whole code of <= kLutBits bits
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 // Per-call device record.  Written by kernels, read by later kernels.

@@ -5,7 +5,10 @@
 //   k_dsetup        header validation against the plan, canonical decoding
 //                   tables and a look-up table over the next kLutBits bits
 //   k_decode        one thread per chunk, canonical Huffman decode into the
-//                   16-bit symbols (the plan's symbol buffer)
+//                   16-bit symbols (the plan's symbol buffer): a bit-position
+//                   window over three registers fed by a per-thread cp.async
+//                   ring, codes in pairs through the table for fields whose
+//                   codes are short
 //   2D fields up to kBandMaxNx columns (reduce, then scan, over bands of rows):
 //     k_band_sum    column sums of the residuals of every band
 //     k_band_carry  exclusive prefix of those sums over the bands
@@ -13,7 +16,13 @@
 //                   sums, then every row's prefix along x is added to them;
 //                   dequantization x' = fmaf((float)q, s, xmin) (midpoint
 //                   reconstruction, Sec. IV) is fused into the write
-//   other shapes (1D, 3D, wider 2D):
+//   3D fields up to kVolMaxNx columns (tiles of 32 planes x a band of rows):
+//     k_vol_sum     per tile: column sums per plane, slab sums per row, and
+//                   the tile's column totals
+//     k_vol_carry   exclusive prefixes of those sums over bands and slabs
+//     k_vol_scan    per tile, plane by plane (planes staged by bulk copies):
+//                   column prefix, then row prefix, dequantized on the write
+//   other shapes (1D, wider 2D and 3D):
 //     k_scan_contig   inclusive prefix sum along x (rows), decoupled look-back
 //                     between tiles of one row; the first pass reads symbols
 //     k_scan_strided  inclusive prefix sum along y or z, decoupled look-back
@@ -179,13 +188,14 @@ __global__ void __launch_bounds__(1024) k_dsetup(const __grid_constant__ Batch<D
     // Table over the next kLutBits bits.  Canonical code ranges tile the
     // left-justified code space in order of length, so prefix v (a) holds one
     // whole code of length l <= kLutBits: entry (sym << 8) | l; (b) lies inside
-    // the range of a single length l > kLutBits: entry kLutLen | l (the decoder
-    // finds the symbol from its canonical index); or (c) straddles the ranges of
-    // several lengths or has no code: entry 0 (the decoder searches the range
-    // ends).  Case (c) holds for at most one prefix per length boundary.
+    // the range of a single length l > kLutBits: entry kLutSlow | kLutLen | l
+    // (the decoder finds the symbol from its canonical index); or (c) straddles
+    // the ranges of several lengths or has no code: entry kLutSlow (the decoder
+    // searches the range ends).  Case (c) holds for at most one prefix per
+    // length boundary.
     for (uint32_t v = tid; v < (1u << kLutBits); v += blockDim.x) {
         const unsigned long long w = (unsigned long long)v << (32 - kLutBits);
-        uint32_t e = 0;
+        uint32_t e = kLutSlow;
         for (uint32_t l = 1; l <= lmax; l++) {
             const unsigned long long lje =
                 (unsigned long long)(par->d_first_code[l] + par->d_count[l]) << (32 - l);
@@ -195,7 +205,7 @@ __global__ void __launch_bounds__(1024) k_dsetup(const __grid_constant__ Batch<D
                     const uint32_t k = code - par->d_first_code[l];
                     if (k < par->d_count[l]) e = ((uint32_t)syms[par->d_first_index[l] + k] << 8) | l;
                 } else if (w + (1ull << (32 - kLutBits)) <= lje) {
-                    e = kLutLen | l;
+                    e = kLutSlow | kLutLen | l;
                 }
                 break;
             }
@@ -204,19 +214,29 @@ __global__ void __launch_bounds__(1024) k_dsetup(const __grid_constant__ Batch<D
     }
 }
 
-// One thread decodes one chunk of `chunk` symbols.  The bit window is 64 bits
-// held as two 32-bit halves (hi holds the next bits, left-justified); a stream
-// word is appended whenever 32 or fewer valid bits remain (checked before
-// every code, or before every second code when no code is longer than 16
-// bits: a refill leaves at least 32 valid bits).  Every symbol is one
-// table read over the next kLutBits bits and a funnel shift: the entry gives
-// the code length, and the symbol itself for codes of up to kLutBits bits;
-// longer codes take their symbol from the canonical index, off the dependency
-// chain of the next code's position.  Prefixes shared by several lengths are
-// resolved by comparing the window with the end of each length's canonical
-// range.  A chunk that consumes more bits than it owns, or meets a prefix no
-// code has, is corrupt.
-constexpr int kDecRing = 4;  // stream quads in flight per thread (power of two)
+// One thread decodes one chunk of `chunk` symbols, reading the stream by bit
+// position p: the next 32 bits are a funnel shift of the two words that hold
+// bit p.  The thread keeps three consecutive words of its chunk in registers
+// (a, b, c) and moves on by one word whenever p crosses a word boundary (no
+// step takes more than 27 bits, the longest code).  The words come from a
+// ring of kDecRing aligned quads in shared memory that cp.async fills three
+// quads ahead of the one being read (an asynchronous copy holds no register,
+// and shared memory per thread stays small whatever the stream's density).
+// Codes go in pairs when the code's long lengths are rare: a table read over
+// the next kLutBits bits gives the first code's length and symbol, a second
+// read at the window shifted by that length gives the second's, and when both
+// are whole codes of at most kLutBits bits (no kLutSlow flag) a byte permute
+// packs both symbols.  Otherwise, and for every code of a field whose long
+// codes are frequent, codes are decoded one by one: a longer code takes its
+// symbol from its canonical index (kLutLen), and a prefix shared by several
+// lengths is resolved by comparing the window with the end of each length's
+// canonical range.  A chunk that consumes more bits than it owns, or meets a
+// prefix no code has, is corrupt.
+constexpr int kDecRing = 8;  // stream quads in a thread's ring (power of two)
+// a field decodes codes in pairs when its mean code length, estimated as the
+// sum over lengths l of l * count[l] * 2^-l (a code of l bits stands for a
+// probability near 2^-l), is below this many bits
+constexpr float kDecPairBits = 5.0f;
 
 // Asynchronous 16-byte copy global -> shared memory through L2 (both 16-byte
 // aligned), one commit group per copy, and waits on the thread's own groups.
@@ -229,11 +249,22 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Copies quad q of the stream into the ring slot it maps to (nothing past
+// the section's qend quads) and closes a copy group.
+template <int THREADS>
+__device__ __forceinline__ void dec_issue(uint32_t* ring, const uint32_t* __restrict__ stream, uint32_t qend,
+                                          uint32_t q) {
+    if (q < qend) cp_async16(ring + (q & (kDecRing - 1)) * (4u * THREADS), stream + 4u * q);
+    cp_async_commit();
+}
+
 // dynamic shared memory of a THREADS-wide decode block: the table, then the
-// stream rings.
+// stream rings
 constexpr uint32_t dec_smem(int threads) {
     return ((1u << kLutBits) + 4u * kDecRing * (uint32_t)threads) * 4u;
 }
+// blocks per SM that the shared memory admits (227 KB, 1 KB reserved a block)
+constexpr int dec_min_blocks(int threads) { return (int)((227u * 1024u) / (dec_smem(threads) + 1536u)); }
 
 struct DecArgs {
     DevParams* par;
@@ -247,34 +278,163 @@ struct DecArgs {
     uint64_t nchunks;
 };
 
+// Decodes the cnt symbols of the chunk that owns stream words [w0, w1) into
+// dst; false when the chunk is corrupt (it reads past its words, or meets a
+// prefix no code has).  ring is the thread's first ring word; quads of the
+// 16-byte padded section end at qend.  The caller has issued quads
+// w0 / 4 .. w0 / 4 + kDecRing - 1 (dec_issue), one copy group each.
+// Every code step is free of branches but for rare long-code cases, so the
+// lanes of a warp stay together: the window slides by a predicated move, and
+// the ring is refilled once per group of 8 codes.  A group moves the window
+// by at most 8 x 27 bits (7 words, 2 quads), so two copies per group keep the
+// ring kDecRing - 1 quads ahead of the quad of word a, and the words a group
+// reads (up to 9 words past a) lie in quads issued two groups earlier: all
+// but the four newest copy groups have landed.
+template <int THREADS, bool PAIRS>
+__device__ __forceinline__ bool dec_chunk(uint32_t* ring, const uint32_t* __restrict__ stream, uint32_t qend,
+                                          uint32_t w0, uint32_t w1, uint32_t cnt, uint16_t* __restrict__ dst,
+                                          const uint32_t* __restrict__ lut, const uint32_t* __restrict__ base,
+                                          const unsigned long long* __restrict__ lje,
+                                          const uint16_t* __restrict__ syms, uint32_t lmax) {
+    // word w of the stream sits in slot (w / 4) mod kDecRing of the ring
+    auto word = [&](uint32_t w) -> uint32_t {
+        return ring[((w >> 2) & (kDecRing - 1)) * (4u * THREADS) + (w & 3u)];
+    };
+    uint32_t qi = (w0 >> 2) + kDecRing - 1;  // last quad issued
+    cp_async_wait<kDecRing - 2>();           // quads w0 / 4 and w0 / 4 + 1 landed
+    uint32_t a = word(w0), b = word(w0 + 1), c = word(w0 + 2);
+    uint32_t p = 0;   // bits consumed since word w0
+    uint32_t wr = 0;  // a holds word w0 + wr
+    bool bad = false;
+    auto refill = [&]() {
+        const uint32_t want = ((w0 + wr) >> 2) + kDecRing - 1;
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            if (qi < want) {
+                qi++;
+                if (qi < qend) cp_async16(ring + (qi & (kDecRing - 1)) * (4u * THREADS), stream + 4u * qi);
+            }
+            cp_async_commit();
+        }
+        cp_async_wait<4>();
+    };
+    // p moved by at most 27 bits: slide the three words along by at most one
+    auto step = [&]() {
+        const bool cross = (p >> 5) != wr;
+        wr += cross ? 1u : 0u;
+        a = cross ? b : a;
+        b = cross ? c : b;
+        if (cross) c = word(w0 + wr + 2);
+    };
+    // one code of any length
+    auto one = [&]() -> uint32_t {
+        const uint32_t win = __funnelshift_l(b, a, p);  // bits p .. p + 31 of the chunk
+        const uint32_t e = lut[win >> (32 - kLutBits)];
+        uint32_t l = e & 31u;
+        uint32_t sym = e >> 8;
+        if (e == kLutSlow) {
+            // a prefix shared by several lengths (or by none): the first length
+            // whose canonical range ends above the window, by a fixed number of
+            // bisection steps over kLutBits + 1 .. lmax
+            uint32_t lo = kLutBits + 1, hi = lmax;
+            bad |= (unsigned long long)win >= lje[lmax];  // no code has this prefix
+#pragma unroll
+            for (int it = 0; it < 5; it++) {
+                if (lo < hi) {
+                    const uint32_t m = (lo + hi) >> 1;
+                    if ((unsigned long long)win < lje[m]) hi = m;
+                    else lo = m + 1;
+                }
+            }
+            l = lo;
+        }
+        // a code longer than kLutBits bits: its symbol from its canonical index,
+        // off the dependency chain of the next code's position
+        if (e & kLutSlow) sym = __ldg(&syms[(base[l] + (win >> (32 - l))) & 0xffffu]);
+        p += l;
+        step();
+        return sym;
+    };
+    const uint32_t cnt8 = cnt & ~7u;
+    uint4 prev = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t i = 0; i < cnt8; i += 8) {
+        refill();
+        uint32_t s[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if constexpr (PAIRS) {
+                const uint32_t win = __funnelshift_l(b, a, p);
+                const uint32_t e1 = lut[win >> (32 - kLutBits)];
+                const uint32_t e2 = lut[(win << (e1 & 31u)) >> (32 - kLutBits)];
+                if (((e1 | e2) & kLutSlow) == 0u) {
+                    s[k] = __byte_perm(e1, e2, 0x6521);  // bits 8..23 of each entry
+                    p += (e1 & 31u) + (e2 & 31u);
+                    step();
+                    continue;
+                }
+            }
+            const uint32_t s0 = one();
+            s[k] = s0 | (one() << 16);
+        }
+        // each group is stored after the next one is decoded: the symbol loads of
+        // long codes land meanwhile
+        if (i) *reinterpret_cast<uint4*>(dst + i - 8) = prev;
+        prev = make_uint4(s[0], s[1], s[2], s[3]);
+    }
+    if (cnt8) *reinterpret_cast<uint4*>(dst + cnt8 - 8) = prev;
+    if (cnt8 < cnt) {
+        refill();
+        for (uint32_t i = cnt8; i < cnt; i++) dst[i] = (uint16_t)one();
+    }
+    return !bad && p <= 32u * (w1 - w0);
+}
+
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_decode(const __grid_constant__ Batch<DecArgs> B) {
+__global__ void __launch_bounds__(THREADS, dec_min_blocks(THREADS)) k_decode(const __grid_constant__ Batch<DecArgs> B) {
     const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
     const DecArgs& A = B.a[fld];
     const uint32_t bid = blockIdx.x - B.off[fld];
     DevParams* par = A.par;
-    const uint32_t* __restrict__ lut_g = A.lut_g;
-    const uint16_t* __restrict__ syms = A.syms;
     const uint64_t n = A.n;
     const uint32_t chunk = A.chunk;
     const uint64_t nchunks = A.nchunks;
     extern __shared__ __align__(16) uint32_t slut[];  // decode table, then the stream rings
     __shared__ uint32_t s_base[32];  // first index - first code of every length (mod 2^32)
-    __shared__ uint32_t s_short;     // every code has at most 16 bits
     __shared__ unsigned long long s_lje[33];
+    __shared__ uint32_t s_pairs;     // codes longer than kLutBits bits are rare
     __shared__ __align__(8) unsigned long long s_mbar;
     // constant fields have no stream: their residuals are all zero
     if (par->flags & (kFlagError | kFlagConstant)) return;
     const uint32_t words = par->d_words;
     const uint32_t* __restrict__ tab = reinterpret_cast<const uint32_t*>(A.blob + par->off_ct);
     const uint32_t* __restrict__ stream = reinterpret_cast<const uint32_t*>(A.blob + par->off_st);
+    // the chunk's first quads are in flight while the block sets up its table
+    const uint64_t c = (uint64_t)bid * THREADS + threadIdx.x;
+    const bool live = c < nchunks;
+    uint32_t w0 = 0u, w1 = 0u;
+    bool sane = false;
+    uint32_t* ring = slut + (1u << kLutBits) + 4u * threadIdx.x;
+    const uint32_t qend = (words + 3u) >> 2;  // quads in the 16-byte padded section
+    if (live) {
+        w0 = tab[c];
+        w1 = (c + 1 < nchunks) ? tab[c + 1] : words;
+        // (a chunk owns fewer than 2^22 words: 65536 codes of <= 27 bits)
+        sane = w0 <= w1 && w1 <= words && w1 - w0 < (1u << 22);
+        if (sane) {
+#pragma unroll
+            for (uint32_t r = 0; r < (uint32_t)kDecRing; r++) dec_issue<THREADS>(ring, stream, qend, (w0 >> 2) + r);
+        }
+    }
     if (threadIdx.x < 32) {
         const uint32_t l = threadIdx.x;
+        const uint32_t cl = par->d_count[l];
         s_base[l] = par->d_first_index[l] - par->d_first_code[l];
         // end of length l's codes, left-justified in 32 bits (2^32 once the code is complete)
-        s_lje[l] = l ? (unsigned long long)(par->d_first_code[l] + par->d_count[l]) << (32 - l) : 0ull;
-        const uint32_t used = __ballot_sync(0xffffffffu, l && par->d_count[l] > 0u);
-        if (l == 0) s_short = (used >> 17) == 0u;  // no code longer than 16 bits
+        s_lje[l] = l ? (unsigned long long)(par->d_first_code[l] + cl) << (32 - l) : 0ull;
+        float m = ldexpf((float)(cl * l), -(int)l);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+        if (l == 0) s_pairs = m < kDecPairBits;
     }
     if (threadIdx.x == 0) {
         s_lje[32] = ~0ull;
@@ -284,115 +444,29 @@ __global__ void __launch_bounds__(THREADS, 1280 / THREADS) k_decode(const __grid
     if (threadIdx.x == 0) {
         const uint32_t lut_bytes = (1u << kLutBits) * 4u;
         mbar_arrive_expect_tx(&s_mbar, lut_bytes);
-        bulk_g2s(slut, lut_g, lut_bytes, &s_mbar);
+        bulk_g2s(slut, A.lut_g, lut_bytes, &s_mbar);
     }
     if (!mbar_wait_bounded(&s_mbar, 0, A.spin_limit)) {
-        // never expected; record it, let the copy land (bounded), then leave
+        // never expected; record it, let the copies land (bounded), then leave
         set_error(par, FPSNR_ETIMEOUT);
         mbar_wait_bounded(&s_mbar, 0);
+        cp_async_wait<0>();
         return;
     }
-    const uint64_t c = (uint64_t)bid * THREADS + threadIdx.x;
-    if (c >= nchunks) return;
-    const uint64_t beg = c * chunk;
-    const uint32_t cnt = (uint32_t)(min(beg + chunk, n) - beg);
-    const uint32_t lmax = par->d_lmax;
-    const uint32_t w0 = tab[c];
-    const uint32_t w1 = (c + 1 < nchunks) ? tab[c + 1] : words;
-    if (w0 > w1 || w1 > words) {
+    if (!live) return;
+    if (!sane) {
         set_error(par, FPSNR_ECORRUPT);
         return;
     }
-    uint32_t hi = 0u, lo = 0u;  // window; bits past the valid ones are zero
-    uint32_t nb = 0u;           // valid bits in the window
-    uint32_t wi = w0;           // words appended so far
-    // The chunk's words arrive as aligned quads [4k, 4k + 4) copied by cp.async
-    // into this thread's ring of kDecRing quads in shared memory, kDecRing - 1
-    // quads ahead of the one being read (an asynchronous copy holds no register,
-    // so a refill never waits on a later quad).  Words past the chunk belong to
-    // the next chunk (or are zero past the section) and are never consumed by a
-    // well-formed stream.
-    uint32_t* ring = slut + (1u << kLutBits) + 4u * threadIdx.x;
-    const uint32_t qend = (words + 3u) >> 2;  // quads in the 16-byte padded section
-    uint32_t qk = w0 >> 2, ci = w0 & 3u;
-    auto issue = [&](uint32_t qi) {
-        if (qi < qend) cp_async16(ring + (qi & (kDecRing - 1)) * (4u * THREADS), stream + 4u * qi);
-        cp_async_commit();
-    };
-#pragma unroll
-    for (uint32_t r = 0; r < (uint32_t)kDecRing; r++) issue(qk + r);
-    cp_async_wait<kDecRing - 1>();
-    bool bad = false;
-    // two codes of at most 16 bits each fit the >= 32 valid bits a refill leaves
-    const bool short_codes = s_short != 0u;
-    auto refill = [&]() {
-        if (nb <= 32u) {
-            const uint32_t wd = ring[(qk & (kDecRing - 1)) * (4u * THREADS) + ci];
-            hi |= __funnelshift_rc(wd, 0u, nb);       // wd >> nb (0 when nb == 32)
-            lo = __funnelshift_lc(0u, wd, 32u - nb);  // wd << (32 - nb) (0 when nb == 0)
-            nb += 32u;
-            wi++;
-            if (++ci == 4u) {
-                // quad qk is used up: its slot takes quad qk + kDecRing, and quad
-                // qk + 1 must have landed
-                ci = 0u;
-                issue(qk + kDecRing);
-                qk++;
-                cp_async_wait<kDecRing - 1>();
-            }
-        }
-    };
-    auto dec = [&]() -> uint32_t {
-        const uint32_t e = slut[hi >> (32 - kLutBits)];
-        uint32_t l = e & 31u;
-        uint32_t sym = e >> 8;
-        if (e & kLutLen) {
-            // the symbol is not on the dependency chain of the next code's position
-            sym = __ldg(&syms[(s_base[l] + (hi >> (32 - l))) & 0xffffu]);
-        } else if (l == 0u) {
-            // a prefix shared by several lengths (or by no code): the first length
-            // whose canonical range ends above the window, by a fixed number of
-            // bisection steps over kLutBits + 1 .. lmax
-            uint32_t a = kLutBits + 1, b = lmax;
-            const bool none = (unsigned long long)hi >= s_lje[lmax];  // no code has this prefix
-#pragma unroll
-            for (int it = 0; it < 5; it++) {
-                if (a < b) {
-                    const uint32_t m = (a + b) >> 1;
-                    if ((unsigned long long)hi < s_lje[m]) b = m;
-                    else a = m + 1;
-                }
-            }
-            l = a;
-            sym = none ? 0u : (uint32_t)__ldg(&syms[(s_base[l] + (hi >> (32 - l))) & 0xffffu]);
-            bad |= none;
-        }
-        hi = __funnelshift_l(lo, hi, l);
-        lo <<= l;
-        nb -= l;
-        return sym;
-    };
-    uint16_t* __restrict__ dst = A.out + beg;
-    const uint32_t cnt8 = cnt & ~7u;
-    for (uint32_t i = 0; i < cnt8; i += 8) {
-        uint32_t s[8];
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            if (!short_codes || (k & 1) == 0) refill();  // warp-uniform condition
-            s[k] = dec();
-        }
-        *reinterpret_cast<uint4*>(dst + i) =
-            make_uint4(s[0] | (s[1] << 16), s[2] | (s[3] << 16), s[4] | (s[5] << 16), s[6] | (s[7] << 16));
-    }
-    for (uint32_t i = cnt8; i < cnt; i++) {
-        refill();
-        dst[i] = (uint16_t)dec();
-    }
+    const uint64_t beg = c * chunk;
+    const uint32_t cnt = (uint32_t)(min(beg + chunk, n) - beg);
+    const bool ok = s_pairs ? dec_chunk<THREADS, true>(ring, stream, qend, w0, w1, cnt, A.out + beg, slut, s_base,
+                                                        s_lje, A.syms, par->d_lmax)
+                            : dec_chunk<THREADS, false>(ring, stream, qend, w0, w1, cnt, A.out + beg, slut, s_base,
+                                                         s_lje, A.syms, par->d_lmax);
     // copies still in flight land before the block's shared memory is released
     cp_async_wait<0>();
-    // bits consumed = appended - still valid; the chunk owns (w1 - w0) words
-    const uint64_t used = 32ull * (wi - w0) - nb;
-    if (bad || used > 32ull * (w1 - w0)) set_error(par, FPSNR_ECORRUPT);
+    if (!ok) set_error(par, FPSNR_ECORRUPT);
 }
 
 // Residual of point `idx` from its symbol: code - R, or for symbol 0 (an
@@ -1562,9 +1636,8 @@ int launch_decompress_batch(fpsnr_plan_s* const* P, const void* const* d_blob,
     }
     // decode every field into its plan's symbol buffer
     {
-        // 128-thread blocks spread every field's chunks over all SMs: a field with
-        // long codes (slow chunks) then shares no SM's issue slots with itself more
-        // than the others do
+        // 128-thread blocks (a 16 KB table and 128-byte rings: six per SM) start
+        // and retire often enough that a batch's last wave stays short
         const int T = P[0]->dec_threads ? P[0]->dec_threads : 128;
         Batch<DecArgs> b;
         b.count = 0;
