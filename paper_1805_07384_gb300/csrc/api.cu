@@ -329,7 +329,7 @@ int plan_layout(fpsnr_plan_s** out, int ndim, const uint64_t* dims, double targe
     p->nchunks = cdiv(n, (uint64_t)o.chunk);
     p->nwords = cdiv(n, 32);
     p->nbmblk = cdiv(p->nwords, 1024);
-    p->enc_tiles = cdiv(p->nchunks, 8);
+    p->enc_tiles = cdiv(p->nchunks, fp::kEncTile);
     p->enc_slot_words = (uint32_t)cdiv((uint64_t)p->chunk * (uint64_t)p->lmax, 32);
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {

@@ -26,6 +26,7 @@ constexpr int kMaxLmax = 27;
 constexpr int kFineBins = 4096;  // fine histogram of the bound refinement (psnr_mode 1)
 constexpr uint32_t kZrSeg = 1024;          // lossless container: bytes per segment
 constexpr uint32_t kZrMagic = 0x315A5046u;  // bytes "FPZ1"
+constexpr int kEncTile = 32;        // chunks per encoder tile
 constexpr int kLutBits = 12;        // decode look-up table width
 constexpr uint32_t kLutLen = 0x20u;  // table entry flag: length only, symbol by canonical index
 constexpr uint32_t kLutSlow = 0x40u; // table entry flag: not a whole code of <= kLutBits bits

@@ -826,7 +826,9 @@ __global__ void __launch_bounds__(1024) k_rank_popc(const __grid_constant__ Batc
 
 static __device__ __forceinline__ uint64_t pad16(uint64_t b) { return (b + 15u) & ~(uint64_t)15u; }
 
-constexpr int kEncWarps = 8;  // chunks per tile, one warp each
+constexpr int kEncWarps = 8;                  // warps of an encoder block
+constexpr int kEncCpw = kEncTile / kEncWarps;  // consecutive chunks each warp packs
+static_assert(kEncTile <= 32 && kEncTile % kEncWarps == 0, "a tile's chunk prefix is one warp scan");
 constexpr int kPieceWords = (256 * kMaxLmax + 31) / 32 + 2;
 
 struct EncArgs {
@@ -845,18 +847,20 @@ struct EncArgs {
 };
 
 // Encoder, three launches with no inter-block waiting:
-//   k_enc_pack  one warp per chunk: MSB-first packing into the chunk's own
+//   k_enc_pack  one block per tile of kEncTile chunks, kEncCpw consecutive
+//               chunks per warp: MSB-first packing into each chunk's own
 //               scratch slot (chunks start on word boundaries, so a chunk's
 //               words do not depend on where it lands): pieces of 256 symbols
-//               (8 per lane) are OR-ed into a per-warp shared-memory word
-//               buffer, full words go out coalesced and the partial last word
-//               carries into the next piece.  The chunk's word count and its
-//               tile's (kEncWarps chunks) total are recorded.
+//               (8 per lane, loaded one piece ahead) are OR-ed into a per-warp
+//               shared-memory word buffer, full words go out coalesced and the
+//               partial last word carries into the next piece.  The chunk's
+//               word count and its tile's total are recorded.
 //   k_enc_scan  one block per field: exclusive prefix of the tile totals, the
 //               section layout and the capacity check
-//   k_enc_copy  one warp per chunk: word offset (tile prefix + in-tile prefix),
-//               chunk table entry, and the chunk's words copied from its slot
-//               into the stream.  Every write is checked against the output
+//   k_enc_copy  one block per tile: word offsets (tile prefix + in-tile
+//               prefix), chunk table entries, and the words of each warp's
+//               kEncCpw chunks copied from their slots into the stream by
+//               that warp.  Every write is checked against the output
 //               capacity.
 // The codes are read and looked up once; the packed stream (a fraction of
 // their bytes) is written twice and read once.
@@ -868,21 +872,36 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_enc_pack(const __grid_consta
     __shared__ uint32_t sbuf[kEncWarps][kPieceWords];
     __shared__ uint32_t s_words[kEncWarps];
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-    const uint64_t c = (uint64_t)t * kEncWarps + wib;
-    uint32_t wpos = 0;  // words of the chunk written so far
-    if (c < a.nchunks) {
+    // the warp's chunks: kEncCpw consecutive ones of the tile
+    const uint64_t cw0 = (uint64_t)t * kEncTile + (uint64_t)wib * kEncCpw;
+    const uint64_t cw1 = min(cw0 + kEncCpw, a.nchunks);
+    uint32_t* buf = sbuf[wib];
+    uint32_t warp_words = 0;
+    // The codes of a piece are loaded one piece ahead (16 bytes a lane), so the
+    // load of the next piece is in flight while this one is packed.
+    auto chunk_end = [&](uint64_t c) { return min((c + 1) * a.chunk, a.n); };
+    uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
+    auto prefetch = [&](uint64_t c, uint64_t pb) {
+        const uint64_t i = pb + 8u * lane;
+        if (c < cw1 && i + 8 <= chunk_end(c)) nxt = *reinterpret_cast<const uint4*>(a.codes + i);
+    };
+    if (cw0 < cw1) prefetch(cw0, cw0 * a.chunk);
+    for (uint64_t c = cw0; c < cw1; c++) {
         const uint64_t beg = c * a.chunk;
-        const uint64_t end = min(beg + a.chunk, a.n);
+        const uint64_t end = chunk_end(c);
         uint32_t* dst = a.scratch + c * a.slot_words;
-        uint32_t* buf = sbuf[wib];
         uint32_t carry = 0;  // partial word (bits from previous pieces)
         uint32_t cbits = 0;  // valid bits in carry (< 32)
+        uint32_t wpos = 0;   // words of the chunk written so far
         for (uint64_t pb = beg; pb < end; pb += 256u) {
+            const uint4 v = nxt;
+            // the next piece: further in this chunk, else the warp's next chunk
+            if (pb + 256u < end) prefetch(c, pb + 256u);
+            else prefetch(c + 1, (c + 1) * a.chunk);
             uint32_t cw[8], cl[8];
             uint32_t mybits = 0;
             const uint64_t i = pb + 8u * lane;
             if (i + 8 <= end) {
-                const uint4 v = *reinterpret_cast<const uint4*>(a.codes + i);
                 const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
@@ -948,8 +967,9 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_enc_pack(const __grid_consta
             wpos++;
         }
         if (lane == 0) a.chunk_words[c] = wpos;
+        warp_words += wpos;
     }
-    if (lane == 0) s_words[wib] = wpos;
+    if (lane == 0) s_words[wib] = warp_words;
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t sum = 0;
@@ -998,7 +1018,7 @@ __global__ void __launch_bounds__(1024) k_enc_scan(const __grid_constant__ Batch
 
 // One block per tile: the word offsets of the tile's chunks (tile prefix plus
 // the prefix of their word counts, in shared memory), the chunk table, then
-// every word of the tile's chunks copied by its own thread (the words of a
+// the words of every warp's kEncCpw chunks copied by that warp (the words of a
 // tile are contiguous in the stream).
 __global__ void __launch_bounds__(kEncWarps * 32) k_enc_copy(const __grid_constant__ Batch<EncArgs> B) {
     const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
@@ -1006,9 +1026,9 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_enc_copy(const __grid_consta
     const uint32_t t = blockIdx.x - B.off[fld];
     DevParams* par = a.par;
     if (par->flags & (kFlagConstant | kFlagError)) return;  // uniform over the block
-    __shared__ uint32_t pre[kEncWarps + 1];
-    const uint64_t c0 = (uint64_t)t * kEncWarps;
-    const uint32_t nch = (uint32_t)min((uint64_t)kEncWarps, a.nchunks - c0);
+    __shared__ uint32_t pre[kEncTile + 1];
+    const uint64_t c0 = (uint64_t)t * kEncTile;
+    const uint32_t nch = (uint32_t)min((uint64_t)kEncTile, a.nchunks - c0);
     const uint64_t cap = par->cap;
     const uint64_t off_ct = par->off_ct;
     const uint64_t off_st = par->off_st;
@@ -1018,11 +1038,12 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_enc_copy(const __grid_consta
         const uint32_t w = lane < nch ? a.chunk_words[c0 + lane] : 0u;
         uint32_t incl = w;
 #pragma unroll
-        for (int o = 1; o < 16; o <<= 1) {  // inclusive prefix over lanes 0..15
+        for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= (uint32_t)o) incl += y;
         }
-        if (lane <= (uint32_t)kEncWarps) pre[lane] = incl - w;  // pre[nch..] = the tile's total
+        if (lane < (uint32_t)kEncTile) pre[lane] = incl - w;  // pre[nch..] = the tile's total
+        if (lane == 31) pre[kEncTile] = incl;
         if (lane < nch && off_ct + 4ull * (c0 + lane + 1) <= cap)
             reinterpret_cast<uint32_t*>(a.out + off_ct)[c0 + lane] = tile_off + incl - w;
     }
@@ -1032,10 +1053,16 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_enc_copy(const __grid_consta
     // words that fit the output (the layout already flagged a short buffer)
     const uint64_t room = off_st + 4ull * tile_off <= cap ? (cap - off_st - 4ull * tile_off) / 4ull : 0ull;
     const uint32_t lim = (uint32_t)min((uint64_t)total, room);
-    for (uint32_t w = threadIdx.x; w < lim; w += blockDim.x) {
-        uint32_t k = 0;  // the chunk holding word w: the last k with pre[k] <= w
+    // each warp copies the words of the kEncCpw chunks its pack warp packed
+    // (contiguous in the stream)
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t k0 = min((threadIdx.x >> 5) * (uint32_t)kEncCpw, nch);
+    const uint32_t k1 = min(k0 + (uint32_t)kEncCpw, nch);
+    const uint32_t wend = min(pre[k1], lim);
+    for (uint32_t w = pre[k0] + lane; w < wend; w += 32) {
+        uint32_t k = k0;  // the chunk holding word w: the last k with pre[k] <= w
 #pragma unroll
-        for (int i = 1; i < kEncWarps; i++) k += ((uint32_t)i < nch && pre[i] <= w) ? 1u : 0u;
+        for (int i = 1; i < kEncCpw; i++) k += (k0 + i < k1 && pre[k0 + i] <= w) ? 1u : 0u;
         stream[w] = __ldcs(a.scratch + (c0 + k) * a.slot_words + (w - pre[k]));
     }
 }
@@ -1377,7 +1404,7 @@ int launch_compress_batch(fpsnr_plan_s* const* P, const float* const* d_in, void
             e.n = p->n;
             e.chunk = (uint32_t)p->chunk;
             e.nchunks = p->nchunks;
-            e.ntiles = (uint32_t)((p->nchunks + kEncWarps - 1) / kEncWarps);
+            e.ntiles = (uint32_t)((p->nchunks + kEncTile - 1) / kEncTile);
             e.slot_words = p->enc_slot_words;
             e.scratch = w.enc_scratch;
             e.chunk_words = w.chunk_off;
