@@ -931,11 +931,65 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_enc_pack(const __grid_consta
             __syncwarp();
             if (lane == 0) buf[0] = carry;
             __syncwarp();
-            // the lane's bits start at bit bp of buf: they are assembled in a
-            // 64-bit register (left-aligned, after bp % 32 bits of the word
-            // that belong to earlier lanes) and OR-ed in a word at a time
-            {
-                const uint32_t bp = cbits + incl - mybits;  // bit position in buf
+            // the lane's bits start at bit bp of buf
+            const uint32_t bp = cbits + incl - mybits;  // bit position in buf
+            if (__all_sync(0xffffffffu, mybits <= 64u)) {
+                // every lane's codes fit 64 bits: concatenated in two registers by
+                // funnel shifts, left-aligned, then OR-ed into the (at most three)
+                // words they cover
+                uint32_t ah = 0u, al = 0u;
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    ah = __funnelshift_l(al, ah, cl[k]);  // cl <= 27
+                    al = (al << cl[k]) | cw[k];            // cw < 2^cl
+                }
+                if (mybits) {
+                    uint32_t hi, lo;
+                    if (mybits <= 32u) {
+                        hi = al << (32u - mybits);
+                        lo = 0u;
+                    } else {
+                        hi = __funnelshift_l(al, ah, 64u - mybits);
+                        lo = al << (64u - mybits);
+                    }
+                    const uint32_t o = bp & 31u, w = bp >> 5;
+                    const uint32_t nwd = (o + mybits + 31u) >> 5;  // words covered: 1..3
+                    atomicOr(&buf[w], hi >> o);
+                    if (nwd > 1u) atomicOr(&buf[w + 1], __funnelshift_r(lo, hi, o));
+                    if (nwd > 2u) atomicOr(&buf[w + 2], lo << (32u - o));  // o > 0 here
+                }
+            } else if (mybits <= 128u) {
+                // up to 128 bits: the same in four registers, left-aligned by a
+                // word shift and a bit shift, then OR-ed into up to five words
+                uint32_t a3 = 0u, a2 = 0u, a1 = 0u, a0 = 0u;
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const uint32_t l = cl[k];
+                    a3 = __funnelshift_l(a2, a3, l);
+                    a2 = __funnelshift_l(a1, a2, l);
+                    a1 = __funnelshift_l(a0, a1, l);
+                    a0 = (a0 << l) | cw[k];
+                }
+                if (mybits) {
+                    const uint32_t sh = 128u - mybits, q = sh >> 5, r = sh & 31u;
+                    const uint32_t b3 = q == 0u ? a3 : (q == 1u ? a2 : (q == 2u ? a1 : a0));
+                    const uint32_t b2 = q == 0u ? a2 : (q == 1u ? a1 : (q == 2u ? a0 : 0u));
+                    const uint32_t b1 = q == 0u ? a1 : (q == 1u ? a0 : 0u);
+                    const uint32_t b0 = q == 0u ? a0 : 0u;
+                    const uint32_t v3 = __funnelshift_l(b2, b3, r), v2 = __funnelshift_l(b1, b2, r);
+                    const uint32_t v1 = __funnelshift_l(b0, b1, r), v0 = b0 << r;
+                    const uint32_t o = bp & 31u, w = bp >> 5;
+                    const uint32_t nwd = (o + mybits + 31u) >> 5;  // words covered: 1..5
+                    atomicOr(&buf[w], v3 >> o);
+                    if (nwd > 1u) atomicOr(&buf[w + 1], __funnelshift_r(v2, v3, o));
+                    if (nwd > 2u) atomicOr(&buf[w + 2], __funnelshift_r(v1, v2, o));
+                    if (nwd > 3u) atomicOr(&buf[w + 3], __funnelshift_r(v0, v1, o));
+                    if (nwd > 4u) atomicOr(&buf[w + 4], v0 << (32u - o));  // o > 0 here
+                }
+            } else {
+                // the codes are assembled in a 64-bit register (left-aligned,
+                // after bp % 32 bits of the word that belong to earlier lanes)
+                // and OR-ed in a word at a time
                 uint32_t w = bp >> 5, nbit = bp & 31u;
                 unsigned long long acc = 0ull;
 #pragma unroll
