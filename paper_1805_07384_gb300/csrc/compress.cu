@@ -487,6 +487,8 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * (TY + (MODE == 3 ? 1 : 0)),
     const float2 ssc2 = make_float2(ssc, ssc);
     // -x' 2^-k = fma(q, -s 2^-k, -xmin 2^-k) rounds to exactly the scaled, negated reconstruction
     const float ns = __fmul_rn(-s, ssc), nxmin = __fmul_rn(-xmin, ssc), thr = __fmul_rn(thr0, ssc);
+    const float2 ns2 = make_float2(ns, ns), nxmin2s = make_float2(nxmin, nxmin);
+    const float2 nxmin2 = make_float2(-xmin, -xmin), inv2 = make_float2(inv, inv);  // unscaled, for prequantization
     const bool off = (flags & kFlagLatticeOff) != 0;
     const int R = a.radius;
 
@@ -598,10 +600,17 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * (TY + (MODE == 3 ? 1 : 0)),
         const uint32_t lim = row_limit(rowbase);
         bool in[NP];
         int32_t q[NP];
+        // prequantization two points at a time: fl(fl(x - xmin) * inv) in each
+        // lane (an add feeding a product: nothing to contract), then rounded
+        // to the nearest integer
 #pragma unroll
-        for (int i = 0; i < NP; i++) {
-            in[i] = FULL || (yin && (xb + 128u * (i / 4) + (i % 4) < lim));
-            q[i] = in[i] ? prequant(cur.v[i], xmin, inv, off) : 0;
+        for (int i = 0; i < NP; i += 2) {
+            const float2 pv = __fmul2_rn(__fadd2_rn(make_float2(cur.v[i], cur.v[i + 1]), nxmin2), inv2);
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                in[i + k] = FULL || (yin && (xb + 128u * ((i + k) / 4) + ((i + k) % 4) < lim));
+                q[i + k] = (in[i + k] && !off) ? __float2int_rn(k ? pv.y : pv.x) : 0;
+            }
         }
         int32_t L1[NP];
         row_diff(q, cur.hl ? prequant(cur.l, xmin, inv, off) : 0, L1);
@@ -680,8 +689,8 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * (TY + (MODE == 3 ? 1 : 0)),
             for (int i = 0; i < NP; i += 2) {
                 const float2 x2 = make_float2(cur.v[i], cur.v[i + 1]);
                 const float2 xv = SCALED ? __fmul2_rn(x2, ssc2) : x2;
-                const float2 nxr = make_float2(__fmaf_rn(__int2float_rn(q[i]), ns, nxmin),
-                                               __fmaf_rn(__int2float_rn(q[i + 1]), ns, nxmin));
+                const float2 nxr = __ffma2_rn(make_float2(__int2float_rn(q[i]), __int2float_rn(q[i + 1])), ns2,
+                                              nxmin2s);
                 const float2 df = __fadd2_rn(xv, nxr);  // fl(x - x') per point
                 vb[i] = in[i] && !(fabsf(df.x) <= thr);
                 vb[i + 1] = in[i + 1] && !(fabsf(df.y) <= thr);
