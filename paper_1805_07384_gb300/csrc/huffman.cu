@@ -20,10 +20,13 @@
 // queue only stores weights.  Depths follow from one pass over the rounds in
 // reverse (a parent is always created in a later round than its children).
 //
-// Sorting: used symbols are collected in ascending symbol order; a stable sort
-// by count then gives the (count, symbol) leaf order, and a stable sort by
-// code length gives the canonical order.  Small alphabets use a rank sort,
-// larger ones a stable LSD radix sort with one warp per contiguous segment.
+// Sorting: used symbols are collected in ascending symbol order (each warp a
+// contiguous segment of the histogram); a stable sort by count then gives the
+// (count, symbol) leaf order (a rank sort for small alphabets, else a stable
+// LSD radix sort with one warp per contiguous segment).  The canonical order
+// (ascending length, then symbol) needs no sort: each warp counts its segment
+// of the symbol-ordered list per length, one scan gives its first canonical
+// index per length, and equal lengths are ranked by lane.
 #include "common.cuh"
 
 namespace fp {
@@ -204,9 +207,11 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(const __grid_constant__ Ba
     __shared__ double sdbl[32];
     __shared__ uint32_t s_m, s_a, s_err, s_max;
     __shared__ uint32_t s_cnt[32], s_fc[32], s_fi[32];
+    __shared__ uint32_t s_wn[32], s_wb[32], s_ntot;  // symbol collection: per-warp counts, offsets
+    __shared__ uint32_t s_wc[32][33];                // canonical order: [warp][length] counts, then offsets
     __shared__ uint32_t s_round[kMaxRounds + 2];
     DevParams* par = a.par;
-    const uint32_t tid = threadIdx.x;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;  // 32 warps
     const uint32_t flags = par->flags;
 
     // ---- squared-error total, fixed order ----
@@ -243,32 +248,54 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(const __grid_constant__ Ba
     if (tid == 0 && c0 > 0) a.list[0] = (unsigned long long)c0 << 16;
     const uint32_t lo = par->sym_lo, hi = min(par->sym_hi, a.nsym - 1);
     if (lo <= hi) {
-        // 4 consecutive bins per thread per pass (coalesced); the next pass's
-        // bins are loaded before this pass's scan
-        auto load4 = [&](uint32_t s0, uint32_t (&c)[4]) {
+        // each warp collects a contiguous segment of the bins, a multiple of 32
+        // of them: coalesced loads, ranks within the warp by ballot, one scan of
+        // the warps' counts; the second pass reloads the bins (L1 / L2)
+        const uint32_t S = ((hi - lo + 1u + 31u) / 32u + 31u) & ~31u;
+        const uint32_t wb0 = lo + wid * S;  // the warp's first bin (may lie past hi)
+        auto load8 = [&](uint32_t k, uint32_t (&c)[8]) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) c[k] = (s0 + k <= hi) ? a.hist[s0 + k] : 0u;
-        };
-        uint32_t cn[4];
-        load4(lo + 4 * tid, cn);
-        for (uint32_t base = lo; base <= hi; base += 4 * blockDim.x) {
-            const uint32_t s0 = base + 4 * tid;
-            uint32_t c[4], cnt = 0;
-#pragma unroll
-            for (int k = 0; k < 4; k++) c[k] = cn[k];
-            if (base + 4 * blockDim.x <= hi) load4(s0 + 4 * blockDim.x, cn);
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                cnt += c[k] > 0;
-                maxc = max(maxc, c[k]);
+            for (int u = 0; u < 8; u++) {
+                const uint32_t i = wb0 + k + 32u * u + lane;
+                c[u] = (k + 32u * u < S && i <= hi) ? a.hist[i] : 0u;
             }
-            uint32_t tot;
-            uint32_t pos = n + block_excl_scan(cnt, sh, &tot);
+        };
+        uint32_t wcnt = 0;
+        for (uint32_t k = 0; k < S; k += 256u) {
+            uint32_t c[8];
+            load8(k, c);
 #pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (c[k]) a.list[pos++] = ((unsigned long long)c[k] << 16) | (s0 + k);
-            n += tot;
+            for (int u = 0; u < 8; u++) {
+                wcnt += __popc(__ballot_sync(0xffffffffu, c[u] > 0u));
+                maxc = max(maxc, c[u]);
+            }
         }
+        if (lane == 0) s_wn[wid] = wcnt;
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t v = s_wn[lane];
+            uint32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (uint32_t)o) incl += y;
+            }
+            s_wb[lane] = incl - v;
+            if (lane == 31) s_ntot = incl;
+        }
+        __syncthreads();
+        uint32_t pos = n + s_wb[wid];
+        for (uint32_t k = 0; k < S; k += 256u) {
+            uint32_t c[8];
+            load8(k, c);
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const uint32_t m = __ballot_sync(0xffffffffu, c[u] > 0u);
+                if (c[u]) a.list[pos + __popc(m & lanemask_lt())] = ((unsigned long long)c[u] << 16) | (wb0 + k + 32u * u + lane);
+                pos += __popc(m);
+            }
+        }
+        n += s_ntot;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, o));
@@ -437,32 +464,51 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(const __grid_constant__ Ba
     }
     __syncthreads();
 
-    // ---- canonical order: stable sort of the symbol-ordered list by length ----
-    for (uint32_t i0 = tid; i0 < n; i0 += 4 * blockDim.x) {
-        uint32_t ss[4], ll[4];
+    // ---- canonical order: ascending (length, symbol) ----
+    // The list holds the used symbols in ascending order.  Each warp takes a
+    // contiguous segment of it and counts its symbols per code length; a scan
+    // over (length, warp) gives every warp its first canonical index for each
+    // length, and the warp walks its segment again, ranking equal lengths by
+    // lane, and writes the encoder table and the codebook.
+    const uint32_t S = (n + 31u) / 32u;  // list entries per warp
+    const uint32_t e0 = min(n, wid * S), e1 = min(n, e0 + S);
+    s_wc[wid][lane] = 0u;
+    __syncwarp();
+    // a warp's entries 256 at a time: the symbols, then their lengths, loaded
+    // together before they are ranked
+    auto load8 = [&](uint32_t i0, uint32_t (&sym)[8], uint32_t (&len)[8]) {
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const uint32_t i = i0 + u * blockDim.x;
-            ss[u] = i < n ? (uint32_t)(a.list[i] & 0xffffu) : 0u;
+        for (int u = 0; u < 8; u++) {
+            const uint32_t i = i0 + 32u * u + lane;
+            sym[u] = i < e1 ? (uint32_t)(a.list[i] & 0xffffu) : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) ll[u] = i0 + u * blockDim.x < n ? a.len_sym[ss[u]] : 0u;
+        for (int u = 0; u < 8; u++) len[u] = i0 + 32u * u + lane < e1 ? (uint32_t)a.len_sym[sym[u]] : 0u;
+    };
+    for (uint32_t i0 = e0; i0 < e1; i0 += 256u) {
+        uint32_t sym[8], len[8];
+        load8(i0, sym, len);
 #pragma unroll
-        for (int u = 0; u < 4; u++)
-            if (i0 + u * blockDim.x < n) a.buf2[i0 + u * blockDim.x] = ((unsigned long long)ll[u] << 16) | ss[u];
+        for (int u = 0; u < 8; u++) {
+            const bool v = i0 + 32u * u + lane < e1;
+            const uint32_t l = len[u];  // 1..lmax for a used symbol
+            const uint32_t peers = __match_any_sync(0xffffffffu, l);
+            if (v && lane == (uint32_t)(__ffs(peers) - 1)) s_wc[wid][l] += __popc(peers);
+            __syncwarp();
+        }
     }
-    if (tid < 32) s_cnt[tid] = 0;
     __syncthreads();
-    if (n <= kRankMax) rank_sort(a.buf2, a.buf1, n, kbuf);
-    else radix_pass(a.buf2, a.buf1, n, 16, 31u, whist, sh);
-    const unsigned long long* canon = a.buf1;
-    for (uint32_t i0 = tid; i0 < n; i0 += 4 * blockDim.x) {
-        unsigned long long kk[4];
+    uint32_t wex;  // thread (length wid, warp lane): that warp's symbols of this length before it
+    {
+        const uint32_t v = s_wc[lane][wid];
+        uint32_t incl = v;
 #pragma unroll
-        for (int u = 0; u < 4; u++) kk[u] = i0 + u * blockDim.x < n ? canon[i0 + u * blockDim.x] : 0ull;
-#pragma unroll
-        for (int u = 0; u < 4; u++)
-            if (i0 + u * blockDim.x < n) atomicAdd(&s_cnt[(uint32_t)(kk[u] >> 16)], 1u);
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        wex = incl - v;
+        if (lane == 31) s_cnt[wid] = incl;
     }
     __syncthreads();
     if (tid == 0) {
@@ -477,21 +523,26 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(const __grid_constant__ Ba
         par->off_ct = kHeaderBytes + ((4ull * n + 15u) & ~15ull);
     }
     __syncthreads();
+    if (wid >= 1u && wid <= (uint32_t)kMaxLmax) s_wc[lane][wid] = s_fi[wid] + wex;
+    __syncthreads();
     const bool write_cb = kHeaderBytes + 4ull * n <= par->cap;
     uint32_t* cb = reinterpret_cast<uint32_t*>(a.out + kHeaderBytes);
-    for (uint32_t i0 = tid; i0 < n; i0 += 4 * blockDim.x) {
-        uint32_t ee[4];
+    for (uint32_t i0 = e0; i0 < e1; i0 += 256u) {
+        uint32_t sym[8], len[8];
+        load8(i0, sym, len);
 #pragma unroll
-        for (int u = 0; u < 4; u++) ee[u] = i0 + u * blockDim.x < n ? (uint32_t)canon[i0 + u * blockDim.x] : 0u;
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const uint32_t i = i0 + u * blockDim.x;
-            if (i < n) {
-                const uint32_t e = ee[u];
-                const uint32_t l = e >> 16, s = e & 0xffffu;
-                a.enc[s] = ((s_fc[l] + (i - s_fi[l])) << 5) | l;
-                if (write_cb) cb[i] = e;
+        for (int u = 0; u < 8; u++) {
+            const bool v = i0 + 32u * u + lane < e1;
+            const uint32_t l = len[u];
+            const uint32_t peers = __match_any_sync(0xffffffffu, l);
+            if (v) {
+                const uint32_t idx = s_wc[wid][l] + __popc(peers & lanemask_lt());  // canonical index
+                a.enc[sym[u]] = ((s_fc[l] + (idx - s_fi[l])) << 5) | l;
+                if (write_cb) cb[idx] = (l << 16) | sym[u];
             }
+            __syncwarp();
+            if (v && lane == (uint32_t)(__ffs(peers) - 1)) s_wc[wid][l] += __popc(peers);
+            __syncwarp();
         }
     }
 }
