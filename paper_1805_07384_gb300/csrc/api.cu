@@ -90,7 +90,8 @@ bool pq_geometry(fpsnr_plan_s* p, int tx) {
         g.zs = std::max(32, 16384 / g.tx);
         g.vx = (uint32_t)nx; g.vy = 1; g.vz = (uint32_t)rows;
     } else {
-        g.mode = 3; g.tx = 128; g.ty = 8; g.zs = 16;
+        // slabs of 64 planes: a block re-derives one plane above its slab
+        g.mode = 3; g.tx = 128; g.ty = 8; g.zs = 64;
         g.vx = (uint32_t)d[0]; g.vy = (uint32_t)d[1]; g.vz = (uint32_t)d[2];
     }
     g.vec = (g.vx % 4) == 0;

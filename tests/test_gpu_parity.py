@@ -328,6 +328,36 @@ def test_corrupt_blobs(env):
     assert status_of(good, nbytes) == 0
 
 
+@pytest.mark.parametrize("psnr", [30.0, 110.0])
+def test_decoder_chunk_overrun_is_corrupt(env, psnr):
+    """A chunk whose table entry leaves it no stream words must be reported as
+    corrupt (its codes would read past its words), in both decoding modes: at
+    30 dB the codes are short and go in pairs, at 110 dB most are longer than
+    the 12-bit table and go one by one."""
+    torch, fpsnr, _ = env
+    x = field_for((300, 500), 8)
+    plan, xt, out, nbytes, st, blob = run_gpu(env, x, psnr)
+    assert st["status"] == 0
+    bits = 8.0 * nbytes / x.size
+    assert (bits < 3.0) if psnr == 30.0 else (bits > 9.0), bits
+    good = out[:nbytes].clone()
+    _, status = plan.decompress(good, nbytes)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    off_ct = 128 + ((4 * st["n_sym"] + 15) & ~15)
+    tab = np.frombuffer(blob[off_ct:off_ct + 4 * 64], np.uint32)
+    for c in (0, 17, 40):  # chunk c + 1 starts where chunk c starts: c owns no words
+        b = good.clone()
+        b[off_ct + 4 * (c + 1):off_ct + 4 * (c + 2)] = torch.from_numpy(
+            np.array([tab[c]], np.uint32).view(np.uint8).copy()).cuda()
+        _, status = plan.decompress(b, nbytes)
+        torch.cuda.synchronize()
+        assert int(status.item()) == fpsnr.FPSNR_ECORRUPT, c
+    _, status = plan.decompress(good, nbytes)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+
+
 def test_corrupt_outlier_list(env):
     """The outlier list is checked against the decoded symbols: an index past
     the field, two entries out of order, or an entry moved off its symbol 0
