@@ -87,7 +87,7 @@ bool pq_geometry(fpsnr_plan_s* p, int tx) {
         const uint64_t nx = d[0], rows = nx ? n / nx : 0;
         g.mode = 2; g.ty = 1;
         g.tx = tx ? tx : (nx <= 128 ? 128 : (nx <= 256 ? 256 : (nx <= 512 ? 512 : 1024)));
-        g.zs = std::max(32, 16384 / g.tx);
+        g.zs = std::max(64, 32768 / g.tx);  // rows per block: one warm-up row each
         g.vx = (uint32_t)nx; g.vy = 1; g.vz = (uint32_t)rows;
     } else {
         // slabs of 64 planes: a block re-derives one plane above its slab
