@@ -1263,6 +1263,17 @@ __global__ void __launch_bounds__(512) k_vol_sum(const __grid_constant__ Batch<V
 // count values at p, p + stride, ... replaced by their exclusive prefix
 __device__ __forceinline__ void excl_prefix_strided(uint32_t* p, uint32_t count, uint64_t stride) {
     uint32_t acc = 0u, i = 0;
+    // 16 loads in flight at a time (the sums are latency-bound, not bandwidth-bound)
+    for (; i + 16 <= count; i += 16) {
+        uint32_t v[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++) v[k] = p[(uint64_t)(i + k) * stride];
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            p[(uint64_t)(i + k) * stride] = acc;
+            acc += v[k];
+        }
+    }
     for (; i + 8 <= count; i += 8) {
         uint32_t v[8];
 #pragma unroll
