@@ -71,7 +71,7 @@ struct Workspace {
     uint2* stage_out;       // [n] (idx, delta) in discovery order
     uint2* stage_vb;        // [n] (idx, float bits) in discovery order
     uint32_t* bm;           // [2][nwords] membership bitmaps (kept all-zero between calls)
-    uint32_t* wpre;         // [2][nwords] in-block exclusive popcount prefix
+    uint32_t* wpre;         // [2][nwords] in-block exclusive popcount prefix (words with a set bit only)
     uint32_t* bpre;         // [2][nbmblk] block totals, then exclusive prefix
     double* sse_part;       // [n_pq_blocks]
     float* range_part;      // [3][n_range_blocks]

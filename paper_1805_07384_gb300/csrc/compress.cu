@@ -825,7 +825,8 @@ __global__ void __launch_bounds__(1024) k_rank_popc(const __grid_constant__ Batc
     uint32_t c = w < nwords ? __popc(bm[list * nwords + w]) : 0u;
     uint32_t total;
     uint32_t ex = block_excl_scan(c, sh, &total);
-    if (w < nwords) wpre[list * nwords + w] = ex;
+    // only words holding a set bit are ever looked up (k_emit): the others stay unwritten
+    if (w < nwords && c) wpre[list * nwords + w] = ex;
     if (threadIdx.x == 0) bpre[list * nbmblk + blk] = total;
 }
 
