@@ -552,9 +552,12 @@ def measured_traffic(workload, stage, points):
 
 # ncu --csv logs -> per-launch figures (profiles/ summaries and traffic.json)
 
-# files every kernel's binary depends on besides its own source
+# files every kernel's traffic depends on besides its own source: the shared
+# device header, the build script with the compiler flags, and the plan set-up
+# that chooses tile shapes and slab depths
 _TRAFFIC_DEPS = (os.path.join("paper_1805_07384_gb300", "csrc", "common.cuh"),
-                 os.path.join("paper_1805_07384_gb300", "build.py"))
+                 os.path.join("paper_1805_07384_gb300", "build.py"),
+                 os.path.join("paper_1805_07384_gb300", "csrc", "api.cu"))
 _UNITS = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9,
           "ns": 1e-3, "nsecond": 1e-3, "us": 1, "usecond": 1, "ms": 1e3, "msecond": 1e3}
 # benchmark stages by kernel-name prefix, with the source file that holds them
