@@ -805,7 +805,10 @@ struct RankArgs {
     uint32_t nbmblk;
 };
 
-// 2 * nbmblk blocks per field: list (outliers, verbatims) x bitmap block
+// 2 * ceil(nbmblk / 4) blocks per field: list (outliers, verbatims) x four
+// bitmap blocks of 1024 words, 4 consecutive words per thread; each bitmap
+// block's words get their exclusive popcount prefix within that bitmap block,
+// and the bitmap block its total.
 __global__ void __launch_bounds__(1024) k_rank_popc(const __grid_constant__ Batch<RankArgs> B) {
     const uint32_t fld = batch_field(B.off, B.count, blockIdx.x);
     const RankArgs& A = B.a[fld];
@@ -816,18 +819,36 @@ __global__ void __launch_bounds__(1024) k_rank_popc(const __grid_constant__ Batc
     uint32_t* bpre = A.bpre;
     const uint64_t nwords = A.nwords;
     const uint32_t nbmblk = A.nbmblk;
-    const uint32_t list = bid / nbmblk;
-    const uint32_t blk = bid % nbmblk;
+    const uint32_t nb4 = (nbmblk + 3u) / 4u;
+    const uint32_t list = bid / nb4;
+    const uint32_t blk4 = bid % nb4;
     const uint32_t cnt = list == 0 ? par->n_out : par->n_vb;
     if (cnt == 0 || (par->flags & (kFlagConstant | kFlagError))) return;
     __shared__ uint32_t sh[33];
-    const uint64_t w = (uint64_t)blk * 1024u + threadIdx.x;
-    uint32_t c = w < nwords ? __popc(bm[list * nwords + w]) : 0u;
+    __shared__ uint32_t sseg[4];
+    const uint64_t w0 = (uint64_t)blk4 * 4096u + 4u * threadIdx.x;  // the thread's first word
+    const uint32_t* b = bm + list * nwords;
+    uint32_t v[4], c = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        v[k] = w0 + k < nwords ? b[w0 + k] : 0u;
+        c += __popc(v[k]);
+    }
     uint32_t total;
-    uint32_t ex = block_excl_scan(c, sh, &total);
+    const uint32_t ex = block_excl_scan(c, sh, &total);
+    // bitmap block seg (256 threads) starts at thread 256 seg
+    const uint32_t seg = threadIdx.x >> 8;
+    if ((threadIdx.x & 255u) == 0u) sseg[seg] = ex;
+    __syncthreads();
     // only words holding a set bit are ever looked up (k_emit): the others stay unwritten
-    if (w < nwords && c) wpre[list * nwords + w] = ex;
-    if (threadIdx.x == 0) bpre[list * nbmblk + blk] = total;
+    uint32_t e = ex - sseg[seg];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (w0 + k < nwords && v[k]) wpre[list * nwords + w0 + k] = e;
+        e += __popc(v[k]);
+    }
+    if ((threadIdx.x & 255u) == 0u && blk4 * 4u + seg < nbmblk)
+        bpre[list * nbmblk + blk4 * 4u + seg] = (seg < 3u ? sseg[seg + 1] : total) - sseg[seg];
 }
 
 // ---------------------------------------------------------------------------
@@ -1439,7 +1460,7 @@ int launch_compress_batch(fpsnr_plan_s* const* P, const float* const* d_in, void
             const fpsnr_plan_s* p = P[f];
             const Workspace& w = p->w;
             b.a[f] = RankArgs{w.par, w.bm, w.wpre, w.bpre, p->nwords, (uint32_t)p->nbmblk};
-            blocks[f] = p->n ? 2u * (uint32_t)p->nbmblk : 0u;
+            blocks[f] = p->n ? 2u * (((uint32_t)p->nbmblk + 3u) / 4u) : 0u;
         }
         const uint32_t tot = batch_offsets(b, blocks);
         if (tot) {
