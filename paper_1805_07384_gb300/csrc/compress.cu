@@ -453,7 +453,7 @@ __device__ __forceinline__ int32_t prequant(float x, float xmin, float inv, bool
 // 4 blocks of 256 (3D).
 template <int MODE, int TX, int TY, bool VEC, int SEG>
 __global__ void __launch_bounds__(TX / (4 * SEG) * (TY + (MODE == 3 ? 1 : 0)),
-                                  SEG == 2 ? 1 : (MODE == 3 ? 3 : 896 / (TX / (4 * SEG) * TY)))
+                                  SEG == 2 ? (MODE == 2 && VEC ? 5 : 1) : (MODE == 3 ? 3 : 896 / (TX / (4 * SEG) * TY)))
     k_pq(const __grid_constant__ Batch<PQArgs> B) {
     constexpr int TPR = TX / (4 * SEG);  // threads per tile row
     // MODE 3 adds a halo warp (threadIdx.y == 0) that only forms the row
@@ -612,6 +612,31 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * (TY + (MODE == 3 ? 1 : 0)),
                 q[i + k] = (in[i + k] && !off) ? __float2int_rn(k ? pv.y : pv.x) : 0;
             }
         }
+        // Reconstruction, verbatim test and exact squared error, two points at a
+        // time.  The two-segment kernels do this first, so that their 8 inputs
+        // die before the residuals are formed (5 blocks per SM without spills;
+        // the rare staging path reloads a verbatim point's bits); the others
+        // after the histogram.  The halo warp and the warm-up plane above the
+        // slab count nothing.
+        constexpr bool EARLY = SEG == 2;
+        uint32_t vbm = 0u;  // bit i: point i is stored verbatim
+        auto recon = [&]() {
+#pragma unroll
+            for (int i = 0; i < NP; i += 2) {
+                const float2 x2 = make_float2(cur.v[i], cur.v[i + 1]);
+                const float2 xv = SCALED ? __fmul2_rn(x2, ssc2) : x2;
+                const float2 nxr = __ffma2_rn(make_float2(__int2float_rn(q[i]), __int2float_rn(q[i + 1])), ns2,
+                                              nxmin2s);
+                const float2 df = __fadd2_rn(xv, nxr);  // fl(x - x') per point
+                const bool v0 = in[i] && !(fabsf(df.x) <= thr);
+                const bool v1 = in[i + 1] && !(fabsf(df.y) <= thr);
+                ff2_add_sq_diff(acc, xv, nxr, df, in[i] && !v0, in[i + 1] && !v1);
+                vbm |= (v0 ? 1u << i : 0u) | (v1 ? 2u << i : 0u);
+            }
+        };
+        if constexpr (EARLY) {
+            if (z >= z0 && (MODE != 3 || threadIdx.y != 0)) recon();
+        }
         int32_t L1[NP];
         row_diff(q, cur.hl ? prequant(cur.l, xmin, inv, off) : 0, L1);
 
@@ -682,22 +707,14 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * (TY + (MODE == 3 ? 1 : 0)),
                     }
                 }
             }
-            // reconstruction, verbatim test, exact squared error, two points at a time
-            bool vb[NP], ol[NP];
-            bool rare = false;
+            if constexpr (!EARLY) recon();
+            // outliers: a symbol 0
+            bool ol[NP];
+            bool rare = vbm != 0u;
 #pragma unroll
-            for (int i = 0; i < NP; i += 2) {
-                const float2 x2 = make_float2(cur.v[i], cur.v[i + 1]);
-                const float2 xv = SCALED ? __fmul2_rn(x2, ssc2) : x2;
-                const float2 nxr = __ffma2_rn(make_float2(__int2float_rn(q[i]), __int2float_rn(q[i + 1])), ns2,
-                                              nxmin2s);
-                const float2 df = __fadd2_rn(xv, nxr);  // fl(x - x') per point
-                vb[i] = in[i] && !(fabsf(df.x) <= thr);
-                vb[i + 1] = in[i + 1] && !(fabsf(df.y) <= thr);
+            for (int i = 0; i < NP; i++) {
                 ol[i] = in[i] && code[i] == 0u;
-                ol[i + 1] = in[i + 1] && code[i + 1] == 0u;
-                ff2_add_sq_diff(acc, xv, nxr, df, in[i] && !vb[i], in[i + 1] && !vb[i + 1]);
-                rare |= vb[i] | ol[i] | vb[i + 1] | ol[i + 1];
+                rare |= ol[i];
             }
             // outliers and verbatims are rare: one vote per row decides whether any
             // lane of the warp needs the order-preserving staging below
@@ -706,7 +723,7 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * (TY + (MODE == 3 ? 1 : 0)),
                 // count in the low half, verbatim count in the high half
                 uint32_t mine = 0;
 #pragma unroll
-                for (int i = 0; i < NP; i++) mine += (ol[i] ? 1u : 0u) + (vb[i] ? 0x10000u : 0u);
+                for (int i = 0; i < NP; i++) mine += (ol[i] ? 1u : 0u) + (((vbm >> i) & 1u) ? 0x10000u : 0u);
                 uint32_t incl = mine;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -729,8 +746,9 @@ __global__ void __launch_bounds__(TX / (4 * SEG) * (TY + (MODE == 3 ? 1 : 0)),
                         a.stage_out[so++] = make_uint2(gi, (uint32_t)d[i]);
                         atomicOr(&a.bm_out[gi >> 5], 1u << (gi & 31u));
                     }
-                    if (vb[i]) {
-                        a.stage_vb[sv++] = make_uint2(gi, __float_as_uint(cur.v[i]));
+                    if ((vbm >> i) & 1u) {
+                        // the two-segment kernels reload the bits (rare)
+                        a.stage_vb[sv++] = make_uint2(gi, __float_as_uint(EARLY ? x[gi] : cur.v[i]));
                         atomicOr(&a.bm_vb[gi >> 5], 1u << (gi & 31u));
                     }
                 }
