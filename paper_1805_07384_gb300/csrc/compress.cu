@@ -926,13 +926,19 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_enc_pack(const __grid_consta
     const uint64_t cw1 = min(cw0 + kEncCpw, a.nchunks);
     uint32_t* buf = sbuf[wib];
     uint32_t warp_words = 0;
+    // the arguments the loops use, in registers (else reloaded from the
+    // parameter space inside them)
+    const uint32_t* __restrict__ enc = a.enc;
+    const uint16_t* __restrict__ codes = a.codes;
+    const uint64_t nn = a.n;
+    const uint32_t chunk = a.chunk;
     // The codes of a piece are loaded one piece ahead (16 bytes a lane), so the
     // load of the next piece is in flight while this one is packed.
-    auto chunk_end = [&](uint64_t c) { return min((c + 1) * a.chunk, a.n); };
+    auto chunk_end = [&](uint64_t c) { return min((c + 1) * chunk, nn); };
     uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
     auto prefetch = [&](uint64_t c, uint64_t pb) {
         const uint64_t i = pb + 8u * lane;
-        if (c < cw1 && i + 8 <= chunk_end(c)) nxt = *reinterpret_cast<const uint4*>(a.codes + i);
+        if (c < cw1 && i + 8 <= chunk_end(c)) nxt = *reinterpret_cast<const uint4*>(codes + i);
     };
     if (cw0 < cw1) prefetch(cw0, cw0 * a.chunk);
     for (uint64_t c = cw0; c < cw1; c++) {
@@ -954,15 +960,15 @@ __global__ void __launch_bounds__(kEncWarps * 32) k_enc_pack(const __grid_consta
                 const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
-                    const uint32_t e0 = __ldg(a.enc + (wv[k] & 0xffffu));
-                    const uint32_t e1 = __ldg(a.enc + (wv[k] >> 16));
+                    const uint32_t e0 = __ldg(enc + (wv[k] & 0xffffu));
+                    const uint32_t e1 = __ldg(enc + (wv[k] >> 16));
                     cw[2 * k] = e0 >> 5; cl[2 * k] = e0 & 31u;
                     cw[2 * k + 1] = e1 >> 5; cl[2 * k + 1] = e1 & 31u;
                 }
             } else {
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
-                    const uint32_t e = (i + k < end) ? __ldg(a.enc + a.codes[i + k]) : 0u;
+                    const uint32_t e = (i + k < end) ? __ldg(enc + codes[i + k]) : 0u;
                     cw[k] = e >> 5; cl[k] = e & 31u;
                 }
             }
