@@ -23,7 +23,7 @@
 // Sorting: used symbols are collected in ascending symbol order (each warp a
 // contiguous segment of the histogram); a stable sort by count then gives the
 // (count, symbol) leaf order (a rank sort for small alphabets, else a stable
-// LSD radix sort with one warp per contiguous segment).  The canonical order
+// LSD radix sort on 10-bit digits with one warp per contiguous segment).  The canonical order
 // (ascending length, then symbol) needs no sort: each warp counts its segment
 // of the symbol-ordered list per length, one scan gives its first canonical
 // index per length, and equal lengths are ranked by lane.
@@ -33,6 +33,8 @@ namespace fp {
 
 constexpr uint32_t kRankMax = 1024;     // rank sort up to this many items
 constexpr uint32_t kSmemQueue = 32768;  // internal-node queue in shared memory up to n leaves
+constexpr int kRadixBits = 10;          // digit of the sort by count
+static_assert((32u << kRadixBits) <= kSmemQueue, "the radix histograms fit the queue area");
 constexpr int kMaxRounds = 128;         // w1 grows 1.5x per round: <= 55 rounds for 2^32 points
 
 struct CBArgs {
@@ -73,16 +75,20 @@ __device__ void rank_sort(const unsigned long long* in, unsigned long long* out,
     __syncthreads();
 }
 
-// One stable LSD radix pass on digit (key >> shift) & mask (mask < 256): each
-// warp owns a contiguous segment; per-warp digit counts are scanned in
+// One stable LSD radix pass on the DB-bit digit (key >> shift) & (2^DB - 1):
+// each warp owns a contiguous segment; per-warp digit counts are scanned in
 // (digit, warp) order; within a group of 32 keys, equal digits are ranked by
-// lane.  whist: 32 x 256 u32 of smem.  Block of 1024 threads.
+// lane.  whist: 32 x 2^DB u32 of smem.  Block of 1024 threads.
+template <int DB>
 __device__ void radix_pass(const unsigned long long* in, unsigned long long* out, uint32_t n,
-                           int shift, uint32_t mask, uint32_t* whist, uint32_t* sh) {
+                           int shift, uint32_t* whist, uint32_t* sh) {
+    constexpr uint32_t NB = 1u << DB;
+    constexpr uint32_t mask = NB - 1u;
+    constexpr int EPT = (int)(NB * 32u / 1024u);  // (digit, warp) entries per thread in the scan
     const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const uint32_t S = (n + 31) / 32;
     const uint32_t b0 = min(n, w * S), b1 = min(n, b0 + S);
-    for (uint32_t d = lane; d < 256; d += 32) whist[w * 256 + d] = 0;
+    for (uint32_t d = lane; d < NB; d += 32) whist[w * NB + d] = 0;
     __syncwarp();
     for (uint32_t i0 = b0 + lane; i0 < b1; i0 += 128) {
         unsigned long long kk[4];
@@ -90,22 +96,22 @@ __device__ void radix_pass(const unsigned long long* in, unsigned long long* out
         for (int u = 0; u < 4; u++) kk[u] = i0 + 32u * u < b1 ? in[i0 + 32u * u] : 0ull;
 #pragma unroll
         for (int u = 0; u < 4; u++)
-            if (i0 + 32u * u < b1) atomicAdd(&whist[w * 256 + (uint32_t)((kk[u] >> shift) & mask)], 1u);
+            if (i0 + 32u * u < b1) atomicAdd(&whist[w * NB + (uint32_t)((kk[u] >> shift) & mask)], 1u);
     }
     __syncthreads();
-    uint32_t v[8], sum = 0;
+    uint32_t v[EPT], sum = 0;
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-        const uint32_t e = 8 * threadIdx.x + k;  // e = digit * 32 + warp
-        v[k] = whist[(e & 31u) * 256 + (e >> 5)];
+    for (int k = 0; k < EPT; k++) {
+        const uint32_t e = EPT * threadIdx.x + k;  // e = digit * 32 + warp
+        v[k] = whist[(e & 31u) * NB + (e >> 5)];
         sum += v[k];
     }
     uint32_t tot;
     uint32_t ex = block_excl_scan(sum, sh, &tot);
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-        const uint32_t e = 8 * threadIdx.x + k;
-        whist[(e & 31u) * 256 + (e >> 5)] = ex;
+    for (int k = 0; k < EPT; k++) {
+        const uint32_t e = EPT * threadIdx.x + k;
+        whist[(e & 31u) * NB + (e >> 5)] = ex;
         ex += v[k];
     }
     __syncthreads();
@@ -126,18 +132,18 @@ __device__ void radix_pass(const unsigned long long* in, unsigned long long* out
             // lanes holding the same digit: one ballot per digit bit
             uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
-            for (int b = 0; b < 8; b++) {
+            for (int b = 0; b < DB; b++) {
                 const bool bit = (d >> b) & 1u;
                 const uint32_t bb = __ballot_sync(0xffffffffu, bit);
                 peers &= bit ? bb : ~bb;
             }
             const uint32_t rank = __popc(peers & lanemask_lt());
             uint32_t pos = 0;
-            if (valid) pos = whist[w * 256 + d] + rank;
+            if (valid) pos = whist[w * NB + d] + rank;
             __syncwarp();
             if (valid) {
                 out[pos] = key;
-                if ((uint32_t)(__ffs(peers) - 1) == lane) whist[w * 256 + d] += __popc(peers);
+                if ((uint32_t)(__ffs(peers) - 1) == lane) whist[w * NB + d] += __popc(peers);
             }
             __syncwarp();
         }
@@ -322,12 +328,13 @@ __global__ void __launch_bounds__(1024, 1) k_codebook(const __grid_constant__ Ba
                 leaves = a.buf1;
                 spare = a.buf2;
             } else {
+                // 10-bit digits: the per-warp histograms (128 KB) fill the queue area
                 const int bits = 32 - __clz(maxc);
-                const int passes = (bits + 7) / 8;
+                const int passes = (bits + kRadixBits - 1) / kRadixBits;
                 const unsigned long long* src = a.list;
                 unsigned long long* dst = a.buf1;
                 for (int pss = 0; pss < passes; pss++) {
-                    radix_pass(src, dst, n, 16 + 8 * pss, 255u, whist, sh);
+                    radix_pass<kRadixBits>(src, dst, n, 16 + kRadixBits * pss, whist, sh);
                     src = dst;
                     dst = (dst == a.buf1) ? a.buf2 : a.buf1;
                 }
